@@ -1,0 +1,351 @@
+"""Throughput benchmark of the KiloNeuS sphere-traced render path (one JSON line on rank 0).
+
+A step renders one batch: the 16^3 Kilo-grid (3 hidden layers of width 32, 128^3 occupancy
+mask) from 8 seeded orbit cameras at 800x800, max 128 steps, eps 1e-4: 5.12 M primary rays,
+sphere-traced, normal and colour at each hit (kns_render).  The grid is resident in HBM
+before timing starts.  Each timed step is bracketed by CUDA events on the launching stream;
+between steps a 512 MiB buffer is overwritten to flush the 126 MB L2 (the grid's weights fit
+in L2), outside the events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16]
+                    [--workload c2|c3s|c3l|c1] [--impl kns|reference]
+
+Multi-GPU (torchrun): every rank renders its own batch on its own GPU (replicas, no
+collective on the data path); value = rays of all ranks / max-over-ranks time.
+`--impl reference` times the FP64 CPU oracle on this host's cores on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s sphere-traced+shaded, BF16 vs FP32 at stated error; serving p50/p99 ms"
+UNIT = "Mrays/s"
+FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (max SM clock)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="kns", choices=["kns", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload_config(name, desc, cams, W, H, ms, eps, precision):
+    return {"workload": "%s: %d^3 Kilo-grid, SDF MLP %d hidden x %d (softplus beta=%g, PE L=%d), colour MLP "
+                        "%d hidden x %d, occupancy %s; %d orbit cameras x %dx%d, max %d steps, eps %g; %s"
+                        % (name, desc.N, desc.sdf_hidden, desc.sdf_width, desc.softplus_beta, desc.pe_pos_L,
+                           desc.col_hidden, desc.col_width,
+                           ("%d^3" % desc.occ_res) if desc.occ_res else "none",
+                           cams.shape[0], W, H, ms, eps, precision),
+            "rays_per_step": int(cams.shape[0] * W * H), "grid": "%d^3" % desc.N, "sdf_width": desc.sdf_width,
+            "sdf_hidden": desc.sdf_hidden, "resolution": "%dx%d" % (W, H), "n_cameras": int(cams.shape[0]),
+            "max_steps": ms, "eps": eps, "precision": precision,
+            "l2": "flushed between steps (512 MiB write outside the timed events)",
+            "inputs": "synthetic SAL near-sphere grid (seed 0), seeded orbit cameras"}
+
+
+def mac_counts(desc):
+    """Algorithmic multiply-adds: per trace sample (d only) and per hit (full SDF + gradient + colour)."""
+    IN = 3 + 6 * desc.pe_pos_L
+    Wd, Hd = desc.sdf_width, desc.sdf_hidden
+    trace = IN * Wd + (Hd - 1) * Wd * Wd + Wd
+    full_fwd = IN * Wd + (Hd - 1) * Wd * Wd + Wd * (1 + desc.feat_dim)
+    bwd = (Hd - 1) * Wd * Wd + IN * Wd
+    cin = desc.feat_dim + 3 + 3 + 6 * desc.pe_dir_L + (3 if desc.col_use_x else 0)
+    colour = cin * desc.col_width + desc.col_width * 3
+    return trace, full_fwd + bwd + colour
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+                power.append(float(p[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def profile_traffic(kernel_tag: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel sources still match."""
+    src_hash = kernel_source_hash()
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for fn in sorted(os.listdir(pdir)):
+        if not fn.endswith((".md", ".txt")):
+            continue
+        text = open(os.path.join(pdir, fn)).read()
+        m_tag = re.search(r"kernel_tag:\s*(\S+)", text)
+        m_hash = re.search(r"kernel_source_sha1:\s*([0-9a-f]+)", text)
+        m_b = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+        if m_tag and m_hash and m_b and m_tag.group(1) == kernel_tag and m_hash.group(1) == src_hash:
+            return float(m_b.group(1))
+    return None
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha1()
+    cdir = os.path.join(ROOT, "paper_2206_10885_gb300", "csrc")
+    for fn in sorted(os.listdir(cdir)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(cdir, fn), "rb").read())
+    return h.hexdigest()
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def oracle_rate(desc, w, cams, W, H, ms, eps, seconds: float, seed: int = 0):
+    """Times the FP64 oracle (as it stands) on a seeded random sample of the workload's rays."""
+    import oracle as O
+    occ = O.occupancy(desc, w) if desc.occ_res else None
+    n_pix = cams.shape[0] * W * H
+    rng = np.random.default_rng(seed)
+    done, elapsed, batch = 0, 0.0, 4096
+    while elapsed < seconds:
+        sel = np.sort(rng.integers(0, n_pix, batch))
+        t0 = time.perf_counter()
+        O.render(desc, w, occ, cams, W, H, ms, eps, sel=sel)
+        dt = time.perf_counter() - t0
+        elapsed += dt
+        done += batch
+        if dt < seconds / 8:
+            batch *= 2
+    return done / elapsed / 1e6, done, elapsed, O.num_threads()
+
+
+def run_reference(args, rank, world):
+    from paper_2206_10885_gb300 import synth as S
+    if rank != 0:
+        return
+    desc, w, cams, W, H, ms, eps = S.workload(args.workload)
+    per_step = max(1.0, args.cpu_seconds / max(1, args.steps))
+    for _ in range(args.warmup):
+        oracle_rate(desc, w, cams, W, H, ms, eps, 0.2)
+    vals = []
+    total_rays, total_s, cores = 0, 0.0, 1
+    for k in range(args.steps):
+        v, n, s, cores = oracle_rate(desc, w, cams, W, H, ms, eps, per_step, seed=k + 1)
+        vals.append(v)
+        total_rays += n
+        total_s += s
+    value = total_rays / total_s / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * cams.shape[0] * W * H / (value * 1e6), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.workload, desc, cams, W, H, ms, eps, "fp64 oracle"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d seeded random rays of the workload over %d steps (%.1f s)"
+                                       % (total_rays, args.steps, total_s)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_kns(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2206_10885_gb300 as kns
+    from paper_2206_10885_gb300 import build as kbuild
+    from paper_2206_10885_gb300 import synth as S
+
+    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_2206_10885_gb300", "libkns.so")):
+        kbuild.build()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    desc, w, cams, W, H, ms, eps = S.workload(args.workload)
+    precision = kns.KNS_BF16 if args.precision == "bf16" else kns.KNS_FP32
+    ctx = kns.Context(local_rank)
+    grid = kns.Grid.load(ctx, desc, w)  # occupancy mask built on the device, untimed
+    n_rays = cams.shape[0] * W * H
+    stream = torch.cuda.current_stream()
+    frame = kns.alloc_frame(n_rays, dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        kns.render(ctx, grid, cams, W, H, ms, eps, precision=precision, out=frame, stream=stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    ctx.sync(stream)
+    # algorithmic units of one launch: SDF evaluations (trace samples) and hits
+    steps_np = frame[0]["steps"].cpu().numpy().astype(np.int64)
+    hits = int(frame[0]["hit"].sum().item())
+    samples = int(steps_np.sum())
+    mac_trace, mac_hit = mac_counts(desc)
+    flop_per_launch = 2.0 * (samples * mac_trace + hits * mac_hit)
+
+    clocks = ClockSampler(local_rank).start() if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    times = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(times)
+    st = ctx.sync(stream)
+    # e2e through the public API: cameras from host memory, outputs read back to pinned host buffers
+    host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in frame[0].items()
+            if k in ("rgb", "depth", "normal", "hit")}
+    d2h = sum(v.numel() * v.element_size() for v in host.values())
+    h2d = cams.nbytes
+    for _ in range(2):
+        step()
+        for k, v in host.items():
+            v.copy_(frame[0][k], non_blocking=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+        for k, v in host.items():
+            v.copy_(frame[0][k], non_blocking=True)
+        stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    clock_info = clocks.stop() if clocks else None
+
+    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    e_max = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        dist.all_reduce(e_max, op=dist.ReduceOp.MAX)
+    total_ms, e2e_s = float(t_max.item()), float(e_max.item())
+    ms_per_step = total_ms / args.steps
+    value = world * n_rays * args.steps / (total_ms * 1e-3) / 1e6
+    e2e_value = world * n_rays * args.steps / e2e_s / 1e6
+
+    if rank == 0:
+        peaks = load_peaks()
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+        achieved = flop_per_launch / (ms_per_step * 1e-3) / 1e12
+        kernel_tag = "render_%s_%s" % (args.precision, args.workload)
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": profile_traffic(kernel_tag),
+                "kernel": kernel_tag, "peak_source": FP32_PEAK_NOTE,
+                "flop_per_launch": flop_per_launch, "sdf_evaluations_per_launch": samples,
+                "hits_per_launch": hits}
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            v, n, s, cores = oracle_rate(desc, w, cams, W, H, ms, eps, args.cpu_seconds)
+            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": "%d seeded random rays of the %d-ray workload (%.1f s of FP64 oracle work)"
+                             % (n, n_rays, s)}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if precision == kns.KNS_FP32 else "bf16",
+                "data": "synthetic",
+                "config": dict(workload_config(args.workload, desc, cams, W, H, ms, eps, args.precision),
+                               parallelism="replicas" if world > 1 else "single GPU"),
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": int(d2h)},
+                "clocks": clock_info, "gpu_launches": args.steps * math.ceil(cams.shape[0] / 64),
+                "step_ms_min": min(times), "step_ms_median": statistics.median(times)}
+        print(json.dumps(line), flush=True)
+    grid.free()
+    ctx.close()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_kns(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

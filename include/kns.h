@@ -1,0 +1,183 @@
+/*
+ * kns.h -- C ABI of the KiloNeuS sphere-tracing library (GB300, sm_103a).
+ *
+ * KiloNeuS (Sec. 3.1) stores a signed distance field and a colour field in a
+ * regular N^3 grid of tiny MLPs over a fixed bounding box.  Rendering
+ * (Sec. 3.4.1) sphere-traces each camera ray inside the box: at every sample
+ * it finds the sample's cell m(x), evaluates that cell's SDF MLP on the
+ * positional encoding gamma(x) (Eq. 1, Eq. 2), and stops when |d| < eps; at
+ * the hit it takes the normalised analytic input-gradient of the SDF as the
+ * normal and evaluates the cell's colour MLP (Eq. 3).
+ *
+ * Conventions shared by every entry point
+ *  - Status: every call returns a kns_status; KNS_OK (0) is success.  A
+ *    failing call enqueues nothing.  kns_last_error() gives a message.
+ *  - Argument errors are detected on the host before any work is enqueued.
+ *  - Asynchrony: compute calls enqueue on the caller's CUDA stream
+ *    (`cuda_stream`, a cudaStream_t; NULL = the legacy default stream) and
+ *    return without waiting.  Device-side failures (a bounded wait that ran
+ *    out, a bounds check that tripped) are recorded in a per-context status
+ *    word and returned by the next kns_sync() on that context.
+ *  - Memory: the caller owns every input and output buffer and passes plain
+ *    pointers (device pointers unless stated "host").  The library never
+ *    frees caller memory.  Grids own the device copies of their weights.
+ *  - Threads: a context may be used from several host threads; calls on one
+ *    context are serialised internally.
+ *
+ * Canonical weight layout (host, FP32, every loader takes it)
+ *   cells in x-fastest order, cell = ix + N*(iy + N*iz); per cell the SDF MLP
+ *   layers, then the colour MLP layers; per layer W[out][in] row-major, then
+ *   b[out].  SDF layers: (3+6*pe_pos_L) -> sdf_width (x sdf_hidden, softplus)
+ *   -> 1+feat_dim (linear: row 0 is d, rows 1.. are the feature z).  Colour
+ *   layers: (feat_dim + 3 + 3+6*pe_dir_L [+3 if col_use_x]) -> col_width
+ *   (x col_hidden, ReLU) -> 3 (sigmoid).  Colour input order: z, n, gamma(v),
+ *   then x when col_use_x.  gamma_L(p) = [p, then for k = 0..L-1:
+ *   sin(2^k pi p_c) for c = x,y,z, then cos(2^k pi p_c) for c = x,y,z].
+ *
+ * Occupancy mask layout: res^3 bits, bit index ix + res*(iy + res*iz), packed
+ *   little-endian into uint64 words (bit b of word k is voxel 64k + b).
+ */
+#ifndef KNS_H_
+#define KNS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum kns_status {
+    KNS_OK = 0,
+    KNS_ERR_INVALID_ARG = 1,   /* a null required pointer, a size out of range, ... */
+    KNS_ERR_OUT_OF_MEMORY = 2, /* a device or host allocation failed */
+    KNS_ERR_CUDA = 3,          /* a CUDA runtime call failed (message has the CUDA error) */
+    KNS_ERR_FORMAT = 4,        /* a grid file is malformed or truncated */
+    KNS_ERR_UNSUPPORTED = 5,   /* a descriptor shape the kernels are not built for */
+    KNS_ERR_TIMEOUT = 6,       /* kns_sync ran out of time, or a device wait gave up */
+    KNS_ERR_BUSY = 7,          /* the resource is in use */
+    KNS_ERR_INTERNAL = 8       /* a device-side consistency check failed */
+} kns_status;
+
+/* Arithmetic of the render path. */
+enum { KNS_FP32 = 0, /* every MLP evaluation in FP32 on the CUDA cores */
+       KNS_BF16 = 1  /* trace MLPs in BF16 on the tensor cores (FP32 accumulate), then the
+                        last sphere steps, the normal and the colour in FP32 */ };
+
+typedef struct kns_ctx kns_ctx;   /* opaque: one device, its scratch, its status word */
+typedef struct kns_grid kns_grid; /* opaque: one resident Kilo-grid */
+
+/* Shape of a Kilo-grid (Sec. 3.1).  The paper uses N = 16, pe_pos_L = 6, pe_dir_L = 4,
+ * bounding box [-1,1]^3 (Sec. 3.2.1). */
+typedef struct kns_grid_desc {
+    int32_t N;           /* cells per axis (1..64) */
+    int32_t pe_pos_L;    /* encoding frequencies of x (Eq. 1) */
+    int32_t pe_dir_L;    /* encoding frequencies of the view direction */
+    int32_t sdf_hidden;  /* hidden layers of the SDF MLP */
+    int32_t sdf_width;   /* their width */
+    int32_t feat_dim;    /* feature z passed to the colour MLP */
+    int32_t col_hidden;  /* hidden layers of the colour MLP */
+    int32_t col_width;   /* their width */
+    int32_t col_use_x;   /* 1: the colour MLP also takes raw x (Eq. 3); 0: it does not */
+    int32_t occ_res;     /* occupancy voxels per axis (0 = no empty-space skipping; a multiple of N) */
+    float softplus_beta; /* softplus sharpness of the SDF MLP (100 in the synthetic grids) */
+    float bbox_min[3];   /* bounding box of the grid */
+    float bbox_max[3];
+} kns_grid_desc;
+
+/* Pinhole camera: c2w is a row-major 3x4 matrix whose columns are the camera's right, down and
+ * forward axes and its position in world space; pixel (i, j) (row i from the top, column j)
+ * looks along normalize(c2w[:, :3] * ((j+0.5-cx)/fx, (i+0.5-cy)/fy, 1)). */
+typedef struct kns_camera {
+    float c2w[12];
+    float fx, fy, cx, cy;
+} kns_camera;
+
+/* Per-pixel outputs (device pointers), indexed p = cam*H*W + i*W + j.  rgb and depth are
+ * required; the rest may be NULL.  Misses: rgb = 0, depth = +inf, normal = 0, cell = -1,
+ * hit = 0.  steps counts SDF evaluations of the trace (the hit evaluation included). */
+typedef struct kns_frame {
+    float *rgb;     /* 3 floats per pixel */
+    float *depth;   /* ray parameter t at the hit (unit directions: distance from the camera) */
+    float *normal;  /* 3 floats per pixel, unit length on hits */
+    int32_t *cell;  /* hit cell m(x) */
+    int32_t *steps; /* SDF evaluations */
+    uint8_t *hit;   /* 1 on a hit */
+} kns_frame;
+
+/* Options of kns_render (NULL = FP32 defaults). */
+typedef struct kns_render_opts {
+    int32_t precision;    /* KNS_FP32 or KNS_BF16 */
+    float eps_coarse;     /* KNS_BF16: hit threshold of the BF16 trace (<= 0: max(eps, 4e-3)) */
+    int32_t refine_steps; /* KNS_BF16: FP32 sphere steps after the BF16 hit (< 0: 2) */
+} kns_render_opts;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  *out receives the handle.
+ * Errors: INVALID_ARG (out NULL, bad device), CUDA, OUT_OF_MEMORY. */
+kns_status kns_create(int device, kns_ctx **out);
+
+/* Destroy a context after its work has finished (grids must be freed first).  NULL is a no-op. */
+void kns_destroy(kns_ctx *ctx);
+
+/* Message of the last failure on this context (or of the last kns_create failure when ctx is NULL).
+ * The string stays valid until the next call on the context. */
+const char *kns_last_error(const kns_ctx *ctx);
+
+/* Wait up to timeout_ms (< 0: forever) for the work enqueued on `cuda_stream`, then report the
+ * context's device status word.  Returns OK, TIMEOUT (work still running), CUDA (an asynchronous
+ * CUDA error), or the status a kernel recorded (TIMEOUT, INTERNAL).  Reading clears the word. */
+kns_status kns_sync(kns_ctx *ctx, void *cuda_stream, int64_t timeout_ms);
+
+/* ------------------------------------------------------------------ grids */
+
+/* Upload a Kilo-grid (Sec. 3.1).  host_weights: canonical FP32 layout (header comment), exactly
+ * n_floats = N^3 * (SDF + colour parameters) floats, host memory, copied.  occ_words: host uint64
+ * occupancy words for desc->occ_res (copied), or NULL to build the mask on the device as
+ * |d(voxel centre)| < voxel diagonal when occ_res > 0.  The call returns after the upload.
+ * Errors: INVALID_ARG (NULL pointer, n_floats mismatch, N or occ_res out of range),
+ * UNSUPPORTED (a width, depth or encoding the kernels are not built for), OUT_OF_MEMORY, CUDA. */
+kns_status kns_load_grid(kns_ctx *ctx, const kns_grid_desc *desc, const float *host_weights,
+                         size_t n_floats, const uint64_t *occ_words, kns_grid **out);
+
+/* Load a grid file ("KNS1" header, canonical FP32 weights, optional occupancy words; all
+ * little-endian).  Errors: as kns_load_grid, plus FORMAT for a bad magic, version or size. */
+kns_status kns_load_grid_file(kns_ctx *ctx, const char *path, kns_grid **out);
+
+/* Free a grid and its device memory (waits for the device first).  NULL is a no-op. */
+void kns_free_grid(kns_grid *grid);
+
+/* Copy a grid's descriptor to *out (host). */
+kns_status kns_grid_get_desc(const kns_grid *grid, kns_grid_desc *out);
+
+/* Copy the grid's occupancy mask into host_words (n_words uint64 words, host).  Synchronous.
+ * Errors: INVALID_ARG (no mask, or n_words too small), CUDA. */
+kns_status kns_copy_occupancy(kns_ctx *ctx, const kns_grid *grid, uint64_t *host_words, size_t n_words);
+
+/* ---------------------------------------------------------------- compute */
+
+/* Sphere-trace and shade n_cams x H x W primary rays (Sec. 3.4.1), one per pixel centre.
+ * cams: n_cams cameras in HOST memory (read before the call returns).  max_steps: SDF
+ * evaluations per ray (>= 1).  eps: hit threshold on |d| (> 0).  out: device buffers of
+ * n_cams*H*W pixels (kns_frame).  opts: NULL or precision options.  Rays start at the box
+ * entry max(t_near, 0) and miss when t leaves [max(t_near, 0), t_far] or the budget is spent.
+ * n_cams, W or H equal to 0 is a successful no-op.
+ * Errors: INVALID_ARG (NULL grid/cams/out/rgb/depth, negative sizes, n_cams*W*H > 2^40,
+ * max_steps < 1, eps <= 0 or not finite, unknown precision), CUDA. */
+kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams, int n_cams,
+                      int W, int H, int max_steps, float eps, const kns_render_opts *opts,
+                      const kns_frame *out, void *cuda_stream);
+
+/* Batch field query (the vectorised per-cell MLP query of Sec. 3.3): for n points (device,
+ * n x 3 FP32, row-major) evaluate the SDF MLP of cell m(x): sdf (device, n floats), feat (device,
+ * n x feat_dim, or NULL), grad (device, n x 3 analytic input gradient, or NULL).
+ * n = 0 is a successful no-op.  Errors: INVALID_ARG (NULL pts/sdf with n > 0, n < 0), CUDA. */
+kns_status kns_sdf(kns_ctx *ctx, const kns_grid *grid, const float *pts, int64_t n, float *sdf,
+                   float *feat, float *grad, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KNS_H_ */

@@ -1,0 +1,120 @@
+"""KiloNeuS sphere-tracing path for GB300: a thin Python layer over the C ABI (include/kns.h).
+
+PyTorch is used only to own device memory and streams; every step of the path
+runs in libkns.so's CUDA kernels.  The raw binding with the C names lives in
+``_capi``; the helpers here allocate output tensors and marshal arguments.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _capi as capi
+from ._capi import KNS_BF16, KNS_FP32, KnsError
+
+__all__ = ["capi", "KnsError", "KNS_FP32", "KNS_BF16", "Context", "Grid", "alloc_frame", "render", "sdf"]
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+class Context:
+    """One kns_ctx on a CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        self.handle = capi.kns_create(device)
+
+    def sync(self, stream=None, timeout_ms: int = -1) -> None:
+        capi.kns_sync(self.handle, _stream_ptr(stream), timeout_ms)
+
+    def close(self) -> None:
+        if self.handle:
+            capi.kns_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Grid:
+    """A resident Kilo-grid (weights and occupancy mask on the device)."""
+
+    def __init__(self, ctx: Context, handle: int, desc):
+        self.ctx, self.handle, self.desc = ctx, handle, desc
+
+    @classmethod
+    def load(cls, ctx: Context, desc, weights: np.ndarray, occ_words: np.ndarray = None) -> "Grid":
+        w = np.ascontiguousarray(weights, dtype=np.float32)
+        occ = None if occ_words is None else np.ascontiguousarray(occ_words, dtype=np.uint64)
+        h = capi.kns_load_grid(ctx.handle, desc, w.ctypes.data, w.size, None if occ is None else occ.ctypes.data)
+        return cls(ctx, h, desc)
+
+    @classmethod
+    def from_file(cls, ctx: Context, path: str) -> "Grid":
+        h = capi.kns_load_grid_file(ctx.handle, path)
+        return cls(ctx, h, capi.kns_grid_get_desc(h))
+
+    def occupancy(self) -> np.ndarray:
+        res = int(self.desc.occ_res)
+        out = np.zeros((res ** 3 + 63) // 64, dtype=np.uint64)
+        capi.kns_copy_occupancy(self.ctx.handle, self.handle, out.ctypes.data, out.size)
+        return out
+
+    def free(self) -> None:
+        if self.handle:
+            capi.kns_free_grid(self.handle)
+            self.handle = None
+
+
+def alloc_frame(n_pix: int, device="cuda", extras: bool = True):
+    """Output tensors of n_pix pixels plus the kns_frame that points at them."""
+    import torch
+    t = dict(rgb=torch.empty((n_pix, 3), dtype=torch.float32, device=device),
+             depth=torch.empty(n_pix, dtype=torch.float32, device=device))
+    if extras:
+        t.update(normal=torch.empty((n_pix, 3), dtype=torch.float32, device=device),
+                 cell=torch.empty(n_pix, dtype=torch.int32, device=device),
+                 steps=torch.empty(n_pix, dtype=torch.int32, device=device),
+                 hit=torch.empty(n_pix, dtype=torch.uint8, device=device))
+    f = capi.kns_frame()
+    for k in ("rgb", "depth", "normal", "cell", "steps", "hit"):
+        setattr(f, k, t[k].data_ptr() if k in t else None)
+    return t, f
+
+
+def render_opts(precision: int = KNS_FP32, eps_coarse: float = 0.0, refine_steps: int = -1):
+    o = capi.kns_render_opts()
+    o.precision, o.eps_coarse, o.refine_steps = precision, eps_coarse, refine_steps
+    return o
+
+
+def render(ctx: Context, grid: Grid, cams: np.ndarray, W: int, H: int, max_steps: int, eps: float,
+           precision: int = KNS_FP32, out=None, stream=None, eps_coarse: float = 0.0, refine_steps: int = -1):
+    """kns_render into fresh (or given) tensors; returns the dict of output tensors."""
+    cams = np.ascontiguousarray(cams, dtype=np.float32).reshape(-1, 16)
+    n_pix = cams.shape[0] * W * H
+    if out is None:
+        out = alloc_frame(n_pix, "cuda:%d" % ctx.device)
+    t, f = out
+    capi.kns_render(ctx.handle, grid.handle, cams.ctypes.data, cams.shape[0], W, H, max_steps, eps,
+                    render_opts(precision, eps_coarse, refine_steps), f, _stream_ptr(stream))
+    return t
+
+
+def sdf(ctx: Context, grid: Grid, pts, want_feat: bool = True, want_grad: bool = True, stream=None):
+    """kns_sdf on a (n, 3) float32 CUDA tensor; returns (d, feat, grad) tensors."""
+    import torch
+    pts = pts.contiguous()
+    n = pts.shape[0]
+    d = torch.empty(n, dtype=torch.float32, device=pts.device)
+    feat = torch.empty((n, int(grid.desc.feat_dim)), dtype=torch.float32, device=pts.device) if want_feat else None
+    grad = torch.empty((n, 3), dtype=torch.float32, device=pts.device) if want_grad else None
+    capi.kns_sdf(ctx.handle, grid.handle, pts.data_ptr(), n, d.data_ptr(), feat.data_ptr() if want_feat else None,
+                 grad.data_ptr() if want_grad else None, _stream_ptr(stream))
+    return d, feat, grad

@@ -1,0 +1,172 @@
+"""ctypes binding of include/kns.h: the same names, argument marshalling only.
+
+Every function raises KnsError on a non-OK status.  Pointers are plain integers
+(device addresses from torch tensors' data_ptr(), or host addresses).  Loading
+fails loudly when libkns.so has not been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkns.so")
+
+KNS_OK = 0
+KNS_ERR_INVALID_ARG = 1
+KNS_ERR_OUT_OF_MEMORY = 2
+KNS_ERR_CUDA = 3
+KNS_ERR_FORMAT = 4
+KNS_ERR_UNSUPPORTED = 5
+KNS_ERR_TIMEOUT = 6
+KNS_ERR_BUSY = 7
+KNS_ERR_INTERNAL = 8
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "FORMAT", 5: "UNSUPPORTED",
+                6: "TIMEOUT", 7: "BUSY", 8: "INTERNAL"}
+KNS_FP32 = 0
+KNS_BF16 = 1
+
+
+class KnsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("kns %s (%d): %s" % (STATUS_NAMES.get(status, "?"), status, msg))
+        self.status = status
+
+
+class kns_grid_desc(C.Structure):
+    _fields_ = [("N", C.c_int32), ("pe_pos_L", C.c_int32), ("pe_dir_L", C.c_int32), ("sdf_hidden", C.c_int32),
+                ("sdf_width", C.c_int32), ("feat_dim", C.c_int32), ("col_hidden", C.c_int32),
+                ("col_width", C.c_int32), ("col_use_x", C.c_int32), ("occ_res", C.c_int32),
+                ("softplus_beta", C.c_float), ("bbox_min", C.c_float * 3), ("bbox_max", C.c_float * 3)]
+
+
+class kns_camera(C.Structure):
+    _fields_ = [("c2w", C.c_float * 12), ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float),
+                ("cy", C.c_float)]
+
+
+class kns_frame(C.Structure):
+    _fields_ = [("rgb", C.c_void_p), ("depth", C.c_void_p), ("normal", C.c_void_p), ("cell", C.c_void_p),
+                ("steps", C.c_void_p), ("hit", C.c_void_p)]
+
+
+class kns_render_opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("eps_coarse", C.c_float), ("refine_steps", C.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libkns.so (raises if it is missing: the product path has no CPU fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError("libkns.so is not built (run __graft_entry__.build() or "
+                                  "python -m paper_2206_10885_gb300.build): %s" % LIB_PATH)
+            L = C.CDLL(LIB_PATH)
+            vp, st = C.c_void_p, C.c_int
+            L.kns_create.argtypes = [C.c_int, C.POINTER(vp)]
+            L.kns_create.restype = st
+            L.kns_destroy.argtypes = [vp]
+            L.kns_destroy.restype = None
+            L.kns_last_error.argtypes = [vp]
+            L.kns_last_error.restype = C.c_char_p
+            L.kns_sync.argtypes = [vp, vp, C.c_int64]
+            L.kns_sync.restype = st
+            L.kns_load_grid.argtypes = [vp, C.POINTER(kns_grid_desc), vp, C.c_size_t, vp, C.POINTER(vp)]
+            L.kns_load_grid.restype = st
+            L.kns_load_grid_file.argtypes = [vp, C.c_char_p, C.POINTER(vp)]
+            L.kns_load_grid_file.restype = st
+            L.kns_free_grid.argtypes = [vp]
+            L.kns_free_grid.restype = None
+            L.kns_grid_get_desc.argtypes = [vp, C.POINTER(kns_grid_desc)]
+            L.kns_grid_get_desc.restype = st
+            L.kns_copy_occupancy.argtypes = [vp, vp, vp, C.c_size_t]
+            L.kns_copy_occupancy.restype = st
+            L.kns_render.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float,
+                                     C.POINTER(kns_render_opts), C.POINTER(kns_frame), vp]
+            L.kns_render.restype = st
+            L.kns_sdf.argtypes = [vp, vp, vp, C.c_int64, vp, vp, vp, vp]
+            L.kns_sdf.restype = st
+            _lib = L
+    return _lib
+
+
+def _check(status: int, ctx) -> None:
+    if status != KNS_OK:
+        msg = lib().kns_last_error(ctx)
+        raise KnsError(status, msg.decode() if msg else "")
+
+
+def kns_create(device: int = 0) -> int:
+    h = C.c_void_p()
+    _check(lib().kns_create(device, C.byref(h)), None)
+    return h.value
+
+
+def kns_destroy(ctx: int) -> None:
+    lib().kns_destroy(ctx)
+
+
+def kns_last_error(ctx) -> str:
+    m = lib().kns_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def kns_sync(ctx: int, stream: int = 0, timeout_ms: int = -1) -> None:
+    _check(lib().kns_sync(ctx, stream, timeout_ms), ctx)
+
+
+def desc_struct(desc) -> kns_grid_desc:
+    d = kns_grid_desc()
+    for k in ("N", "pe_pos_L", "pe_dir_L", "sdf_hidden", "sdf_width", "feat_dim", "col_hidden", "col_width",
+              "col_use_x", "occ_res"):
+        setattr(d, k, int(getattr(desc, k)))
+    d.softplus_beta = float(desc.softplus_beta)
+    for a in range(3):
+        d.bbox_min[a] = float(desc.bbox_min[a])
+        d.bbox_max[a] = float(desc.bbox_max[a])
+    return d
+
+
+def kns_load_grid(ctx: int, desc, host_weights_ptr: int, n_floats: int, occ_words_ptr: int = None) -> int:
+    h = C.c_void_p()
+    d = desc_struct(desc)
+    _check(lib().kns_load_grid(ctx, C.byref(d), host_weights_ptr, n_floats, occ_words_ptr, C.byref(h)), ctx)
+    return h.value
+
+
+def kns_load_grid_file(ctx: int, path: str) -> int:
+    h = C.c_void_p()
+    _check(lib().kns_load_grid_file(ctx, path.encode(), C.byref(h)), ctx)
+    return h.value
+
+
+def kns_free_grid(grid: int) -> None:
+    lib().kns_free_grid(grid)
+
+
+def kns_grid_get_desc(grid: int) -> kns_grid_desc:
+    d = kns_grid_desc()
+    _check(lib().kns_grid_get_desc(grid, C.byref(d)), None)
+    return d
+
+
+def kns_copy_occupancy(ctx: int, grid: int, host_words_ptr: int, n_words: int) -> None:
+    _check(lib().kns_copy_occupancy(ctx, grid, host_words_ptr, n_words), ctx)
+
+
+def kns_render(ctx: int, grid: int, cams_host_ptr: int, n_cams: int, W: int, H: int, max_steps: int, eps: float,
+               opts: kns_render_opts = None, frame: kns_frame = None, stream: int = 0) -> None:
+    _check(lib().kns_render(ctx, grid, cams_host_ptr, n_cams, W, H, max_steps, eps,
+                            C.byref(opts) if opts is not None else None,
+                            C.byref(frame) if frame is not None else None, stream), ctx)
+
+
+def kns_sdf(ctx: int, grid: int, pts_ptr: int, n: int, sdf_ptr: int, feat_ptr: int = None, grad_ptr: int = None,
+            stream: int = 0) -> None:
+    _check(lib().kns_sdf(ctx, grid, pts_ptr, n, sdf_ptr, feat_ptr, grad_ptr, stream), ctx)

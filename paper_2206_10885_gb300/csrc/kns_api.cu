@@ -1,0 +1,449 @@
+// kns_api.cu -- the C ABI runtime: contexts, resident grids, argument checks, launches, status.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "kns.h"
+#include "kns_device.cuh"
+#include "kns_kernels.h"
+
+struct kns_ctx {
+    int device = 0;
+    std::mutex mu;
+    std::string err;
+    int *d_status = nullptr;  // device status word written by kernels (0 = fine)
+};
+
+struct kns_grid {
+    kns_ctx *ctx = nullptr;
+    kns_grid_desc desc{};
+    kns::Shape shape{};
+    float *d_w = nullptr;
+    uint32_t *d_occ = nullptr;
+    size_t occ_words64 = 0;
+    kns::GridView view{};
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+kns_status set_err(kns_ctx *ctx, kns_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (ctx)
+        ctx->err = buf;
+    else
+        g_create_err = buf;
+    return st;
+}
+
+kns_status cuda_err(kns_ctx *ctx, cudaError_t e, const char *what) {
+    return set_err(ctx, e == cudaErrorMemoryAllocation ? KNS_ERR_OUT_OF_MEMORY : KNS_ERR_CUDA, "%s: %s (%s)", what,
+                   cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+// Makes the context's device current for the scope and restores the caller's device after.
+struct DeviceScope {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceScope(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceScope() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int64_t canon_sdf_params(const kns_grid_desc &d) {
+    const int64_t in = 3 + 6 * d.pe_pos_L;
+    int64_t p = in * d.sdf_width + d.sdf_width;
+    p += (int64_t)(d.sdf_hidden - 1) * (d.sdf_width * d.sdf_width + d.sdf_width);
+    p += (int64_t)d.sdf_width * (1 + d.feat_dim) + (1 + d.feat_dim);
+    return p;
+}
+int64_t canon_col_in(const kns_grid_desc &d) { return d.feat_dim + 3 + 3 + 6 * d.pe_dir_L + (d.col_use_x ? 3 : 0); }
+int64_t canon_col_params(const kns_grid_desc &d) {
+    const int64_t in = canon_col_in(d);
+    int64_t p = in * d.col_width + d.col_width;
+    p += (int64_t)(d.col_hidden - 1) * (d.col_width * d.col_width + d.col_width);
+    p += (int64_t)d.col_width * 3 + 3;
+    return p;
+}
+
+kns_status check_desc(kns_ctx *ctx, const kns_grid_desc &d) {
+    if (d.N < 1 || d.N > 64) return set_err(ctx, KNS_ERR_INVALID_ARG, "N=%d out of range [1, 64]", d.N);
+    if (d.pe_pos_L < 0 || d.pe_pos_L > 12 || d.pe_dir_L < 0 || d.pe_dir_L > 12)
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "encoding frequencies out of range");
+    if (d.sdf_hidden < 1 || d.sdf_width < 1 || d.col_hidden < 1 || d.col_width < 1 || d.feat_dim < 0)
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "MLP shape out of range");
+    if (d.col_use_x != 0 && d.col_use_x != 1) return set_err(ctx, KNS_ERR_INVALID_ARG, "col_use_x must be 0 or 1");
+    if (!(d.softplus_beta > 0.f) || !std::isfinite(d.softplus_beta))
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "softplus_beta must be positive and finite");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(d.bbox_min[a]) || !std::isfinite(d.bbox_max[a]) || !(d.bbox_max[a] > d.bbox_min[a]))
+            return set_err(ctx, KNS_ERR_INVALID_ARG, "bounding box axis %d is empty or not finite", a);
+    if (d.occ_res < 0 || d.occ_res > 1024 || (d.occ_res > 0 && d.occ_res % d.N != 0))
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "occ_res=%d must be 0 or a multiple of N up to 1024", d.occ_res);
+    kns::Shape sh{d.sdf_width, d.sdf_hidden, d.pe_pos_L, d.pe_dir_L};
+    if (d.feat_dim != kns::FEAT || d.col_hidden != 1 || d.col_width != d.sdf_width || !kns::shape_supported(sh))
+        return set_err(ctx, KNS_ERR_UNSUPPORTED,
+                       "unsupported grid shape (built: widths 32/64, 2-3 SDF hidden layers, (L, Ld) = (4, 2) or "
+                       "(6, 4), feat_dim 15, one colour hidden layer of the SDF width)");
+    return KNS_OK;
+}
+
+// Canonical FP32 layout -> device layout (see kns_device.cuh), one cell at a time.
+void convert_cell(const kns_grid_desc &d, int dev_floats, const float *src, float *dst) {
+    const int W = d.sdf_width, H = d.sdf_hidden, IN = 3 + 6 * d.pe_pos_L, INP = kns::round4(IN);
+    const int CIN_NOX = d.feat_dim + 3 + 3 + 6 * d.pe_dir_L, CIN_DEV = CIN_NOX + 3, CINP = kns::round4(CIN_DEV);
+    std::memset(dst, 0, sizeof(float) * dev_floats);
+    int64_t s = 0, o = 0;
+    // SDF layer 0
+    for (int r = 0; r < W; ++r)
+        for (int c = 0; c < IN; ++c) dst[o + r * INP + c] = src[s + r * IN + c];
+    s += (int64_t)W * IN;
+    o += (int64_t)W * INP;
+    for (int r = 0; r < W; ++r) dst[o + r] = src[s + r];
+    s += W;
+    o += W;
+    // hidden layers
+    for (int l = 1; l < H; ++l) {
+        std::memcpy(dst + o, src + s, sizeof(float) * (W * W + W));
+        s += W * W + W;
+        o += W * W + W;
+    }
+    // last SDF layer
+    std::memcpy(dst + o, src + s, sizeof(float) * (kns::SDF_OUT * W + kns::SDF_OUT));
+    s += kns::SDF_OUT * W + kns::SDF_OUT;
+    o += kns::SDF_OUT * W + kns::SDF_OUT;
+    // colour layer 0: [z, n, gamma(v)] columns, then the x slot
+    const int cin = (int)canon_col_in(d);
+    for (int r = 0; r < W; ++r) {
+        for (int c = 0; c < CIN_NOX; ++c) dst[o + r * CINP + c] = src[s + r * cin + c];
+        if (d.col_use_x)
+            for (int c = 0; c < 3; ++c) dst[o + r * CINP + CIN_NOX + c] = src[s + r * cin + CIN_NOX + c];
+    }
+    s += (int64_t)W * cin;
+    o += (int64_t)W * CINP;
+    for (int r = 0; r < W; ++r) dst[o + r] = src[s + r];
+    s += W;
+    o += W;
+    // colour last layer (3 rows padded to 4)
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < W; ++c) dst[o + r * W + c] = src[s + r * W + c];
+    s += 3 * W;
+    o += 4 * W;
+    for (int r = 0; r < 3; ++r) dst[o + r] = src[s + r];
+}
+
+void fill_view(kns_grid *g) {
+    kns::GridView &v = g->view;
+    const kns_grid_desc &d = g->desc;
+    v.w = g->d_w;
+    v.cell_stride = kns::cell_floats(g->shape);
+    v.N = d.N;
+    for (int a = 0; a < 3; ++a) {
+        v.bmin[a] = d.bbox_min[a];
+        v.bmax[a] = d.bbox_max[a];
+        v.cscale[a] = (float)d.N / (d.bbox_max[a] - d.bbox_min[a]);
+        v.oscale[a] = d.occ_res > 0 ? (float)d.occ_res / (d.bbox_max[a] - d.bbox_min[a]) : 0.f;
+        v.ovox[a] = d.occ_res > 0 ? (d.bbox_max[a] - d.bbox_min[a]) / (float)d.occ_res : 0.f;
+    }
+    v.occ = g->d_occ;
+    v.occ_res = d.occ_res;
+    v.occ_per_cell = d.occ_res > 0 ? d.occ_res / d.N : 1;
+    v.beta = d.softplus_beta;
+    v.inv_beta = 1.f / d.softplus_beta;
+}
+
+}  // namespace
+
+extern "C" {
+
+kns_status kns_create(int device, kns_ctx **out) {
+    if (!out) return set_err(nullptr, KNS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return cuda_err(nullptr, e, "cudaGetDeviceCount");
+    if (device < 0 || device >= n) return set_err(nullptr, KNS_ERR_INVALID_ARG, "device %d of %d", device, n);
+    kns_ctx *c = new (std::nothrow) kns_ctx();
+    if (!c) return set_err(nullptr, KNS_ERR_OUT_OF_MEMORY, "host allocation failed");
+    c->device = device;
+    DeviceScope ds(device);
+    if ((e = cudaMalloc(&c->d_status, sizeof(int))) != cudaSuccess) {
+        delete c;
+        return cuda_err(nullptr, e, "cudaMalloc(status)");
+    }
+    if ((e = cudaMemset(c->d_status, 0, sizeof(int))) != cudaSuccess) {
+        cudaFree(c->d_status);
+        delete c;
+        return cuda_err(nullptr, e, "cudaMemset(status)");
+    }
+    *out = c;
+    return KNS_OK;
+}
+
+void kns_destroy(kns_ctx *ctx) {
+    if (!ctx) return;
+    {
+        DeviceScope ds(ctx->device);
+        cudaFree(ctx->d_status);
+    }
+    delete ctx;
+}
+
+const char *kns_last_error(const kns_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+
+kns_status kns_sync(kns_ctx *ctx, void *cuda_stream, int64_t timeout_ms) {
+    if (!ctx) return KNS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    DeviceScope ds(ctx->device);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const auto start = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t q = cudaStreamQuery(s);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) return cuda_err(ctx, q, "stream");
+        if (timeout_ms >= 0 &&
+            std::chrono::steady_clock::now() - start > std::chrono::milliseconds(timeout_ms))
+            return set_err(ctx, KNS_ERR_TIMEOUT, "work on the stream did not finish within %lld ms",
+                           (long long)timeout_ms);
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    int status = 0;
+    cudaError_t e = cudaMemcpyAsync(&status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "status read");
+    if (status != 0) {
+        cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s);
+        cudaStreamSynchronize(s);
+        return set_err(ctx, (kns_status)status, "a kernel reported status %d", status);
+    }
+    return KNS_OK;
+}
+
+kns_status kns_load_grid(kns_ctx *ctx, const kns_grid_desc *desc, const float *host_weights, size_t n_floats,
+                         const uint64_t *occ_words, kns_grid **out) {
+    if (!ctx) return KNS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!desc || !host_weights || !out) return set_err(ctx, KNS_ERR_INVALID_ARG, "NULL desc, weights or out");
+    *out = nullptr;
+    kns_status st = check_desc(ctx, *desc);
+    if (st != KNS_OK) return st;
+    const kns_grid_desc d = *desc;
+    const int64_t ncell = (int64_t)d.N * d.N * d.N;
+    const int64_t pcell = canon_sdf_params(d) + canon_col_params(d);
+    if ((int64_t)n_floats != ncell * pcell)
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "n_floats=%zu, the descriptor needs %lld", n_floats,
+                       (long long)(ncell * pcell));
+    DeviceScope ds(ctx->device);
+    kns_grid *g = new (std::nothrow) kns_grid();
+    if (!g) return set_err(ctx, KNS_ERR_OUT_OF_MEMORY, "host allocation failed");
+    g->ctx = ctx;
+    g->desc = d;
+    g->shape = kns::Shape{d.sdf_width, d.sdf_hidden, d.pe_pos_L, d.pe_dir_L};
+    const int dev_floats = kns::cell_floats(g->shape);
+    std::vector<float> host;
+    try {
+        host.resize((size_t)(ncell * dev_floats));
+    } catch (...) {
+        delete g;
+        return set_err(ctx, KNS_ERR_OUT_OF_MEMORY, "host staging allocation failed");
+    }
+    for (int64_t c = 0; c < ncell; ++c) convert_cell(d, dev_floats, host_weights + c * pcell, host.data() + c * dev_floats);
+    cudaError_t e = cudaMalloc(&g->d_w, host.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_w, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(g->d_w);
+        delete g;
+        return cuda_err(ctx, e, "grid upload");
+    }
+    if (d.occ_res > 0) {
+        const int64_t nvox = (int64_t)d.occ_res * d.occ_res * d.occ_res;
+        g->occ_words64 = (size_t)((nvox + 63) / 64);
+        e = cudaMalloc(&g->d_occ, g->occ_words64 * 8);
+        if (e == cudaSuccess) e = cudaMemset(g->d_occ, 0, g->occ_words64 * 8);
+        if (e == cudaSuccess && occ_words)
+            e = cudaMemcpy(g->d_occ, occ_words, g->occ_words64 * 8, cudaMemcpyHostToDevice);
+        fill_view(g);
+        if (e == cudaSuccess && !occ_words) {
+            float diag = 0.f;
+            for (int a = 0; a < 3; ++a) diag += g->view.ovox[a] * g->view.ovox[a];
+            diag = std::sqrt(diag);
+            kns::GridView v = g->view;
+            v.occ = nullptr;
+            e = kns::launch_occupancy_f32(g->shape, v, diag, g->d_occ, 0);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        }
+        if (e != cudaSuccess) {
+            cudaFree(g->d_w);
+            cudaFree(g->d_occ);
+            delete g;
+            return cuda_err(ctx, e, "occupancy");
+        }
+    }
+    fill_view(g);
+    *out = g;
+    return KNS_OK;
+}
+
+kns_status kns_load_grid_file(kns_ctx *ctx, const char *path, kns_grid **out) {
+    if (!ctx) return KNS_ERR_INVALID_ARG;
+    if (!path || !out) return set_err(ctx, KNS_ERR_INVALID_ARG, "NULL path or out");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return set_err(ctx, KNS_ERR_INVALID_ARG, "cannot open %s", path);
+    char magic[4];
+    uint32_t version = 0;
+    int32_t iv[10];
+    float fv[7];
+    uint64_t nf = 0, nocc = 0;
+    bool ok = std::fread(magic, 1, 4, f) == 4 && std::fread(&version, 4, 1, f) == 1 &&
+              std::fread(iv, 4, 10, f) == 10 && std::fread(fv, 4, 7, f) == 7 && std::fread(&nf, 8, 1, f) == 1 &&
+              std::fread(&nocc, 8, 1, f) == 1;
+    if (!ok || std::memcmp(magic, "KNS1", 4) != 0 || version != 1) {
+        std::fclose(f);
+        return set_err(ctx, KNS_ERR_FORMAT, "%s: not a version-1 KNS1 grid file", path);
+    }
+    kns_grid_desc d{};
+    d.N = iv[0];
+    d.pe_pos_L = iv[1];
+    d.pe_dir_L = iv[2];
+    d.sdf_hidden = iv[3];
+    d.sdf_width = iv[4];
+    d.feat_dim = iv[5];
+    d.col_hidden = iv[6];
+    d.col_width = iv[7];
+    d.col_use_x = iv[8];
+    d.occ_res = iv[9];
+    d.softplus_beta = fv[0];
+    for (int a = 0; a < 3; ++a) {
+        d.bbox_min[a] = fv[1 + a];
+        d.bbox_max[a] = fv[4 + a];
+    }
+    if (nf > ((uint64_t)1 << 34) || nocc > ((uint64_t)1 << 30)) {
+        std::fclose(f);
+        return set_err(ctx, KNS_ERR_FORMAT, "%s: implausible sizes in header", path);
+    }
+    std::vector<float> w;
+    std::vector<uint64_t> occ;
+    try {
+        w.resize(nf);
+        occ.resize(nocc);
+    } catch (...) {
+        std::fclose(f);
+        return set_err(ctx, KNS_ERR_OUT_OF_MEMORY, "host allocation failed");
+    }
+    ok = std::fread(w.data(), 4, nf, f) == nf && std::fread(occ.data(), 8, nocc, f) == nocc;
+    std::fclose(f);
+    if (!ok) return set_err(ctx, KNS_ERR_FORMAT, "%s: truncated", path);
+    if (nocc) {
+        const int64_t nvox = (int64_t)d.occ_res * d.occ_res * d.occ_res;
+        if (d.occ_res <= 0 || (int64_t)nocc != (nvox + 63) / 64)
+            return set_err(ctx, KNS_ERR_FORMAT, "%s: occupancy size does not match occ_res", path);
+    }
+    return kns_load_grid(ctx, &d, w.data(), w.size(), nocc ? occ.data() : nullptr, out);
+}
+
+void kns_free_grid(kns_grid *g) {
+    if (!g) return;
+    {
+        std::lock_guard<std::mutex> lk(g->ctx->mu);
+        DeviceScope ds(g->ctx->device);
+        cudaDeviceSynchronize();
+        cudaFree(g->d_w);
+        cudaFree(g->d_occ);
+    }
+    delete g;
+}
+
+kns_status kns_grid_get_desc(const kns_grid *g, kns_grid_desc *out) {
+    if (!g || !out) return KNS_ERR_INVALID_ARG;
+    *out = g->desc;
+    return KNS_OK;
+}
+
+kns_status kns_copy_occupancy(kns_ctx *ctx, const kns_grid *g, uint64_t *host_words, size_t n_words) {
+    if (!ctx) return KNS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!g || !host_words) return set_err(ctx, KNS_ERR_INVALID_ARG, "NULL grid or buffer");
+    if (!g->d_occ) return set_err(ctx, KNS_ERR_INVALID_ARG, "grid has no occupancy mask");
+    if (n_words < g->occ_words64)
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "buffer holds %zu words, mask needs %zu", n_words, g->occ_words64);
+    DeviceScope ds(ctx->device);
+    cudaError_t e = cudaMemcpy(host_words, g->d_occ, g->occ_words64 * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "occupancy copy");
+    return KNS_OK;
+}
+
+kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams, int n_cams, int W, int H,
+                      int max_steps, float eps, const kns_render_opts *opts, const kns_frame *out,
+                      void *cuda_stream) {
+    if (!ctx) return KNS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!grid || !cams || !out) return set_err(ctx, KNS_ERR_INVALID_ARG, "NULL grid, cams or out");
+    if (n_cams < 0 || W < 0 || H < 0) return set_err(ctx, KNS_ERR_INVALID_ARG, "negative size");
+    if ((int64_t)n_cams * W * H > ((int64_t)1 << 40)) return set_err(ctx, KNS_ERR_INVALID_ARG, "too many rays");
+    if (max_steps < 1) return set_err(ctx, KNS_ERR_INVALID_ARG, "max_steps=%d < 1", max_steps);
+    if (!(eps > 0.f) || !std::isfinite(eps)) return set_err(ctx, KNS_ERR_INVALID_ARG, "eps must be > 0 and finite");
+    if (!out->rgb || !out->depth) return set_err(ctx, KNS_ERR_INVALID_ARG, "rgb and depth buffers are required");
+    const int precision = opts ? opts->precision : KNS_FP32;
+    if (precision != KNS_FP32 && precision != KNS_BF16)
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "unknown precision %d", precision);
+    if (precision == KNS_BF16) return set_err(ctx, KNS_ERR_UNSUPPORTED, "BF16 path not built");
+    if (n_cams == 0 || W == 0 || H == 0) return KNS_OK;
+    if ((int64_t)W * H > INT32_MAX) return set_err(ctx, KNS_ERR_INVALID_ARG, "W*H exceeds 2^31-1");
+    DeviceScope ds(ctx->device);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    kns::RenderArgs a{};
+    a.W = W;
+    a.H = H;
+    a.max_steps = max_steps;
+    a.eps = eps;
+    a.rgb = out->rgb;
+    a.depth = out->depth;
+    a.normal = out->normal;
+    a.cell = out->cell;
+    a.steps = out->steps;
+    a.hit = out->hit;
+    for (int c0 = 0; c0 < n_cams; c0 += kns::MAX_CAMS_PER_LAUNCH) {
+        const int nc = std::min(kns::MAX_CAMS_PER_LAUNCH, n_cams - c0);
+        kns::CamBatch cb;
+        for (int c = 0; c < nc; ++c) std::memcpy(cb.c[c], &cams[c0 + c], sizeof(float) * 16);
+        a.cam_base = c0;
+        cudaError_t e = kns::launch_render_f32(grid->shape, grid->view, cb, nc, a, s);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "render launch");
+    }
+    return KNS_OK;
+}
+
+kns_status kns_sdf(kns_ctx *ctx, const kns_grid *grid, const float *pts, int64_t n, float *sdf, float *feat,
+                   float *grad, void *cuda_stream) {
+    if (!ctx) return KNS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!grid) return set_err(ctx, KNS_ERR_INVALID_ARG, "NULL grid");
+    if (n < 0) return set_err(ctx, KNS_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return KNS_OK;
+    if (!pts || !sdf) return set_err(ctx, KNS_ERR_INVALID_ARG, "NULL pts or sdf");
+    if (n > ((int64_t)1 << 36)) return set_err(ctx, KNS_ERR_INVALID_ARG, "n too large");
+    DeviceScope ds(ctx->device);
+    cudaError_t e = kns::launch_sdf_f32(grid->shape, grid->view, pts, n, sdf, feat, grad, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "sdf launch");
+    return KNS_OK;
+}
+
+}  // extern "C"

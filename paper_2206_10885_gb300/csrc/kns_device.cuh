@@ -1,0 +1,386 @@
+// kns_device.cuh -- private device-side definitions of the KiloNeuS CUDA library.
+//
+// Device weight layout (FP32, one block per cell, cell stride a multiple of 32 floats):
+//   SDF layer 0:    W0[W][INP]  b0[W]          INP = 3+6L rounded up to 4 (zero pad)
+//   SDF layer l:    Wl[W][W]    bl[W]          l = 1..H-1
+//   SDF last:       WL[16][W]   bL[16]         row 0 = d, rows 1..15 = feature z
+//   colour layer 0: C0[CW][CIN] c0[CW]         CIN = 15 + 3 + (3+6LD) + 3 (x slot; zero when unused)
+//   colour last:    C1[4][CW]   c1[4]          row 3 zero
+// Rows are 16-byte aligned so a warp that shares a cell reads weights with uniform float4 loads.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kns {
+
+constexpr int FEAT = 15;
+constexpr int SDF_OUT = 1 + FEAT;
+
+__host__ __device__ constexpr int round4(int v) { return (v + 3) & ~3; }
+__host__ __device__ constexpr int round32(int v) { return (v + 31) & ~31; }
+
+// Compile-time shape of one supported grid configuration.
+template <int W_, int H_, int L_, int LD_>
+struct Cfg {
+    static constexpr int W = W_;    // SDF hidden width (= colour hidden width)
+    static constexpr int H = H_;    // SDF hidden layers
+    static constexpr int L = L_;    // encoding frequencies of x
+    static constexpr int LD = LD_;  // encoding frequencies of the view direction
+    static constexpr int IN = 3 + 6 * L;
+    static constexpr int INP = round4(IN);
+    static constexpr int CIN = FEAT + 3 + (3 + 6 * LD) + 3;
+    static constexpr int CINP = round4(CIN);
+    // offsets (floats) inside one cell block
+    static constexpr int oW0 = 0;
+    static constexpr int ob0 = oW0 + W * INP;
+    static constexpr int oH1 = ob0 + W;  // start of hidden layer 1
+    static constexpr int HSZ = W * W + W;
+    __host__ __device__ static constexpr int oWl(int l) { return oH1 + (l - 1) * HSZ; }
+    __host__ __device__ static constexpr int obl(int l) { return oH1 + (l - 1) * HSZ + W * W; }
+    static constexpr int oWL = oH1 + (H - 1) * HSZ;
+    static constexpr int obL = oWL + SDF_OUT * W;
+    static constexpr int oC0 = obL + SDF_OUT;
+    static constexpr int oc0 = oC0 + W * CINP;
+    static constexpr int oC1 = oc0 + W;
+    static constexpr int oc1 = oC1 + 4 * W;
+    static constexpr int SIZE = round32(oc1 + 4);
+};
+
+// Everything a kernel needs to read a resident grid (passed by value).
+struct GridView {
+    const float *w;       // FP32 device layout
+    int cell_stride;      // floats per cell block
+    int N;                // cells per axis
+    float bmin[3], bmax[3];
+    float cscale[3];      // N / (bmax - bmin)
+    const uint32_t *occ;  // occupancy bits (x-fastest), NULL = no skipping
+    int occ_res;
+    int occ_per_cell;     // occ_res / N
+    float oscale[3];      // occ_res / (bmax - bmin)
+    float ovox[3];        // voxel edge (bmax - bmin) / occ_res
+    float beta, inv_beta;
+};
+
+// ------------------------------------------------------------------ activations
+__device__ __forceinline__ float softplus_f32(float s, float beta, float inv_beta) {
+    // max(s, 0) + log(1 + exp(-beta |s|)) / beta
+    float e = __expf(-beta * fabsf(s));
+    return fmaxf(s, 0.f) + __logf(1.f + e) * inv_beta;
+}
+// derivative of softplus_beta: sigmoid(beta s)
+__device__ __forceinline__ float dsoftplus_f32(float s, float beta) {
+    return 1.f / (1.f + __expf(-beta * s));
+}
+__device__ __forceinline__ float sigmoid_f32(float s) { return 1.f / (1.f + __expf(-s)); }
+
+// ------------------------------------------------------------------ Eq. 1 encoding
+// out[0..2] = p; out[3+6k+c] = sin(2^k pi p_c); out[3+6k+3+c] = cos(2^k pi p_c); zero pad.
+template <int L, int NOUT>
+__device__ __forceinline__ void encode3(float px, float py, float pz, float (&out)[NOUT]) {
+    out[0] = px;
+    out[1] = py;
+    out[2] = pz;
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        const float f = (float)(1 << k);
+        float s, c;
+        sincospif(f * px, &s, &c);
+        out[3 + 6 * k + 0] = s;
+        out[3 + 6 * k + 3] = c;
+        sincospif(f * py, &s, &c);
+        out[3 + 6 * k + 1] = s;
+        out[3 + 6 * k + 4] = c;
+        sincospif(f * pz, &s, &c);
+        out[3 + 6 * k + 2] = s;
+        out[3 + 6 * k + 5] = c;
+    }
+#pragma unroll
+    for (int i = 3 + 6 * L; i < NOUT; ++i) out[i] = 0.f;
+}
+
+// y = act(W x + b) with W[OUT][IN] row-major (IN % 4 == 0), weights through the read-only path.
+template <int IN, int OUT, bool SOFTPLUS>
+__device__ __forceinline__ void dense_f32(const float *__restrict__ Wt, const float *__restrict__ bias,
+                                          const float (&x)[IN], float (&y)[OUT], float beta, float inv_beta) {
+#pragma unroll
+    for (int o = 0; o < OUT; ++o) {
+        float acc = __ldg(bias + o);
+#pragma unroll
+        for (int i = 0; i < IN; i += 4) {
+            const float4 w4 = __ldg(reinterpret_cast<const float4 *>(Wt + o * IN + i));
+            acc = fmaf(w4.x, x[i + 0], acc);
+            acc = fmaf(w4.y, x[i + 1], acc);
+            acc = fmaf(w4.z, x[i + 2], acc);
+            acc = fmaf(w4.w, x[i + 3], acc);
+        }
+        y[o] = SOFTPLUS ? softplus_f32(acc, beta, inv_beta) : acc;
+    }
+}
+
+// Trace form of the SDF MLP (Eq. 2): only the d row of the last layer.
+template <class C>
+__device__ __forceinline__ float sdf_trace_f32(const float *__restrict__ cw, float px, float py, float pz,
+                                               float beta, float inv_beta) {
+    float in[C::INP];
+    encode3<C::L>(px, py, pz, in);
+    float h[C::W], g[C::W];
+    dense_f32<C::INP, C::W, true>(cw + C::oW0, cw + C::ob0, in, h, beta, inv_beta);
+#pragma unroll
+    for (int l = 1; l < C::H; ++l) {
+        dense_f32<C::W, C::W, true>(cw + C::oWl(l), cw + C::obl(l), h, g, beta, inv_beta);
+#pragma unroll
+        for (int i = 0; i < C::W; ++i) h[i] = g[i];
+    }
+    float d = __ldg(cw + C::obL);
+#pragma unroll
+    for (int i = 0; i < C::W; i += 4) {
+        const float4 w4 = __ldg(reinterpret_cast<const float4 *>(cw + C::oWL + i));
+        d = fmaf(w4.x, h[i], d);
+        d = fmaf(w4.y, h[i + 1], d);
+        d = fmaf(w4.z, h[i + 2], d);
+        d = fmaf(w4.w, h[i + 3], d);
+    }
+    return d;
+}
+
+// Full form: d, the feature z, and the analytic input gradient by reverse mode (Sec. 3.1).
+template <class C>
+__device__ __noinline__ float sdf_full_f32(const float *__restrict__ cw, float px, float py, float pz,
+                                           float beta, float inv_beta, float (&z)[FEAT], float (&grad)[3]) {
+    float in[C::INP];
+    encode3<C::L>(px, py, pz, in);
+    float dsp[C::H][C::W];  // softplus'(pre-activation) of every hidden unit
+    float h[C::W];
+    // layer 0
+#pragma unroll
+    for (int o = 0; o < C::W; ++o) {
+        float acc = __ldg(cw + C::ob0 + o);
+#pragma unroll
+        for (int i = 0; i < C::INP; i += 4) {
+            const float4 w4 = __ldg(reinterpret_cast<const float4 *>(cw + C::oW0 + o * C::INP + i));
+            acc = fmaf(w4.x, in[i], fmaf(w4.y, in[i + 1], fmaf(w4.z, in[i + 2], fmaf(w4.w, in[i + 3], acc))));
+        }
+        h[o] = softplus_f32(acc, beta, inv_beta);
+        dsp[0][o] = dsoftplus_f32(acc, beta);
+    }
+#pragma unroll
+    for (int l = 1; l < C::H; ++l) {
+        float g[C::W];
+#pragma unroll
+        for (int o = 0; o < C::W; ++o) {
+            float acc = __ldg(cw + C::obl(l) + o);
+#pragma unroll
+            for (int i = 0; i < C::W; i += 4) {
+                const float4 w4 = __ldg(reinterpret_cast<const float4 *>(cw + C::oWl(l) + o * C::W + i));
+                acc = fmaf(w4.x, h[i], fmaf(w4.y, h[i + 1], fmaf(w4.z, h[i + 2], fmaf(w4.w, h[i + 3], acc))));
+            }
+            g[o] = softplus_f32(acc, beta, inv_beta);
+            dsp[l][o] = dsoftplus_f32(acc, beta);
+        }
+#pragma unroll
+        for (int i = 0; i < C::W; ++i) h[i] = g[i];
+    }
+    float out[SDF_OUT];
+#pragma unroll
+    for (int o = 0; o < SDF_OUT; ++o) {
+        float acc = __ldg(cw + C::obL + o);
+#pragma unroll
+        for (int i = 0; i < C::W; i += 4) {
+            const float4 w4 = __ldg(reinterpret_cast<const float4 *>(cw + C::oWL + o * C::W + i));
+            acc = fmaf(w4.x, h[i], fmaf(w4.y, h[i + 1], fmaf(w4.z, h[i + 2], fmaf(w4.w, h[i + 3], acc))));
+        }
+        out[o] = acc;
+    }
+#pragma unroll
+    for (int k = 0; k < FEAT; ++k) z[k] = out[1 + k];
+    // reverse mode: delta = dd/dh of the last hidden layer = row 0 of WL
+    float delta[C::W];
+#pragma unroll
+    for (int i = 0; i < C::W; ++i) delta[i] = __ldg(cw + C::oWL + i);
+#pragma unroll
+    for (int l = C::H - 1; l >= 1; --l) {
+        float nd[C::W];
+#pragma unroll
+        for (int i = 0; i < C::W; ++i) nd[i] = 0.f;
+#pragma unroll
+        for (int o = 0; o < C::W; ++o) {
+            const float dl = delta[o] * dsp[l][o];
+#pragma unroll
+            for (int i = 0; i < C::W; i += 4) {
+                const float4 w4 = __ldg(reinterpret_cast<const float4 *>(cw + C::oWl(l) + o * C::W + i));
+                nd[i] = fmaf(w4.x, dl, nd[i]);
+                nd[i + 1] = fmaf(w4.y, dl, nd[i + 1]);
+                nd[i + 2] = fmaf(w4.z, dl, nd[i + 2]);
+                nd[i + 3] = fmaf(w4.w, dl, nd[i + 3]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < C::W; ++i) delta[i] = nd[i];
+    }
+    float din[C::INP];
+#pragma unroll
+    for (int i = 0; i < C::INP; ++i) din[i] = 0.f;
+#pragma unroll
+    for (int o = 0; o < C::W; ++o) {
+        const float dl = delta[o] * dsp[0][o];
+#pragma unroll
+        for (int i = 0; i < C::INP; i += 4) {
+            const float4 w4 = __ldg(reinterpret_cast<const float4 *>(cw + C::oW0 + o * C::INP + i));
+            din[i] = fmaf(w4.x, dl, din[i]);
+            din[i + 1] = fmaf(w4.y, dl, din[i + 1]);
+            din[i + 2] = fmaf(w4.z, dl, din[i + 2]);
+            din[i + 3] = fmaf(w4.w, dl, din[i + 3]);
+        }
+    }
+    // through the encoding: d sin(f p)/dp = f cos(f p), d cos(f p)/dp = -f sin(f p)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float gc = din[c];
+#pragma unroll
+        for (int k = 0; k < C::L; ++k) {
+            const float f = 3.14159265358979323846f * (float)(1 << k);
+            gc = fmaf(din[3 + 6 * k + c] * f, in[3 + 6 * k + 3 + c], gc);
+            gc = fmaf(-din[3 + 6 * k + 3 + c] * f, in[3 + 6 * k + c], gc);
+        }
+        grad[c] = gc;
+    }
+    return out[0];
+}
+
+// Colour MLP (Eq. 3): u = [z, n, gamma_LD(v), x] -> ReLU(W) -> 3 -> sigmoid.
+template <class C>
+__device__ __noinline__ void colour_f32(const float *__restrict__ cw, const float (&z)[FEAT], const float (&n)[3],
+                                        float vx, float vy, float vz, float px, float py, float pz,
+                                        float (&rgb)[3]) {
+    float u[C::CINP];
+#pragma unroll
+    for (int k = 0; k < FEAT; ++k) u[k] = z[k];
+    u[FEAT + 0] = n[0];
+    u[FEAT + 1] = n[1];
+    u[FEAT + 2] = n[2];
+    float gv[3 + 6 * C::LD];
+    encode3<C::LD>(vx, vy, vz, gv);
+#pragma unroll
+    for (int k = 0; k < 3 + 6 * C::LD; ++k) u[FEAT + 3 + k] = gv[k];
+    u[C::CIN - 3] = px;
+    u[C::CIN - 2] = py;
+    u[C::CIN - 1] = pz;
+#pragma unroll
+    for (int i = C::CIN; i < C::CINP; ++i) u[i] = 0.f;
+    float h[C::W];
+#pragma unroll
+    for (int o = 0; o < C::W; ++o) {
+        float acc = __ldg(cw + C::oc0 + o);
+#pragma unroll
+        for (int i = 0; i < C::CINP; i += 4) {
+            const float4 w4 = __ldg(reinterpret_cast<const float4 *>(cw + C::oC0 + o * C::CINP + i));
+            acc = fmaf(w4.x, u[i], fmaf(w4.y, u[i + 1], fmaf(w4.z, u[i + 2], fmaf(w4.w, u[i + 3], acc))));
+        }
+        h[o] = fmaxf(acc, 0.f);
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        float acc = __ldg(cw + C::oc1 + r);
+#pragma unroll
+        for (int i = 0; i < C::W; i += 4) {
+            const float4 w4 = __ldg(reinterpret_cast<const float4 *>(cw + C::oC1 + r * C::W + i));
+            acc = fmaf(w4.x, h[i], fmaf(w4.y, h[i + 1], fmaf(w4.z, h[i + 2], fmaf(w4.w, h[i + 3], acc))));
+        }
+        rgb[r] = sigmoid_f32(acc);
+    }
+}
+
+// ------------------------------------------------------------------ cell map m(x) (Sec. 3.1)
+__device__ __forceinline__ int grid_axis(float x, float bmin, float scale, int res) {
+    float u = floorf((x - bmin) * scale);
+    u = fminf(fmaxf(u, 0.f), (float)(res - 1));
+    return (int)u;
+}
+__device__ __forceinline__ int cell_of(const GridView &g, float x, float y, float z) {
+    const int ix = grid_axis(x, g.bmin[0], g.cscale[0], g.N);
+    const int iy = grid_axis(y, g.bmin[1], g.cscale[1], g.N);
+    const int iz = grid_axis(z, g.bmin[2], g.cscale[2], g.N);
+    return ix + g.N * (iy + g.N * iz);
+}
+
+__device__ __forceinline__ bool occ_test(const uint32_t *__restrict__ occ, int res, int ix, int iy, int iz) {
+    const unsigned v = (unsigned)ix + (unsigned)res * ((unsigned)iy + (unsigned)res * (unsigned)iz);
+    return (__ldg(occ + (v >> 5)) >> (v & 31u)) & 1u;
+}
+
+// ------------------------------------------------------------------ rays
+struct Ray {
+    float ox, oy, oz, wx, wy, wz;
+};
+
+// Pixel (i, j) of camera cam (16 floats: c2w 3x4 row-major, fx, fy, cx, cy).
+__device__ __forceinline__ Ray make_ray(const float *cam, int i, int j) {
+    const float dx = ((float)j + 0.5f - cam[14]) / cam[12];
+    const float dy = ((float)i + 0.5f - cam[15]) / cam[13];
+    float wx = fmaf(cam[0], dx, fmaf(cam[1], dy, cam[2]));
+    float wy = fmaf(cam[4], dx, fmaf(cam[5], dy, cam[6]));
+    float wz = fmaf(cam[8], dx, fmaf(cam[9], dy, cam[10]));
+    const float inv = 1.f / sqrtf(fmaf(wx, wx, fmaf(wy, wy, wz * wz)));
+    Ray r;
+    r.wx = wx * inv;
+    r.wy = wy * inv;
+    r.wz = wz * inv;
+    r.ox = cam[3];
+    r.oy = cam[7];
+    r.oz = cam[11];
+    return r;
+}
+
+// Slab test against the grid box; on overlap returns true with t0 = max(t_near, 0) and tf = t_far.
+__device__ __forceinline__ bool clip_box(const GridView &g, const Ray &r, float &t0, float &tf) {
+    float a = -INFINITY, b = INFINITY;
+    const float o[3] = {r.ox, r.oy, r.oz}, w[3] = {r.wx, r.wy, r.wz};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (w[k] != 0.f) {
+            const float t1 = (g.bmin[k] - o[k]) / w[k], t2 = (g.bmax[k] - o[k]) / w[k];
+            a = fmaxf(a, fminf(t1, t2));
+            b = fminf(b, fmaxf(t1, t2));
+        } else if (o[k] < g.bmin[k] || o[k] > g.bmax[k]) {
+            return false;
+        }
+    }
+    if (a > b || b < 0.f) return false;
+    t0 = fmaxf(a, 0.f);
+    tf = b;
+    return true;
+}
+
+// Integer 3D-DDA (Amanatides & Woo) from voxel v to the entry of the next occupied voxel.
+// Returns true with te and v updated; false when the ray leaves the grid or passes tf.
+__device__ __forceinline__ bool dda_next(const GridView &g, const Ray &r, int (&v)[3], float tf, float &te) {
+    const float o[3] = {r.ox, r.oy, r.oz}, w[3] = {r.wx, r.wy, r.wz};
+    const int res = g.occ_res;
+    // at most 3*res voxel crossings before the ray leaves the grid
+    for (int guard = 0; guard < 3 * res + 3; ++guard) {
+        float tm[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (w[a] == 0.f) {
+                tm[a] = INFINITY;
+            } else {
+                const float plane = g.bmin[a] + (float)(v[a] + (w[a] > 0.f ? 1 : 0)) * g.ovox[a];
+                tm[a] = (plane - o[a]) / w[a];
+            }
+        }
+        int ax = 0;
+        if (tm[1] < tm[ax]) ax = 1;
+        if (tm[2] < tm[ax]) ax = 2;
+        v[ax] += w[ax] > 0.f ? 1 : -1;
+        if (v[ax] < 0 || v[ax] >= res) return false;
+        if (tm[ax] > tf) return false;
+        if (occ_test(g.occ, res, v[0], v[1], v[2])) {
+            te = tm[ax];
+            return true;
+        }
+    }
+    return false;
+}
+
+}  // namespace kns

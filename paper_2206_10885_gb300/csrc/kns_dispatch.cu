@@ -1,0 +1,52 @@
+// kns_dispatch.cu -- maps a runtime grid shape to the compiled configuration's launchers.
+#include "kns_device.cuh"
+#include "kns_kernels.h"
+
+namespace kns {
+
+// Calls f(Cfg<...>{}) for the compiled configuration matching sh.  The list must match the
+// configurations build.py instantiates.
+template <class F>
+static cudaError_t dispatch(const Shape &sh, F &&f) {
+    if (sh.W == 32 && sh.H == 2 && sh.L == 4 && sh.LD == 2) return f(Cfg<32, 2, 4, 2>{});
+    if (sh.W == 32 && sh.H == 3 && sh.L == 4 && sh.LD == 2) return f(Cfg<32, 3, 4, 2>{});
+    if (sh.W == 64 && sh.H == 2 && sh.L == 4 && sh.LD == 2) return f(Cfg<64, 2, 4, 2>{});
+    if (sh.W == 64 && sh.H == 3 && sh.L == 4 && sh.LD == 2) return f(Cfg<64, 3, 4, 2>{});
+    if (sh.W == 32 && sh.H == 2 && sh.L == 6 && sh.LD == 4) return f(Cfg<32, 2, 6, 4>{});
+    if (sh.W == 32 && sh.H == 3 && sh.L == 6 && sh.LD == 4) return f(Cfg<32, 3, 6, 4>{});
+    if (sh.W == 64 && sh.H == 2 && sh.L == 6 && sh.LD == 4) return f(Cfg<64, 2, 6, 4>{});
+    if (sh.W == 64 && sh.H == 3 && sh.L == 6 && sh.LD == 4) return f(Cfg<64, 3, 6, 4>{});
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_render_f32(const Shape &sh, const GridView &g, const CamBatch &cams, int n_cams,
+                              const RenderArgs &a, cudaStream_t s) {
+    return dispatch(sh, [&](auto c) { return launch_render_cfg<decltype(c)>(g, cams, n_cams, a, s); });
+}
+
+cudaError_t launch_sdf_f32(const Shape &sh, const GridView &g, const float *pts, int64_t n, float *sdf,
+                           float *feat, float *grad, cudaStream_t s) {
+    return dispatch(sh, [&](auto c) { return launch_sdf_cfg<decltype(c)>(g, pts, n, sdf, feat, grad, s); });
+}
+
+cudaError_t launch_occupancy_f32(const Shape &sh, const GridView &g, float thresh, uint32_t *words,
+                                 cudaStream_t s) {
+    return dispatch(sh, [&](auto c) { return launch_occ_cfg<decltype(c)>(g, thresh, words, s); });
+}
+
+bool shape_supported(const Shape &sh) {
+    const bool wl = (sh.W == 32 || sh.W == 64) && (sh.H == 2 || sh.H == 3);
+    const bool enc = (sh.L == 4 && sh.LD == 2) || (sh.L == 6 && sh.LD == 4);
+    return wl && enc;
+}
+
+int cell_floats(const Shape &sh) {
+    int size = 0;
+    dispatch(sh, [&](auto c) {
+        size = decltype(c)::SIZE;
+        return cudaSuccess;
+    });
+    return size;
+}
+
+}  // namespace kns

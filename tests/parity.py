@@ -1,0 +1,54 @@
+"""Comparison helpers for CUDA-vs-oracle parity tests (test infrastructure).
+
+Tolerances (FP32 path):
+  - hit, cell and step count: identical on every decision-robust ray (the oracle's margins
+    show no threshold test within DELTA_D of |d| = eps, within DELTA_X of a cell or voxel
+    face, of t_far, or of a DDA axis tie), and identical on >= 99.9% of all rays;
+  - depth within 1e-4 scene units and RGB within 1e-5 per channel on rays both sides hit
+    in the same cell with the same step count;
+  - normal within 1e-4 per component on those rays.
+"""
+import numpy as np
+
+import oracle as O
+
+DELTA_D = 2e-6
+DELTA_X = 1e-5
+TOL_DEPTH = 1e-4
+TOL_RGB = 1e-5
+TOL_NORMAL = 1e-4
+
+
+def to_np(t):
+    return {k: v.detach().cpu().numpy() for k, v in t.items()}
+
+
+def compare_render(gpu: dict, ora: dict, min_agree: float = 0.999, tol_depth=TOL_DEPTH, tol_rgb=TOL_RGB,
+                   tol_normal=TOL_NORMAL, delta_d=DELTA_D, delta_x=DELTA_X, label=""):
+    """gpu: per-ray numpy arrays (same rays as ora).  Returns a summary dict; asserts the gates."""
+    n = ora["hit"].shape[0]
+    g_hit = gpu["hit"].astype(bool)
+    o_hit = ora["hit"].astype(bool)
+    robust = O.robust_mask(ora["margins"], delta_d, delta_x)
+    same_dec = (g_hit == o_hit) & (gpu["cell"] == ora["cell"]) & (gpu["steps"] == ora["steps"])
+    bad_robust = np.where(robust & ~same_dec)[0]
+    assert bad_robust.size == 0, (label, "robust rays disagree", bad_robust[:10], gpu["steps"][bad_robust[:5]],
+                                  ora["steps"][bad_robust[:5]], ora["margins"][bad_robust[:5]])
+    agree = float(np.mean(same_dec))
+    assert agree >= min_agree, (label, "decision agreement", agree)
+    both = g_hit & o_hit & same_dec
+    dd = np.abs(gpu["depth"][both].astype(np.float64) - ora["depth"][both])
+    dr = np.abs(gpu["rgb"][both].astype(np.float64) - ora["rgb"][both])
+    dn = np.abs(gpu["normal"][both].astype(np.float64) - ora["normal"][both])
+    summary = dict(n=n, hits=int(o_hit.sum()), robust=float(robust.mean()), agree=agree,
+                   max_depth_err=float(dd.max()) if dd.size else 0.0,
+                   max_rgb_err=float(dr.max()) if dr.size else 0.0,
+                   max_normal_err=float(dn.max()) if dn.size else 0.0)
+    if dd.size:
+        assert dd.max() <= tol_depth, (label, summary)
+        assert dr.max() <= tol_rgb, (label, summary)
+        assert dn.max() <= tol_normal, (label, summary)
+    misses = ~g_hit
+    assert np.all(np.isinf(gpu["depth"][misses])) and np.all(gpu["rgb"][misses] == 0)
+    assert np.all(gpu["cell"][misses] == -1)
+    return summary
