@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cams", type=int, default=0, help="use only the first N cameras (small profiling cases)")
     return ap.parse_args()
 
 
@@ -229,6 +230,8 @@ def run_kns(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     desc, w, cams, W, H, ms, eps = S.workload(args.workload)
+    if args.cams:
+        cams = cams[:args.cams]
     precision = kns.KNS_BF16 if args.precision == "bf16" else kns.KNS_FP32
     ctx = kns.Context(local_rank)
     grid = kns.Grid.load(ctx, desc, w)  # occupancy mask built on the device, untimed

@@ -72,8 +72,8 @@ def lib():
             L.ko_sdf_batch.argtypes = [D, f, C.c_int64, d, d, d, d, i32]
             L.ko_occupancy.argtypes = [D, f, C.c_int, C.c_double, u64]
             L.ko_ray.argtypes = [f, C.c_int, C.c_int, d, d]
-            L.ko_render.argtypes = [D, f, u64, f, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int64,
-                                    i64, f, f, f, i32, u8, i32, d, u8]
+            L.ko_render.argtypes = [D, f, u64, f, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                    C.c_int64, i64, f, f, f, i32, u8, i32, d, u8]
             L.ko_trace_rays.argtypes = [D, f, u64, C.c_int64, d, d, C.c_int, C.c_double, d, i32, i32, d, d]
             L.ko_march_roots.argtypes = [D, f, C.c_int64, d, d, d, d, C.c_double, C.c_double, d]
             L.ko_first_occupied.restype = C.c_int
@@ -186,11 +186,14 @@ def ray(cam, i: int, j: int):
     return o, d
 
 
-def render(g, w, occ, cams, W: int, H: int, max_steps: int, eps: float, sel=None):
+def render(g, w, occ, cams, W: int, H: int, max_steps: int, eps: float, sel=None, delta_step: float = 0.0):
     """Sphere-trace the selected pixels (or all).  Returns a dict of per-ray arrays.
 
     occ: uint64 occupancy words or None (no empty-space skipping).
     sel: global pixel ids cam*H*W + i*W + j, or None for every pixel.
+    delta_step: > 0 makes the margins conditioning-aware (see ko_trace_cond in kns_oracle.c):
+    each margin then has the predicted deviation of a trajectory computed with per-step error
+    delta_step subtracted.  0 gives the raw margins and skips the extra gradient evaluations.
     """
     w = _f32(w)
     cams = _f32(cams).reshape(-1, 16)
@@ -204,7 +207,8 @@ def render(g, w, occ, cams, W: int, H: int, max_steps: int, eps: float, sel=None
                normal=np.zeros((n, 3), np.float32), cell=np.zeros(n, np.int32), hit=np.zeros(n, np.uint8),
                steps=np.zeros(n, np.int32), margins=np.zeros((n, 4)), by_max=np.zeros(n, np.uint8))
     lib().ko_render(C.byref(_desc(g)), _p(w, C.c_float), _p(occ, C.c_uint64), _p(cams, C.c_float),
-                    cams.shape[0], W, H, max_steps, eps, n if sel is not None else 0, _p(sel, C.c_int64),
+                    cams.shape[0], W, H, max_steps, eps, float(delta_step), n if sel is not None else 0,
+                    _p(sel, C.c_int64),
                     _p(out["rgb"], C.c_float), _p(out["depth"], C.c_float), _p(out["normal"], C.c_float),
                     _p(out["cell"], C.c_int32), _p(out["hit"], C.c_uint8), _p(out["steps"], C.c_int32),
                     _p(out["margins"], C.c_double), _p(out["by_max"], C.c_uint8))

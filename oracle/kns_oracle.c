@@ -357,9 +357,13 @@ typedef struct {
     double m_d, m_t, m_x, m_dda; /* decision margins */
 } ko_ray_out;
 
-/* Sphere-trace one ray (Sec. 3.4.1).  occ may be NULL. */
-void ko_trace(const ko_desc *g, const float *weights, const uint64_t *occ, const double o[3], const double w[3],
-              int max_steps, double eps, ko_ray_out *r) {
+/* Sphere-trace one ray (Sec. 3.4.1).  occ may be NULL.
+ * delta_step > 0 switches on conditioning-aware margins: the oracle then also evaluates grad d at
+ * every step and propagates a predicted deviation E of a less precise trajectory,
+ * E_{k+1} = |1 + grad d(x_k) . w| E_k + delta_step (the step map t -> t + d(t) has slope 1 + grad d . w),
+ * and subtracts it from each margin: |d| vs eps loses |grad d . w| E_k, faces and t_far lose E_k. */
+void ko_trace_cond(const ko_desc *g, const float *weights, const uint64_t *occ, const double o[3],
+                   const double w[3], int max_steps, double eps, double delta_step, ko_ray_out *r) {
     memset(r, 0, sizeof(*r));
     r->depth = INFINITY;
     r->cell = -1;
@@ -368,12 +372,13 @@ void ko_trace(const ko_desc *g, const float *weights, const uint64_t *occ, const
     if (!ko_clip(g, o, w, &tn, &tf, &r->m_t)) return;
     double t = tn;
     int res = g->occ_res;
+    double E = delta_step > 0 ? 0.5 * delta_step : 0.0; /* predicted deviation of t */
     for (int k = 0; k < max_steps; k++) {
         double x[3] = {o[0] + t * w[0], o[1] + t * w[1], o[2] + t * w[2]};
         int cell;
         if (occ) {
             int v[3] = {grid_index(g, res, 0, x[0]), grid_index(g, res, 1, x[1]), grid_index(g, res, 2, x[2])};
-            r->m_x = fmin(r->m_x, interior_face_distance(g, res, x));
+            r->m_x = fmin(r->m_x, interior_face_distance(g, res, x) - E);
             if (!occ_test(occ, res, v[0], v[1], v[2])) {
                 double te;
                 if (!dda_next(g, occ, res, o, w, v, tf, &te, &r->m_dda, &r->m_t)) return; /* miss */
@@ -387,15 +392,23 @@ void ko_trace(const ko_desc *g, const float *weights, const uint64_t *occ, const
                 cell = v[0] / f + g->N * (v[1] / f + g->N * (v[2] / f));
             } else {
                 cell = ko_cell(g, x);
-                r->m_x = fmin(r->m_x, interior_face_distance(g, g->N, x));
+                r->m_x = fmin(r->m_x, interior_face_distance(g, g->N, x) - E);
             }
         } else {
             cell = ko_cell(g, x);
-            r->m_x = fmin(r->m_x, interior_face_distance(g, g->N, x));
+            r->m_x = fmin(r->m_x, interior_face_distance(g, g->N, x) - E);
         }
-        double d = ko_sdf_eval(g, weights, cell, x, NULL, NULL);
+        double gw = 0.0;
+        double d;
+        if (delta_step > 0) {
+            double gr[3];
+            d = ko_sdf_eval(g, weights, cell, x, NULL, gr);
+            gw = gr[0] * w[0] + gr[1] * w[1] + gr[2] * w[2];
+        } else {
+            d = ko_sdf_eval(g, weights, cell, x, NULL, NULL);
+        }
         r->steps++;
-        r->m_d = fmin(r->m_d, fabs(fabs(d) - eps));
+        r->m_d = fmin(r->m_d, fabs(fabs(d) - eps) - fabs(gw) * E);
         if (fabs(d) < eps) {
             double feat[KO_MAXIN], grad[3], nrm = 0;
             ko_sdf_eval(g, weights, cell, x, feat, grad);
@@ -409,17 +422,24 @@ void ko_trace(const ko_desc *g, const float *weights, const uint64_t *occ, const
             return;
         }
         t += d;
-        r->m_t = fmin(r->m_t, fmin(fabs(t - tf), fabs(t - tn)));
+        if (delta_step > 0) E = fabs(1.0 + gw) * E + delta_step;
+        r->m_t = fmin(r->m_t, fmin(fabs(t - tf), fabs(t - tn)) - E);
         if (t > tf || t < tn) return; /* left the box interval [t_near, t_far] */
     }
     r->by_max_steps = 1;
 }
 
+void ko_trace(const ko_desc *g, const float *weights, const uint64_t *occ, const double o[3], const double w[3],
+              int max_steps, double eps, ko_ray_out *r) {
+    ko_trace_cond(g, weights, occ, o, w, max_steps, eps, 0.0, r);
+}
+
 /* Render selected pixels.  sel: n_sel global pixel ids (cam*H*W + i*W + j), or NULL for all.
  * Outputs are per selected ray; any output pointer may be NULL. margins: 4 doubles per ray. */
 void ko_render(const ko_desc *g, const float *weights, const uint64_t *occ, const float *cams, int n_cams, int W,
-               int H, int max_steps, double eps, int64_t n_sel, const int64_t *sel, float *rgb, float *depth,
-               float *normal, int32_t *cell, uint8_t *hit, int32_t *steps, double *margins, uint8_t *by_max) {
+               int H, int max_steps, double eps, double delta_step, int64_t n_sel, const int64_t *sel, float *rgb,
+               float *depth, float *normal, int32_t *cell, uint8_t *hit, int32_t *steps, double *margins,
+               uint8_t *by_max) {
     int64_t n = sel ? n_sel : (int64_t)n_cams * W * H;
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t q = 0; q < n; q++) {
@@ -429,7 +449,7 @@ void ko_render(const ko_desc *g, const float *weights, const uint64_t *occ, cons
         double o[3], w[3];
         ko_ray(cams + 16 * cam, i, j, o, w);
         ko_ray_out r;
-        ko_trace(g, weights, occ, o, w, max_steps, eps, &r);
+        ko_trace_cond(g, weights, occ, o, w, max_steps, eps, delta_step, &r);
         if (rgb)
             for (int c = 0; c < 3; c++) rgb[3 * q + c] = (float)r.rgb[c];
         if (depth) depth[q] = (float)r.depth;

@@ -125,3 +125,15 @@ def fib_dirs(n: int) -> np.ndarray:
     phi = np.arccos(1 - 2 * i / n)
     th = math.pi * (1 + 5 ** 0.5) * i
     return np.stack([np.cos(th) * np.sin(phi), np.sin(th) * np.sin(phi), np.cos(phi)], 1)
+
+
+def plane_side_cameras(a, n: int, W: int, H: int, seed: int) -> np.ndarray:
+    """Cameras at radius 2.5 on the positive side of the plane a.x + b (looking at the origin)."""
+    rng = np.random.default_rng(seed)
+    a = np.asarray(a, dtype=np.float64)
+    cams = []
+    for _ in range(n):
+        p = a + 0.35 * rng.normal(size=3)
+        p = 2.5 * p / np.linalg.norm(p)
+        cams.append(S.look_at_camera(p, W, H))
+    return np.stack(cams)

@@ -1,17 +1,19 @@
 """Comparison helpers for CUDA-vs-oracle parity tests (test infrastructure).
 
 Tolerances (FP32 path):
-  - hit, cell and step count: identical on every decision-robust ray (the oracle's margins
-    show no threshold test within DELTA_D of |d| = eps, within DELTA_X of a cell or voxel
-    face, of t_far, or of a DDA axis tie), and identical on >= 99.9% of all rays;
-  - depth within 1e-4 scene units and RGB within 1e-5 per channel on rays both sides hit
-    in the same cell with the same step count;
-  - normal within 1e-4 per component on those rays.
+  - hit, cell and step count: identical on every decision-robust ray, and identical on
+    >= 99.9% of all rays.  A ray is decision-robust when the oracle's conditioning-aware
+    margins (computed with a per-step FP32 error model of DELTA_STEP) show no threshold test
+    within DELTA_D of |d| = eps and none within DELTA_X of a cell or voxel face, of the box
+    interval's ends, or of a DDA axis tie;
+  - on robust rays both sides hit: depth within 1e-4 scene units, RGB within 1e-5 per channel,
+    normal within 1e-4 per component.
 """
 import numpy as np
 
 import oracle as O
 
+DELTA_STEP = 2e-6  # bound on |d_fp32 - d_fp64| of one SDF evaluation (measured by the sdf tests)
 DELTA_D = 2e-6
 DELTA_X = 1e-5
 TOL_DEPTH = 1e-4
@@ -36,7 +38,7 @@ def compare_render(gpu: dict, ora: dict, min_agree: float = 0.999, tol_depth=TOL
                                   ora["steps"][bad_robust[:5]], ora["margins"][bad_robust[:5]])
     agree = float(np.mean(same_dec))
     assert agree >= min_agree, (label, "decision agreement", agree)
-    both = g_hit & o_hit & same_dec
+    both = g_hit & o_hit & same_dec & robust
     dd = np.abs(gpu["depth"][both].astype(np.float64) - ora["depth"][both])
     dr = np.abs(gpu["rgb"][both].astype(np.float64) - ora["rgb"][both])
     dn = np.abs(gpu["normal"][both].astype(np.float64) - ora["normal"][both])

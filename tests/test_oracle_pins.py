@@ -466,3 +466,17 @@ def test_near_sphere_hits_match_brute_force_roots():
     assert np.sum(~close[both] & ~later[both]) == 0
     # rays the brute force says have no root must not report a hit
     assert not np.any(hit & ~np.isfinite(roots))
+
+
+def test_conditioning_margins_only_shrink():
+    """Conditioning-aware margins (a test-harness aid) never exceed the raw ones, and vanish at
+    delta 0: the decisions and outputs themselves do not change."""
+    desc, w, cams, W, H, ms, eps = S.workload("c1")
+    cams = cams[:1]
+    r0 = O.render(desc, w, None, cams, 24, 24, ms, eps)
+    r1 = O.render(desc, w, None, cams, 24, 24, ms, eps, delta_step=2e-6)
+    for k in ("rgb", "depth", "normal", "cell", "hit", "steps"):
+        assert np.array_equal(r0[k], r1[k]), k
+    m0, m1 = r0["margins"], r1["margins"]
+    fin = np.isfinite(m0)
+    assert np.all(m1[fin] <= m0[fin] + 1e-15)
