@@ -15,18 +15,35 @@
 #include "kns_device.cuh"
 #include "kns_kernels.h"
 
+// Device scratch of the wavefront render, owned by the context and grown on demand.
+struct WaveScratch {
+    int64_t rays = 0;  // capacity in rays
+    int nc = 0;        // capacity in cells
+    int cams = 0;      // capacity in cameras
+    float *t_ray = nullptr;
+    int *steps_ray = nullptr, *cell_ray = nullptr, *q[2] = {nullptr, nullptr}, *qcell[2] = {nullptr, nullptr};
+    int *sorted = nullptr, *hits = nullptr;
+    int *cellbuf = nullptr;  // count[2], fill[2], off, tile_off (6 * (nc + 1) ints)
+    float *d_cams = nullptr;
+    kns::WaveCtrl *ctrl = nullptr;
+};
+
 struct kns_ctx {
     int device = 0;
+    int sm_count = 1;
     std::mutex mu;
     std::string err;
     int *d_status = nullptr;  // device status word written by kernels (0 = fine)
+    WaveScratch ws;
 };
 
 struct kns_grid {
     kns_ctx *ctx = nullptr;
     kns_grid_desc desc{};
     kns::Shape shape{};
-    float *d_w = nullptr;
+    float *d_w = nullptr;   // per-thread layout (shading, field queries, occupancy)
+    float *d_wt = nullptr;  // k-major trace layout (wavefront tile GEMM)
+    int wt_stride = 0;
     uint32_t *d_occ = nullptr;
     size_t occ_words64 = 0;
     kns::GridView view{};
@@ -150,6 +167,32 @@ void convert_cell(const kns_grid_desc &d, int dev_floats, const float *src, floa
     for (int r = 0; r < 3; ++r) dst[o + r] = src[s + r];
 }
 
+// Canonical SDF layers -> k-major trace layout (kns_device.cuh, Cfg::tW0..tbL), one cell.
+void convert_cell_trace(const kns_grid_desc &d, int dev_floats, const float *src, float *dst) {
+    const int W = d.sdf_width, H = d.sdf_hidden, IN = 3 + 6 * d.pe_pos_L, INP = kns::round4(IN);
+    std::memset(dst, 0, sizeof(float) * dev_floats);
+    int64_t s = 0, o = 0;
+    for (int r = 0; r < W; ++r)
+        for (int c = 0; c < IN; ++c) dst[o + c * W + r] = src[s + r * IN + c];
+    s += (int64_t)W * IN;
+    o += (int64_t)W * INP;
+    for (int r = 0; r < W; ++r) dst[o + r] = src[s + r];
+    s += W;
+    o += W;
+    for (int l = 1; l < H; ++l) {
+        for (int r = 0; r < W; ++r)
+            for (int c = 0; c < W; ++c) dst[o + c * W + r] = src[s + r * W + c];
+        s += W * W;
+        o += W * W;
+        for (int r = 0; r < W; ++r) dst[o + r] = src[s + r];
+        s += W;
+        o += W;
+    }
+    for (int c = 0; c < W; ++c) dst[o + c] = src[s + c];  // row 0 (d) of the last layer
+    o += W;
+    dst[o] = src[s + (int64_t)kns::SDF_OUT * W];  // its bias
+}
+
 void fill_view(kns_grid *g) {
     kns::GridView &v = g->view;
     const kns_grid_desc &d = g->desc;
@@ -170,6 +213,57 @@ void fill_view(kns_grid *g) {
     v.inv_beta = 1.f / d.softplus_beta;
 }
 
+void free_scratch(WaveScratch &w) {
+    cudaFree(w.t_ray);
+    cudaFree(w.steps_ray);
+    cudaFree(w.cell_ray);
+    cudaFree(w.q[0]);
+    cudaFree(w.q[1]);
+    cudaFree(w.qcell[0]);
+    cudaFree(w.qcell[1]);
+    cudaFree(w.sorted);
+    cudaFree(w.hits);
+    cudaFree(w.cellbuf);
+    cudaFree(w.d_cams);
+    cudaFree(w.ctrl);
+    w = WaveScratch{};
+}
+
+// Grows the context's wavefront scratch to hold `rays` rays, `nc` cells and `cams` cameras.
+kns_status ensure_scratch(kns_ctx *ctx, int64_t rays, int nc, int cams) {
+    WaveScratch &w = ctx->ws;
+    if (rays <= w.rays && nc <= w.nc && cams <= w.cams) return KNS_OK;
+    cudaDeviceSynchronize();  // earlier renders may still use the old buffers
+    const int64_t R = std::max(rays, w.rays);
+    const int NC = std::max(nc, w.nc);
+    const int NCAM = std::max(cams, w.cams);
+    free_scratch(w);
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](auto **p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc((void **)p, bytes);
+    };
+    alloc(&w.t_ray, sizeof(float) * R);
+    alloc(&w.steps_ray, sizeof(int) * R);
+    alloc(&w.cell_ray, sizeof(int) * R);
+    alloc(&w.q[0], sizeof(int) * R);
+    alloc(&w.q[1], sizeof(int) * R);
+    alloc(&w.qcell[0], sizeof(int) * R);
+    alloc(&w.qcell[1], sizeof(int) * R);
+    alloc(&w.sorted, sizeof(int) * R);
+    alloc(&w.hits, sizeof(int) * R);
+    alloc(&w.cellbuf, sizeof(int) * 6 * (size_t)(NC + 1));
+    alloc(&w.d_cams, sizeof(kns_camera) * NCAM);
+    alloc(&w.ctrl, sizeof(kns::WaveCtrl));
+    if (e != cudaSuccess) {
+        free_scratch(w);
+        return cuda_err(ctx, e, "render scratch");
+    }
+    w.rays = R;
+    w.nc = NC;
+    w.cams = NCAM;
+    return KNS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -185,6 +279,8 @@ kns_status kns_create(int device, kns_ctx **out) {
     if (!c) return set_err(nullptr, KNS_ERR_OUT_OF_MEMORY, "host allocation failed");
     c->device = device;
     DeviceScope ds(device);
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (c->sm_count < 1) c->sm_count = 1;
     if ((e = cudaMalloc(&c->d_status, sizeof(int))) != cudaSuccess) {
         delete c;
         return cuda_err(nullptr, e, "cudaMalloc(status)");
@@ -202,6 +298,8 @@ void kns_destroy(kns_ctx *ctx) {
     if (!ctx) return;
     {
         DeviceScope ds(ctx->device);
+        cudaDeviceSynchronize();
+        free_scratch(ctx->ws);
         cudaFree(ctx->d_status);
     }
     delete ctx;
@@ -268,8 +366,24 @@ kns_status kns_load_grid(kns_ctx *ctx, const kns_grid_desc *desc, const float *h
     for (int64_t c = 0; c < ncell; ++c) convert_cell(d, dev_floats, host_weights + c * pcell, host.data() + c * dev_floats);
     cudaError_t e = cudaMalloc(&g->d_w, host.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(g->d_w, host.data(), host.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        g->wt_stride = kns::trace_cell_floats(g->shape);
+        std::vector<float> ht;
+        try {
+            ht.resize((size_t)(ncell * g->wt_stride));
+        } catch (...) {
+            cudaFree(g->d_w);
+            delete g;
+            return set_err(ctx, KNS_ERR_OUT_OF_MEMORY, "host staging allocation failed");
+        }
+        for (int64_t c = 0; c < ncell; ++c)
+            convert_cell_trace(d, g->wt_stride, host_weights + c * pcell, ht.data() + c * g->wt_stride);
+        e = cudaMalloc(&g->d_wt, ht.size() * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemcpy(g->d_wt, ht.data(), ht.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         cudaFree(g->d_w);
+        cudaFree(g->d_wt);
         delete g;
         return cuda_err(ctx, e, "grid upload");
     }
@@ -292,6 +406,7 @@ kns_status kns_load_grid(kns_ctx *ctx, const kns_grid_desc *desc, const float *h
         }
         if (e != cudaSuccess) {
             cudaFree(g->d_w);
+            cudaFree(g->d_wt);
             cudaFree(g->d_occ);
             delete g;
             return cuda_err(ctx, e, "occupancy");
@@ -366,6 +481,7 @@ void kns_free_grid(kns_grid *g) {
         DeviceScope ds(g->ctx->device);
         cudaDeviceSynchronize();
         cudaFree(g->d_w);
+        cudaFree(g->d_wt);
         cudaFree(g->d_occ);
     }
     delete g;
@@ -409,23 +525,59 @@ kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams
     if ((int64_t)W * H > INT32_MAX) return set_err(ctx, KNS_ERR_INVALID_ARG, "W*H exceeds 2^31-1");
     DeviceScope ds(ctx->device);
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    kns::RenderArgs a{};
-    a.W = W;
-    a.H = H;
-    a.max_steps = max_steps;
-    a.eps = eps;
-    a.rgb = out->rgb;
-    a.depth = out->depth;
-    a.normal = out->normal;
-    a.cell = out->cell;
-    a.steps = out->steps;
-    a.hit = out->hit;
-    for (int c0 = 0; c0 < n_cams; c0 += kns::MAX_CAMS_PER_LAUNCH) {
-        const int nc = std::min(kns::MAX_CAMS_PER_LAUNCH, n_cams - c0);
-        kns::CamBatch cb;
-        for (int c = 0; c < nc; ++c) std::memcpy(cb.c[c], &cams[c0 + c], sizeof(float) * 16);
-        a.cam_base = c0;
-        cudaError_t e = kns::launch_render_f32(grid->shape, grid->view, cb, nc, a, s);
+    const int64_t hw = (int64_t)W * H;
+    const int per_chunk = (int)std::max<int64_t>(1, std::min<int64_t>(n_cams, (int64_t)INT32_MAX / hw));
+    const int NC = grid->desc.N * grid->desc.N * grid->desc.N;
+    kns_status st = ensure_scratch(ctx, (int64_t)per_chunk * hw, NC, per_chunk);
+    if (st != KNS_OK) return st;
+    WaveScratch &w = ctx->ws;
+    for (int c0 = 0; c0 < n_cams; c0 += per_chunk) {
+        const int nc = std::min(per_chunk, n_cams - c0);
+        const int64_t base = (int64_t)c0 * hw;
+        kns::WaveArgs a{};
+        a.W = W;
+        a.H = H;
+        a.n_cams = nc;
+        a.max_steps = max_steps;
+        a.eps = eps;
+        a.NC = NC;
+        a.cams = w.d_cams;
+        a.wt = grid->d_wt;
+        a.wt_stride = grid->wt_stride;
+        a.rgb = out->rgb + 3 * base;
+        a.depth = out->depth + base;
+        a.normal = out->normal ? out->normal + 3 * base : nullptr;
+        a.cell_out = out->cell ? out->cell + base : nullptr;
+        a.steps_out = out->steps ? out->steps + base : nullptr;
+        a.hit_out = out->hit ? out->hit + base : nullptr;
+        a.t_ray = w.t_ray;
+        a.steps_ray = w.steps_ray;
+        a.cell_ray = w.cell_ray;
+        a.q[0] = w.q[0];
+        a.q[1] = w.q[1];
+        a.qcell[0] = w.qcell[0];
+        a.qcell[1] = w.qcell[1];
+        a.sorted = w.sorted;
+        a.hits = w.hits;
+        a.count[0] = w.cellbuf;
+        a.count[1] = w.cellbuf + (NC + 1);
+        a.fill[0] = w.cellbuf + 2 * (NC + 1);
+        a.fill[1] = w.cellbuf + 3 * (NC + 1);
+        a.off = w.cellbuf + 4 * (NC + 1);
+        a.tile_off = w.cellbuf + 5 * (NC + 1);
+        a.ctrl = w.ctrl;
+        cudaError_t e = cudaMemcpyAsync(w.d_cams, &cams[c0], sizeof(kns_camera) * nc, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.ctrl, 0, sizeof(kns::WaveCtrl), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.cellbuf, 0, sizeof(int) * 4 * (NC + 1), s);
+        if (e == cudaSuccess) e = kns::launch_wave_gen(grid->shape, grid->view, a, s);
+        const int eval_blocks = ctx->sm_count * 8, scatter_blocks = ctx->sm_count * 4;
+        for (int k = 0; k < max_steps && e == cudaSuccess; ++k) {
+            const int cur = k & 1;
+            e = kns::launch_wave_scan(a, cur, s);
+            if (e == cudaSuccess) e = kns::launch_wave_scatter(a, cur, scatter_blocks, s);
+            if (e == cudaSuccess) e = kns::launch_wave_eval(grid->shape, grid->view, a, cur, eval_blocks, s);
+        }
+        if (e == cudaSuccess) e = kns::launch_wave_shade(grid->shape, grid->view, a, ctx->sm_count * 8, s);
         if (e != cudaSuccess) return cuda_err(ctx, e, "render launch");
     }
     return KNS_OK;

@@ -45,6 +45,16 @@ struct Cfg {
     static constexpr int oC1 = oc0 + W;
     static constexpr int oc1 = oC1 + 4 * W;
     static constexpr int SIZE = round32(oc1 + 4);
+    // k-major copy of the SDF trace weights (used by the wavefront tile GEMM):
+    //   T0[INP][W] t0[W]  |  Tl[W][W] tl[W] (l = 1..H-1)  |  dL[W] (row 0 of the last layer) bL0 (+3 pad)
+    static constexpr int tW0 = 0;
+    static constexpr int tb0 = INP * W;
+    static constexpr int tH1 = tb0 + W;
+    __host__ __device__ static constexpr int tWl(int l) { return tH1 + (l - 1) * HSZ; }
+    __host__ __device__ static constexpr int tbl(int l) { return tH1 + (l - 1) * HSZ + W * W; }
+    static constexpr int tdL = tH1 + (H - 1) * HSZ;
+    static constexpr int tbL = tdL + W;
+    static constexpr int TSIZE = round32(tbL + 4);
 };
 
 // Everything a kernel needs to read a resident grid (passed by value).

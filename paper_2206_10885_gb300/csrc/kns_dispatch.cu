@@ -19,11 +19,6 @@ static cudaError_t dispatch(const Shape &sh, F &&f) {
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_render_f32(const Shape &sh, const GridView &g, const CamBatch &cams, int n_cams,
-                              const RenderArgs &a, cudaStream_t s) {
-    return dispatch(sh, [&](auto c) { return launch_render_cfg<decltype(c)>(g, cams, n_cams, a, s); });
-}
-
 cudaError_t launch_sdf_f32(const Shape &sh, const GridView &g, const float *pts, int64_t n, float *sdf,
                            float *feat, float *grad, cudaStream_t s) {
     return dispatch(sh, [&](auto c) { return launch_sdf_cfg<decltype(c)>(g, pts, n, sdf, feat, grad, s); });
@@ -32,6 +27,26 @@ cudaError_t launch_sdf_f32(const Shape &sh, const GridView &g, const float *pts,
 cudaError_t launch_occupancy_f32(const Shape &sh, const GridView &g, float thresh, uint32_t *words,
                                  cudaStream_t s) {
     return dispatch(sh, [&](auto c) { return launch_occ_cfg<decltype(c)>(g, thresh, words, s); });
+}
+
+cudaError_t launch_wave_gen(const Shape &sh, const GridView &g, const WaveArgs &a, cudaStream_t s) {
+    return dispatch(sh, [&](auto c) { return launch_wave_gen_cfg<decltype(c)>(g, a, s); });
+}
+cudaError_t launch_wave_eval(const Shape &sh, const GridView &g, const WaveArgs &a, int cur, int blocks,
+                             cudaStream_t s) {
+    return dispatch(sh, [&](auto c) { return launch_wave_eval_cfg<decltype(c)>(g, a, cur, blocks, s); });
+}
+cudaError_t launch_wave_shade(const Shape &sh, const GridView &g, const WaveArgs &a, int blocks, cudaStream_t s) {
+    return dispatch(sh, [&](auto c) { return launch_wave_shade_cfg<decltype(c)>(g, a, blocks, s); });
+}
+
+int trace_cell_floats(const Shape &sh) {
+    int size = 0;
+    dispatch(sh, [&](auto c) {
+        size = decltype(c)::TSIZE;
+        return cudaSuccess;
+    });
+    return size;
 }
 
 bool shape_supported(const Shape &sh) {

@@ -13,26 +13,45 @@ struct Shape {
     int W, H, L, LD;
 };
 
-constexpr int MAX_CAMS_PER_LAUNCH = 64;
-
-// Cameras passed by value as kernel parameters (no device scratch needed for them).
-struct CamBatch {
-    float c[MAX_CAMS_PER_LAUNCH][16];
+// Device counters of one wavefront render.
+struct WaveCtrl {
+    int n_live[2];  // samples queued for the current / next wave
+    int n_hits;     // rays that converged (queued for shading)
+    int n_tiles;    // warp tiles of the current wave
+    int status;
+    int pad[3];
 };
 
-struct RenderArgs {
-    int W, H, max_steps;
+// Everything the wavefront kernels read and write (device pointers; passed by value).
+struct WaveArgs {
+    int W, H, n_cams, max_steps;
     float eps;
-    int cam_base;  // index of the first camera of this launch in the output frame
+    int NC;               // cells N^3
+    const float *cams;    // n_cams x 16 floats
+    const float *wt;      // k-major trace weights (see kns_device.cuh)
+    int wt_stride;        // floats per cell
+    // outputs, indexed by ray id r = cam*H*W + i*W + j
     float *rgb, *depth, *normal;
-    int32_t *cell, *steps;
-    uint8_t *hit;
+    int32_t *cell_out, *steps_out;
+    uint8_t *hit_out;
+    // per-ray state
+    float *t_ray;
+    int *steps_ray, *cell_ray;
+    // wave queues (double-buffered), cell-sorted samples, hits
+    int *q[2], *qcell[2];
+    int *sorted, *hits;
+    int *count[2], *fill[2];  // per-cell sample counts and scatter cursors
+    int *off, *tile_off;      // NC+1 exclusive scans: samples and tiles per cell
+    WaveCtrl *ctrl;
 };
 
 // Per-configuration launchers (explicitly instantiated, one object file per configuration).
 template <class C>
-cudaError_t launch_render_cfg(const GridView &g, const CamBatch &cams, int n_cams, const RenderArgs &a,
-                              cudaStream_t s);
+cudaError_t launch_wave_gen_cfg(const GridView &g, const WaveArgs &a, cudaStream_t s);
+template <class C>
+cudaError_t launch_wave_eval_cfg(const GridView &g, const WaveArgs &a, int cur, int blocks, cudaStream_t s);
+template <class C>
+cudaError_t launch_wave_shade_cfg(const GridView &g, const WaveArgs &a, int blocks, cudaStream_t s);
 template <class C>
 cudaError_t launch_sdf_cfg(const GridView &g, const float *pts, int64_t n, float *sdf, float *feat, float *grad,
                            cudaStream_t s);
@@ -41,9 +60,15 @@ cudaError_t launch_occ_cfg(const GridView &g, float thresh, uint32_t *words, cud
 
 bool shape_supported(const Shape &sh);
 int cell_floats(const Shape &sh);
+int trace_cell_floats(const Shape &sh);
 
-cudaError_t launch_render_f32(const Shape &sh, const GridView &g, const CamBatch &cams, int n_cams,
-                              const RenderArgs &a, cudaStream_t s);
+cudaError_t launch_wave_gen(const Shape &sh, const GridView &g, const WaveArgs &a, cudaStream_t s);
+cudaError_t launch_wave_eval(const Shape &sh, const GridView &g, const WaveArgs &a, int cur, int blocks,
+                             cudaStream_t s);
+cudaError_t launch_wave_shade(const Shape &sh, const GridView &g, const WaveArgs &a, int blocks, cudaStream_t s);
+cudaError_t launch_wave_scan(const WaveArgs &a, int cur, cudaStream_t s);
+cudaError_t launch_wave_scatter(const WaveArgs &a, int cur, int blocks, cudaStream_t s);
+
 cudaError_t launch_sdf_f32(const Shape &sh, const GridView &g, const float *pts, int64_t n, float *sdf,
                            float *feat, float *grad, cudaStream_t s);
 cudaError_t launch_occupancy_f32(const Shape &sh, const GridView &g, float thresh, uint32_t *words,

@@ -1,0 +1,121 @@
+// kns_sort.cu -- per-wave counting sort of samples by cell (configuration independent).
+//
+// scan:    one block turns the wave's per-cell sample counts into exclusive offsets off[0..NC]
+//          and per-cell warp-tile offsets tile_off[0..NC] (ceil(count / 16) tiles per cell),
+//          publishes the tile count, and clears the next wave's counters.
+// scatter: each sample goes to off[cell] + (its rank among the wave's samples of that cell);
+//          lanes of a warp that share a cell take consecutive slots with one atomic.
+#include "kns_wave.cuh"
+
+namespace kns {
+
+constexpr int SCAN_THREADS = 1024;
+
+// Inclusive block-wide scan of two values at once (1024 threads).
+__device__ __forceinline__ void block_scan2(int &a, int &b, int *wa, int *wb) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int ya = __shfl_up_sync(FULL, a, o), yb = __shfl_up_sync(FULL, b, o);
+        if (lane >= o) {
+            a += ya;
+            b += yb;
+        }
+    }
+    if (lane == 31) {
+        wa[warp] = a;
+        wb[warp] = b;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int sa = wa[lane], sb = wb[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int ya = __shfl_up_sync(FULL, sa, o), yb = __shfl_up_sync(FULL, sb, o);
+            if (lane >= o) {
+                sa += ya;
+                sb += yb;
+            }
+        }
+        wa[lane] = sa;
+        wb[lane] = sb;
+    }
+    __syncthreads();
+    if (warp > 0) {
+        a += wa[warp - 1];
+        b += wb[warp - 1];
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) wave_scan_kernel(WaveArgs a, int cur) {
+    __shared__ int wa[32], wb[32];
+    const int nxt = cur ^ 1;
+    const int NC = a.NC;
+    // clear the next wave's counters (nothing reads them during this wave)
+    for (int c = threadIdx.x; c < NC; c += SCAN_THREADS) {
+        a.count[nxt][c] = 0;
+        a.fill[nxt][c] = 0;
+    }
+    if (threadIdx.x == 0) a.ctrl->n_live[nxt] = 0;
+    if (a.ctrl->n_live[cur] == 0) {
+        if (threadIdx.x == 0) a.ctrl->n_tiles = 0;
+        return;
+    }
+    // each thread owns a contiguous run of cells
+    const int per = (NC + SCAN_THREADS - 1) / SCAN_THREADS;
+    const int c0 = threadIdx.x * per, c1 = min(NC, c0 + per);
+    int sum = 0, tiles = 0;
+    for (int c = c0; c < c1; ++c) {
+        const int n = a.count[cur][c];
+        sum += n;
+        tiles += (n + TILE - 1) / TILE;
+    }
+    int incl_s = sum, incl_t = tiles;
+    block_scan2(incl_s, incl_t, wa, wb);
+    int run_s = incl_s - sum, run_t = incl_t - tiles;
+    for (int c = c0; c < c1; ++c) {
+        const int n = a.count[cur][c];
+        a.off[c] = run_s;
+        a.tile_off[c] = run_t;
+        run_s += n;
+        run_t += (n + TILE - 1) / TILE;
+    }
+    if (threadIdx.x == SCAN_THREADS - 1) {
+        a.off[NC] = incl_s;
+        a.tile_off[NC] = incl_t;
+        a.ctrl->n_tiles = incl_t;
+    }
+}
+
+__global__ void __launch_bounds__(256) wave_scatter_kernel(WaveArgs a, int cur) {
+    const int n = a.ctrl->n_live[cur];
+    const int lane = threadIdx.x & 31;
+    const int stride = gridDim.x * blockDim.x;
+    const int bound = (n + 31) & ~31;  // warp-uniform loop bound
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < bound; i += stride) {
+        const bool pred = i < n;
+        const int c = pred ? a.qcell[cur][i] : 0;
+        const int r = pred ? a.q[cur][i] : 0;
+        const unsigned m = __ballot_sync(FULL, pred);
+        if (pred) {
+            const unsigned grp = __match_any_sync(m, c);
+            const int leader = __ffs(grp) - 1;
+            int base = 0;
+            if (lane == leader) base = __ldg(a.off + c) + atomicAdd(a.fill[cur] + c, __popc(grp));
+            base = __shfl_sync(grp, base, leader);
+            a.sorted[base + __popc(grp & lanemask_lt())] = r;
+        }
+    }
+}
+
+cudaError_t launch_wave_scan(const WaveArgs &a, int cur, cudaStream_t s) {
+    wave_scan_kernel<<<1, SCAN_THREADS, 0, s>>>(a, cur);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wave_scatter(const WaveArgs &a, int cur, int blocks, cudaStream_t s) {
+    wave_scatter_kernel<<<blocks, 256, 0, s>>>(a, cur);
+    return cudaGetLastError();
+}
+
+}  // namespace kns

@@ -1,0 +1,91 @@
+// kns_wave.cuh -- wavefront sphere tracing: shared state, ray advance, warp-aggregated queues.
+//
+// One render is a sequence of waves.  Wave k holds every ray that still needs its k-th SDF
+// evaluation.  Per wave:
+//   sort:  counting sort of the wave's samples by cell (histogram built while the samples were
+//          emitted, one exclusive scan over the N^3 cells, a scatter into cell order);
+//   eval:  each warp takes a tile of up to 16 samples of one cell and evaluates the cell's SDF
+//          MLP (Eq. 2) for all of them at once (a small GEMM per layer), then updates each ray:
+//          hit test |d| < eps, step t += d, interval and budget checks, and the advance to its
+//          next sample (cell lookup m(x), occupancy skip) which it emits into wave k+1.
+// Hits are shaded after the last wave (normal from the analytic gradient, colour MLP of Eq. 3).
+#pragma once
+
+#include "kns_device.cuh"
+#include "kns_kernels.h"
+
+namespace kns {
+
+constexpr int TILE = 16;  // samples per warp tile
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Appends the predicated lanes of a warp to a queue; returns this lane's slot (or -1).
+// Must be called by all 32 lanes.
+__device__ __forceinline__ int warp_append(int *counter, bool pred) {
+    const unsigned m = __ballot_sync(FULL, pred);
+    if (!m) return -1;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(counter, __popc(m));
+    base = __shfl_sync(FULL, base, leader);
+    return pred ? base + __popc(m & lanemask_lt()) : -1;
+}
+
+// Adds one to count[cell] for each predicated lane, one atomic per distinct cell in the warp.
+__device__ __forceinline__ void warp_count_cells(int *count, bool pred, int cell) {
+    const unsigned m = __ballot_sync(FULL, pred);
+    if (pred) {
+        const unsigned grp = __match_any_sync(m, cell);
+        if ((threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(count + cell, __popc(grp));
+    }
+}
+
+__device__ __forceinline__ Ray ray_of(const WaveArgs &a, int r, int &cam) {
+    const int hw = a.W * a.H;
+    cam = r / hw;
+    const int pix = r - cam * hw;
+    const int i = pix / a.W, j = pix - i * a.W;
+    return make_ray(a.cams + 16 * cam, i, j);
+}
+
+__device__ __forceinline__ void write_miss(const WaveArgs &a, int r, int steps) {
+    a.rgb[3 * (int64_t)r + 0] = 0.f;
+    a.rgb[3 * (int64_t)r + 1] = 0.f;
+    a.rgb[3 * (int64_t)r + 2] = 0.f;
+    a.depth[r] = INFINITY;
+    if (a.normal) {
+        a.normal[3 * (int64_t)r + 0] = 0.f;
+        a.normal[3 * (int64_t)r + 1] = 0.f;
+        a.normal[3 * (int64_t)r + 2] = 0.f;
+    }
+    if (a.cell_out) a.cell_out[r] = -1;
+    if (a.steps_out) a.steps_out[r] = steps;
+    if (a.hit_out) a.hit_out[r] = 0;
+}
+
+// Moves a ray at parameter t to its next sample: the cell at x(t), or, when x(t) lies in an empty
+// occupancy voxel, the entry face of the next occupied voxel (t moves there; the voxel fixes the
+// cell exactly).  Returns the cell, or -1 when the ray leaves the grid (a miss).
+__device__ __forceinline__ int advance_ray(const GridView &g, const Ray &r, float &t, float tf) {
+    const float x = fmaf(t, r.wx, r.ox), y = fmaf(t, r.wy, r.oy), z = fmaf(t, r.wz, r.oz);
+    if (g.occ) {
+        int v[3] = {grid_axis(x, g.bmin[0], g.oscale[0], g.occ_res), grid_axis(y, g.bmin[1], g.oscale[1], g.occ_res),
+                    grid_axis(z, g.bmin[2], g.oscale[2], g.occ_res)};
+        if (!occ_test(g.occ, g.occ_res, v[0], v[1], v[2])) {
+            float te;
+            if (!dda_next(g, r, v, tf, te)) return -1;
+            t = te;
+            const int f = g.occ_per_cell;
+            return v[0] / f + g.N * (v[1] / f + g.N * (v[2] / f));
+        }
+    }
+    return cell_of(g, x, y, z);
+}
+
+}  // namespace kns
