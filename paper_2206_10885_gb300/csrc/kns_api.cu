@@ -35,6 +35,8 @@ struct kns_ctx {
     std::string err;
     int *d_status = nullptr;  // device status word written by kernels (0 = fine)
     WaveScratch ws;
+    int *h_live = nullptr;                 // pinned: live-sample counts of recent rounds
+    cudaEvent_t ev_live[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 struct kns_grid {
@@ -229,6 +231,10 @@ void free_scratch(WaveScratch &w) {
     w = WaveScratch{};
 }
 
+// Render tiling: samples per block tile (4 warps x 16) and in-tile sphere steps per round.
+constexpr int kRenderBlockTile = 64;
+constexpr int kRenderInnerSteps = 16;
+
 // Grows the context's wavefront scratch to hold `rays` rays, `nc` cells and `cams` cameras.
 kns_status ensure_scratch(kns_ctx *ctx, int64_t rays, int nc, int cams) {
     WaveScratch &w = ctx->ws;
@@ -285,10 +291,19 @@ kns_status kns_create(int device, kns_ctx **out) {
         delete c;
         return cuda_err(nullptr, e, "cudaMalloc(status)");
     }
-    if ((e = cudaMemset(c->d_status, 0, sizeof(int))) != cudaSuccess) {
+    if ((e = cudaMemset(c->d_status, 0, sizeof(int))) != cudaSuccess ||
+        (e = cudaHostAlloc((void **)&c->h_live, 4 * sizeof(int), cudaHostAllocDefault)) != cudaSuccess) {
         cudaFree(c->d_status);
         delete c;
-        return cuda_err(nullptr, e, "cudaMemset(status)");
+        return cuda_err(nullptr, e, "context set-up");
+    }
+    for (int i = 0; i < 4; ++i) {
+        if ((e = cudaEventCreateWithFlags(&c->ev_live[i], cudaEventDisableTiming)) != cudaSuccess) {
+            cudaFree(c->d_status);
+            cudaFreeHost(c->h_live);
+            delete c;
+            return cuda_err(nullptr, e, "cudaEventCreate");
+        }
     }
     *out = c;
     return KNS_OK;
@@ -301,6 +316,9 @@ void kns_destroy(kns_ctx *ctx) {
         cudaDeviceSynchronize();
         free_scratch(ctx->ws);
         cudaFree(ctx->d_status);
+        cudaFreeHost(ctx->h_live);
+        for (int i = 0; i < 4; ++i)
+            if (ctx->ev_live[i]) cudaEventDestroy(ctx->ev_live[i]);
     }
     delete ctx;
 }
@@ -541,6 +559,9 @@ kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams
         a.max_steps = max_steps;
         a.eps = eps;
         a.NC = NC;
+        a.btile = kRenderBlockTile;
+        a.inner_steps = kRenderInnerSteps;
+        a.status = ctx->d_status;
         a.cams = w.d_cams;
         a.wt = grid->d_wt;
         a.wt_stride = grid->wt_stride;
@@ -571,9 +592,20 @@ kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams
         if (e == cudaSuccess) e = cudaMemsetAsync(w.cellbuf, 0, sizeof(int) * 4 * (NC + 1), s);
         if (e == cudaSuccess) e = kns::launch_wave_gen(grid->shape, grid->view, a, s);
         const int eval_blocks = ctx->sm_count * 8, scatter_blocks = ctx->sm_count * 4;
+        // Rounds: at most max_steps (each live ray takes >= 1 step per round).  The host reads the
+        // live count of round k-2 before launching round k and stops once a round was empty, so it
+        // runs at most two rounds ahead of the device.
         for (int k = 0; k < max_steps && e == cudaSuccess; ++k) {
             const int cur = k & 1;
+            if (k >= 2) {
+                e = cudaEventSynchronize(ctx->ev_live[(k - 2) & 3]);
+                if (e != cudaSuccess || ctx->h_live[(k - 2) & 3] == 0) break;
+            }
             e = kns::launch_wave_scan(a, cur, s);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(ctx->h_live + (k & 3), &w.ctrl->n_live[cur], sizeof(int), cudaMemcpyDeviceToHost,
+                                    s);
+            if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_live[k & 3], s);
             if (e == cudaSuccess) e = kns::launch_wave_scatter(a, cur, scatter_blocks, s);
             if (e == cudaSuccess) e = kns::launch_wave_eval(grid->shape, grid->view, a, cur, eval_blocks, s);
         }

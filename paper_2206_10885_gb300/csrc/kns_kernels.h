@@ -15,10 +15,10 @@ struct Shape {
 
 // Device counters of one wavefront render.
 struct WaveCtrl {
-    int n_live[2];  // samples queued for the current / next wave
+    int n_live[2];  // samples queued for the current / next round
     int n_hits;     // rays that converged (queued for shading)
-    int n_tiles;    // warp tiles of the current wave
-    int status;
+    int n_tiles;    // block tiles of the current round
+    int next_tile;  // dynamic tile counter of the current round
     int pad[3];
 };
 
@@ -27,6 +27,9 @@ struct WaveArgs {
     int W, H, n_cams, max_steps;
     float eps;
     int NC;               // cells N^3
+    int btile;            // samples per block tile (cell-sorted samples are cut into such tiles)
+    int inner_steps;      // sphere steps a tile may take in one round while its rays stay in the cell
+    int *status;          // context status word (kns_status of a device-side failure, 0 = fine)
     const float *cams;    // n_cams x 16 floats
     const float *wt;      // k-major trace weights (see kns_device.cuh)
     int wt_stride;        // floats per cell

@@ -1,7 +1,7 @@
 // kns_sort.cu -- per-wave counting sort of samples by cell (configuration independent).
 //
 // scan:    one block turns the wave's per-cell sample counts into exclusive offsets off[0..NC]
-//          and per-cell warp-tile offsets tile_off[0..NC] (ceil(count / 16) tiles per cell),
+//          and per-cell block-tile offsets tile_off[0..NC] (ceil(count / btile) tiles per cell),
 //          publishes the tile count, and clears the next wave's counters.
 // scatter: each sample goes to off[cell] + (its rank among the wave's samples of that cell);
 //          lanes of a warp that share a cell take consecutive slots with one atomic.
@@ -56,7 +56,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) wave_scan_kernel(WaveArgs a, int
         a.count[nxt][c] = 0;
         a.fill[nxt][c] = 0;
     }
-    if (threadIdx.x == 0) a.ctrl->n_live[nxt] = 0;
+    if (threadIdx.x == 0) {
+        a.ctrl->n_live[nxt] = 0;
+        a.ctrl->next_tile = 0;
+    }
     if (a.ctrl->n_live[cur] == 0) {
         if (threadIdx.x == 0) a.ctrl->n_tiles = 0;
         return;
@@ -68,7 +71,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) wave_scan_kernel(WaveArgs a, int
     for (int c = c0; c < c1; ++c) {
         const int n = a.count[cur][c];
         sum += n;
-        tiles += (n + TILE - 1) / TILE;
+        tiles += (n + a.btile - 1) / a.btile;
     }
     int incl_s = sum, incl_t = tiles;
     block_scan2(incl_s, incl_t, wa, wb);
@@ -78,7 +81,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) wave_scan_kernel(WaveArgs a, int
         a.off[c] = run_s;
         a.tile_off[c] = run_t;
         run_s += n;
-        run_t += (n + TILE - 1) / TILE;
+        run_t += (n + a.btile - 1) / a.btile;
     }
     if (threadIdx.x == SCAN_THREADS - 1) {
         a.off[NC] = incl_s;

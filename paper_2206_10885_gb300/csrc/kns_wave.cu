@@ -20,7 +20,7 @@ __device__ __forceinline__ void tile_layer_f32(const float *__restrict__ Wt, con
     float acc[4][NPL];
 #pragma unroll
     for (int j = 0; j < NPL; j += 4) {
-        const float4 bb = __ldg(reinterpret_cast<const float4 *>(b + ng * NPL + j));
+        const float4 bb = *reinterpret_cast<const float4 *>(b + ng * NPL + j);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             acc[i][j] = bb.x;
@@ -34,7 +34,7 @@ __device__ __forceinline__ void tile_layer_f32(const float *__restrict__ Wt, con
         const float4 a = *reinterpret_cast<const float4 *>(hin + k * TILE + 4 * sg);
 #pragma unroll
         for (int j = 0; j < NPL; j += 4) {
-            const float4 w = __ldg(reinterpret_cast<const float4 *>(Wt + k * W + ng * NPL + j));
+            const float4 w = *reinterpret_cast<const float4 *>(Wt + k * W + ng * NPL + j);
             acc[0][j] = fmaf(a.x, w.x, acc[0][j]);
             acc[0][j + 1] = fmaf(a.x, w.y, acc[0][j + 1]);
             acc[0][j + 2] = fmaf(a.x, w.z, acc[0][j + 2]);
@@ -84,10 +84,10 @@ __device__ __forceinline__ float tile_sdf_f32(const float *__restrict__ wt, floa
 #pragma unroll
     for (int k = 0; k < C::W / 2; ++k) {
         const int kk = half * (C::W / 2) + k;
-        acc = fmaf(__ldg(wt + C::tdL + kk), src[kk * TILE + s], acc);
+        acc = fmaf(wt[C::tdL + kk], src[kk * TILE + s], acc);
     }
     acc += __shfl_xor_sync(FULL, acc, 16);
-    return acc + __ldg(wt + C::tbL);
+    return acc + wt[C::tbL];
 }
 
 // Wave 0: one thread per pixel (16x8 pixels per block, 8x4 per warp); clip, advance, emit.
@@ -126,83 +126,139 @@ __global__ void __launch_bounds__(128) wave_gen_kernel(GridView g, WaveArgs a) {
     warp_count_cells(a.count[0], alive, cell);
 }
 
-// Wave k: each warp evaluates tiles of the cell-sorted samples, updates the rays, emits wave k+1.
+// Round k: each block takes a tile of up to 64 cell-sorted samples of one cell (dynamic
+// scheduling), stages the cell's k-major weights in shared memory with one TMA bulk copy, and each
+// of its 4 warps evaluates 16 samples.  Rays whose next sample stays in the same cell keep
+// stepping inside the tile (up to inner_steps evaluations this round); the others are emitted to
+// round k+1 (with their next cell), converge (hit list) or terminate (miss written).
+constexpr int EVAL_WARPS = 4;
+
 template <class C>
-__global__ void __launch_bounds__(128) wave_eval_kernel(GridView g, WaveArgs a, int cur) {
-    constexpr int HROWS = C::INP > C::W ? C::INP : C::W;
-    __shared__ __align__(16) float sh[4][2][HROWS * TILE];
+__host__ __device__ constexpr int eval_hrows() {
+    return C::INP > C::W ? C::INP : C::W;
+}
+template <class C>
+__host__ __device__ constexpr int eval_smem_bytes() {
+    return (C::TSIZE + EVAL_WARPS * 2 * eval_hrows<C>() * TILE) * (int)sizeof(float);
+}
+
+template <class C>
+__global__ void __launch_bounds__(EVAL_WARPS * 32) wave_eval_kernel(GridView g, WaveArgs a, int cur) {
+    extern __shared__ __align__(128) float dyn[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_tile, s_cell, s_start, s_len;
+    float *wsm = dyn;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *hA = sh[warp][0], *hB = sh[warp][1];
+    float *hA = dyn + C::TSIZE + warp * 2 * eval_hrows<C>() * TILE;
+    float *hB = hA + eval_hrows<C>() * TILE;
     const int nxt = cur ^ 1;
     const int n_tiles = a.ctrl->n_tiles;
-    const int per_block = (n_tiles + gridDim.x - 1) / gridDim.x;
-    const int t_begin = blockIdx.x * per_block;
-    const int t_end = min(n_tiles, t_begin + per_block);
-    for (int tile = t_begin + warp; tile < t_end; tile += 4) {
-        // the cell c with tile_off[c] <= tile < tile_off[c+1]
-        int lo = 0, hi = a.NC;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (__ldg(a.tile_off + mid) <= tile) lo = mid; else hi = mid;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    int cached = -1;
+    uint32_t phase = 0;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int tile = atomicAdd(&a.ctrl->next_tile, 1);
+            s_tile = tile;
+            if (tile < n_tiles) {
+                int lo = 0, hi = a.NC;  // the cell c with tile_off[c] <= tile < tile_off[c+1]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (__ldg(a.tile_off + mid) <= tile) lo = mid; else hi = mid;
+                }
+                const int start = __ldg(a.off + lo) + (tile - __ldg(a.tile_off + lo)) * a.btile;
+                s_cell = lo;
+                s_start = start;
+                s_len = min(a.btile, __ldg(a.off + lo + 1) - start);
+                if (lo != cached)
+                    bulk_load(wsm, a.wt + (int64_t)lo * a.wt_stride, C::TSIZE * sizeof(float), &bar);
+            }
         }
-        const int c = lo;
-        const int start = __ldg(a.off + c) + (tile - __ldg(a.tile_off + c)) * TILE;
-        const int len = min(TILE, __ldg(a.off + c + 1) - start);
+        __syncthreads();
+        if (s_tile >= n_tiles) break;
+        const int c = s_cell;
+        const bool fresh = c != cached;
+        cached = c;
+        // this warp's samples
+        const int wstart = s_start + warp * TILE;
+        const int wlen = max(0, min(TILE, s_len - warp * TILE));
         const int s = lane & 15;
-        const bool own = lane < TILE && s < len;
-        int r = 0;
+        bool active = lane < TILE && s < wlen;
+        int r = 0, steps = 0;
         float t = 0.f, t0 = 0.f, tf = 0.f;
         Ray ray{};
-        if (lane < TILE) {
-            float in[C::INP];
-            if (own) {
-                r = a.sorted[start + s];
-                t = a.t_ray[r];
-                int cam;
-                ray = ray_of(a, r, cam);
-                clip_box(g, ray, t0, tf);
-                encode3<C::L>(fmaf(t, ray.wx, ray.ox), fmaf(t, ray.wy, ray.oy), fmaf(t, ray.wz, ray.oz), in);
-            } else {
-#pragma unroll
-                for (int k = 0; k < C::INP; ++k) in[k] = 0.f;
-            }
-#pragma unroll
-            for (int k = 0; k < C::INP; ++k) hA[k * TILE + s] = in[k];
+        if (active) {
+            r = a.sorted[wstart + s];
+            t = a.t_ray[r];
+            steps = a.steps_ray[r];
+            int cam;
+            ray = ray_of(a, r, cam);
+            clip_box(g, ray, t0, tf);
         }
-        __syncwarp();
-        const float d = tile_sdf_f32<C>(a.wt + (int64_t)c * a.wt_stride, hA, hB, lane, g.beta, g.inv_beta);
-        bool hit = false, alive = false;
-        int ncell = -1;
-        if (own) {
-            const int steps = a.steps_ray[r] + 1;
-            a.steps_ray[r] = steps;
-            if (fabsf(d) < a.eps) {
-                hit = true;
-                a.cell_ray[r] = c;
-            } else {
-                t += d;
-                if (t > tf || t < t0 || steps >= a.max_steps) {
-                    write_miss(a, r, steps);
+        if (fresh) {
+            const bool ok = mbar_wait(&bar, phase, 1u << 26);
+            phase ^= 1u;
+            if (__syncthreads_or(!ok)) {  // the copy never landed: report and leave
+                if (threadIdx.x == 0) atomicCAS(a.status, 0, (int)6 /* KNS_ERR_TIMEOUT */);
+                mbar_wait(&bar, phase ^ 1u, 1u << 20);
+                return;
+            }
+        }
+        for (int it = 0; it < a.inner_steps; ++it) {
+            if (!__any_sync(FULL, active)) break;
+            if (lane < TILE) {
+                float in[C::INP];
+                if (active) {
+                    encode3<C::L>(fmaf(t, ray.wx, ray.ox), fmaf(t, ray.wy, ray.oy), fmaf(t, ray.wz, ray.oz), in);
                 } else {
-                    ncell = advance_ray(g, ray, t, tf);
-                    if (ncell < 0) {
+#pragma unroll
+                    for (int k = 0; k < C::INP; ++k) in[k] = 0.f;
+                }
+#pragma unroll
+                for (int k = 0; k < C::INP; ++k) hA[k * TILE + s] = in[k];
+            }
+            __syncwarp();
+            const float d = tile_sdf_f32<C>(wsm, hA, hB, lane, g.beta, g.inv_beta);
+            bool hit = false, emit = false, stay = false;
+            int ncell = -1;
+            if (active) {
+                ++steps;
+                if (fabsf(d) < a.eps) {
+                    hit = true;
+                    a.cell_ray[r] = c;
+                    a.t_ray[r] = t;
+                    a.steps_ray[r] = steps;
+                } else {
+                    t += d;
+                    if (t > tf || t < t0 || steps >= a.max_steps) {
                         write_miss(a, r, steps);
                     } else {
-                        alive = true;
-                        a.t_ray[r] = t;
+                        ncell = advance_ray(g, ray, t, tf);
+                        if (ncell < 0) {
+                            write_miss(a, r, steps);
+                        } else if (ncell == c && it + 1 < a.inner_steps) {
+                            stay = true;
+                        } else {
+                            emit = true;
+                            a.t_ray[r] = t;
+                            a.steps_ray[r] = steps;
+                        }
                     }
                 }
             }
+            const int hp = warp_append(&a.ctrl->n_hits, hit);
+            if (hit) a.hits[hp] = r;
+            const int qp = warp_append(&a.ctrl->n_live[nxt], emit);
+            if (emit) {
+                a.q[nxt][qp] = r;
+                a.qcell[nxt][qp] = ncell;
+            }
+            warp_count_cells(a.count[nxt], emit, ncell);
+            active = stay;
+            __syncwarp();
         }
-        const int hp = warp_append(&a.ctrl->n_hits, hit);
-        if (hit) a.hits[hp] = r;
-        const int qp = warp_append(&a.ctrl->n_live[nxt], alive);
-        if (alive) {
-            a.q[nxt][qp] = r;
-            a.qcell[nxt][qp] = ncell;
-        }
-        warp_count_cells(a.count[nxt], alive, ncell);
-        __syncwarp();
+        __syncthreads();  // the weights buffer and tile slots are reused by the next tile
     }
 }
 
@@ -249,7 +305,11 @@ cudaError_t launch_wave_gen_cfg(const GridView &g, const WaveArgs &a, cudaStream
 }
 template <class C>
 cudaError_t launch_wave_eval_cfg(const GridView &g, const WaveArgs &a, int cur, int blocks, cudaStream_t s) {
-    wave_eval_kernel<C><<<blocks, 128, 0, s>>>(g, a, cur);
+    constexpr int smem = eval_smem_bytes<C>();
+    static_assert(smem <= 200 * 1024, "eval tile does not fit in shared memory");
+    cudaError_t e = cudaFuncSetAttribute(wave_eval_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    wave_eval_kernel<C><<<blocks, EVAL_WARPS * 32, smem, s>>>(g, a, cur);
     return cudaGetLastError();
 }
 template <class C>

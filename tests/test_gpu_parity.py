@@ -185,11 +185,13 @@ def test_render_plane_cell_colours(kns, ctx):
     cams = K.plane_side_cameras(a, 3, 64, 48, seed=7)
     grid = kns.Grid.load(ctx, desc, w)
     try:
-        g = gpu_render(kns, ctx, grid, cams, 64, 48, 64, 1e-5)
+        g = gpu_render(kns, ctx, grid, cams, 64, 48, 64, 1e-4)
     finally:
         grid.free()
-    o = O.render(desc, w, None, cams, 64, 48, 64, 1e-5, delta_step=P.DELTA_STEP)
-    s = P.compare_render(g, o, label="plane")
+    o = O.render(desc, w, None, cams, 64, 48, 64, 1e-4, delta_step=P.DELTA_STEP)
+    # an exact plane converges geometrically, so many steps land close to |d| = eps: every robust
+    # ray must agree exactly; the non-robust remainder may flip
+    s = P.compare_render(g, o, min_agree=0.995, label="plane")
     assert s["hits"] > 1000
 
 
