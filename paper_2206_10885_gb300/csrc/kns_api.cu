@@ -233,7 +233,8 @@ void free_scratch(WaveScratch &w) {
 
 // Render tiling: samples per block tile (4 warps x 16) and in-tile sphere steps per round.
 constexpr int kRenderBlockTile = 64;
-constexpr int kRenderInnerSteps = 16;
+constexpr int kRenderInnerSteps = 32;
+constexpr int kRenderTailRays = 4096;  // rounds this small finish one thread per ray
 
 // Grows the context's wavefront scratch to hold `rays` rays, `nc` cells and `cams` cameras.
 kns_status ensure_scratch(kns_ctx *ctx, int64_t rays, int nc, int cams) {
@@ -561,6 +562,7 @@ kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams
         a.NC = NC;
         a.btile = kRenderBlockTile;
         a.inner_steps = kRenderInnerSteps;
+        a.tail_max = kRenderTailRays;
         a.status = ctx->d_status;
         a.cams = w.d_cams;
         a.wt = grid->d_wt;

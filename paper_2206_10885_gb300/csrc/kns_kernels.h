@@ -19,7 +19,8 @@ struct WaveCtrl {
     int n_hits;     // rays that converged (queued for shading)
     int n_tiles;    // block tiles of the current round
     int next_tile;  // dynamic tile counter of the current round
-    int pad[3];
+    int tail;       // 1: the current round is small enough to finish one thread per ray
+    int pad[2];
 };
 
 // Everything the wavefront kernels read and write (device pointers; passed by value).
@@ -28,7 +29,8 @@ struct WaveArgs {
     float eps;
     int NC;               // cells N^3
     int btile;            // samples per block tile (cell-sorted samples are cut into such tiles)
-    int inner_steps;      // sphere steps a tile may take in one round while its rays stay in the cell
+    int inner_steps;      // sphere steps a tile may take in one round while its rays stay in its cells
+    int tail_max;         // a round with at most this many rays is finished one thread per ray
     int *status;          // context status word (kns_status of a device-side failure, 0 = fine)
     const float *cams;    // n_cams x 16 floats
     const float *wt;      // k-major trace weights (see kns_device.cuh)

@@ -60,7 +60,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) wave_scan_kernel(WaveArgs a, int
         a.ctrl->n_live[nxt] = 0;
         a.ctrl->next_tile = 0;
     }
-    if (a.ctrl->n_live[cur] == 0) {
+    const int n_live = a.ctrl->n_live[cur];
+    if (threadIdx.x == 0) a.ctrl->tail = n_live <= a.tail_max ? 1 : 0;
+    if (n_live == 0 || n_live <= a.tail_max) {  // nothing to sort: empty, or finished per thread
         if (threadIdx.x == 0) a.ctrl->n_tiles = 0;
         return;
     }
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) wave_scan_kernel(WaveArgs a, int
 }
 
 __global__ void __launch_bounds__(256) wave_scatter_kernel(WaveArgs a, int cur) {
-    const int n = a.ctrl->n_live[cur];
+    const int n = a.ctrl->tail ? 0 : a.ctrl->n_live[cur];
     const int lane = threadIdx.x & 31;
     const int stride = gridDim.x * blockDim.x;
     const int bound = (n + 31) & ~31;  // warp-uniform loop bound

@@ -64,13 +64,14 @@ __device__ __forceinline__ void tile_layer_f32(const float *__restrict__ Wt, con
     }
 }
 
-// SDF trace form for a tile whose encoded inputs are in hA[k][s]; returns d of sample lane % 16.
+// SDF trace form for a tile whose encoded inputs are in hin[k][s] (left intact); P and Q are the
+// ping-pong activation buffers.  Returns d of sample lane % 16.
 template <class C>
-__device__ __forceinline__ float tile_sdf_f32(const float *__restrict__ wt, float *hA, float *hB, int lane,
-                                              float beta, float inv_beta) {
-    tile_layer_f32<C::INP, C::W>(wt + C::tW0, wt + C::tb0, hA, hB, lane, beta, inv_beta);
+__device__ __forceinline__ float tile_sdf_f32(const float *__restrict__ wt, const float *hin, float *P, float *Q,
+                                              int lane, float beta, float inv_beta) {
+    tile_layer_f32<C::INP, C::W>(wt + C::tW0, wt + C::tb0, hin, P, lane, beta, inv_beta);
     __syncwarp();
-    float *src = hB, *dst = hA;
+    float *src = P, *dst = Q;
 #pragma unroll
     for (int l = 1; l < C::H; ++l) {
         tile_layer_f32<C::W, C::W>(wt + C::tWl(l), wt + C::tbl(l), src, dst, lane, beta, inv_beta);
@@ -87,6 +88,7 @@ __device__ __forceinline__ float tile_sdf_f32(const float *__restrict__ wt, floa
         acc = fmaf(wt[C::tdL + kk], src[kk * TILE + s], acc);
     }
     acc += __shfl_xor_sync(FULL, acc, 16);
+    __syncwarp();
     return acc + wt[C::tbL];
 }
 
@@ -126,41 +128,104 @@ __global__ void __launch_bounds__(128) wave_gen_kernel(GridView g, WaveArgs a) {
     warp_count_cells(a.count[0], alive, cell);
 }
 
-// Round k: each block takes a tile of up to 64 cell-sorted samples of one cell (dynamic
-// scheduling), stages the cell's k-major weights in shared memory with one TMA bulk copy, and each
-// of its 4 warps evaluates 16 samples.  Rays whose next sample stays in the same cell keep
-// stepping inside the tile (up to inner_steps evaluations this round); the others are emitted to
-// round k+1 (with their next cell), converge (hit list) or terminate (miss written).
+// Round k: each block takes a tile of up to 64 cell-sorted samples of one cell A (dynamic
+// scheduling), stages A's k-major weights in shared memory with one TMA bulk copy, and each of its
+// 4 warps evaluates 16 samples as a tile GEMM.  A ray whose next sample lies in A, or in the one
+// neighbour cell B the block has taken on, keeps stepping inside the tile; B is taken on by the
+// first ray that needs a second cell (its weights arrive by a second bulk copy), which keeps rays
+// that oscillate across a cell seam (the per-cell fields disagree there) inside one tile.  Other
+// rays are emitted to round k+1 with their next cell; hits join the shading list; misses are
+// written.  A round with few rays (tail) is instead finished one thread per ray.
 constexpr int EVAL_WARPS = 4;
 
 template <class C>
-__host__ __device__ constexpr int eval_hrows() {
-    return C::INP > C::W ? C::INP : C::W;
+__host__ __device__ constexpr int eval_slots() {
+    return C::W <= 32 ? 2 : 1;  // weight slots per block (W = 64 keeps one to stay in shared memory)
+}
+template <class C>
+__host__ __device__ constexpr int eval_warp_floats() {
+    return (C::INP + 2 * C::W) * TILE;  // encoded inputs + two activation buffers
 }
 template <class C>
 __host__ __device__ constexpr int eval_smem_bytes() {
-    return (C::TSIZE + EVAL_WARPS * 2 * eval_hrows<C>() * TILE) * (int)sizeof(float);
+    return (eval_slots<C>() * C::TSIZE + EVAL_WARPS * eval_warp_floats<C>()) * (int)sizeof(float);
+}
+
+// Tail: one thread runs one ray to its end with the per-thread evaluator (weights via L1).
+template <class C>
+__device__ __noinline__ void finish_ray_f32(const GridView &g, const WaveArgs &a, int r, int cell, bool &hit_out) {
+    int cam;
+    const Ray ray = ray_of(a, r, cam);
+    float t0, tf;
+    clip_box(g, ray, t0, tf);
+    float t = a.t_ray[r];
+    int steps = a.steps_ray[r];
+    hit_out = false;
+    for (;;) {
+        const float d = sdf_trace_f32<C>(g.w + (int64_t)cell * g.cell_stride, fmaf(t, ray.wx, ray.ox),
+                                         fmaf(t, ray.wy, ray.oy), fmaf(t, ray.wz, ray.oz), g.beta, g.inv_beta);
+        ++steps;
+        if (fabsf(d) < a.eps) {
+            a.cell_ray[r] = cell;
+            a.t_ray[r] = t;
+            a.steps_ray[r] = steps;
+            hit_out = true;
+            return;
+        }
+        t += d;
+        if (t > tf || t < t0 || steps >= a.max_steps) break;
+        cell = advance_ray(g, ray, t, tf);
+        if (cell < 0) break;
+    }
+    write_miss(a, r, steps);
+}
+
+// A tail round: one thread per ray, to the end.
+template <class C>
+__global__ void __launch_bounds__(128) wave_tail_kernel(GridView g, WaveArgs a, int cur) {
+    if (!a.ctrl->tail) return;
+    const int n = a.ctrl->n_live[cur];
+    const int bound = (n + 31) & ~31;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < bound; q += gridDim.x * blockDim.x) {
+        bool hit = false;
+        int r = 0;
+        if (q < n) {
+            r = a.q[cur][q];
+            finish_ray_f32<C>(g, a, r, a.qcell[cur][q], hit);
+        }
+        const int hp = warp_append(&a.ctrl->n_hits, hit);
+        if (hit) a.hits[hp] = r;
+    }
 }
 
 template <class C>
 __global__ void __launch_bounds__(EVAL_WARPS * 32) wave_eval_kernel(GridView g, WaveArgs a, int cur) {
+    constexpr int SLOTS = eval_slots<C>();
     extern __shared__ __align__(128) float dyn[];
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ int s_tile, s_cell, s_start, s_len;
-    float *wsm = dyn;
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_tile, s_start, s_len, s_slot_cell[2];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *hA = dyn + C::TSIZE + warp * 2 * eval_hrows<C>() * TILE;
-    float *hB = hA + eval_hrows<C>() * TILE;
     const int nxt = cur ^ 1;
+
+    if (a.ctrl->tail) return;  // finished one thread per ray by wave_tail_kernel
+
+    float *wslot0 = dyn, *wslot1 = dyn + (SLOTS > 1 ? C::TSIZE : 0);
+    float *hin = dyn + SLOTS * C::TSIZE + warp * eval_warp_floats<C>();
+    float *P = hin + C::INP * TILE, *Q = P + C::W * TILE;
     const int n_tiles = a.ctrl->n_tiles;
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        s_slot_cell[0] = -1;
+        s_slot_cell[1] = -1;
+    }
     __syncthreads();
-    int cached = -1;
-    uint32_t phase = 0;
+    uint32_t ph0 = 0, ph1 = 0;
     for (;;) {
         if (threadIdx.x == 0) {
             const int tile = atomicAdd(&a.ctrl->next_tile, 1);
             s_tile = tile;
+            s_slot_cell[1] = -1;
             if (tile < n_tiles) {
                 int lo = 0, hi = a.NC;  // the cell c with tile_off[c] <= tile < tile_off[c+1]
                 while (hi - lo > 1) {
@@ -168,28 +233,27 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) wave_eval_kernel(GridView g, 
                     if (__ldg(a.tile_off + mid) <= tile) lo = mid; else hi = mid;
                 }
                 const int start = __ldg(a.off + lo) + (tile - __ldg(a.tile_off + lo)) * a.btile;
-                s_cell = lo;
                 s_start = start;
                 s_len = min(a.btile, __ldg(a.off + lo + 1) - start);
-                if (lo != cached)
-                    bulk_load(wsm, a.wt + (int64_t)lo * a.wt_stride, C::TSIZE * sizeof(float), &bar);
+                if (lo != s_slot_cell[0]) {
+                    s_slot_cell[0] = -2 - lo;  // marks "loading": becomes lo below
+                    bulk_load(wslot0, a.wt + (int64_t)lo * a.wt_stride, C::TSIZE * sizeof(float), &bar[0]);
+                }
             }
         }
         __syncthreads();
         if (s_tile >= n_tiles) break;
-        const int c = s_cell;
-        const bool fresh = c != cached;
-        cached = c;
+        const bool fresh = s_slot_cell[0] < -1;
+        const int cA = fresh ? -2 - s_slot_cell[0] : s_slot_cell[0];
         // this warp's samples
-        const int wstart = s_start + warp * TILE;
         const int wlen = max(0, min(TILE, s_len - warp * TILE));
         const int s = lane & 15;
         bool active = lane < TILE && s < wlen;
-        int r = 0, steps = 0;
+        int r = 0, steps = 0, slot = 0;
         float t = 0.f, t0 = 0.f, tf = 0.f;
         Ray ray{};
         if (active) {
-            r = a.sorted[wstart + s];
+            r = a.sorted[s_start + warp * TILE + s];
             t = a.t_ray[r];
             steps = a.steps_ray[r];
             int cam;
@@ -197,14 +261,15 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) wave_eval_kernel(GridView g, 
             clip_box(g, ray, t0, tf);
         }
         if (fresh) {
-            const bool ok = mbar_wait(&bar, phase, 1u << 26);
-            phase ^= 1u;
-            if (__syncthreads_or(!ok)) {  // the copy never landed: report and leave
+            const bool ok = mbar_wait(&bar[0], ph0, 1u << 26);
+            ph0 ^= 1u;
+            if (__syncthreads_or(!ok)) {  // the weights never landed: report and leave
                 if (threadIdx.x == 0) atomicCAS(a.status, 0, (int)6 /* KNS_ERR_TIMEOUT */);
-                mbar_wait(&bar, phase ^ 1u, 1u << 20);
                 return;
             }
+            if (threadIdx.x == 0) s_slot_cell[0] = cA;
         }
+        bool waited1 = false;
         for (int it = 0; it < a.inner_steps; ++it) {
             if (!__any_sync(FULL, active)) break;
             if (lane < TILE) {
@@ -216,33 +281,68 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) wave_eval_kernel(GridView g, 
                     for (int k = 0; k < C::INP; ++k) in[k] = 0.f;
                 }
 #pragma unroll
-                for (int k = 0; k < C::INP; ++k) hA[k * TILE + s] = in[k];
+                for (int k = 0; k < C::INP; ++k) hin[k * TILE + s] = in[k];
             }
             __syncwarp();
-            const float d = tile_sdf_f32<C>(wsm, hA, hB, lane, g.beta, g.inv_beta);
-            bool hit = false, emit = false, stay = false;
+            float d = 0.f;
+            if (__any_sync(FULL, active && slot == 0)) {
+                const float dA = tile_sdf_f32<C>(wslot0, hin, P, Q, lane, g.beta, g.inv_beta);
+                if (slot == 0) d = dA;
+            }
+            if (SLOTS > 1 && __any_sync(FULL, active && slot == 1)) {
+                if (!waited1) {
+                    if (!mbar_wait(&bar[1], ph1, 1u << 26)) {
+                        atomicCAS(a.status, 0, (int)6 /* KNS_ERR_TIMEOUT */);
+                        active = false;  // leave these rays unfinished; the status reports it
+                    }
+                    waited1 = true;
+                }
+                const float dB = tile_sdf_f32<C>(wslot1, hin, P, Q, lane, g.beta, g.inv_beta);
+                if (slot == 1) d = dB;
+            }
+            bool hit = false, emit = false;
             int ncell = -1;
             if (active) {
                 ++steps;
+                const int cur_cell = slot ? s_slot_cell[1] : cA;
                 if (fabsf(d) < a.eps) {
                     hit = true;
-                    a.cell_ray[r] = c;
+                    a.cell_ray[r] = cur_cell;
                     a.t_ray[r] = t;
                     a.steps_ray[r] = steps;
+                    active = false;
                 } else {
                     t += d;
                     if (t > tf || t < t0 || steps >= a.max_steps) {
                         write_miss(a, r, steps);
+                        active = false;
                     } else {
                         ncell = advance_ray(g, ray, t, tf);
                         if (ncell < 0) {
                             write_miss(a, r, steps);
-                        } else if (ncell == c && it + 1 < a.inner_steps) {
-                            stay = true;
+                            active = false;
+                        } else if (it + 1 >= a.inner_steps) {
+                            emit = true;
+                        } else if (ncell == cA) {
+                            slot = 0;
+                        } else if (SLOTS > 1) {
+                            int b = s_slot_cell[1];
+                            if (b == -1) {
+                                b = atomicCAS(&s_slot_cell[1], -1, ncell);
+                                if (b == -1) {  // this ray takes the neighbour cell on for the block
+                                    bulk_load(wslot1, a.wt + (int64_t)ncell * a.wt_stride, C::TSIZE * sizeof(float),
+                                              &bar[1]);
+                                    b = ncell;
+                                }
+                            }
+                            if (b == ncell) slot = 1; else emit = true;
                         } else {
                             emit = true;
+                        }
+                        if (emit) {
                             a.t_ray[r] = t;
                             a.steps_ray[r] = steps;
+                            active = false;
                         }
                     }
                 }
@@ -255,10 +355,14 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) wave_eval_kernel(GridView g, 
                 a.qcell[nxt][qp] = ncell;
             }
             warp_count_cells(a.count[nxt], emit, ncell);
-            active = stay;
-            __syncwarp();
         }
-        __syncthreads();  // the weights buffer and tile slots are reused by the next tile
+        __syncthreads();
+        // a neighbour load issued this tile must land before the slot is reused
+        if (SLOTS > 1 && s_slot_cell[1] != -1) {
+            if (!waited1) mbar_wait(&bar[1], ph1, 1u << 26);
+            ph1 ^= 1u;
+        }
+        __syncthreads();
     }
 }
 
@@ -310,6 +414,8 @@ cudaError_t launch_wave_eval_cfg(const GridView &g, const WaveArgs &a, int cur, 
     cudaError_t e = cudaFuncSetAttribute(wave_eval_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     wave_eval_kernel<C><<<blocks, EVAL_WARPS * 32, smem, s>>>(g, a, cur);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    wave_tail_kernel<C><<<blocks / 4 + 1, 128, 0, s>>>(g, a, cur);
     return cudaGetLastError();
 }
 template <class C>
