@@ -234,7 +234,7 @@ void free_scratch(WaveScratch &w) {
 // Render tiling: samples per block tile (4 warps x 16) and in-tile sphere steps per round.
 constexpr int kRenderBlockTile = 64;
 constexpr int kRenderInnerSteps = 32;
-constexpr int kRenderTailRays = 4096;  // rounds this small finish one thread per ray
+constexpr int kRenderTailRays = 512;  // rounds this small finish one thread per ray
 
 // Grows the context's wavefront scratch to hold `rays` rays, `nc` cells and `cams` cameras.
 kns_status ensure_scratch(kns_ctx *ctx, int64_t rays, int nc, int cams) {

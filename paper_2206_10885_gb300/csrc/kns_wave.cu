@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(128) wave_gen_kernel(GridView g, WaveArgs a) {
 // rays are emitted to round k+1 with their next cell; hits join the shading list; misses are
 // written.  A round with few rays (tail) is instead finished one thread per ray.
 constexpr int EVAL_WARPS = 4;
+constexpr int kMinActive = 6;  // rays of a 16-sample warp tile below which it stops stepping in-tile
 
 template <class C>
 __host__ __device__ constexpr int eval_slots() {
@@ -302,6 +303,9 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) wave_eval_kernel(GridView g, 
             }
             bool hit = false, emit = false;
             int ncell = -1;
+            // a thinned-out warp hands its remaining rays to the next round, where they are
+            // regrouped into full tiles, instead of running 16-sample GEMMs for a few rays
+            const bool sparse = __popc(__ballot_sync(FULL, active)) < kMinActive;
             if (active) {
                 ++steps;
                 const int cur_cell = slot ? s_slot_cell[1] : cA;
@@ -321,7 +325,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) wave_eval_kernel(GridView g, 
                         if (ncell < 0) {
                             write_miss(a, r, steps);
                             active = false;
-                        } else if (it + 1 >= a.inner_steps) {
+                        } else if (it + 1 >= a.inner_steps || sparse) {
                             emit = true;
                         } else if (ncell == cA) {
                             slot = 0;
