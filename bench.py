@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--cams", type=int, default=0, help="use only the first N cameras (small profiling cases)")
+    ap.add_argument("--tune", default="cache", choices=["cache", "force", "off"],
+                    help="schedule autotuning before timing: use the cached best (tuning once if absent), "
+                         "re-tune, or use the library defaults")
     return ap.parse_args()
 
 
@@ -159,6 +162,21 @@ def kernel_source_hash() -> str:
     return h.hexdigest()
 
 
+def count_launches(step) -> int:
+    """Kernels one render launches, counted with the torch profiler's CUDA activity (untimed)."""
+    import torch
+    from torch.profiler import ProfilerActivity, profile
+    torch.cuda.synchronize()
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        step()
+        torch.cuda.synchronize()
+    n = 0
+    for ev in prof.events():
+        if ev.device_type == torch.autograd.DeviceType.CUDA and "kns::" in ev.name:
+            n += 1
+    return n
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -240,12 +258,21 @@ def run_kns(args, rank, world, local_rank):
     frame = kns.alloc_frame(n_rays, dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
+    tuning = None
+    if args.tune != "off":
+        from paper_2206_10885_gb300 import autotune
+        tuning, tuned_ms, tried = autotune.tune(ctx, grid, cams, W, H, ms, eps, precision,
+                                                use_cache=args.tune == "cache")
+        if rank == 0 and tried:
+            print("# autotune: %d settings, best %s at %.3f ms" % (len(tried), tuning, tuned_ms), file=sys.stderr)
+
     def step():
-        kns.render(ctx, grid, cams, W, H, ms, eps, precision=precision, out=frame, stream=stream)
+        kns.render(ctx, grid, cams, W, H, ms, eps, precision=precision, out=frame, stream=stream, tuning=tuning)
 
     for _ in range(max(3, args.warmup)):
         step()
     ctx.sync(stream)
+    launches_per_step = count_launches(step)
     # algorithmic units of one launch: SDF evaluations (trace samples) and hits
     steps_np = frame[0]["steps"].cpu().numpy().astype(np.int64)
     hits = int(frame[0]["hit"].sum().item())
@@ -324,7 +351,7 @@ def run_kns(args, rank, world, local_rank):
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
-                "clocks": clock_info, "gpu_launches": args.steps * math.ceil(cams.shape[0] / 64),
+                "clocks": clock_info, "gpu_launches": args.steps * launches_per_step, "tuning": tuning,
                 "step_ms_min": min(times), "step_ms_median": statistics.median(times)}
         print(json.dumps(line), flush=True)
     grid.free()

@@ -105,11 +105,18 @@ typedef struct kns_frame {
     uint8_t *hit;   /* 1 on a hit */
 } kns_frame;
 
-/* Options of kns_render (NULL = FP32 defaults). */
+/* Options of kns_render (NULL = FP32 defaults).  The tuning fields change only the schedule of
+ * the work, never a result; 0 selects the built-in default. */
 typedef struct kns_render_opts {
     int32_t precision;    /* KNS_FP32 or KNS_BF16 */
     float eps_coarse;     /* KNS_BF16: hit threshold of the BF16 trace (<= 0: max(eps, 4e-3)) */
     int32_t refine_steps; /* KNS_BF16: FP32 sphere steps after the BF16 hit (< 0: 2) */
+    /* tuning (0 = default) */
+    int32_t inner_steps;   /* sphere steps a tile may take per round while its rays stay in its cells (1..1024) */
+    int32_t min_active;    /* a 16-ray warp tile with fewer live rays hands them to the next round (1..16) */
+    int32_t tail_rays;     /* a round with at most this many rays is finished one thread per ray (>= 0; -1: never) */
+    int32_t blocks_per_sm; /* evaluation blocks launched per SM (1..32) */
+    int32_t static_tiles;  /* 1: each block takes a contiguous run of tiles; 2: tiles handed out dynamically */
 } kns_render_opts;
 
 /* ---------------------------------------------------------------- context */

@@ -88,22 +88,33 @@ def alloc_frame(n_pix: int, device="cuda", extras: bool = True):
     return t, f
 
 
-def render_opts(precision: int = KNS_FP32, eps_coarse: float = 0.0, refine_steps: int = -1):
+TUNING_FIELDS = ("inner_steps", "min_active", "tail_rays", "blocks_per_sm", "static_tiles")
+
+
+def render_opts(precision: int = KNS_FP32, eps_coarse: float = 0.0, refine_steps: int = -1, tuning=None):
     o = capi.kns_render_opts()
     o.precision, o.eps_coarse, o.refine_steps = precision, eps_coarse, refine_steps
+    for k, v in (tuning or {}).items():
+        if k not in TUNING_FIELDS:
+            raise KeyError(k)
+        setattr(o, k, int(v))
     return o
 
 
 def render(ctx: Context, grid: Grid, cams: np.ndarray, W: int, H: int, max_steps: int, eps: float,
-           precision: int = KNS_FP32, out=None, stream=None, eps_coarse: float = 0.0, refine_steps: int = -1):
-    """kns_render into fresh (or given) tensors; returns the dict of output tensors."""
+           precision: int = KNS_FP32, out=None, stream=None, eps_coarse: float = 0.0, refine_steps: int = -1,
+           tuning=None):
+    """kns_render into fresh (or given) tensors; returns the dict of output tensors.
+
+    tuning: optional dict of schedule knobs (see kns_render_opts); results do not depend on them.
+    """
     cams = np.ascontiguousarray(cams, dtype=np.float32).reshape(-1, 16)
     n_pix = cams.shape[0] * W * H
     if out is None:
         out = alloc_frame(n_pix, "cuda:%d" % ctx.device)
     t, f = out
     capi.kns_render(ctx.handle, grid.handle, cams.ctypes.data, cams.shape[0], W, H, max_steps, eps,
-                    render_opts(precision, eps_coarse, refine_steps), f, _stream_ptr(stream))
+                    render_opts(precision, eps_coarse, refine_steps, tuning), f, _stream_ptr(stream))
     return t
 
 

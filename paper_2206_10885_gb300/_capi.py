@@ -52,7 +52,9 @@ class kns_frame(C.Structure):
 
 
 class kns_render_opts(C.Structure):
-    _fields_ = [("precision", C.c_int32), ("eps_coarse", C.c_float), ("refine_steps", C.c_int32)]
+    _fields_ = [("precision", C.c_int32), ("eps_coarse", C.c_float), ("refine_steps", C.c_int32),
+                ("inner_steps", C.c_int32), ("min_active", C.c_int32), ("tail_rays", C.c_int32),
+                ("blocks_per_sm", C.c_int32), ("static_tiles", C.c_int32)]
 
 
 _lib = None

@@ -1,0 +1,111 @@
+"""Autotuner of the render schedule (the tuning fields of kns_render_opts).
+
+The knobs change only how work is scheduled on the device (rounds, in-tile steps, tile hand-out,
+launch width, per-thread tail), never a result; the tests check that renders are bit-identical
+across settings.  tune() times each candidate with CUDA events around kns_render, flushing L2
+between repetitions, and returns the fastest setting.  Results are cached per (device, grid shape,
+image shape, precision) in a JSON file next to this module (or the path in KNS_TUNE_CACHE).
+"""
+from __future__ import annotations
+
+import itertools
+import json
+import os
+import time
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+DEFAULT_CACHE = os.path.join(_HERE, "_tune_cache.json")
+
+# candidate values of each knob (0 would mean the library default)
+SPACE = {
+    "inner_steps": (1, 4, 16, 64),
+    "min_active": (1, 8, 12),
+    "static_tiles": (1, 2),
+    "blocks_per_sm": (4, 8),
+    "tail_rays": (-1, 512, 4096),
+}
+
+
+def _key(grid, n_cams, W, H, max_steps, precision, device_name):
+    d = grid.desc
+    return "|".join(str(v) for v in (device_name, d.N, d.sdf_width, d.sdf_hidden, d.pe_pos_L, d.occ_res,
+                                      n_cams, W, H, max_steps, precision))
+
+
+def _cache_path():
+    return os.environ.get("KNS_TUNE_CACHE", DEFAULT_CACHE)
+
+
+def load_cached(key):
+    try:
+        with open(_cache_path()) as f:
+            return json.load(f).get(key)
+    except (OSError, ValueError):
+        return None
+
+
+def _store(key, value):
+    path = _cache_path()
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        data = {}
+    data[key] = value
+    tmp = path + ".tmp%d" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def candidates(space=None):
+    space = space or SPACE
+    keys = sorted(space)
+    for vals in itertools.product(*(space[k] for k in keys)):
+        yield dict(zip(keys, vals))
+
+
+def time_setting(kns, ctx, grid, cams, W, H, max_steps, eps, precision, tuning, out, flush, reps=2):
+    import torch
+    stream = torch.cuda.current_stream()
+    kns.render(ctx, grid, cams, W, H, max_steps, eps, precision=precision, out=out, stream=stream, tuning=tuning)
+    best = float("inf")
+    for k in range(reps):
+        flush.fill_(k & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        kns.render(ctx, grid, cams, W, H, max_steps, eps, precision=precision, out=out, stream=stream,
+                   tuning=tuning)
+        b.record(stream)
+        b.synchronize()
+        best = min(best, a.elapsed_time(b))
+    ctx.sync(stream)
+    return best
+
+
+def tune(ctx, grid, cams, W, H, max_steps, eps, precision=0, space=None, use_cache=True, budget_s=120.0,
+         verbose=False):
+    """Returns (best tuning dict, best ms, list of (tuning, ms)) for this workload shape."""
+    import torch
+
+    import paper_2206_10885_gb300 as kns
+    dev = torch.cuda.get_device_name(ctx.device)
+    key = _key(grid, len(cams), W, H, max_steps, precision, dev)
+    if use_cache:
+        hit = load_cached(key)
+        if hit:
+            return hit["tuning"], hit["ms"], []
+    out = kns.alloc_frame(len(cams) * W * H, "cuda:%d" % ctx.device)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda:%d" % ctx.device)
+    results = []
+    t_start = time.time()
+    for tuning in candidates(space):
+        ms = time_setting(kns, ctx, grid, cams, W, H, max_steps, eps, precision, tuning, out, flush)
+        results.append((tuning, ms))
+        if verbose:
+            print("tune", tuning, "%.3f ms" % ms, flush=True)
+        if time.time() - t_start > budget_s:
+            break
+    best, best_ms = min(results, key=lambda x: x[1])
+    _store(key, {"tuning": best, "ms": best_ms})
+    return best, best_ms, results

@@ -233,8 +233,11 @@ void free_scratch(WaveScratch &w) {
 
 // Render tiling: samples per block tile (4 warps x 16) and in-tile sphere steps per round.
 constexpr int kRenderBlockTile = 64;
-constexpr int kRenderInnerSteps = 32;
+constexpr int kRenderInnerSteps = 4;
+constexpr int kRenderMinActive = 8;
 constexpr int kRenderTailRays = 512;  // rounds this small finish one thread per ray
+constexpr int kRenderBlocksPerSM = 8;
+constexpr int kRenderStaticTiles = 1;
 
 // Grows the context's wavefront scratch to hold `rays` rays, `nc` cells and `cams` cameras.
 kns_status ensure_scratch(kns_ctx *ctx, int64_t rays, int nc, int cams) {
@@ -540,6 +543,16 @@ kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams
     if (precision != KNS_FP32 && precision != KNS_BF16)
         return set_err(ctx, KNS_ERR_INVALID_ARG, "unknown precision %d", precision);
     if (precision == KNS_BF16) return set_err(ctx, KNS_ERR_UNSUPPORTED, "BF16 path not built");
+    auto knob = [](int32_t v, int32_t def) { return v == 0 ? def : v; };
+    const int inner_steps = opts ? knob(opts->inner_steps, kRenderInnerSteps) : kRenderInnerSteps;
+    const int min_active = opts ? knob(opts->min_active, kRenderMinActive) : kRenderMinActive;
+    int tail_rays = opts ? knob(opts->tail_rays, kRenderTailRays) : kRenderTailRays;
+    const int blocks_per_sm = opts ? knob(opts->blocks_per_sm, kRenderBlocksPerSM) : kRenderBlocksPerSM;
+    const int static_tiles = (opts ? knob(opts->static_tiles, kRenderStaticTiles) : kRenderStaticTiles) == 1;
+    if (inner_steps < 1 || inner_steps > 1024 || min_active < 1 || min_active > 16 || tail_rays < -1 ||
+        blocks_per_sm < 1 || blocks_per_sm > 32 || (opts && (opts->static_tiles < 0 || opts->static_tiles > 2)))
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "render tuning field out of range");
+    if (tail_rays < 0) tail_rays = 0;
     if (n_cams == 0 || W == 0 || H == 0) return KNS_OK;
     if ((int64_t)W * H > INT32_MAX) return set_err(ctx, KNS_ERR_INVALID_ARG, "W*H exceeds 2^31-1");
     DeviceScope ds(ctx->device);
@@ -561,8 +574,10 @@ kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams
         a.eps = eps;
         a.NC = NC;
         a.btile = kRenderBlockTile;
-        a.inner_steps = kRenderInnerSteps;
-        a.tail_max = kRenderTailRays;
+        a.inner_steps = inner_steps;
+        a.tail_max = tail_rays;
+        a.min_active = min_active;
+        a.static_tiles = static_tiles;
         a.status = ctx->d_status;
         a.cams = w.d_cams;
         a.wt = grid->d_wt;
@@ -593,7 +608,7 @@ kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams
         if (e == cudaSuccess) e = cudaMemsetAsync(w.ctrl, 0, sizeof(kns::WaveCtrl), s);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.cellbuf, 0, sizeof(int) * 4 * (NC + 1), s);
         if (e == cudaSuccess) e = kns::launch_wave_gen(grid->shape, grid->view, a, s);
-        const int eval_blocks = ctx->sm_count * 8, scatter_blocks = ctx->sm_count * 4;
+        const int eval_blocks = ctx->sm_count * blocks_per_sm, scatter_blocks = ctx->sm_count * 4;
         // Rounds: at most max_steps (each live ray takes >= 1 step per round).  The host reads the
         // live count of round k-2 before launching round k and stops once a round was empty, so it
         // runs at most two rounds ahead of the device.

@@ -31,6 +31,8 @@ struct WaveArgs {
     int btile;            // samples per block tile (cell-sorted samples are cut into such tiles)
     int inner_steps;      // sphere steps a tile may take in one round while its rays stay in its cells
     int tail_max;         // a round with at most this many rays is finished one thread per ray
+    int min_active;       // warp tiles with fewer live rays hand them to the next round
+    int static_tiles;     // 1: contiguous runs of tiles per block (weight reuse); 0: dynamic
     int *status;          // context status word (kns_status of a device-side failure, 0 = fine)
     const float *cams;    // n_cams x 16 floats
     const float *wt;      // k-major trace weights (see kns_device.cuh)

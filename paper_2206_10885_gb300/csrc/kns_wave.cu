@@ -137,7 +137,6 @@ __global__ void __launch_bounds__(128) wave_gen_kernel(GridView g, WaveArgs a) {
 // rays are emitted to round k+1 with their next cell; hits join the shading list; misses are
 // written.  A round with few rays (tail) is instead finished one thread per ray.
 constexpr int EVAL_WARPS = 4;
-constexpr int kMinActive = 6;  // rays of a 16-sample warp tile below which it stops stepping in-tile
 
 template <class C>
 __host__ __device__ constexpr int eval_slots() {
@@ -222,9 +221,15 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) wave_eval_kernel(GridView g, 
     }
     __syncthreads();
     uint32_t ph0 = 0, ph1 = 0;
+    // static schedule: block b owns tiles [b*per, (b+1)*per) so consecutive same-cell tiles reuse
+    // one weight load; dynamic: tiles are handed out one at a time
+    const int per = (n_tiles + gridDim.x - 1) / gridDim.x;
+    int next_static = blockIdx.x * per;
+    const int end_static = min(n_tiles, next_static + per);
     for (;;) {
         if (threadIdx.x == 0) {
-            const int tile = atomicAdd(&a.ctrl->next_tile, 1);
+            const int tile = a.static_tiles ? (next_static < end_static ? next_static : n_tiles)
+                                            : atomicAdd(&a.ctrl->next_tile, 1);
             s_tile = tile;
             s_slot_cell[1] = -1;
             if (tile < n_tiles) {
@@ -243,6 +248,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) wave_eval_kernel(GridView g, 
             }
         }
         __syncthreads();
+        ++next_static;
         if (s_tile >= n_tiles) break;
         const bool fresh = s_slot_cell[0] < -1;
         const int cA = fresh ? -2 - s_slot_cell[0] : s_slot_cell[0];
@@ -305,7 +311,7 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) wave_eval_kernel(GridView g, 
             int ncell = -1;
             // a thinned-out warp hands its remaining rays to the next round, where they are
             // regrouped into full tiles, instead of running 16-sample GEMMs for a few rays
-            const bool sparse = __popc(__ballot_sync(FULL, active)) < kMinActive;
+            const bool sparse = __popc(__ballot_sync(FULL, active)) < a.min_active;
             if (active) {
                 ++steps;
                 const int cur_cell = slot ? s_slot_cell[1] : cA;

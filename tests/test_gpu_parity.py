@@ -302,3 +302,23 @@ def test_grid_file_roundtrip(kns, ctx, tmp_path):
     with pytest.raises(kns.KnsError) as e:
         kns.Grid.from_file(ctx, path)
     assert e.value.status == kns.capi.KNS_ERR_FORMAT
+
+
+def test_schedule_knobs_do_not_change_results(kns, ctx):
+    """The tuning fields of kns_render_opts reorder work only: every output is bit-identical."""
+    desc = S.config_desc("c2")
+    w = S.sal_sphere_grid(desc)
+    cams = S.orbit_cameras(2, 160, 120, seed=8)
+    grid = kns.Grid.load(ctx, desc, w)
+    try:
+        ref = gpu_render(kns, ctx, grid, cams, 160, 120, 128, 1e-4)
+        for tuning in [dict(inner_steps=1, min_active=1, static_tiles=2, tail_rays=-1),
+                       dict(inner_steps=64, min_active=16, static_tiles=1, blocks_per_sm=2, tail_rays=4096),
+                       dict(inner_steps=7, min_active=3, static_tiles=2, blocks_per_sm=16, tail_rays=100000)]:
+            got = gpu_render(kns, ctx, grid, cams, 160, 120, 128, 1e-4, tuning=tuning)
+            for k in ref:
+                assert np.array_equal(ref[k], got[k]), (k, tuning)
+        with pytest.raises(kns.KnsError):
+            kns.render(ctx, grid, cams, 160, 120, 128, 1e-4, tuning=dict(min_active=17))
+    finally:
+        grid.free()
