@@ -233,11 +233,12 @@ void free_scratch(WaveScratch &w) {
 
 // Render tiling: samples per block tile (4 warps x 16) and in-tile sphere steps per round.
 constexpr int kRenderBlockTile = 64;
+// Defaults picked by the autotuner on the 16^3 / width-32 grid at 8 x 800x800.
 constexpr int kRenderInnerSteps = 4;
 constexpr int kRenderMinActive = 8;
-constexpr int kRenderTailRays = 512;  // rounds this small finish one thread per ray
-constexpr int kRenderBlocksPerSM = 8;
-constexpr int kRenderStaticTiles = 1;
+constexpr int kRenderTailRays = 4096;  // rounds this small finish one thread per ray
+constexpr int kRenderBlocksPerSM = 4;
+constexpr int kRenderStaticTiles = 2;
 
 // Grows the context's wavefront scratch to hold `rays` rays, `nc` cells and `cams` cameras.
 kns_status ensure_scratch(kns_ctx *ctx, int64_t rays, int nc, int cams) {

@@ -80,16 +80,14 @@ __device__ __forceinline__ float tile_sdf_f32(const float *__restrict__ wt, cons
         src = dst;
         dst = tmp;
     }
-    const int s = lane & 15, half = lane >> 4;
-    float acc = 0.f;
-#pragma unroll
-    for (int k = 0; k < C::W / 2; ++k) {
-        const int kk = half * (C::W / 2) + k;
-        acc = fmaf(wt[C::tdL + kk], src[kk * TILE + s], acc);
-    }
-    acc += __shfl_xor_sync(FULL, acc, 16);
+    // the d row: bias first, then one sequential FMA chain over k, the same order as the
+    // per-thread evaluator, so a sample's d does not depend on which path evaluated it
+    const int s = lane & 15;
+    float acc = wt[C::tbL];
+#pragma unroll 8
+    for (int k = 0; k < C::W; ++k) acc = fmaf(wt[C::tdL + k], src[k * TILE + s], acc);
     __syncwarp();
-    return acc + wt[C::tbL];
+    return acc;
 }
 
 // Wave 0: one thread per pixel (16x8 pixels per block, 8x4 per warp); clip, advance, emit.
