@@ -231,13 +231,13 @@ void free_scratch(WaveScratch &w) {
     w = WaveScratch{};
 }
 
-// Render tiling: samples per block tile (4 warps x 16) and in-tile sphere steps per round.
-constexpr int kRenderBlockTile = 64;
+// Render tiling: samples per tile (one warp evaluates one tile).
+constexpr int kRenderBlockTile = 16;
 // Defaults picked by the autotuner on the 16^3 / width-32 grid at 8 x 800x800.
 constexpr int kRenderInnerSteps = 4;
 constexpr int kRenderMinActive = 8;
 constexpr int kRenderTailRays = 4096;  // rounds this small finish one thread per ray
-constexpr int kRenderBlocksPerSM = 4;
+constexpr int kRenderBlocksPerSM = 16;
 constexpr int kRenderStaticTiles = 2;
 
 // Grows the context's wavefront scratch to hold `rays` rays, `nc` cells and `cams` cameras.
@@ -551,7 +551,7 @@ kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams
     const int blocks_per_sm = opts ? knob(opts->blocks_per_sm, kRenderBlocksPerSM) : kRenderBlocksPerSM;
     const int static_tiles = (opts ? knob(opts->static_tiles, kRenderStaticTiles) : kRenderStaticTiles) == 1;
     if (inner_steps < 1 || inner_steps > 1024 || min_active < 1 || min_active > 16 || tail_rays < -1 ||
-        blocks_per_sm < 1 || blocks_per_sm > 32 || (opts && (opts->static_tiles < 0 || opts->static_tiles > 2)))
+        blocks_per_sm < 1 || blocks_per_sm > 64 || (opts && (opts->static_tiles < 0 || opts->static_tiles > 2)))
         return set_err(ctx, KNS_ERR_INVALID_ARG, "render tuning field out of range");
     if (tail_rays < 0) tail_rays = 0;
     if (n_cams == 0 || W == 0 || H == 0) return KNS_OK;

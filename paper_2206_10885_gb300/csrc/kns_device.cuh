@@ -362,31 +362,44 @@ __device__ __forceinline__ bool clip_box(const GridView &g, const Ray &r, float 
     return true;
 }
 
-// Integer 3D-DDA (Amanatides & Woo) from voxel v to the entry of the next occupied voxel.
-// Returns true with te and v updated; false when the ray leaves the grid or passes tf.
-__device__ __forceinline__ bool dda_next(const GridView &g, const Ray &r, int (&v)[3], float tf, float &te) {
-    const float o[3] = {r.ox, r.oy, r.oz}, w[3] = {r.wx, r.wy, r.wz};
+// Integer 3D-DDA (Amanatides & Woo) from voxel (vx, vy, vz) to the entry of the next occupied voxel.
+// Returns true with te and the voxel updated; false when the ray leaves the grid or passes tf.
+// The crossing parameter of each axis is (face - o) / w with the face coordinate exact; after a
+// step only the crossed axis' value changes, so only it is recomputed.
+__device__ __forceinline__ float dda_face_t(float bmin, int v, bool up, float vox, float o, float w) {
+    return w == 0.f ? INFINITY : (bmin + (float)(v + (up ? 1 : 0)) * vox - o) / w;
+}
+__device__ __forceinline__ bool dda_next(const GridView &g, const Ray &r, int &vx, int &vy, int &vz, float tf,
+                                         float &te) {
     const int res = g.occ_res;
+    const bool ux = r.wx > 0.f, uy = r.wy > 0.f, uz = r.wz > 0.f;
+    float tx = dda_face_t(g.bmin[0], vx, ux, g.ovox[0], r.ox, r.wx);
+    float ty = dda_face_t(g.bmin[1], vy, uy, g.ovox[1], r.oy, r.wy);
+    float tz = dda_face_t(g.bmin[2], vz, uz, g.ovox[2], r.oz, r.wz);
     // at most 3*res voxel crossings before the ray leaves the grid
     for (int guard = 0; guard < 3 * res + 3; ++guard) {
-        float tm[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            if (w[a] == 0.f) {
-                tm[a] = INFINITY;
-            } else {
-                const float plane = g.bmin[a] + (float)(v[a] + (w[a] > 0.f ? 1 : 0)) * g.ovox[a];
-                tm[a] = (plane - o[a]) / w[a];
-            }
+        float tm;
+        int va;
+        if (tx <= ty && tx <= tz) {  // ties go to the lowest axis
+            tm = tx;
+            vx += ux ? 1 : -1;
+            va = vx;
+            tx = dda_face_t(g.bmin[0], vx, ux, g.ovox[0], r.ox, r.wx);
+        } else if (ty <= tz) {
+            tm = ty;
+            vy += uy ? 1 : -1;
+            va = vy;
+            ty = dda_face_t(g.bmin[1], vy, uy, g.ovox[1], r.oy, r.wy);
+        } else {
+            tm = tz;
+            vz += uz ? 1 : -1;
+            va = vz;
+            tz = dda_face_t(g.bmin[2], vz, uz, g.ovox[2], r.oz, r.wz);
         }
-        int ax = 0;
-        if (tm[1] < tm[ax]) ax = 1;
-        if (tm[2] < tm[ax]) ax = 2;
-        v[ax] += w[ax] > 0.f ? 1 : -1;
-        if (v[ax] < 0 || v[ax] >= res) return false;
-        if (tm[ax] > tf) return false;
-        if (occ_test(g.occ, res, v[0], v[1], v[2])) {
-            te = tm[ax];
+        if (va < 0 || va >= res) return false;
+        if (tm > tf) return false;
+        if (occ_test(g.occ, res, vx, vy, vz)) {
+            te = tm;
             return true;
         }
     }

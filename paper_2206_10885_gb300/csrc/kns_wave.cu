@@ -10,12 +10,22 @@
 
 namespace kns {
 
-// One layer of the tile: hout[o][s] = softplus(sum_k Wt[k][o] hin[k][s] + b[o]).
+// Activations of a 16-sample tile are sample-major: h[s][k] with a row stride S(K) floats, S(K)/4
+// odd, so that the float4 accesses below are free of bank conflicts.
+__host__ __device__ constexpr int act_stride(int K) {
+    return round4(K) + (((round4(K) / 4) % 2 == 0) ? 4 : 0);
+}
+
+// One layer of the tile: hout[s][o] = softplus(b[o] + sum_k Wt[k][o] hin[s][k]), k ascending.
+// Lane (sg, ng) = (lane / 8, lane % 8) owns samples sg, sg+4, sg+8, sg+12 and outputs
+// NPL*ng .. NPL*ng + NPL - 1: per 4 inputs it loads 4 float4 of activations and NPL float4 of
+// weights and issues 16*NPL FMAs.
 template <int K, int W>
 __device__ __forceinline__ void tile_layer_f32(const float *__restrict__ Wt, const float *__restrict__ b,
                                                const float *hin, float *hout, int lane, float beta,
                                                float inv_beta) {
-    constexpr int NPL = W / 8;  // output units per lane
+    constexpr int NPL = W / 8;
+    constexpr int SIN = act_stride(K), SOUT = act_stride(W);
     const int sg = lane >> 3, ng = lane & 7;
     float acc[4][NPL];
 #pragma unroll
@@ -29,42 +39,42 @@ __device__ __forceinline__ void tile_layer_f32(const float *__restrict__ Wt, con
             acc[i][j + 3] = bb.w;
         }
     }
-#pragma unroll 4
-    for (int k = 0; k < K; ++k) {
-        const float4 a = *reinterpret_cast<const float4 *>(hin + k * TILE + 4 * sg);
+#pragma unroll 2
+    for (int k0 = 0; k0 < K; k0 += 4) {
+        float4 av[4];
 #pragma unroll
-        for (int j = 0; j < NPL; j += 4) {
-            const float4 w = *reinterpret_cast<const float4 *>(Wt + k * W + ng * NPL + j);
-            acc[0][j] = fmaf(a.x, w.x, acc[0][j]);
-            acc[0][j + 1] = fmaf(a.x, w.y, acc[0][j + 1]);
-            acc[0][j + 2] = fmaf(a.x, w.z, acc[0][j + 2]);
-            acc[0][j + 3] = fmaf(a.x, w.w, acc[0][j + 3]);
-            acc[1][j] = fmaf(a.y, w.x, acc[1][j]);
-            acc[1][j + 1] = fmaf(a.y, w.y, acc[1][j + 1]);
-            acc[1][j + 2] = fmaf(a.y, w.z, acc[1][j + 2]);
-            acc[1][j + 3] = fmaf(a.y, w.w, acc[1][j + 3]);
-            acc[2][j] = fmaf(a.z, w.x, acc[2][j]);
-            acc[2][j + 1] = fmaf(a.z, w.y, acc[2][j + 1]);
-            acc[2][j + 2] = fmaf(a.z, w.z, acc[2][j + 2]);
-            acc[2][j + 3] = fmaf(a.z, w.w, acc[2][j + 3]);
-            acc[3][j] = fmaf(a.w, w.x, acc[3][j]);
-            acc[3][j + 1] = fmaf(a.w, w.y, acc[3][j + 1]);
-            acc[3][j + 2] = fmaf(a.w, w.z, acc[3][j + 2]);
-            acc[3][j + 3] = fmaf(a.w, w.w, acc[3][j + 3]);
+        for (int i = 0; i < 4; ++i) av[i] = *reinterpret_cast<const float4 *>(hin + (sg + 4 * i) * SIN + k0);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+            for (int j = 0; j < NPL; j += 4) {
+                const float4 w = *reinterpret_cast<const float4 *>(Wt + (k0 + kk) * W + ng * NPL + j);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float a = kk == 0 ? av[i].x : kk == 1 ? av[i].y : kk == 2 ? av[i].z : av[i].w;
+                    acc[i][j] = fmaf(a, w.x, acc[i][j]);
+                    acc[i][j + 1] = fmaf(a, w.y, acc[i][j + 1]);
+                    acc[i][j + 2] = fmaf(a, w.z, acc[i][j + 2]);
+                    acc[i][j + 3] = fmaf(a, w.w, acc[i][j + 3]);
+                }
+            }
         }
     }
 #pragma unroll
-    for (int j = 0; j < NPL; ++j) {
-        float4 v;
-        v.x = softplus_f32(acc[0][j], beta, inv_beta);
-        v.y = softplus_f32(acc[1][j], beta, inv_beta);
-        v.z = softplus_f32(acc[2][j], beta, inv_beta);
-        v.w = softplus_f32(acc[3][j], beta, inv_beta);
-        *reinterpret_cast<float4 *>(hout + (ng * NPL + j) * TILE + 4 * sg) = v;
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int j = 0; j < NPL; j += 4) {
+            float4 v;
+            v.x = softplus_f32(acc[i][j], beta, inv_beta);
+            v.y = softplus_f32(acc[i][j + 1], beta, inv_beta);
+            v.z = softplus_f32(acc[i][j + 2], beta, inv_beta);
+            v.w = softplus_f32(acc[i][j + 3], beta, inv_beta);
+            *reinterpret_cast<float4 *>(hout + (sg + 4 * i) * SOUT + ng * NPL + j) = v;
+        }
     }
 }
 
-// SDF trace form for a tile whose encoded inputs are in hin[k][s] (left intact); P and Q are the
+// SDF trace form for a tile whose encoded inputs are in hin[s][k] (left intact); P and Q are the
 // ping-pong activation buffers.  Returns d of sample lane % 16.
 template <class C>
 __device__ __forceinline__ float tile_sdf_f32(const float *__restrict__ wt, const float *hin, float *P, float *Q,
@@ -82,10 +92,18 @@ __device__ __forceinline__ float tile_sdf_f32(const float *__restrict__ wt, cons
     }
     // the d row: bias first, then one sequential FMA chain over k, the same order as the
     // per-thread evaluator, so a sample's d does not depend on which path evaluated it
+    constexpr int S = act_stride(C::W);
     const int s = lane & 15;
     float acc = wt[C::tbL];
-#pragma unroll 8
-    for (int k = 0; k < C::W; ++k) acc = fmaf(wt[C::tdL + k], src[k * TILE + s], acc);
+#pragma unroll
+    for (int k = 0; k < C::W; k += 4) {
+        const float4 h = *reinterpret_cast<const float4 *>(src + s * S + k);
+        const float4 w = *reinterpret_cast<const float4 *>(wt + C::tdL + k);
+        acc = fmaf(w.x, h.x, acc);
+        acc = fmaf(w.y, h.y, acc);
+        acc = fmaf(w.z, h.z, acc);
+        acc = fmaf(w.w, h.w, acc);
+    }
     __syncwarp();
     return acc;
 }
@@ -126,27 +144,16 @@ __global__ void __launch_bounds__(128) wave_gen_kernel(GridView g, WaveArgs a) {
     warp_count_cells(a.count[0], alive, cell);
 }
 
-// Round k: each block takes a tile of up to 64 cell-sorted samples of one cell A (dynamic
-// scheduling), stages A's k-major weights in shared memory with one TMA bulk copy, and each of its
-// 4 warps evaluates 16 samples as a tile GEMM.  A ray whose next sample lies in A, or in the one
-// neighbour cell B the block has taken on, keeps stepping inside the tile; B is taken on by the
-// first ray that needs a second cell (its weights arrive by a second bulk copy), which keeps rays
-// that oscillate across a cell seam (the per-cell fields disagree there) inside one tile.  Other
-// rays are emitted to round k+1 with their next cell; hits join the shading list; misses are
-// written.  A round with few rays (tail) is instead finished one thread per ray.
-constexpr int EVAL_WARPS = 4;
-
-template <class C>
-__host__ __device__ constexpr int eval_slots() {
-    return C::W <= 32 ? 2 : 1;  // weight slots per block (W = 64 keeps one to stay in shared memory)
-}
-template <class C>
-__host__ __device__ constexpr int eval_warp_floats() {
-    return (C::INP + 2 * C::W) * TILE;  // encoded inputs + two activation buffers
-}
+// Round k: each warp (a block of its own) takes tiles of up to 16 cell-sorted samples of one cell,
+// stages the cell's k-major weights in its shared memory with one TMA bulk copy (skipped when the
+// next tile has the same cell), and evaluates the 16 samples as a tile GEMM.  A ray whose next
+// sample lies in the same cell keeps stepping inside the tile (up to inner_steps evaluations this
+// round, while at least min_active rays remain); the others are emitted to round k+1 with their
+// next cell, converge (hit list) or terminate (miss written).  A round with few rays (tail) is
+// finished one thread per ray by wave_tail_kernel.
 template <class C>
 __host__ __device__ constexpr int eval_smem_bytes() {
-    return (eval_slots<C>() * C::TSIZE + EVAL_WARPS * eval_warp_floats<C>()) * (int)sizeof(float);
+    return (C::TSIZE + TILE * (act_stride(C::INP) + 2 * act_stride(C::W))) * (int)sizeof(float);
 }
 
 // Tail: one thread runs one ray to its end with the per-thread evaluator (weights via L1).
@@ -197,68 +204,57 @@ __global__ void __launch_bounds__(128) wave_tail_kernel(GridView g, WaveArgs a, 
 }
 
 template <class C>
-__global__ void __launch_bounds__(EVAL_WARPS * 32) wave_eval_kernel(GridView g, WaveArgs a, int cur) {
-    constexpr int SLOTS = eval_slots<C>();
+__global__ void __launch_bounds__(32) wave_eval_kernel(GridView g, WaveArgs a, int cur) {
     extern __shared__ __align__(128) float dyn[];
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ int s_tile, s_start, s_len, s_slot_cell[2];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nxt = cur ^ 1;
-
+    __shared__ __align__(8) uint64_t bar;
     if (a.ctrl->tail) return;  // finished one thread per ray by wave_tail_kernel
-
-    float *wslot0 = dyn, *wslot1 = dyn + (SLOTS > 1 ? C::TSIZE : 0);
-    float *hin = dyn + SLOTS * C::TSIZE + warp * eval_warp_floats<C>();
-    float *P = hin + C::INP * TILE, *Q = P + C::W * TILE;
+    const int lane = threadIdx.x;
+    const int nxt = cur ^ 1;
+    float *wsm = dyn;
+    float *hin = dyn + C::TSIZE;
+    float *P = hin + TILE * act_stride(C::INP), *Q = P + TILE * act_stride(C::W);
+    constexpr int SIN = act_stride(C::INP);
     const int n_tiles = a.ctrl->n_tiles;
-    if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        s_slot_cell[0] = -1;
-        s_slot_cell[1] = -1;
-    }
-    __syncthreads();
-    uint32_t ph0 = 0, ph1 = 0;
+    if (lane == 0) mbar_init(&bar, 1);
+    __syncwarp();
     // static schedule: block b owns tiles [b*per, (b+1)*per) so consecutive same-cell tiles reuse
     // one weight load; dynamic: tiles are handed out one at a time
     const int per = (n_tiles + gridDim.x - 1) / gridDim.x;
     int next_static = blockIdx.x * per;
     const int end_static = min(n_tiles, next_static + per);
+    int cached = -1;
+    uint32_t phase = 0;
     for (;;) {
-        if (threadIdx.x == 0) {
-            const int tile = a.static_tiles ? (next_static < end_static ? next_static : n_tiles)
-                                            : atomicAdd(&a.ctrl->next_tile, 1);
-            s_tile = tile;
-            s_slot_cell[1] = -1;
-            if (tile < n_tiles) {
-                int lo = 0, hi = a.NC;  // the cell c with tile_off[c] <= tile < tile_off[c+1]
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (__ldg(a.tile_off + mid) <= tile) lo = mid; else hi = mid;
-                }
-                const int start = __ldg(a.off + lo) + (tile - __ldg(a.tile_off + lo)) * a.btile;
-                s_start = start;
-                s_len = min(a.btile, __ldg(a.off + lo + 1) - start);
-                if (lo != s_slot_cell[0]) {
-                    s_slot_cell[0] = -2 - lo;  // marks "loading": becomes lo below
-                    bulk_load(wslot0, a.wt + (int64_t)lo * a.wt_stride, C::TSIZE * sizeof(float), &bar[0]);
-                }
-            }
-        }
-        __syncthreads();
+        int tile = 0;
+        if (lane == 0) tile = a.static_tiles ? (next_static < end_static ? next_static : n_tiles)
+                                             : atomicAdd(&a.ctrl->next_tile, 1);
+        tile = __shfl_sync(FULL, tile, 0);
         ++next_static;
-        if (s_tile >= n_tiles) break;
-        const bool fresh = s_slot_cell[0] < -1;
-        const int cA = fresh ? -2 - s_slot_cell[0] : s_slot_cell[0];
-        // this warp's samples
-        const int wlen = max(0, min(TILE, s_len - warp * TILE));
+        if (tile >= n_tiles) break;
+        int c = 0, start = 0, len = 0;
+        if (lane == 0) {
+            int lo = 0, hi = a.NC;  // the cell c with tile_off[c] <= tile < tile_off[c+1]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(a.tile_off + mid) <= tile) lo = mid; else hi = mid;
+            }
+            c = lo;
+            start = __ldg(a.off + lo) + (tile - __ldg(a.tile_off + lo)) * TILE;
+            len = min(TILE, __ldg(a.off + lo + 1) - start);
+            if (c != cached) bulk_load(wsm, a.wt + (int64_t)c * a.wt_stride, C::TSIZE * sizeof(float), &bar);
+        }
+        c = __shfl_sync(FULL, c, 0);
+        start = __shfl_sync(FULL, start, 0);
+        len = __shfl_sync(FULL, len, 0);
+        const bool fresh = c != cached;
+        cached = c;
         const int s = lane & 15;
-        bool active = lane < TILE && s < wlen;
-        int r = 0, steps = 0, slot = 0;
+        bool active = lane < TILE && s < len;
+        int r = 0, steps = 0;
         float t = 0.f, t0 = 0.f, tf = 0.f;
         Ray ray{};
         if (active) {
-            r = a.sorted[s_start + warp * TILE + s];
+            r = a.sorted[start + s];
             t = a.t_ray[r];
             steps = a.steps_ray[r];
             int cam;
@@ -266,15 +262,13 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) wave_eval_kernel(GridView g, 
             clip_box(g, ray, t0, tf);
         }
         if (fresh) {
-            const bool ok = mbar_wait(&bar[0], ph0, 1u << 26);
-            ph0 ^= 1u;
-            if (__syncthreads_or(!ok)) {  // the weights never landed: report and leave
-                if (threadIdx.x == 0) atomicCAS(a.status, 0, (int)6 /* KNS_ERR_TIMEOUT */);
+            const bool ok = mbar_wait(&bar, phase, 1u << 26);
+            phase ^= 1u;
+            if (!__all_sync(FULL, ok)) {  // the weights never landed: report and leave
+                if (lane == 0) atomicCAS(a.status, 0, (int)6 /* KNS_ERR_TIMEOUT */);
                 return;
             }
-            if (threadIdx.x == 0) s_slot_cell[0] = cA;
         }
-        bool waited1 = false;
         for (int it = 0; it < a.inner_steps; ++it) {
             if (!__any_sync(FULL, active)) break;
             if (lane < TILE) {
@@ -286,36 +280,21 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) wave_eval_kernel(GridView g, 
                     for (int k = 0; k < C::INP; ++k) in[k] = 0.f;
                 }
 #pragma unroll
-                for (int k = 0; k < C::INP; ++k) hin[k * TILE + s] = in[k];
+                for (int k = 0; k < C::INP; k += 4)
+                    *reinterpret_cast<float4 *>(hin + s * SIN + k) = make_float4(in[k], in[k + 1], in[k + 2], in[k + 3]);
             }
             __syncwarp();
-            float d = 0.f;
-            if (__any_sync(FULL, active && slot == 0)) {
-                const float dA = tile_sdf_f32<C>(wslot0, hin, P, Q, lane, g.beta, g.inv_beta);
-                if (slot == 0) d = dA;
-            }
-            if (SLOTS > 1 && __any_sync(FULL, active && slot == 1)) {
-                if (!waited1) {
-                    if (!mbar_wait(&bar[1], ph1, 1u << 26)) {
-                        atomicCAS(a.status, 0, (int)6 /* KNS_ERR_TIMEOUT */);
-                        active = false;  // leave these rays unfinished; the status reports it
-                    }
-                    waited1 = true;
-                }
-                const float dB = tile_sdf_f32<C>(wslot1, hin, P, Q, lane, g.beta, g.inv_beta);
-                if (slot == 1) d = dB;
-            }
+            const float d = tile_sdf_f32<C>(wsm, hin, P, Q, lane, g.beta, g.inv_beta);
             bool hit = false, emit = false;
             int ncell = -1;
-            // a thinned-out warp hands its remaining rays to the next round, where they are
+            // a thinned-out tile hands its remaining rays to the next round, where they are
             // regrouped into full tiles, instead of running 16-sample GEMMs for a few rays
             const bool sparse = __popc(__ballot_sync(FULL, active)) < a.min_active;
             if (active) {
                 ++steps;
-                const int cur_cell = slot ? s_slot_cell[1] : cA;
                 if (fabsf(d) < a.eps) {
                     hit = true;
-                    a.cell_ray[r] = cur_cell;
+                    a.cell_ray[r] = c;
                     a.t_ray[r] = t;
                     a.steps_ray[r] = steps;
                     active = false;
@@ -329,25 +308,8 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) wave_eval_kernel(GridView g, 
                         if (ncell < 0) {
                             write_miss(a, r, steps);
                             active = false;
-                        } else if (it + 1 >= a.inner_steps || sparse) {
+                        } else if (ncell != c || it + 1 >= a.inner_steps || sparse) {
                             emit = true;
-                        } else if (ncell == cA) {
-                            slot = 0;
-                        } else if (SLOTS > 1) {
-                            int b = s_slot_cell[1];
-                            if (b == -1) {
-                                b = atomicCAS(&s_slot_cell[1], -1, ncell);
-                                if (b == -1) {  // this ray takes the neighbour cell on for the block
-                                    bulk_load(wslot1, a.wt + (int64_t)ncell * a.wt_stride, C::TSIZE * sizeof(float),
-                                              &bar[1]);
-                                    b = ncell;
-                                }
-                            }
-                            if (b == ncell) slot = 1; else emit = true;
-                        } else {
-                            emit = true;
-                        }
-                        if (emit) {
                             a.t_ray[r] = t;
                             a.steps_ray[r] = steps;
                             active = false;
@@ -364,13 +326,6 @@ __global__ void __launch_bounds__(EVAL_WARPS * 32) wave_eval_kernel(GridView g, 
             }
             warp_count_cells(a.count[nxt], emit, ncell);
         }
-        __syncthreads();
-        // a neighbour load issued this tile must land before the slot is reused
-        if (SLOTS > 1 && s_slot_cell[1] != -1) {
-            if (!waited1) mbar_wait(&bar[1], ph1, 1u << 26);
-            ph1 ^= 1u;
-        }
-        __syncthreads();
     }
 }
 
@@ -421,7 +376,7 @@ cudaError_t launch_wave_eval_cfg(const GridView &g, const WaveArgs &a, int cur, 
     static_assert(smem <= 200 * 1024, "eval tile does not fit in shared memory");
     cudaError_t e = cudaFuncSetAttribute(wave_eval_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    wave_eval_kernel<C><<<blocks, EVAL_WARPS * 32, smem, s>>>(g, a, cur);
+    wave_eval_kernel<C><<<blocks, 32, smem, s>>>(g, a, cur);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     wave_tail_kernel<C><<<blocks / 4 + 1, 128, 0, s>>>(g, a, cur);
     return cudaGetLastError();

@@ -109,14 +109,14 @@ __device__ __forceinline__ void write_miss(const WaveArgs &a, int r, int steps) 
 __device__ __forceinline__ int advance_ray(const GridView &g, const Ray &r, float &t, float tf) {
     const float x = fmaf(t, r.wx, r.ox), y = fmaf(t, r.wy, r.oy), z = fmaf(t, r.wz, r.oz);
     if (g.occ) {
-        int v[3] = {grid_axis(x, g.bmin[0], g.oscale[0], g.occ_res), grid_axis(y, g.bmin[1], g.oscale[1], g.occ_res),
-                    grid_axis(z, g.bmin[2], g.oscale[2], g.occ_res)};
-        if (!occ_test(g.occ, g.occ_res, v[0], v[1], v[2])) {
+        int vx = grid_axis(x, g.bmin[0], g.oscale[0], g.occ_res), vy = grid_axis(y, g.bmin[1], g.oscale[1], g.occ_res),
+            vz = grid_axis(z, g.bmin[2], g.oscale[2], g.occ_res);
+        if (!occ_test(g.occ, g.occ_res, vx, vy, vz)) {
             float te;
-            if (!dda_next(g, r, v, tf, te)) return -1;
+            if (!dda_next(g, r, vx, vy, vz, tf, te)) return -1;
             t = te;
             const int f = g.occ_per_cell;
-            return v[0] / f + g.N * (v[1] / f + g.N * (v[2] / f));
+            return vx / f + g.N * (vy / f + g.N * (vz / f));
         }
     }
     return cell_of(g, x, y, z);
