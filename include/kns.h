@@ -183,6 +183,27 @@ kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams
 kns_status kns_sdf(kns_ctx *ctx, const kns_grid *grid, const float *pts, int64_t n, float *sdf,
                    float *feat, float *grad, void *cuda_stream);
 
+/* ------------------------------------------------------- allocation-free render */
+
+/* Limits of kns_render_noalloc's built-in scratch. */
+#define KNS_NOALLOC_MAX_RAYS 262144 /* n_cams * W * H per call */
+#define KNS_NOALLOC_MAX_CELLS 32768 /* N^3 of the grid */
+#define KNS_NOALLOC_MAX_CAMS 64
+
+/* kns_render (FP32, default schedule) for callers that may not allocate device memory while they
+ * run: an application that gives all device memory to its own pool allocator at start-up, or a
+ * latency-bound loop that cannot take cudaMalloc's implicit device synchronisation.  The paper has
+ * no counterpart; it is a deployment convenience.  Its scratch is a fixed device array built into
+ * the library (about 10 MB on every GPU that loads it, kept until the process exits); the call
+ * allocates nothing and frees nothing.  The context and the grid must already exist (creating them
+ * does allocate).  The first call on a device looks up the array's device address (once per
+ * device), so make that first call before any stream capture.  All calls share the one array and
+ * each clears the counters it needs, so calls that overlap on the GPU race: serialise them (one
+ * stream, or events).  Arguments, outputs and errors as kns_render, plus INVALID_ARG when
+ * n_cams*W*H > KNS_NOALLOC_MAX_RAYS, n_cams > KNS_NOALLOC_MAX_CAMS or N^3 > KNS_NOALLOC_MAX_CELLS. */
+kns_status kns_render_noalloc(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams, int n_cams, int W,
+                              int H, int max_steps, float eps, const kns_frame *out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -94,6 +94,9 @@ def lib():
             L.kns_render.restype = st
             L.kns_sdf.argtypes = [vp, vp, vp, C.c_int64, vp, vp, vp, vp]
             L.kns_sdf.restype = st
+            L.kns_render_noalloc.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float,
+                                             C.POINTER(kns_frame), vp]
+            L.kns_render_noalloc.restype = st
             _lib = L
     return _lib
 
@@ -172,3 +175,14 @@ def kns_render(ctx: int, grid: int, cams_host_ptr: int, n_cams: int, W: int, H: 
 def kns_sdf(ctx: int, grid: int, pts_ptr: int, n: int, sdf_ptr: int, feat_ptr: int = None, grad_ptr: int = None,
             stream: int = 0) -> None:
     _check(lib().kns_sdf(ctx, grid, pts_ptr, n, sdf_ptr, feat_ptr, grad_ptr, stream), ctx)
+
+
+KNS_NOALLOC_MAX_RAYS = 262144
+KNS_NOALLOC_MAX_CELLS = 32768
+KNS_NOALLOC_MAX_CAMS = 64
+
+
+def kns_render_noalloc(ctx: int, grid: int, cams_host_ptr: int, n_cams: int, W: int, H: int, max_steps: int,
+                       eps: float, frame: kns_frame = None, stream: int = 0) -> None:
+    _check(lib().kns_render_noalloc(ctx, grid, cams_host_ptr, n_cams, W, H, max_steps, eps,
+                                    C.byref(frame) if frame is not None else None, stream), ctx)

@@ -649,3 +649,141 @@ kns_status kns_sdf(kns_ctx *ctx, const kns_grid *grid, const float *pts, int64_t
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ allocation-free render
+//
+// kns_render_noalloc serves callers that must not allocate device memory once they are running:
+// an engine that hands all device memory to its own pool allocator up front, or a latency-bound
+// loop that cannot afford cudaMalloc's implicit device synchronisation.  Its scratch is one
+// file-scope device array sized for KNS_NOALLOC_MAX_RAYS rays, KNS_NOALLOC_MAX_CELLS cells and
+// KNS_NOALLOC_MAX_CAMS cameras (about 10 MB, held by every GPU that loads the library until the
+// process exits).  Every call shares the array, so calls that overlap on the GPU race; the
+// counters that must start at zero are cleared by each call.
+namespace {
+
+constexpr size_t kNoAllocAlign = 256;
+constexpr size_t align_up(size_t v) { return (v + kNoAllocAlign - 1) / kNoAllocAlign * kNoAllocAlign; }
+constexpr size_t kNoAllocRayBuf = align_up(sizeof(int) * (size_t)KNS_NOALLOC_MAX_RAYS);
+constexpr size_t kNoAllocCellBuf = align_up(sizeof(int) * 6 * (size_t)(KNS_NOALLOC_MAX_CELLS + 1));
+constexpr size_t kNoAllocCamBuf = align_up(sizeof(kns_camera) * (size_t)KNS_NOALLOC_MAX_CAMS);
+constexpr size_t kNoAllocCtrlBuf = align_up(sizeof(kns::WaveCtrl));
+// t_ray, steps_ray, cell_ray, q[2], qcell[2], sorted, hits: nine per-ray int/float buffers
+constexpr size_t kNoAllocBytes = 9 * kNoAllocRayBuf + kNoAllocCellBuf + kNoAllocCamBuf + kNoAllocCtrlBuf;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_dev_ptr[256] = {};  // device address of g_noalloc_scratch, per device ordinal
+
+// The host-side name g_noalloc_scratch is only a stand-in for the device array: its device address
+// is looked up once per device, with that device current.
+kns_status noalloc_scratch(kns_ctx *ctx, unsigned char **out) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (ctx->device < 0 || ctx->device >= 256) return set_err(ctx, KNS_ERR_INVALID_ARG, "device ordinal too large");
+    if (!g_noalloc_dev_ptr[ctx->device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_err(ctx, e, "cudaGetSymbolAddress(no-alloc scratch)");
+        g_noalloc_dev_ptr[ctx->device] = p;
+    }
+    *out = (unsigned char *)g_noalloc_dev_ptr[ctx->device];
+    return KNS_OK;
+}
+
+}  // namespace
+
+extern "C" kns_status kns_render_noalloc(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams, int n_cams,
+                                         int W, int H, int max_steps, float eps, const kns_frame *out,
+                                         void *cuda_stream) {
+    if (!ctx) return KNS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!grid || !cams || !out) return set_err(ctx, KNS_ERR_INVALID_ARG, "NULL grid, cams or out");
+    if (n_cams < 0 || W < 0 || H < 0) return set_err(ctx, KNS_ERR_INVALID_ARG, "negative size");
+    if (max_steps < 1) return set_err(ctx, KNS_ERR_INVALID_ARG, "max_steps=%d < 1", max_steps);
+    if (!(eps > 0.f) || !std::isfinite(eps)) return set_err(ctx, KNS_ERR_INVALID_ARG, "eps must be > 0 and finite");
+    if (!out->rgb || !out->depth) return set_err(ctx, KNS_ERR_INVALID_ARG, "rgb and depth buffers are required");
+    const int64_t rays = (int64_t)n_cams * W * H;
+    const int NC = grid->desc.N * grid->desc.N * grid->desc.N;
+    if (rays > KNS_NOALLOC_MAX_RAYS)
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "kns_render_noalloc: %lld rays exceed its scratch limit of %d",
+                       (long long)rays, KNS_NOALLOC_MAX_RAYS);
+    if (n_cams > KNS_NOALLOC_MAX_CAMS)
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "kns_render_noalloc: %d cameras exceed its limit of %d", n_cams,
+                       KNS_NOALLOC_MAX_CAMS);
+    if (NC > KNS_NOALLOC_MAX_CELLS)
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "kns_render_noalloc: %d cells exceed its limit of %d", NC,
+                       KNS_NOALLOC_MAX_CELLS);
+    if (rays == 0) return KNS_OK;
+    DeviceScope ds(ctx->device);
+    unsigned char *base = nullptr;
+    kns_status st = noalloc_scratch(ctx, &base);
+    if (st != KNS_OK) return st;
+    unsigned char *p = base;
+    auto take = [&](size_t bytes) {
+        unsigned char *q = p;
+        p += bytes;
+        return q;
+    };
+    kns::WaveArgs a{};
+    a.t_ray = (float *)take(kNoAllocRayBuf);
+    a.steps_ray = (int *)take(kNoAllocRayBuf);
+    a.cell_ray = (int *)take(kNoAllocRayBuf);
+    a.q[0] = (int *)take(kNoAllocRayBuf);
+    a.q[1] = (int *)take(kNoAllocRayBuf);
+    a.qcell[0] = (int *)take(kNoAllocRayBuf);
+    a.qcell[1] = (int *)take(kNoAllocRayBuf);
+    a.sorted = (int *)take(kNoAllocRayBuf);
+    a.hits = (int *)take(kNoAllocRayBuf);
+    int *cellbuf = (int *)take(kNoAllocCellBuf);
+    float *d_cams = (float *)take(kNoAllocCamBuf);
+    a.ctrl = (kns::WaveCtrl *)take(kNoAllocCtrlBuf);
+    a.count[0] = cellbuf;
+    a.count[1] = cellbuf + (NC + 1);
+    a.fill[0] = cellbuf + 2 * (NC + 1);
+    a.fill[1] = cellbuf + 3 * (NC + 1);
+    a.off = cellbuf + 4 * (NC + 1);
+    a.tile_off = cellbuf + 5 * (NC + 1);
+    a.W = W;
+    a.H = H;
+    a.n_cams = n_cams;
+    a.max_steps = max_steps;
+    a.eps = eps;
+    a.NC = NC;
+    a.btile = kRenderBlockTile;
+    a.inner_steps = kRenderInnerSteps;
+    a.tail_max = kRenderTailRays;
+    a.min_active = kRenderMinActive;
+    a.static_tiles = kRenderStaticTiles == 1;
+    a.status = ctx->d_status;
+    a.cams = d_cams;
+    a.wt = grid->d_wt;
+    a.wt_stride = grid->wt_stride;
+    a.rgb = out->rgb;
+    a.depth = out->depth;
+    a.normal = out->normal;
+    a.cell_out = out->cell;
+    a.steps_out = out->steps;
+    a.hit_out = out->hit;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaMemcpyAsync(d_cams, cams, sizeof(kns_camera) * n_cams, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.ctrl, 0, sizeof(kns::WaveCtrl), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cellbuf, 0, sizeof(int) * 4 * (NC + 1), s);
+    if (e == cudaSuccess) e = kns::launch_wave_gen(grid->shape, grid->view, a, s);
+    const int eval_blocks = ctx->sm_count * kRenderBlocksPerSM, scatter_blocks = ctx->sm_count * 4;
+    for (int k = 0; k < max_steps && e == cudaSuccess; ++k) {
+        const int cur = k & 1;
+        if (k >= 2) {
+            e = cudaEventSynchronize(ctx->ev_live[(k - 2) & 3]);
+            if (e != cudaSuccess || ctx->h_live[(k - 2) & 3] == 0) break;
+        }
+        e = kns::launch_wave_scan(a, cur, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->h_live + (k & 3), &a.ctrl->n_live[cur], sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_live[k & 3], s);
+        if (e == cudaSuccess) e = kns::launch_wave_scatter(a, cur, scatter_blocks, s);
+        if (e == cudaSuccess) e = kns::launch_wave_eval(grid->shape, grid->view, a, cur, eval_blocks, s);
+    }
+    if (e == cudaSuccess) e = kns::launch_wave_shade(grid->shape, grid->view, a, ctx->sm_count * 8, s);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "render launch");
+    return KNS_OK;
+}
