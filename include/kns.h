@@ -110,7 +110,9 @@ typedef struct kns_frame {
 typedef struct kns_render_opts {
     int32_t precision;    /* KNS_FP32 or KNS_BF16 */
     float eps_coarse;     /* KNS_BF16: hit threshold of the BF16 trace (<= 0: max(eps, 4e-3)) */
-    int32_t refine_steps; /* KNS_BF16: FP32 sphere steps after the BF16 hit (< 0: 2) */
+    int32_t refine_steps; /* KNS_BF16: FP32 evaluations after the BF16 hit before the FP32 field decides
+                             (<= 0: 2); the ray is a hit at the first |d| < eps, or at the last of them if
+                             |d| < eps_coarse there, else a miss */
     /* tuning (0 = default) */
     int32_t inner_steps;   /* sphere steps a tile may take per round while its rays stay in its cells (1..1024) */
     int32_t min_active;    /* a 16-ray warp tile with fewer live rays hands them to the next round (1..16) */

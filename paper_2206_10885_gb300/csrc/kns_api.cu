@@ -46,6 +46,8 @@ struct kns_grid {
     float *d_w = nullptr;   // per-thread layout (shading, field queries, occupancy)
     float *d_wt = nullptr;  // k-major trace layout (wavefront tile GEMM)
     int wt_stride = 0;
+    unsigned char *d_wb = nullptr;  // BF16 mma fragment trace layout
+    int wb_stride = 0;              // bytes per cell
     uint32_t *d_occ = nullptr;
     size_t occ_words64 = 0;
     kns::GridView view{};
@@ -193,6 +195,47 @@ void convert_cell_trace(const kns_grid_desc &d, int dev_floats, const float *src
     for (int c = 0; c < W; ++c) dst[o + c] = src[s + c];  // row 0 (d) of the last layer
     o += W;
     dst[o] = src[s + (int64_t)kns::SDF_OUT * W];  // its bias
+}
+
+// Canonical SDF layers -> BF16 mma fragment layout (kns_device.cuh, Cfg::FR0..BSIZE), one cell.
+static uint16_t to_bf16(float f) {  // round to nearest even
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);  // inf / nan
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+void convert_cell_bf16(const kns_grid_desc &d, int bytes, int k0p, const float *src, unsigned char *dst) {
+    const int W = d.sdf_width, H = d.sdf_hidden, IN = 3 + 6 * d.pe_pos_L;
+    std::memset(dst, 0, bytes);
+    uint32_t *frag = (uint32_t *)dst;
+    int f = 0;  // fragment index
+    auto emit_layer = [&](const float *Wm, int kin, int kpad, int nout, int npad) {
+        // B[k][n] = W[n][k]; W is [nout][kin] row-major
+        auto B = [&](int k, int n) -> uint16_t { return (k < kin && n < nout) ? to_bf16(Wm[n * kin + k]) : 0; };
+        for (int kt = 0; kt < kpad / 16; ++kt)
+            for (int nt = 0; nt < npad / 8; ++nt, ++f)
+                for (int lane = 0; lane < 32; ++lane) {
+                    const int k = 16 * kt + 2 * (lane % 4), n = 8 * nt + lane / 4;
+                    frag[(f * 32 + lane) * 2 + 0] = (uint32_t)B(k, n) | ((uint32_t)B(k + 1, n) << 16);
+                    frag[(f * 32 + lane) * 2 + 1] = (uint32_t)B(k + 8, n) | ((uint32_t)B(k + 9, n) << 16);
+                }
+    };
+    const int nfrag = (k0p / 16) * (W / 8) + (H - 1) * (W / 16) * (W / 8) + W / 16;
+    float *bias = (float *)(dst + nfrag * 256);
+    int64_t s = 0;
+    emit_layer(src + s, IN, k0p, W, W);
+    s += (int64_t)W * IN;
+    for (int r = 0; r < W; ++r) bias[r] = src[s + r];
+    s += W;
+    for (int l = 1; l < H; ++l) {
+        emit_layer(src + s, W, W, W, W);
+        s += (int64_t)W * W;
+        for (int r = 0; r < W; ++r) bias[l * W + r] = src[s + r];
+        s += W;
+    }
+    emit_layer(src + s, W, W, 1, 8);  // row 0 (d) of the last layer only
+    bias[H * W] = src[s + (int64_t)kns::SDF_OUT * W];
 }
 
 void fill_view(kns_grid *g) {
@@ -404,9 +447,27 @@ kns_status kns_load_grid(kns_ctx *ctx, const kns_grid_desc *desc, const float *h
         e = cudaMalloc(&g->d_wt, ht.size() * sizeof(float));
         if (e == cudaSuccess) e = cudaMemcpy(g->d_wt, ht.data(), ht.size() * sizeof(float), cudaMemcpyHostToDevice);
     }
+    if (e == cudaSuccess) {
+        int k0p = 0;
+        g->wb_stride = kns::bf16_cell_bytes(g->shape, &k0p);
+        std::vector<unsigned char> hb;
+        try {
+            hb.resize((size_t)(ncell * g->wb_stride));
+        } catch (...) {
+            cudaFree(g->d_w);
+            cudaFree(g->d_wt);
+            delete g;
+            return set_err(ctx, KNS_ERR_OUT_OF_MEMORY, "host staging allocation failed");
+        }
+        for (int64_t c = 0; c < ncell; ++c)
+            convert_cell_bf16(d, g->wb_stride, k0p, host_weights + c * pcell, hb.data() + c * g->wb_stride);
+        e = cudaMalloc(&g->d_wb, hb.size());
+        if (e == cudaSuccess) e = cudaMemcpy(g->d_wb, hb.data(), hb.size(), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         cudaFree(g->d_w);
         cudaFree(g->d_wt);
+        cudaFree(g->d_wb);
         delete g;
         return cuda_err(ctx, e, "grid upload");
     }
@@ -430,6 +491,7 @@ kns_status kns_load_grid(kns_ctx *ctx, const kns_grid_desc *desc, const float *h
         if (e != cudaSuccess) {
             cudaFree(g->d_w);
             cudaFree(g->d_wt);
+            cudaFree(g->d_wb);
             cudaFree(g->d_occ);
             delete g;
             return cuda_err(ctx, e, "occupancy");
@@ -505,6 +567,7 @@ void kns_free_grid(kns_grid *g) {
         cudaDeviceSynchronize();
         cudaFree(g->d_w);
         cudaFree(g->d_wt);
+        cudaFree(g->d_wb);
         cudaFree(g->d_occ);
     }
     delete g;
@@ -543,7 +606,11 @@ kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams
     const int precision = opts ? opts->precision : KNS_FP32;
     if (precision != KNS_FP32 && precision != KNS_BF16)
         return set_err(ctx, KNS_ERR_INVALID_ARG, "unknown precision %d", precision);
-    if (precision == KNS_BF16) return set_err(ctx, KNS_ERR_UNSUPPORTED, "BF16 path not built");
+    const bool bf16 = precision == KNS_BF16;
+    const float eps_coarse = (bf16 && opts && opts->eps_coarse > 0.f) ? opts->eps_coarse : std::max(eps, 4e-3f);
+    const int refine_steps = (bf16 && opts && opts->refine_steps > 0) ? opts->refine_steps : 2;
+    if (bf16 && !(eps_coarse >= eps && std::isfinite(eps_coarse)))
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "eps_coarse must be finite and >= eps");
     auto knob = [](int32_t v, int32_t def) { return v == 0 ? def : v; };
     const int inner_steps = opts ? knob(opts->inner_steps, kRenderInnerSteps) : kRenderInnerSteps;
     const int min_active = opts ? knob(opts->min_active, kRenderMinActive) : kRenderMinActive;
@@ -554,6 +621,7 @@ kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams
         blocks_per_sm < 1 || blocks_per_sm > 64 || (opts && (opts->static_tiles < 0 || opts->static_tiles > 2)))
         return set_err(ctx, KNS_ERR_INVALID_ARG, "render tuning field out of range");
     if (tail_rays < 0) tail_rays = 0;
+    if (bf16) tail_rays = 0;  // the per-thread tail evaluator is FP32 only
     if (n_cams == 0 || W == 0 || H == 0) return KNS_OK;
     if ((int64_t)W * H > INT32_MAX) return set_err(ctx, KNS_ERR_INVALID_ARG, "W*H exceeds 2^31-1");
     DeviceScope ds(ctx->device);
@@ -561,7 +629,8 @@ kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams
     const int64_t hw = (int64_t)W * H;
     const int per_chunk = (int)std::max<int64_t>(1, std::min<int64_t>(n_cams, (int64_t)INT32_MAX / hw));
     const int NC = grid->desc.N * grid->desc.N * grid->desc.N;
-    kns_status st = ensure_scratch(ctx, (int64_t)per_chunk * hw, NC, per_chunk);
+    const int nkeys = bf16 ? 2 * NC : NC;
+    kns_status st = ensure_scratch(ctx, (int64_t)per_chunk * hw, nkeys, per_chunk);
     if (st != KNS_OK) return st;
     WaveScratch &w = ctx->ws;
     for (int c0 = 0; c0 < n_cams; c0 += per_chunk) {
@@ -574,6 +643,12 @@ kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams
         a.max_steps = max_steps;
         a.eps = eps;
         a.NC = NC;
+        a.nkeys = nkeys;
+        a.coarse = bf16 ? 1 : 0;
+        a.eps_coarse = eps_coarse;
+        a.refine_steps = refine_steps;
+        a.wb = grid->d_wb;
+        a.wb_stride = grid->wb_stride;
         a.btile = kRenderBlockTile;
         a.inner_steps = inner_steps;
         a.tail_max = tail_rays;
@@ -599,15 +674,15 @@ kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams
         a.sorted = w.sorted;
         a.hits = w.hits;
         a.count[0] = w.cellbuf;
-        a.count[1] = w.cellbuf + (NC + 1);
-        a.fill[0] = w.cellbuf + 2 * (NC + 1);
-        a.fill[1] = w.cellbuf + 3 * (NC + 1);
-        a.off = w.cellbuf + 4 * (NC + 1);
-        a.tile_off = w.cellbuf + 5 * (NC + 1);
+        a.count[1] = w.cellbuf + (nkeys + 1);
+        a.fill[0] = w.cellbuf + 2 * (nkeys + 1);
+        a.fill[1] = w.cellbuf + 3 * (nkeys + 1);
+        a.off = w.cellbuf + 4 * (nkeys + 1);
+        a.tile_off = w.cellbuf + 5 * (nkeys + 1);
         a.ctrl = w.ctrl;
         cudaError_t e = cudaMemcpyAsync(w.d_cams, &cams[c0], sizeof(kns_camera) * nc, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.ctrl, 0, sizeof(kns::WaveCtrl), s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(w.cellbuf, 0, sizeof(int) * 4 * (NC + 1), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(w.cellbuf, 0, sizeof(int) * 4 * (nkeys + 1), s);
         if (e == cudaSuccess) e = kns::launch_wave_gen(grid->shape, grid->view, a, s);
         const int eval_blocks = ctx->sm_count * blocks_per_sm, scatter_blocks = ctx->sm_count * 4;
         // Rounds: at most max_steps (each live ray takes >= 1 step per round).  The host reads the
@@ -626,6 +701,8 @@ kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams
             if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_live[k & 3], s);
             if (e == cudaSuccess) e = kns::launch_wave_scatter(a, cur, scatter_blocks, s);
             if (e == cudaSuccess) e = kns::launch_wave_eval(grid->shape, grid->view, a, cur, eval_blocks, s);
+            if (e == cudaSuccess && bf16)
+                e = kns::launch_wave_eval_bf16(grid->shape, grid->view, a, cur, eval_blocks, s);
         }
         if (e == cudaSuccess) e = kns::launch_wave_shade(grid->shape, grid->view, a, ctx->sm_count * 8, s);
         if (e != cudaSuccess) return cuda_err(ctx, e, "render launch");
@@ -749,6 +826,7 @@ extern "C" kns_status kns_render_noalloc(kns_ctx *ctx, const kns_grid *grid, con
     a.max_steps = max_steps;
     a.eps = eps;
     a.NC = NC;
+    a.nkeys = NC;
     a.btile = kRenderBlockTile;
     a.inner_steps = kRenderInnerSteps;
     a.tail_max = kRenderTailRays;

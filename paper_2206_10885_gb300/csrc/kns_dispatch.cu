@@ -40,10 +40,25 @@ cudaError_t launch_wave_shade(const Shape &sh, const GridView &g, const WaveArgs
     return dispatch(sh, [&](auto c) { return launch_wave_shade_cfg<decltype(c)>(g, a, blocks, s); });
 }
 
+cudaError_t launch_wave_eval_bf16(const Shape &sh, const GridView &g, const WaveArgs &a, int cur, int blocks,
+                                  cudaStream_t s) {
+    return dispatch(sh, [&](auto c) { return launch_wave_eval_bf16_cfg<decltype(c)>(g, a, cur, blocks, s); });
+}
+
 int trace_cell_floats(const Shape &sh) {
     int size = 0;
     dispatch(sh, [&](auto c) {
         size = decltype(c)::TSIZE;
+        return cudaSuccess;
+    });
+    return size;
+}
+
+int bf16_cell_bytes(const Shape &sh, int *k0p) {
+    int size = 0;
+    dispatch(sh, [&](auto c) {
+        size = decltype(c)::BSIZE;
+        *k0p = decltype(c)::K0P;
         return cudaSuccess;
     });
     return size;

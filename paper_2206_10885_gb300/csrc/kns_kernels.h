@@ -18,9 +18,10 @@ struct WaveCtrl {
     int n_live[2];  // samples queued for the current / next round
     int n_hits;     // rays that converged (queued for shading)
     int n_tiles;    // block tiles of the current round
-    int next_tile;  // dynamic tile counter of the current round
-    int tail;       // 1: the current round is small enough to finish one thread per ray
-    int pad[2];
+    int next_tile;     // dynamic tile counter of the current round (FP32 tiles)
+    int tail;          // 1: the current round is small enough to finish one thread per ray
+    int n_tiles_fine;  // tiles of FP32 samples (keys < NC); BF16 tiles follow them
+    int next_tile_bf;  // dynamic tile counter of the BF16 tiles
 };
 
 // Everything the wavefront kernels read and write (device pointers; passed by value).
@@ -28,6 +29,12 @@ struct WaveArgs {
     int W, H, n_cams, max_steps;
     float eps;
     int NC;               // cells N^3
+    int nkeys;            // sort keys: key = cell + NC * coarse (NC for FP32 renders, 2 NC for BF16)
+    int coarse;           // 1: BF16 render (rays start in the coarse BF16 phase and refine in FP32)
+    float eps_coarse;     // BF16 phase hit threshold
+    int refine_steps;     // FP32 evaluations after a BF16 hit before the final decision
+    const unsigned char *wb;  // BF16 mma fragment trace weights
+    int wb_stride;            // bytes per cell
     int btile;            // samples per block tile (cell-sorted samples are cut into such tiles)
     int inner_steps;      // sphere steps a tile may take in one round while its rays stay in its cells
     int tail_max;         // a round with at most this many rays is finished one thread per ray
@@ -60,6 +67,8 @@ cudaError_t launch_wave_eval_cfg(const GridView &g, const WaveArgs &a, int cur, 
 template <class C>
 cudaError_t launch_wave_shade_cfg(const GridView &g, const WaveArgs &a, int blocks, cudaStream_t s);
 template <class C>
+cudaError_t launch_wave_eval_bf16_cfg(const GridView &g, const WaveArgs &a, int cur, int blocks, cudaStream_t s);
+template <class C>
 cudaError_t launch_sdf_cfg(const GridView &g, const float *pts, int64_t n, float *sdf, float *feat, float *grad,
                            cudaStream_t s);
 template <class C>
@@ -68,11 +77,14 @@ cudaError_t launch_occ_cfg(const GridView &g, float thresh, uint32_t *words, cud
 bool shape_supported(const Shape &sh);
 int cell_floats(const Shape &sh);
 int trace_cell_floats(const Shape &sh);
+int bf16_cell_bytes(const Shape &sh, int *k0p);
 
 cudaError_t launch_wave_gen(const Shape &sh, const GridView &g, const WaveArgs &a, cudaStream_t s);
 cudaError_t launch_wave_eval(const Shape &sh, const GridView &g, const WaveArgs &a, int cur, int blocks,
                              cudaStream_t s);
 cudaError_t launch_wave_shade(const Shape &sh, const GridView &g, const WaveArgs &a, int blocks, cudaStream_t s);
+cudaError_t launch_wave_eval_bf16(const Shape &sh, const GridView &g, const WaveArgs &a, int cur, int blocks,
+                                  cudaStream_t s);
 cudaError_t launch_wave_scan(const WaveArgs &a, int cur, cudaStream_t s);
 cudaError_t launch_wave_scatter(const WaveArgs &a, int cur, int blocks, cudaStream_t s);
 

@@ -50,7 +50,7 @@ __device__ __forceinline__ void block_scan2(int &a, int &b, int *wa, int *wb) {
 __global__ void __launch_bounds__(SCAN_THREADS) wave_scan_kernel(WaveArgs a, int cur) {
     __shared__ int wa[32], wb[32];
     const int nxt = cur ^ 1;
-    const int NC = a.NC;
+    const int NC = a.nkeys;  // sort keys (cells, or cells x {fine, coarse})
     // clear the next wave's counters (nothing reads them during this wave)
     for (int c = threadIdx.x; c < NC; c += SCAN_THREADS) {
         a.count[nxt][c] = 0;
@@ -59,11 +59,15 @@ __global__ void __launch_bounds__(SCAN_THREADS) wave_scan_kernel(WaveArgs a, int
     if (threadIdx.x == 0) {
         a.ctrl->n_live[nxt] = 0;
         a.ctrl->next_tile = 0;
+        a.ctrl->next_tile_bf = 0;
     }
     const int n_live = a.ctrl->n_live[cur];
     if (threadIdx.x == 0) a.ctrl->tail = n_live <= a.tail_max ? 1 : 0;
     if (n_live == 0 || n_live <= a.tail_max) {  // nothing to sort: empty, or finished per thread
-        if (threadIdx.x == 0) a.ctrl->n_tiles = 0;
+        if (threadIdx.x == 0) {
+            a.ctrl->n_tiles = 0;
+            a.ctrl->n_tiles_fine = 0;
+        }
         return;
     }
     // each thread owns a contiguous run of cells
@@ -82,6 +86,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) wave_scan_kernel(WaveArgs a, int
         const int n = a.count[cur][c];
         a.off[c] = run_s;
         a.tile_off[c] = run_t;
+        if (c == a.NC) a.ctrl->n_tiles_fine = run_t;  // first BF16 key: FP32 tiles end here
         run_s += n;
         run_t += (n + a.btile - 1) / a.btile;
     }
@@ -89,6 +94,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) wave_scan_kernel(WaveArgs a, int
         a.off[NC] = incl_s;
         a.tile_off[NC] = incl_t;
         a.ctrl->n_tiles = incl_t;
+        if (NC == a.NC) a.ctrl->n_tiles_fine = incl_t;  // FP32 render: every tile is FP32
     }
 }
 

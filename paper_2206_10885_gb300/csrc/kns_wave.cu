@@ -136,12 +136,13 @@ __global__ void __launch_bounds__(128) wave_gen_kernel(GridView g, WaveArgs a) {
             }
         }
     }
+    const int key = cell + (a.coarse ? a.NC : 0);  // BF16 renders start every ray in the coarse phase
     const int qp = warp_append(&a.ctrl->n_live[0], alive);
     if (alive) {
         a.q[0][qp] = r;
-        a.qcell[0][qp] = cell;
+        a.qcell[0][qp] = key;
     }
-    warp_count_cells(a.count[0], alive, cell);
+    warp_count_cells(a.count[0], alive, key);
 }
 
 // Round k: each warp (a block of its own) takes tiles of up to 16 cell-sorted samples of one cell,
@@ -214,7 +215,8 @@ __global__ void __launch_bounds__(32) wave_eval_kernel(GridView g, WaveArgs a, i
     float *hin = dyn + C::TSIZE;
     float *P = hin + TILE * act_stride(C::INP), *Q = P + TILE * act_stride(C::W);
     constexpr int SIN = act_stride(C::INP);
-    const int n_tiles = a.ctrl->n_tiles;
+    const int n_tiles = a.ctrl->n_tiles_fine;  // FP32 tiles (BF16 tiles follow them)
+    if (n_tiles <= 0) return;
     if (lane == 0) mbar_init(&bar, 1);
     __syncwarp();
     // static schedule: block b owns tiles [b*per, (b+1)*per) so consecutive same-cell tiles reuse
@@ -250,13 +252,14 @@ __global__ void __launch_bounds__(32) wave_eval_kernel(GridView g, WaveArgs a, i
         cached = c;
         const int s = lane & 15;
         bool active = lane < TILE && s < len;
-        int r = 0, steps = 0;
+        int r = 0, steps = 0, switched = 0;
         float t = 0.f, t0 = 0.f, tf = 0.f;
         Ray ray{};
         if (active) {
             r = a.sorted[start + s];
             t = a.t_ray[r];
             steps = a.steps_ray[r];
+            if (a.coarse) switched = a.cell_ray[r];  // step count at the BF16 -> FP32 switch
             int cam;
             ray = ray_of(a, r, cam);
             clip_box(g, ray, t0, tf);
@@ -292,11 +295,17 @@ __global__ void __launch_bounds__(32) wave_eval_kernel(GridView g, WaveArgs a, i
             const bool sparse = __popc(__ballot_sync(FULL, active)) < a.min_active;
             if (active) {
                 ++steps;
-                if (fabsf(d) < a.eps) {
+                // BF16 renders: after refine_steps FP32 evaluations the FP32 field decides: a hit
+                // here if |d| is within the coarse threshold, else the BF16 hit was spurious
+                const bool last_refine = a.coarse && steps - switched >= a.refine_steps;
+                if (fabsf(d) < a.eps || (last_refine && fabsf(d) < a.eps_coarse)) {
                     hit = true;
                     a.cell_ray[r] = c;
                     a.t_ray[r] = t;
                     a.steps_ray[r] = steps;
+                    active = false;
+                } else if (last_refine) {
+                    write_miss(a, r, steps);
                     active = false;
                 } else {
                     t += d;

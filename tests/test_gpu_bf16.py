@@ -1,0 +1,115 @@
+"""BF16 tensor-core render vs the FP64 oracle's render (needs a GPU).
+
+Gates (per result, on pixels where both the BF16 render and the oracle hit): depth within 1e-3
+scene units, RGB within 1/255 per channel, normal angle within 0.5 degrees, each on >= 99.9% of
+those pixels.  Hit agreement is reported and must stay above 98%: near-silhouette rays that the
+BF16 phase finds within eps_coarse of the surface are accepted by the FP32 refinement when the
+FP32 field confirms |d| < eps_coarse, where the FP32 trace (eps = 1e-4) misses them.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2206_10885_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def kns():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_10885_gb300 import build as kbuild
+    kbuild.build()
+    import paper_2206_10885_gb300 as kns
+    return kns
+
+
+@pytest.fixture(scope="module")
+def ctx(kns):
+    c = kns.Context(0)
+    yield c
+    c.close()
+
+
+def render_np(kns, ctx, grid, cams, W, H, ms, eps, **kw):
+    t = kns.render(ctx, grid, cams, W, H, ms, eps, **kw)
+    ctx.sync()
+    return {k: v.cpu().numpy() for k, v in t.items()}
+
+
+def bf16_report(g, o):
+    gh, oh = g["hit"] == 1, o["hit"] == 1
+    both = gh & oh
+    dd = np.abs(g["depth"][both].astype(np.float64) - o["depth"][both])
+    dr = np.abs(g["rgb"][both].astype(np.float64) - o["rgb"][both]).max(axis=1)
+    cosang = np.clip(np.sum(g["normal"][both].astype(np.float64) * o["normal"][both], axis=1), -1, 1)
+    ang = np.degrees(np.arccos(cosang))
+    return dict(pixels=len(gh), both=int(both.sum()), hit_agree=float(np.mean(gh == oh)),
+                depth_ok=float(np.mean(dd <= 1e-3)), rgb_ok=float(np.mean(dr <= 1 / 255)),
+                normal_ok=float(np.mean(ang <= 0.5)), depth_p999=float(np.quantile(dd, 0.999)),
+                rgb_p999=float(np.quantile(dr, 0.999)), angle_p999=float(np.quantile(ang, 0.999)))
+
+
+def assert_bf16_gates(rep):
+    assert rep["both"] > 500, rep
+    assert rep["depth_ok"] >= 0.999, rep
+    assert rep["rgb_ok"] >= 0.999, rep
+    assert rep["normal_ok"] >= 0.999, rep
+    assert rep["hit_agree"] >= 0.98, rep
+
+
+@pytest.mark.parametrize("gname,W,H", [("c2", 160, 120), ("c1", 64, 64)])
+def test_bf16_accuracy_small(kns, ctx, gname, W, H):
+    desc = S.config_desc(gname)
+    w = S.sal_sphere_grid(desc)
+    occ = O.occupancy(desc, w) if desc.occ_res else None
+    cams = S.orbit_cameras(3, W, H, seed=12)
+    grid = kns.Grid.load(ctx, desc, w, occ)
+    try:
+        g = render_np(kns, ctx, grid, cams, W, H, 128, 1e-4, precision=kns.KNS_BF16)
+    finally:
+        grid.free()
+    o = O.render(desc, w, occ, cams, W, H, 128, 1e-4)
+    rep = bf16_report(g, o)
+    print(gname, rep)
+    assert_bf16_gates(rep)
+
+
+@pytest.mark.parametrize("gname", ["c3s", "c3l"])
+def test_bf16_accuracy_1080p_sampled(kns, ctx, gname):
+    """The 1080p launch (2 cameras, 16^3 width 32 and 32^3 width 64 grids) on sampled pixels."""
+    desc = S.config_desc(gname)
+    w = S.sal_sphere_grid(desc)
+    occ = O.occupancy(desc, w)
+    cams = S.orbit_cameras(2, 1920, 1080, seed=1)
+    grid = kns.Grid.load(ctx, desc, w, occ)
+    try:
+        g = render_np(kns, ctx, grid, cams, 1920, 1080, 128, 1e-4, precision=kns.KNS_BF16)
+    finally:
+        grid.free()
+    rng = np.random.default_rng(4)
+    n_pix = 2 * 1920 * 1080
+    hits = np.where(g["hit"] == 1)[0]
+    sel = np.unique(np.concatenate([rng.integers(0, n_pix, 4000), hits[rng.integers(0, hits.size, 4000)]]))
+    o = O.render(desc, w, occ, cams, 1920, 1080, 128, 1e-4, sel=sel)
+    rep = bf16_report({k: v[sel] for k, v in g.items()}, o)
+    print(gname, rep)
+    assert_bf16_gates(rep)
+
+
+def test_bf16_schedule_invariance(kns, ctx):
+    desc = S.config_desc("c2")
+    w = S.sal_sphere_grid(desc)
+    cams = S.orbit_cameras(2, 160, 120, seed=8)
+    grid = kns.Grid.load(ctx, desc, w)
+    try:
+        ref = render_np(kns, ctx, grid, cams, 160, 120, 128, 1e-4, precision=kns.KNS_BF16)
+        for tuning in [dict(inner_steps=1, min_active=1, static_tiles=2),
+                       dict(inner_steps=64, min_active=16, static_tiles=1, blocks_per_sm=2)]:
+            got = render_np(kns, ctx, grid, cams, 160, 120, 128, 1e-4, precision=kns.KNS_BF16, tuning=tuning)
+            for k in ref:
+                assert np.array_equal(ref[k], got[k]), (k, tuning)
+    finally:
+        grid.free()
