@@ -49,6 +49,7 @@ struct kns_grid {
     unsigned char *d_wb = nullptr;  // BF16 mma fragment trace layout
     int wb_stride = 0;              // bytes per cell
     uint32_t *d_occ = nullptr;
+    uint32_t *d_occ_coarse = nullptr;  // 8^3-voxel block mask (res % 8 == 0)
     size_t occ_words64 = 0;
     kns::GridView view{};
 };
@@ -252,6 +253,8 @@ void fill_view(kns_grid *g) {
         v.ovox[a] = d.occ_res > 0 ? (d.bbox_max[a] - d.bbox_min[a]) / (float)d.occ_res : 0.f;
     }
     v.occ = g->d_occ;
+    v.occ_coarse = g->d_occ_coarse;
+    v.cres = d.occ_res / 8;
     v.occ_res = d.occ_res;
     v.occ_per_cell = d.occ_res > 0 ? d.occ_res / d.N : 1;
     v.beta = d.softplus_beta;
@@ -488,11 +491,18 @@ kns_status kns_load_grid(kns_ctx *ctx, const kns_grid_desc *desc, const float *h
             e = kns::launch_occupancy_f32(g->shape, v, diag, g->d_occ, 0);
             if (e == cudaSuccess) e = cudaDeviceSynchronize();
         }
+        if (e == cudaSuccess && d.occ_res % 8 == 0) {
+            const int64_t nb = (int64_t)(d.occ_res / 8) * (d.occ_res / 8) * (d.occ_res / 8);
+            e = cudaMalloc(&g->d_occ_coarse, (size_t)((nb + 31) / 32) * 4);
+            if (e == cudaSuccess) e = kns::launch_coarse_occupancy(g->d_occ, d.occ_res, g->d_occ_coarse, 0);
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        }
         if (e != cudaSuccess) {
             cudaFree(g->d_w);
             cudaFree(g->d_wt);
             cudaFree(g->d_wb);
             cudaFree(g->d_occ);
+            cudaFree(g->d_occ_coarse);
             delete g;
             return cuda_err(ctx, e, "occupancy");
         }
@@ -569,6 +579,7 @@ void kns_free_grid(kns_grid *g) {
         cudaFree(g->d_wt);
         cudaFree(g->d_wb);
         cudaFree(g->d_occ);
+        cudaFree(g->d_occ_coarse);
     }
     delete g;
 }

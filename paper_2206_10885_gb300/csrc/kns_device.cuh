@@ -84,6 +84,8 @@ struct GridView {
     float oscale[3];      // occ_res / (bmax - bmin)
     float ovox[3];        // voxel edge (bmax - bmin) / occ_res
     float beta, inv_beta;
+    const uint32_t *occ_coarse;  // bit per block of 8^3 voxels: any voxel occupied (NULL = none)
+    int cres;                    // blocks per axis (occ_res / 8)
 };
 
 // ------------------------------------------------------------------ activations
@@ -383,6 +385,28 @@ __device__ __forceinline__ bool clip_box(const GridView &g, const Ray &r, float 
 __device__ __forceinline__ float dda_face_t(float bmin, int v, bool up, float vox, float o, float w) {
     return w == 0.f ? INFINITY : (bmin + (float)(v + (up ? 1 : 0)) * vox - o) / w;
 }
+__device__ __forceinline__ bool coarse_empty(const GridView &g, int vx, int vy, int vz) {
+    if (!g.occ_coarse) return false;
+    return !occ_test(g.occ_coarse, g.cres, vx >> 3, vy >> 3, vz >> 3);
+}
+
+// Fine voxel index along one axis at parameter t, or -1 when x(t) lies within 1e-3 voxel of a
+// voxel face (where rounding could disagree with the face-by-face walk).
+__device__ __forceinline__ int unambiguous_index(float o, float w, float t, float bmin, float scale, int res) {
+    const float u = (fmaf(t, w, o) - bmin) * scale;
+    const float f = floorf(u);
+    if (u - f < 1e-3f || f + 1.f - u < 1e-3f) return -1;
+    return (int)fminf(fmaxf(f, 0.f), (float)(res - 1));
+}
+
+// Integer 3D-DDA (Amanatides & Woo) from voxel (vx, vy, vz) to the entry of the next occupied voxel.
+// Returns true with te and the voxel updated; false when the ray leaves the grid or passes tf.
+// The crossing parameter of each axis is (face - o) / w with the face coordinate exact; after a
+// step only the crossed axis' value changes, so only it is recomputed.  Blocks of 8^3 voxels that
+// the coarse mask marks empty are crossed in one step: the exit face is found among the block's
+// faces with the same formula and tie rule, and the other two voxel indices at the exit are taken
+// from the position there unless it lies within 1e-3 voxel of a face, in which case the block is
+// walked voxel by voxel.  Either way the voxel and parameter reached are those of the voxel walk.
 __device__ __forceinline__ bool dda_next(const GridView &g, const Ray &r, int &vx, int &vy, int &vz, float tf,
                                          float &te) {
     const int res = g.occ_res;
@@ -392,6 +416,50 @@ __device__ __forceinline__ bool dda_next(const GridView &g, const Ray &r, int &v
     float tz = dda_face_t(g.bmin[2], vz, uz, g.ovox[2], r.oz, r.wz);
     // at most 3*res voxel crossings before the ray leaves the grid
     for (int guard = 0; guard < 3 * res + 3; ++guard) {
+        if (coarse_empty(g, vx, vy, vz)) {
+            // the last voxel of this block along each axis in the direction of travel
+            const int bx = ux ? (vx | 7) : (vx & ~7), by = uy ? (vy | 7) : (vy & ~7), bz = uz ? (vz | 7) : (vz & ~7);
+            const float Tx = dda_face_t(g.bmin[0], bx, ux, g.ovox[0], r.ox, r.wx);
+            const float Ty = dda_face_t(g.bmin[1], by, uy, g.ovox[1], r.oy, r.wy);
+            const float Tz = dda_face_t(g.bmin[2], bz, uz, g.ovox[2], r.oz, r.wz);
+            int nx, ny, nz, va;
+            float T;
+            if (Tx <= Ty && Tx <= Tz) {
+                T = Tx;
+                nx = bx + (ux ? 1 : -1);
+                ny = unambiguous_index(r.oy, r.wy, T, g.bmin[1], g.oscale[1], res);
+                nz = unambiguous_index(r.oz, r.wz, T, g.bmin[2], g.oscale[2], res);
+                va = nx;
+            } else if (Ty <= Tz) {
+                T = Ty;
+                ny = by + (uy ? 1 : -1);
+                nx = unambiguous_index(r.ox, r.wx, T, g.bmin[0], g.oscale[0], res);
+                nz = unambiguous_index(r.oz, r.wz, T, g.bmin[2], g.oscale[2], res);
+                va = ny;
+            } else {
+                T = Tz;
+                nz = bz + (uz ? 1 : -1);
+                nx = unambiguous_index(r.ox, r.wx, T, g.bmin[0], g.oscale[0], res);
+                ny = unambiguous_index(r.oy, r.wy, T, g.bmin[1], g.oscale[1], res);
+                va = nz;
+            }
+            if (nx >= 0 && ny >= 0 && nz >= 0) {
+                if (va < 0 || va >= res) return false;  // left the grid inside empty space
+                if (T > tf) return false;
+                vx = nx;
+                vy = ny;
+                vz = nz;
+                if (occ_test(g.occ, res, vx, vy, vz)) {
+                    te = T;
+                    return true;
+                }
+                tx = dda_face_t(g.bmin[0], vx, ux, g.ovox[0], r.ox, r.wx);
+                ty = dda_face_t(g.bmin[1], vy, uy, g.ovox[1], r.oy, r.wy);
+                tz = dda_face_t(g.bmin[2], vz, uz, g.ovox[2], r.oz, r.wz);
+                continue;
+            }
+            // ambiguous exit: walk this block voxel by voxel
+        }
         float tm;
         int va;
         if (tx <= ty && tx <= tz) {  // ties go to the lowest axis

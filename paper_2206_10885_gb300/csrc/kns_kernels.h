@@ -86,6 +86,7 @@ cudaError_t launch_wave_shade(const Shape &sh, const GridView &g, const WaveArgs
 cudaError_t launch_wave_eval_bf16(const Shape &sh, const GridView &g, const WaveArgs &a, int cur, int blocks,
                                   cudaStream_t s);
 cudaError_t launch_wave_scan(const WaveArgs &a, int cur, cudaStream_t s);
+cudaError_t launch_coarse_occupancy(const uint32_t *occ, int res, uint32_t *coarse, cudaStream_t s);
 cudaError_t launch_wave_scatter(const WaveArgs &a, int cur, int blocks, cudaStream_t s);
 
 cudaError_t launch_sdf_f32(const Shape &sh, const GridView &g, const float *pts, int64_t n, float *sdf,

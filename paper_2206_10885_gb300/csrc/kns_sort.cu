@@ -119,6 +119,31 @@ __global__ void __launch_bounds__(256) wave_scatter_kernel(WaveArgs a, int cur) 
     }
 }
 
+// Coarse occupancy: block (bx, by, bz) of 8^3 voxels is set iff any of its voxels is occupied.
+// The 8 voxels of a block row are 8 consecutive bits of one 32-bit word (res % 8 == 0).
+__global__ void coarse_occupancy_kernel(const uint32_t *occ, int res, uint32_t *coarse) {
+    const int cres = res / 8;
+    const int64_t nb = (int64_t)cres * cres * cres;
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool any = false;
+    if (b < nb) {
+        const int bx = (int)(b % cres), by = (int)((b / cres) % cres), bz = (int)(b / ((int64_t)cres * cres));
+        for (int z = 0; z < 8 && !any; ++z)
+            for (int y = 0; y < 8 && !any; ++y) {
+                const int64_t v = 8 * bx + (int64_t)res * ((8 * by + y) + (int64_t)res * (8 * bz + z));
+                any = ((occ[v >> 5] >> (v & 31)) & 0xffu) != 0;
+            }
+    }
+    const unsigned ball = __ballot_sync(FULL, any);
+    if ((threadIdx.x & 31) == 0 && b < nb) coarse[b >> 5] = ball;
+}
+
+cudaError_t launch_coarse_occupancy(const uint32_t *occ, int res, uint32_t *coarse, cudaStream_t s) {
+    const int64_t nb = (int64_t)(res / 8) * (res / 8) * (res / 8);
+    coarse_occupancy_kernel<<<(unsigned)((nb + 127) / 128), 128, 0, s>>>(occ, res, coarse);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_wave_scan(const WaveArgs &a, int cur, cudaStream_t s) {
     wave_scan_kernel<<<1, SCAN_THREADS, 0, s>>>(a, cur);
     return cudaGetLastError();
