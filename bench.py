@@ -273,12 +273,12 @@ def run_kns(args, rank, world, local_rank):
         step()
     ctx.sync(stream)
     launches_per_step = count_launches(step)
-    # algorithmic units of one launch: SDF evaluations (trace samples) and hits
-    steps_np = frame[0]["steps"].cpu().numpy().astype(np.int64)
-    hits = int(frame[0]["hit"].sum().item())
-    samples = int(steps_np.sum())
+    # algorithmic units of one render, from the library's own counters: SDF evaluations per precision
+    # and converged rays; per-kernel-class device time from a render timed with CUDA events
+    tuning_t = dict(tuning or {}, timing=1)
+    kns.render(ctx, grid, cams, W, H, ms, eps, precision=precision, out=frame, stream=stream, tuning=tuning_t)
+    st = ctx.render_stats()
     mac_trace, mac_hit = mac_counts(desc)
-    flop_per_launch = 2.0 * (samples * mac_trace + hits * mac_hit)
 
     clocks = ClockSampler(local_rank).start() if rank == 0 else None
     if world > 1:
@@ -295,7 +295,7 @@ def run_kns(args, rank, world, local_rank):
         dist.barrier()
     times = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(times)
-    st = ctx.sync(stream)
+    ctx.sync(stream)
     # e2e through the public API: cameras from host memory, outputs read back to pinned host buffers
     host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in frame[0].items()
             if k in ("rgb", "depth", "normal", "hit")}
@@ -329,13 +329,27 @@ def run_kns(args, rank, world, local_rank):
         peaks = load_peaks()
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
-        achieved = flop_per_launch / (ms_per_step * 1e-3) / 1e12
-        kernel_tag = "render_%s_%s" % (args.precision, args.workload)
-        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": profile_traffic(kernel_tag),
-                "kernel": kernel_tag, "peak_source": FP32_PEAK_NOTE,
-                "flop_per_launch": flop_per_launch, "sdf_evaluations_per_launch": samples,
-                "hits_per_launch": hits}
+        if precision == kns.KNS_FP32:
+            # dominant kernel: the FP32 tile evaluation (wave_eval_kernel), FMA-bound
+            flops = 2.0 * st["samples_fp32"] * mac_trace
+            kms = st["ms_eval_fp32"]
+            roof = {"bound": "alu", "peak": fp32_peak, "unit": "TFLOP/s", "kernel": "wave_eval_kernel",
+                    "peak_source": FP32_PEAK_NOTE}
+        else:
+            # dominant kernel: the BF16 tensor-core tile evaluation (wave_eval_bf16_kernel)
+            flops = 2.0 * st["samples_bf16"] * mac_trace
+            kms = st["ms_eval_bf16"]
+            roof = {"bound": "tensor", "peak": float(peaks.get("bf16_tflops", 1944.1)), "unit": "TFLOP/s",
+                    "kernel": "wave_eval_bf16_kernel", "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured)"}
+        achieved = flops / (kms * 1e-3) / 1e12 if kms > 0 else 0.0
+        launches = st["rounds"]
+        kernel_tag = "%s_%s_%s" % (roof["kernel"], args.precision, args.workload)
+        roof.update({"achieved": achieved, "frac": achieved / roof["peak"], "traffic": profile_traffic(kernel_tag),
+                     "launches_per_render": launches, "algorithmic_flop_per_render": flops,
+                     "kernel_ms_per_render": kms, "flop_per_sample": 2 * mac_trace})
+        phases = {k: st[k] for k in ("ms_generate", "ms_sort", "ms_eval_fp32", "ms_eval_bf16", "ms_shade",
+                                     "ms_total")}
+        counts = {k: st[k] for k in ("rounds", "rays", "hits", "samples_fp32", "samples_bf16")}
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             v, n, s, cores = oracle_rate(desc, w, cams, W, H, ms, eps, args.cpu_seconds)
@@ -348,7 +362,7 @@ def run_kns(args, rank, world, local_rank):
                 "data": "synthetic",
                 "config": dict(workload_config(args.workload, desc, cams, W, H, ms, eps, args.precision),
                                parallelism="replicas" if world > 1 else "single GPU"),
-                "roofline": roof, "cpu_baseline": cpu,
+                "roofline": roof, "cpu_baseline": cpu, "phases_ms_per_render": phases, "counts_per_render": counts,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
                 "clocks": clock_info, "gpu_launches": args.steps * launches_per_step, "tuning": tuning,

@@ -119,7 +119,19 @@ typedef struct kns_render_opts {
     int32_t tail_rays;     /* a round with at most this many rays is finished one thread per ray (>= 0; -1: never) */
     int32_t blocks_per_sm; /* evaluation blocks (one warp each) launched per SM (1..64) */
     int32_t static_tiles;  /* 1: each block takes a contiguous run of tiles; 2: tiles handed out dynamically */
+    int32_t timing;        /* 1: time each kernel class with CUDA events for kns_get_render_stats (adds host work) */
 } kns_render_opts;
+
+/* Counters of the last kns_render on a context (kns_get_render_stats). */
+typedef struct kns_render_stats {
+    int32_t rounds;        /* sort + evaluate rounds that ran */
+    int64_t rays;          /* primary rays */
+    int64_t hits;          /* rays that converged (shaded) */
+    int64_t samples_fp32;  /* SDF evaluations in FP32 (sphere-trace samples, refinement included) */
+    int64_t samples_bf16;  /* SDF evaluations in BF16 */
+    /* device time (ms) per kernel class, summed over the render's launches; 0 unless opts->timing */
+    float ms_generate, ms_sort, ms_eval_fp32, ms_eval_bf16, ms_shade, ms_total;
+} kns_render_stats;
 
 /* ---------------------------------------------------------------- context */
 
@@ -177,6 +189,10 @@ kns_status kns_copy_occupancy(kns_ctx *ctx, const kns_grid *grid, uint64_t *host
 kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams, int n_cams,
                       int W, int H, int max_steps, float eps, const kns_render_opts *opts,
                       const kns_frame *out, void *cuda_stream);
+
+/* Counters (and, when the render ran with opts->timing = 1, per-kernel-class device times) of the last
+ * kns_render on this context.  Waits for that render to finish.  Errors: INVALID_ARG (no render yet), CUDA. */
+kns_status kns_get_render_stats(kns_ctx *ctx, kns_render_stats *out);
 
 /* Batch field query (the vectorised per-cell MLP query of Sec. 3.3): for n points (device,
  * n x 3 FP32, row-major) evaluate the SDF MLP of cell m(x): sdf (device, n floats), feat (device,

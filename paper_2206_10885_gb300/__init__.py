@@ -30,6 +30,10 @@ class Context:
     def sync(self, stream=None, timeout_ms: int = -1) -> None:
         capi.kns_sync(self.handle, _stream_ptr(stream), timeout_ms)
 
+    def render_stats(self) -> dict:
+        """Counters (and per-kernel-class device ms when rendered with tuning={'timing': 1}) of the last render."""
+        return capi.kns_get_render_stats(self.handle)
+
     def close(self) -> None:
         if self.handle:
             capi.kns_destroy(self.handle)
@@ -88,7 +92,7 @@ def alloc_frame(n_pix: int, device="cuda", extras: bool = True):
     return t, f
 
 
-TUNING_FIELDS = ("inner_steps", "min_active", "tail_rays", "blocks_per_sm", "static_tiles")
+TUNING_FIELDS = ("inner_steps", "min_active", "tail_rays", "blocks_per_sm", "static_tiles", "timing")
 
 
 def render_opts(precision: int = KNS_FP32, eps_coarse: float = 0.0, refine_steps: int = -1, tuning=None):

@@ -54,7 +54,14 @@ class kns_frame(C.Structure):
 class kns_render_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("eps_coarse", C.c_float), ("refine_steps", C.c_int32),
                 ("inner_steps", C.c_int32), ("min_active", C.c_int32), ("tail_rays", C.c_int32),
-                ("blocks_per_sm", C.c_int32), ("static_tiles", C.c_int32)]
+                ("blocks_per_sm", C.c_int32), ("static_tiles", C.c_int32), ("timing", C.c_int32)]
+
+
+class kns_render_stats(C.Structure):
+    _fields_ = [("rounds", C.c_int32), ("rays", C.c_int64), ("hits", C.c_int64), ("samples_fp32", C.c_int64),
+                ("samples_bf16", C.c_int64), ("ms_generate", C.c_float), ("ms_sort", C.c_float),
+                ("ms_eval_fp32", C.c_float), ("ms_eval_bf16", C.c_float), ("ms_shade", C.c_float),
+                ("ms_total", C.c_float)]
 
 
 _lib = None
@@ -97,6 +104,8 @@ def lib():
             L.kns_render_noalloc.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float,
                                              C.POINTER(kns_frame), vp]
             L.kns_render_noalloc.restype = st
+            L.kns_get_render_stats.argtypes = [vp, C.POINTER(kns_render_stats)]
+            L.kns_get_render_stats.restype = st
             _lib = L
     return _lib
 
@@ -170,6 +179,12 @@ def kns_render(ctx: int, grid: int, cams_host_ptr: int, n_cams: int, W: int, H: 
     _check(lib().kns_render(ctx, grid, cams_host_ptr, n_cams, W, H, max_steps, eps,
                             C.byref(opts) if opts is not None else None,
                             C.byref(frame) if frame is not None else None, stream), ctx)
+
+
+def kns_get_render_stats(ctx: int) -> dict:
+    st = kns_render_stats()
+    _check(lib().kns_get_render_stats(ctx, C.byref(st)), ctx)
+    return {k: getattr(st, k) for k, _ in kns_render_stats._fields_}
 
 
 def kns_sdf(ctx: int, grid: int, pts_ptr: int, n: int, sdf_ptr: int, feat_ptr: int = None, grad_ptr: int = None,

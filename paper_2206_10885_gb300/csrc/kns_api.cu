@@ -37,6 +37,13 @@ struct kns_ctx {
     WaveScratch ws;
     int *h_live = nullptr;                 // pinned: live-sample counts of recent rounds
     cudaEvent_t ev_live[4] = {nullptr, nullptr, nullptr, nullptr};
+    // last render's statistics
+    bool have_stats = false;
+    kns_render_stats stats{};
+    cudaStream_t stats_stream = nullptr;
+    std::vector<cudaEvent_t> ev_pool;                   // timing events (created on demand)
+    std::vector<std::pair<int, int>> ev_marks;          // (kernel class, index of the begin event)
+    size_t ev_used = 0;
 };
 
 struct kns_grid {
@@ -286,6 +293,27 @@ constexpr int kRenderTailRays = 4096;  // rounds this small finish one thread pe
 constexpr int kRenderBlocksPerSM = 16;
 constexpr int kRenderStaticTiles = 2;
 
+// Kernel classes timed by kns_render when opts->timing is set.
+enum { kTGen = 0, kTSort = 1, kTEvalF32 = 2, kTEvalBF16 = 3, kTShade = 4 };
+
+// Records a begin event for a kernel class; returns its index (or -1 when timing is off).
+int timing_begin(kns_ctx *ctx, bool on, int cls, cudaStream_t s) {
+    if (!on) return -1;
+    while (ctx->ev_pool.size() < ctx->ev_used + 2) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        ctx->ev_pool.push_back(e);
+    }
+    const int i = (int)ctx->ev_used;
+    ctx->ev_used += 2;
+    cudaEventRecord(ctx->ev_pool[i], s);
+    ctx->ev_marks.push_back({cls, i});
+    return i;
+}
+void timing_end(kns_ctx *ctx, int i, cudaStream_t s) {
+    if (i >= 0) cudaEventRecord(ctx->ev_pool[i + 1], s);
+}
+
 // Grows the context's wavefront scratch to hold `rays` rays, `nc` cells and `cams` cameras.
 kns_status ensure_scratch(kns_ctx *ctx, int64_t rays, int nc, int cams) {
     WaveScratch &w = ctx->ws;
@@ -370,6 +398,7 @@ void kns_destroy(kns_ctx *ctx) {
         cudaFreeHost(ctx->h_live);
         for (int i = 0; i < 4; ++i)
             if (ctx->ev_live[i]) cudaEventDestroy(ctx->ev_live[i]);
+        for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
     }
     delete ctx;
 }
@@ -637,6 +666,13 @@ kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams
     if ((int64_t)W * H > INT32_MAX) return set_err(ctx, KNS_ERR_INVALID_ARG, "W*H exceeds 2^31-1");
     DeviceScope ds(ctx->device);
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    const bool timing = opts && opts->timing == 1;
+    ctx->ev_marks.clear();
+    ctx->ev_used = 0;
+    ctx->stats = kns_render_stats{};
+    ctx->stats.rays = (int64_t)n_cams * W * H;
+    ctx->stats_stream = s;
+    ctx->have_stats = false;
     const int64_t hw = (int64_t)W * H;
     const int per_chunk = (int)std::max<int64_t>(1, std::min<int64_t>(n_cams, (int64_t)INT32_MAX / hw));
     const int NC = grid->desc.N * grid->desc.N * grid->desc.N;
@@ -694,7 +730,11 @@ kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams
         cudaError_t e = cudaMemcpyAsync(w.d_cams, &cams[c0], sizeof(kns_camera) * nc, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.ctrl, 0, sizeof(kns::WaveCtrl), s);
         if (e == cudaSuccess) e = cudaMemsetAsync(w.cellbuf, 0, sizeof(int) * 4 * (nkeys + 1), s);
-        if (e == cudaSuccess) e = kns::launch_wave_gen(grid->shape, grid->view, a, s);
+        if (e == cudaSuccess) {
+            const int tm = timing_begin(ctx, timing, kTGen, s);
+            e = kns::launch_wave_gen(grid->shape, grid->view, a, s);
+            timing_end(ctx, tm, s);
+        }
         const int eval_blocks = ctx->sm_count * blocks_per_sm, scatter_blocks = ctx->sm_count * 4;
         // Rounds: at most max_steps (each live ray takes >= 1 step per round).  The host reads the
         // live count of round k-2 before launching round k and stops once a round was empty, so it
@@ -705,19 +745,68 @@ kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams
                 e = cudaEventSynchronize(ctx->ev_live[(k - 2) & 3]);
                 if (e != cudaSuccess || ctx->h_live[(k - 2) & 3] == 0) break;
             }
+            ++ctx->stats.rounds;
+            int tm = timing_begin(ctx, timing, kTSort, s);
             e = kns::launch_wave_scan(a, cur, s);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(ctx->h_live + (k & 3), &w.ctrl->n_live[cur], sizeof(int), cudaMemcpyDeviceToHost,
                                     s);
             if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_live[k & 3], s);
             if (e == cudaSuccess) e = kns::launch_wave_scatter(a, cur, scatter_blocks, s);
+            timing_end(ctx, tm, s);
+            tm = timing_begin(ctx, timing, kTEvalF32, s);
             if (e == cudaSuccess) e = kns::launch_wave_eval(grid->shape, grid->view, a, cur, eval_blocks, s);
-            if (e == cudaSuccess && bf16)
+            timing_end(ctx, tm, s);
+            if (e == cudaSuccess && bf16) {
+                tm = timing_begin(ctx, timing, kTEvalBF16, s);
                 e = kns::launch_wave_eval_bf16(grid->shape, grid->view, a, cur, eval_blocks, s);
+                timing_end(ctx, tm, s);
+            }
         }
-        if (e == cudaSuccess) e = kns::launch_wave_shade(grid->shape, grid->view, a, ctx->sm_count * 8, s);
+        if (e == cudaSuccess) {
+            const int tm = timing_begin(ctx, timing, kTShade, s);
+            e = kns::launch_wave_shade(grid->shape, grid->view, a, ctx->sm_count * 8, s);
+            timing_end(ctx, tm, s);
+        }
         if (e != cudaSuccess) return cuda_err(ctx, e, "render launch");
+        // counters of this chunk (the last chunk's device counters are read by kns_get_render_stats)
+        if (c0 + per_chunk < n_cams) {
+            kns::WaveCtrl hc;
+            e = cudaMemcpyAsync(&hc, w.ctrl, sizeof(hc), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return cuda_err(ctx, e, "render counters");
+            ctx->stats.hits += hc.n_hits;
+            ctx->stats.samples_fp32 += (int64_t)hc.samples_f32;
+            ctx->stats.samples_bf16 += (int64_t)hc.samples_bf16;
+        }
     }
+    ctx->have_stats = true;
+    return KNS_OK;
+}
+
+kns_status kns_get_render_stats(kns_ctx *ctx, kns_render_stats *out) {
+    if (!ctx) return KNS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!out) return set_err(ctx, KNS_ERR_INVALID_ARG, "NULL out");
+    if (!ctx->have_stats) return set_err(ctx, KNS_ERR_INVALID_ARG, "no render on this context yet");
+    DeviceScope ds(ctx->device);
+    kns::WaveCtrl hc{};
+    cudaError_t e = cudaSuccess;
+    if (ctx->ws.ctrl) e = cudaMemcpyAsync(&hc, ctx->ws.ctrl, sizeof(hc), cudaMemcpyDeviceToHost, ctx->stats_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stats_stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "render stats");
+    kns_render_stats st = ctx->stats;
+    st.hits += hc.n_hits;
+    st.samples_fp32 += (int64_t)hc.samples_f32;
+    st.samples_bf16 += (int64_t)hc.samples_bf16;
+    float *dst[5] = {&st.ms_generate, &st.ms_sort, &st.ms_eval_fp32, &st.ms_eval_bf16, &st.ms_shade};
+    for (const auto &m : ctx->ev_marks) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->ev_pool[m.second], ctx->ev_pool[m.second + 1]) == cudaSuccess)
+            *dst[m.first] += ms;
+    }
+    st.ms_total = st.ms_generate + st.ms_sort + st.ms_eval_fp32 + st.ms_eval_bf16 + st.ms_shade;
+    *out = st;
     return KNS_OK;
 }
 

@@ -216,6 +216,10 @@ __global__ void __launch_bounds__(32) wave_eval_bf16_kernel(GridView g, WaveArgs
             }
             __syncwarp();
             const float d = tile_sdf_bf16<C>(wsm, pe, lane, g.beta, g.inv_beta);
+            {
+                const unsigned n = __popc(__ballot_sync(FULL, active) & 0xffffu);
+                if (lane == 0) atomicAdd(&a.ctrl->samples_bf16, (unsigned long long)n);
+            }
             __syncwarp();
             bool emit = false;
             int nkey = -1;

@@ -22,6 +22,8 @@ struct WaveCtrl {
     int tail;          // 1: the current round is small enough to finish one thread per ray
     int n_tiles_fine;  // tiles of FP32 samples (keys < NC); BF16 tiles follow them
     int next_tile_bf;  // dynamic tile counter of the BF16 tiles
+    unsigned long long samples_f32;   // SDF evaluations in FP32 tiles and the per-thread tail
+    unsigned long long samples_bf16;  // SDF evaluations in BF16 tiles
 };
 
 // Everything the wavefront kernels read and write (device pointers; passed by value).

@@ -171,6 +171,7 @@ __device__ __noinline__ void finish_ray_f32(const GridView &g, const WaveArgs &a
         const float d = sdf_trace_f32<C>(g.w + (int64_t)cell * g.cell_stride, fmaf(t, ray.wx, ray.ox),
                                          fmaf(t, ray.wy, ray.oy), fmaf(t, ray.wz, ray.oz), g.beta, g.inv_beta);
         ++steps;
+        atomicAdd(&a.ctrl->samples_f32, 1ull);
         if (fabsf(d) < a.eps) {
             a.cell_ray[r] = cell;
             a.t_ray[r] = t;
@@ -288,6 +289,10 @@ __global__ void __launch_bounds__(32) wave_eval_kernel(GridView g, WaveArgs a, i
             }
             __syncwarp();
             const float d = tile_sdf_f32<C>(wsm, hin, P, Q, lane, g.beta, g.inv_beta);
+            {
+                const unsigned n = __popc(__ballot_sync(FULL, active) & 0xffffu);
+                if (lane == 0) atomicAdd(&a.ctrl->samples_f32, (unsigned long long)n);
+            }
             bool hit = false, emit = false;
             int ncell = -1;
             // a thinned-out tile hands its remaining rays to the next round, where they are
