@@ -162,21 +162,6 @@ def kernel_source_hash() -> str:
     return h.hexdigest()
 
 
-def count_launches(step) -> int:
-    """Kernels one render launches, counted with the torch profiler's CUDA activity (untimed)."""
-    import torch
-    from torch.profiler import ProfilerActivity, profile
-    torch.cuda.synchronize()
-    with profile(activities=[ProfilerActivity.CUDA]) as prof:
-        step()
-        torch.cuda.synchronize()
-    n = 0
-    for ev in prof.events():
-        if ev.device_type == torch.autograd.DeviceType.CUDA and "kns::" in ev.name:
-            n += 1
-    return n
-
-
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -272,13 +257,15 @@ def run_kns(args, rank, world, local_rank):
     for _ in range(max(3, args.warmup)):
         step()
     ctx.sync(stream)
-    launches_per_step = count_launches(step)
     # algorithmic units of one render, from the library's own counters: SDF evaluations per precision
     # and converged rays; per-kernel-class device time from a render timed with CUDA events
     tuning_t = dict(tuning or {}, timing=1)
     kns.render(ctx, grid, cams, W, H, ms, eps, precision=precision, out=frame, stream=stream, tuning=tuning_t)
     st = ctx.render_stats()
     mac_trace, mac_hit = mac_counts(desc)
+    # kernels one render launches: generate, per round scan + scatter + FP32 eval + FP32 tail
+    # (+ BF16 eval), shade; counted from the library's round counter
+    launches_per_step = 2 + st["rounds"] * (4 + (1 if precision == kns.KNS_BF16 else 0))
 
     clocks = ClockSampler(local_rank).start() if rank == 0 else None
     if world > 1:
@@ -366,6 +353,7 @@ def run_kns(args, rank, world, local_rank):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
                 "clocks": clock_info, "gpu_launches": args.steps * launches_per_step, "tuning": tuning,
+                "launch_count_source": "library round counter: 2 + rounds x (scan, scatter, eval, tail[, bf16 eval])",
                 "step_ms_min": min(times), "step_ms_median": statistics.median(times)}
         print(json.dumps(line), flush=True)
     grid.free()
