@@ -194,6 +194,23 @@ kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams
  * kns_render on this context.  Waits for that render to finish.  Errors: INVALID_ARG (no render yet), CUDA. */
 kns_status kns_get_render_stats(kns_ctx *ctx, kns_render_stats *out);
 
+/* One view of a multi-view render: camera, image size and its own output buffers (device pointers for
+ * W*H pixels, layout as kns_frame). */
+typedef struct kns_view {
+    kns_camera cam;
+    int32_t W, H;
+    kns_frame out;
+} kns_view;
+
+/* Sphere-trace and shade several views of one grid in one launch sequence (Sec. 3.4.1): the views may
+ * differ in camera and resolution (requests of a render server).  views: host array, read before the
+ * call returns; each view writes only its own buffers, and every pixel gets the same result as a
+ * kns_render of that view alone.  Views with W*H = 0 are skipped.  Errors: INVALID_ARG (NULL grid or
+ * views, a view with negative size or without rgb/depth, more than 2^31-1 rays in total,
+ * max_steps < 1, eps <= 0, bad opts), CUDA, OUT_OF_MEMORY. */
+kns_status kns_render_views(kns_ctx *ctx, const kns_grid *grid, const kns_view *views, int n_views, int max_steps,
+                            float eps, const kns_render_opts *opts, void *cuda_stream);
+
 /* Batch field query (the vectorised per-cell MLP query of Sec. 3.3): for n points (device,
  * n x 3 FP32, row-major) evaluate the SDF MLP of cell m(x): sdf (device, n floats), feat (device,
  * n x feat_dim, or NULL), grad (device, n x 3 analytic input gradient, or NULL).

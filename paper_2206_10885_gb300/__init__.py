@@ -122,6 +122,26 @@ def render(ctx: Context, grid: Grid, cams: np.ndarray, W: int, H: int, max_steps
     return t
 
 
+def render_views(ctx: Context, grid: Grid, requests, max_steps: int, eps: float, precision: int = KNS_FP32,
+                 stream=None, outs=None, tuning=None, eps_coarse: float = 0.0, refine_steps: int = -1):
+    """kns_render_views: several (camera[16], W, H) views of one grid in one launch sequence.
+
+    Returns one dict of output tensors per request (allocated here unless `outs` gives them).
+    """
+    import ctypes as C
+    if outs is None:
+        outs = [alloc_frame(int(W) * int(H), "cuda:%d" % ctx.device) for _, W, H in requests]
+    arr = (capi.kns_view * max(1, len(requests)))()
+    for i, ((cam, W, H), (t, f)) in enumerate(zip(requests, outs)):
+        cam = np.ascontiguousarray(cam, dtype=np.float32).reshape(16)
+        C.memmove(C.addressof(arr[i].cam), cam.ctypes.data, 64)
+        arr[i].W, arr[i].H = int(W), int(H)
+        arr[i].out = f
+    capi.kns_render_views(ctx.handle, grid.handle, arr if requests else [], max_steps, eps,
+                          render_opts(precision, eps_coarse, refine_steps, tuning), _stream_ptr(stream))
+    return [t for t, _ in outs]
+
+
 def sdf(ctx: Context, grid: Grid, pts, want_feat: bool = True, want_grad: bool = True, stream=None):
     """kns_sdf on a (n, 3) float32 CUDA tensor; returns (d, feat, grad) tensors."""
     import torch

@@ -51,6 +51,10 @@ class kns_frame(C.Structure):
                 ("steps", C.c_void_p), ("hit", C.c_void_p)]
 
 
+class kns_view(C.Structure):
+    _fields_ = [("cam", kns_camera), ("W", C.c_int32), ("H", C.c_int32), ("out", kns_frame)]
+
+
 class kns_render_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("eps_coarse", C.c_float), ("refine_steps", C.c_int32),
                 ("inner_steps", C.c_int32), ("min_active", C.c_int32), ("tail_rays", C.c_int32),
@@ -104,6 +108,9 @@ def lib():
             L.kns_render_noalloc.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float,
                                              C.POINTER(kns_frame), vp]
             L.kns_render_noalloc.restype = st
+            L.kns_render_views.argtypes = [vp, vp, C.POINTER(kns_view), C.c_int, C.c_int, C.c_float,
+                                           C.POINTER(kns_render_opts), vp]
+            L.kns_render_views.restype = st
             L.kns_get_render_stats.argtypes = [vp, C.POINTER(kns_render_stats)]
             L.kns_get_render_stats.restype = st
             _lib = L
@@ -179,6 +186,21 @@ def kns_render(ctx: int, grid: int, cams_host_ptr: int, n_cams: int, W: int, H: 
     _check(lib().kns_render(ctx, grid, cams_host_ptr, n_cams, W, H, max_steps, eps,
                             C.byref(opts) if opts is not None else None,
                             C.byref(frame) if frame is not None else None, stream), ctx)
+
+
+def kns_render_views(ctx: int, grid: int, views, max_steps: int, eps: float, opts: kns_render_opts = None,
+                     stream: int = 0) -> None:
+    """views: a ctypes array of kns_view (or a list, converted here)."""
+    if not isinstance(views, C.Array):
+        arr = (kns_view * max(1, len(views)))()
+        for i, v in enumerate(views):
+            arr[i] = v
+        n = len(views)
+        views = arr
+    else:
+        n = len(views)
+    _check(lib().kns_render_views(ctx, grid, views, n, max_steps, eps,
+                                  C.byref(opts) if opts is not None else None, stream), ctx)
 
 
 def kns_get_render_stats(ctx: int) -> dict:

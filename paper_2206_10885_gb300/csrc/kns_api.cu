@@ -24,7 +24,8 @@ struct WaveScratch {
     int *steps_ray = nullptr, *cell_ray = nullptr, *q[2] = {nullptr, nullptr}, *qcell[2] = {nullptr, nullptr};
     int *sorted = nullptr, *hits = nullptr;
     int *cellbuf = nullptr;  // count[2], fill[2], off, tile_off (6 * (nc + 1) ints)
-    float *d_cams = nullptr;
+    int *ray_view = nullptr;
+    kns::ViewDev *d_views = nullptr;
     kns::WaveCtrl *ctrl = nullptr;
 };
 
@@ -279,7 +280,8 @@ void free_scratch(WaveScratch &w) {
     cudaFree(w.sorted);
     cudaFree(w.hits);
     cudaFree(w.cellbuf);
-    cudaFree(w.d_cams);
+    cudaFree(w.ray_view);
+    cudaFree(w.d_views);
     cudaFree(w.ctrl);
     w = WaveScratch{};
 }
@@ -337,7 +339,8 @@ kns_status ensure_scratch(kns_ctx *ctx, int64_t rays, int nc, int cams) {
     alloc(&w.sorted, sizeof(int) * R);
     alloc(&w.hits, sizeof(int) * R);
     alloc(&w.cellbuf, sizeof(int) * 6 * (size_t)(NC + 1));
-    alloc(&w.d_cams, sizeof(kns_camera) * NCAM);
+    alloc(&w.ray_view, sizeof(int) * R);
+    alloc(&w.d_views, sizeof(kns::ViewDev) * NCAM);
     alloc(&w.ctrl, sizeof(kns::WaveCtrl));
     if (e != cudaSuccess) {
         free_scratch(w);
@@ -632,6 +635,179 @@ kns_status kns_copy_occupancy(kns_ctx *ctx, const kns_grid *g, uint64_t *host_wo
     return KNS_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Render settings resolved from kns_render_opts.
+struct RenderCfg {
+    bool bf16 = false, timing = false;
+    float eps_coarse = 4e-3f;
+    int refine_steps = 2, inner_steps = kRenderInnerSteps, min_active = kRenderMinActive,
+        tail_rays = kRenderTailRays, blocks_per_sm = kRenderBlocksPerSM, static_tiles = 1;
+};
+
+kns_status resolve_opts(kns_ctx *ctx, const kns_render_opts *opts, float eps, RenderCfg &c) {
+    const int precision = opts ? opts->precision : KNS_FP32;
+    if (precision != KNS_FP32 && precision != KNS_BF16)
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "unknown precision %d", precision);
+    c.bf16 = precision == KNS_BF16;
+    c.eps_coarse = (c.bf16 && opts && opts->eps_coarse > 0.f) ? opts->eps_coarse : std::max(eps, 4e-3f);
+    c.refine_steps = (c.bf16 && opts && opts->refine_steps > 0) ? opts->refine_steps : 2;
+    if (c.bf16 && !(c.eps_coarse >= eps && std::isfinite(c.eps_coarse)))
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "eps_coarse must be finite and >= eps");
+    auto knob = [](int32_t v, int32_t def) { return v == 0 ? def : v; };
+    c.inner_steps = opts ? knob(opts->inner_steps, kRenderInnerSteps) : kRenderInnerSteps;
+    c.min_active = opts ? knob(opts->min_active, kRenderMinActive) : kRenderMinActive;
+    c.tail_rays = opts ? knob(opts->tail_rays, kRenderTailRays) : kRenderTailRays;
+    c.blocks_per_sm = opts ? knob(opts->blocks_per_sm, kRenderBlocksPerSM) : kRenderBlocksPerSM;
+    c.static_tiles = (opts ? knob(opts->static_tiles, kRenderStaticTiles) : kRenderStaticTiles) == 1;
+    if (c.inner_steps < 1 || c.inner_steps > 1024 || c.min_active < 1 || c.min_active > 16 || c.tail_rays < -1 ||
+        c.blocks_per_sm < 1 || c.blocks_per_sm > 64 || (opts && (opts->static_tiles < 0 || opts->static_tiles > 2)))
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "render tuning field out of range");
+    if (c.tail_rays < 0) c.tail_rays = 0;
+    if (c.bf16) c.tail_rays = 0;  // the per-thread tail evaluator is FP32 only
+    c.timing = opts && opts->timing == 1;
+    return KNS_OK;
+}
+
+void begin_stats(kns_ctx *ctx, cudaStream_t s, int64_t rays) {
+    ctx->ev_marks.clear();
+    ctx->ev_used = 0;
+    ctx->stats = kns_render_stats{};
+    ctx->stats.rays = rays;
+    ctx->stats_stream = s;
+    ctx->have_stats = false;
+}
+
+// Renders one batch of views (their rays numbered consecutively, fewer than 2^31) with the
+// wavefront: generate, rounds of sort + evaluate, shade.  `last` marks the final batch of a call,
+// whose device counters kns_get_render_stats reads later; earlier batches add theirs here.
+kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vector<kns::ViewDev> &views,
+                             int64_t rays, int max_steps, float eps, const RenderCfg &cfg, cudaStream_t s,
+                             bool last) {
+    const int NC = grid->desc.N * grid->desc.N * grid->desc.N;
+    const int nkeys = cfg.bf16 ? 2 * NC : NC;
+    const int nv = (int)views.size();
+    kns_status st = ensure_scratch(ctx, rays, nkeys, nv);
+    if (st != KNS_OK) return st;
+    WaveScratch &w = ctx->ws;
+    int max_W = 0, max_H = 0;
+    for (const auto &v : views) {
+        max_W = std::max(max_W, v.W);
+        max_H = std::max(max_H, v.H);
+    }
+    kns::WaveArgs a{};
+    a.n_views = nv;
+    a.max_W = max_W;
+    a.max_H = max_H;
+    a.views = w.d_views;
+    a.ray_view = w.ray_view;
+    a.max_steps = max_steps;
+    a.eps = eps;
+    a.NC = NC;
+    a.nkeys = nkeys;
+    a.coarse = cfg.bf16 ? 1 : 0;
+    a.eps_coarse = cfg.eps_coarse;
+    a.refine_steps = cfg.refine_steps;
+    a.wb = grid->d_wb;
+    a.wb_stride = grid->wb_stride;
+    a.btile = kRenderBlockTile;
+    a.inner_steps = cfg.inner_steps;
+    a.tail_max = cfg.tail_rays;
+    a.min_active = cfg.min_active;
+    a.static_tiles = cfg.static_tiles;
+    a.status = ctx->d_status;
+    a.wt = grid->d_wt;
+    a.wt_stride = grid->wt_stride;
+    a.t_ray = w.t_ray;
+    a.steps_ray = w.steps_ray;
+    a.cell_ray = w.cell_ray;
+    a.q[0] = w.q[0];
+    a.q[1] = w.q[1];
+    a.qcell[0] = w.qcell[0];
+    a.qcell[1] = w.qcell[1];
+    a.sorted = w.sorted;
+    a.hits = w.hits;
+    a.count[0] = w.cellbuf;
+    a.count[1] = w.cellbuf + (nkeys + 1);
+    a.fill[0] = w.cellbuf + 2 * (nkeys + 1);
+    a.fill[1] = w.cellbuf + 3 * (nkeys + 1);
+    a.off = w.cellbuf + 4 * (nkeys + 1);
+    a.tile_off = w.cellbuf + 5 * (nkeys + 1);
+    a.ctrl = w.ctrl;
+    cudaError_t e = cudaMemcpyAsync(w.d_views, views.data(), sizeof(kns::ViewDev) * nv, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.ctrl, 0, sizeof(kns::WaveCtrl), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.cellbuf, 0, sizeof(int) * 4 * (nkeys + 1), s);
+    if (e == cudaSuccess) {
+        const int tm = timing_begin(ctx, cfg.timing, kTGen, s);
+        e = kns::launch_wave_gen(grid->shape, grid->view, a, s);
+        timing_end(ctx, tm, s);
+    }
+    const int eval_blocks = ctx->sm_count * cfg.blocks_per_sm, scatter_blocks = ctx->sm_count * 4;
+    // Rounds: at most max_steps (each live ray takes >= 1 step per round).  The host reads the
+    // live count of round k-2 before launching round k and stops once a round was empty, so it
+    // runs at most two rounds ahead of the device.
+    for (int k = 0; k < max_steps && e == cudaSuccess; ++k) {
+        const int cur = k & 1;
+        if (k >= 2) {
+            e = cudaEventSynchronize(ctx->ev_live[(k - 2) & 3]);
+            if (e != cudaSuccess || ctx->h_live[(k - 2) & 3] == 0) break;
+        }
+        ++ctx->stats.rounds;
+        int tm = timing_begin(ctx, cfg.timing, kTSort, s);
+        e = kns::launch_wave_scan(a, cur, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->h_live + (k & 3), &w.ctrl->n_live[cur], sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_live[k & 3], s);
+        if (e == cudaSuccess) e = kns::launch_wave_scatter(a, cur, scatter_blocks, s);
+        timing_end(ctx, tm, s);
+        tm = timing_begin(ctx, cfg.timing, kTEvalF32, s);
+        if (e == cudaSuccess) e = kns::launch_wave_eval(grid->shape, grid->view, a, cur, eval_blocks, s);
+        timing_end(ctx, tm, s);
+        if (e == cudaSuccess && cfg.bf16) {
+            tm = timing_begin(ctx, cfg.timing, kTEvalBF16, s);
+            e = kns::launch_wave_eval_bf16(grid->shape, grid->view, a, cur, eval_blocks, s);
+            timing_end(ctx, tm, s);
+        }
+    }
+    if (e == cudaSuccess) {
+        const int tm = timing_begin(ctx, cfg.timing, kTShade, s);
+        e = kns::launch_wave_shade(grid->shape, grid->view, a, ctx->sm_count * 8, s);
+        timing_end(ctx, tm, s);
+    }
+    if (e != cudaSuccess) return cuda_err(ctx, e, "render launch");
+    if (!last) {
+        kns::WaveCtrl hc;
+        e = cudaMemcpyAsync(&hc, w.ctrl, sizeof(hc), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "render counters");
+        ctx->stats.hits += hc.n_hits;
+        ctx->stats.samples_fp32 += (int64_t)hc.samples_f32;
+        ctx->stats.samples_bf16 += (int64_t)hc.samples_bf16;
+    }
+    return KNS_OK;
+}
+
+kns::ViewDev make_view(const kns_camera &cam, int W, int H, int64_t ray_base, const kns_frame &out) {
+    kns::ViewDev v{};
+    std::memcpy(v.cam, &cam, sizeof(float) * 16);
+    v.rgb = out.rgb;
+    v.depth = out.depth;
+    v.normal = out.normal;
+    v.cell = out.cell;
+    v.steps = out.steps;
+    v.hit = out.hit;
+    v.W = W;
+    v.H = H;
+    v.ray_base = (int)ray_base;
+    return v;
+}
+
+}  // namespace
+
+extern "C" {
+
 kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams, int n_cams, int W, int H,
                       int max_steps, float eps, const kns_render_opts *opts, const kns_frame *out,
                       void *cuda_stream) {
@@ -643,143 +819,68 @@ kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams
     if (max_steps < 1) return set_err(ctx, KNS_ERR_INVALID_ARG, "max_steps=%d < 1", max_steps);
     if (!(eps > 0.f) || !std::isfinite(eps)) return set_err(ctx, KNS_ERR_INVALID_ARG, "eps must be > 0 and finite");
     if (!out->rgb || !out->depth) return set_err(ctx, KNS_ERR_INVALID_ARG, "rgb and depth buffers are required");
-    const int precision = opts ? opts->precision : KNS_FP32;
-    if (precision != KNS_FP32 && precision != KNS_BF16)
-        return set_err(ctx, KNS_ERR_INVALID_ARG, "unknown precision %d", precision);
-    const bool bf16 = precision == KNS_BF16;
-    const float eps_coarse = (bf16 && opts && opts->eps_coarse > 0.f) ? opts->eps_coarse : std::max(eps, 4e-3f);
-    const int refine_steps = (bf16 && opts && opts->refine_steps > 0) ? opts->refine_steps : 2;
-    if (bf16 && !(eps_coarse >= eps && std::isfinite(eps_coarse)))
-        return set_err(ctx, KNS_ERR_INVALID_ARG, "eps_coarse must be finite and >= eps");
-    auto knob = [](int32_t v, int32_t def) { return v == 0 ? def : v; };
-    const int inner_steps = opts ? knob(opts->inner_steps, kRenderInnerSteps) : kRenderInnerSteps;
-    const int min_active = opts ? knob(opts->min_active, kRenderMinActive) : kRenderMinActive;
-    int tail_rays = opts ? knob(opts->tail_rays, kRenderTailRays) : kRenderTailRays;
-    const int blocks_per_sm = opts ? knob(opts->blocks_per_sm, kRenderBlocksPerSM) : kRenderBlocksPerSM;
-    const int static_tiles = (opts ? knob(opts->static_tiles, kRenderStaticTiles) : kRenderStaticTiles) == 1;
-    if (inner_steps < 1 || inner_steps > 1024 || min_active < 1 || min_active > 16 || tail_rays < -1 ||
-        blocks_per_sm < 1 || blocks_per_sm > 64 || (opts && (opts->static_tiles < 0 || opts->static_tiles > 2)))
-        return set_err(ctx, KNS_ERR_INVALID_ARG, "render tuning field out of range");
-    if (tail_rays < 0) tail_rays = 0;
-    if (bf16) tail_rays = 0;  // the per-thread tail evaluator is FP32 only
+    RenderCfg cfg;
+    kns_status st = resolve_opts(ctx, opts, eps, cfg);
+    if (st != KNS_OK) return st;
     if (n_cams == 0 || W == 0 || H == 0) return KNS_OK;
     if ((int64_t)W * H > INT32_MAX) return set_err(ctx, KNS_ERR_INVALID_ARG, "W*H exceeds 2^31-1");
     DeviceScope ds(ctx->device);
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    const bool timing = opts && opts->timing == 1;
-    ctx->ev_marks.clear();
-    ctx->ev_used = 0;
-    ctx->stats = kns_render_stats{};
-    ctx->stats.rays = (int64_t)n_cams * W * H;
-    ctx->stats_stream = s;
-    ctx->have_stats = false;
+    begin_stats(ctx, s, (int64_t)n_cams * W * H);
     const int64_t hw = (int64_t)W * H;
     const int per_chunk = (int)std::max<int64_t>(1, std::min<int64_t>(n_cams, (int64_t)INT32_MAX / hw));
-    const int NC = grid->desc.N * grid->desc.N * grid->desc.N;
-    const int nkeys = bf16 ? 2 * NC : NC;
-    kns_status st = ensure_scratch(ctx, (int64_t)per_chunk * hw, nkeys, per_chunk);
-    if (st != KNS_OK) return st;
-    WaveScratch &w = ctx->ws;
+    std::vector<kns::ViewDev> views;
     for (int c0 = 0; c0 < n_cams; c0 += per_chunk) {
         const int nc = std::min(per_chunk, n_cams - c0);
-        const int64_t base = (int64_t)c0 * hw;
-        kns::WaveArgs a{};
-        a.W = W;
-        a.H = H;
-        a.n_cams = nc;
-        a.max_steps = max_steps;
-        a.eps = eps;
-        a.NC = NC;
-        a.nkeys = nkeys;
-        a.coarse = bf16 ? 1 : 0;
-        a.eps_coarse = eps_coarse;
-        a.refine_steps = refine_steps;
-        a.wb = grid->d_wb;
-        a.wb_stride = grid->wb_stride;
-        a.btile = kRenderBlockTile;
-        a.inner_steps = inner_steps;
-        a.tail_max = tail_rays;
-        a.min_active = min_active;
-        a.static_tiles = static_tiles;
-        a.status = ctx->d_status;
-        a.cams = w.d_cams;
-        a.wt = grid->d_wt;
-        a.wt_stride = grid->wt_stride;
-        a.rgb = out->rgb + 3 * base;
-        a.depth = out->depth + base;
-        a.normal = out->normal ? out->normal + 3 * base : nullptr;
-        a.cell_out = out->cell ? out->cell + base : nullptr;
-        a.steps_out = out->steps ? out->steps + base : nullptr;
-        a.hit_out = out->hit ? out->hit + base : nullptr;
-        a.t_ray = w.t_ray;
-        a.steps_ray = w.steps_ray;
-        a.cell_ray = w.cell_ray;
-        a.q[0] = w.q[0];
-        a.q[1] = w.q[1];
-        a.qcell[0] = w.qcell[0];
-        a.qcell[1] = w.qcell[1];
-        a.sorted = w.sorted;
-        a.hits = w.hits;
-        a.count[0] = w.cellbuf;
-        a.count[1] = w.cellbuf + (nkeys + 1);
-        a.fill[0] = w.cellbuf + 2 * (nkeys + 1);
-        a.fill[1] = w.cellbuf + 3 * (nkeys + 1);
-        a.off = w.cellbuf + 4 * (nkeys + 1);
-        a.tile_off = w.cellbuf + 5 * (nkeys + 1);
-        a.ctrl = w.ctrl;
-        cudaError_t e = cudaMemcpyAsync(w.d_cams, &cams[c0], sizeof(kns_camera) * nc, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(w.ctrl, 0, sizeof(kns::WaveCtrl), s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(w.cellbuf, 0, sizeof(int) * 4 * (nkeys + 1), s);
-        if (e == cudaSuccess) {
-            const int tm = timing_begin(ctx, timing, kTGen, s);
-            e = kns::launch_wave_gen(grid->shape, grid->view, a, s);
-            timing_end(ctx, tm, s);
+        views.clear();
+        for (int c = 0; c < nc; ++c) {
+            const int64_t base = (int64_t)(c0 + c) * hw;
+            kns_frame f{};
+            f.rgb = out->rgb + 3 * base;
+            f.depth = out->depth + base;
+            f.normal = out->normal ? out->normal + 3 * base : nullptr;
+            f.cell = out->cell ? out->cell + base : nullptr;
+            f.steps = out->steps ? out->steps + base : nullptr;
+            f.hit = out->hit ? out->hit + base : nullptr;
+            views.push_back(make_view(cams[c0 + c], W, H, (int64_t)c * hw, f));
         }
-        const int eval_blocks = ctx->sm_count * blocks_per_sm, scatter_blocks = ctx->sm_count * 4;
-        // Rounds: at most max_steps (each live ray takes >= 1 step per round).  The host reads the
-        // live count of round k-2 before launching round k and stops once a round was empty, so it
-        // runs at most two rounds ahead of the device.
-        for (int k = 0; k < max_steps && e == cudaSuccess; ++k) {
-            const int cur = k & 1;
-            if (k >= 2) {
-                e = cudaEventSynchronize(ctx->ev_live[(k - 2) & 3]);
-                if (e != cudaSuccess || ctx->h_live[(k - 2) & 3] == 0) break;
-            }
-            ++ctx->stats.rounds;
-            int tm = timing_begin(ctx, timing, kTSort, s);
-            e = kns::launch_wave_scan(a, cur, s);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(ctx->h_live + (k & 3), &w.ctrl->n_live[cur], sizeof(int), cudaMemcpyDeviceToHost,
-                                    s);
-            if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_live[k & 3], s);
-            if (e == cudaSuccess) e = kns::launch_wave_scatter(a, cur, scatter_blocks, s);
-            timing_end(ctx, tm, s);
-            tm = timing_begin(ctx, timing, kTEvalF32, s);
-            if (e == cudaSuccess) e = kns::launch_wave_eval(grid->shape, grid->view, a, cur, eval_blocks, s);
-            timing_end(ctx, tm, s);
-            if (e == cudaSuccess && bf16) {
-                tm = timing_begin(ctx, timing, kTEvalBF16, s);
-                e = kns::launch_wave_eval_bf16(grid->shape, grid->view, a, cur, eval_blocks, s);
-                timing_end(ctx, tm, s);
-            }
-        }
-        if (e == cudaSuccess) {
-            const int tm = timing_begin(ctx, timing, kTShade, s);
-            e = kns::launch_wave_shade(grid->shape, grid->view, a, ctx->sm_count * 8, s);
-            timing_end(ctx, tm, s);
-        }
-        if (e != cudaSuccess) return cuda_err(ctx, e, "render launch");
-        // counters of this chunk (the last chunk's device counters are read by kns_get_render_stats)
-        if (c0 + per_chunk < n_cams) {
-            kns::WaveCtrl hc;
-            e = cudaMemcpyAsync(&hc, w.ctrl, sizeof(hc), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess) return cuda_err(ctx, e, "render counters");
-            ctx->stats.hits += hc.n_hits;
-            ctx->stats.samples_fp32 += (int64_t)hc.samples_f32;
-            ctx->stats.samples_bf16 += (int64_t)hc.samples_bf16;
-        }
+        st = render_views_impl(ctx, grid, views, (int64_t)nc * hw, max_steps, eps, cfg, s, c0 + per_chunk >= n_cams);
+        if (st != KNS_OK) return st;
     }
+    ctx->have_stats = true;
+    return KNS_OK;
+}
+
+kns_status kns_render_views(kns_ctx *ctx, const kns_grid *grid, const kns_view *views, int n_views, int max_steps,
+                            float eps, const kns_render_opts *opts, void *cuda_stream) {
+    if (!ctx) return KNS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!grid || (n_views > 0 && !views)) return set_err(ctx, KNS_ERR_INVALID_ARG, "NULL grid or views");
+    if (n_views < 0 || n_views > (1 << 16)) return set_err(ctx, KNS_ERR_INVALID_ARG, "n_views out of range");
+    if (max_steps < 1) return set_err(ctx, KNS_ERR_INVALID_ARG, "max_steps=%d < 1", max_steps);
+    if (!(eps > 0.f) || !std::isfinite(eps)) return set_err(ctx, KNS_ERR_INVALID_ARG, "eps must be > 0 and finite");
+    RenderCfg cfg;
+    kns_status st = resolve_opts(ctx, opts, eps, cfg);
+    if (st != KNS_OK) return st;
+    std::vector<kns::ViewDev> dv;
+    int64_t rays = 0;
+    for (int i = 0; i < n_views; ++i) {
+        const kns_view &v = views[i];
+        if (v.W < 0 || v.H < 0) return set_err(ctx, KNS_ERR_INVALID_ARG, "view %d: negative size", i);
+        const int64_t n = (int64_t)v.W * v.H;
+        if (n == 0) continue;
+        if (!v.out.rgb || !v.out.depth)
+            return set_err(ctx, KNS_ERR_INVALID_ARG, "view %d: rgb and depth buffers are required", i);
+        if (rays + n > INT32_MAX) return set_err(ctx, KNS_ERR_INVALID_ARG, "views hold more than 2^31-1 rays");
+        dv.push_back(make_view(v.cam, v.W, v.H, rays, v.out));
+        rays += n;
+    }
+    if (dv.empty()) return KNS_OK;
+    DeviceScope ds(ctx->device);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    begin_stats(ctx, s, rays);
+    st = render_views_impl(ctx, grid, dv, rays, max_steps, eps, cfg, s, true);
+    if (st != KNS_OK) return st;
     ctx->have_stats = true;
     return KNS_OK;
 }
@@ -842,10 +943,10 @@ constexpr size_t kNoAllocAlign = 256;
 constexpr size_t align_up(size_t v) { return (v + kNoAllocAlign - 1) / kNoAllocAlign * kNoAllocAlign; }
 constexpr size_t kNoAllocRayBuf = align_up(sizeof(int) * (size_t)KNS_NOALLOC_MAX_RAYS);
 constexpr size_t kNoAllocCellBuf = align_up(sizeof(int) * 6 * (size_t)(KNS_NOALLOC_MAX_CELLS + 1));
-constexpr size_t kNoAllocCamBuf = align_up(sizeof(kns_camera) * (size_t)KNS_NOALLOC_MAX_CAMS);
+constexpr size_t kNoAllocViewBuf = align_up(sizeof(kns::ViewDev) * (size_t)KNS_NOALLOC_MAX_CAMS);
 constexpr size_t kNoAllocCtrlBuf = align_up(sizeof(kns::WaveCtrl));
-// t_ray, steps_ray, cell_ray, q[2], qcell[2], sorted, hits: nine per-ray int/float buffers
-constexpr size_t kNoAllocBytes = 9 * kNoAllocRayBuf + kNoAllocCellBuf + kNoAllocCamBuf + kNoAllocCtrlBuf;
+// t_ray, steps_ray, cell_ray, q[2], qcell[2], sorted, hits, ray_view: ten per-ray int/float buffers
+constexpr size_t kNoAllocBytes = 10 * kNoAllocRayBuf + kNoAllocCellBuf + kNoAllocViewBuf + kNoAllocCtrlBuf;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -911,8 +1012,9 @@ extern "C" kns_status kns_render_noalloc(kns_ctx *ctx, const kns_grid *grid, con
     a.qcell[1] = (int *)take(kNoAllocRayBuf);
     a.sorted = (int *)take(kNoAllocRayBuf);
     a.hits = (int *)take(kNoAllocRayBuf);
+    a.ray_view = (int *)take(kNoAllocRayBuf);
     int *cellbuf = (int *)take(kNoAllocCellBuf);
-    float *d_cams = (float *)take(kNoAllocCamBuf);
+    kns::ViewDev *d_views = (kns::ViewDev *)take(kNoAllocViewBuf);
     a.ctrl = (kns::WaveCtrl *)take(kNoAllocCtrlBuf);
     a.count[0] = cellbuf;
     a.count[1] = cellbuf + (NC + 1);
@@ -920,9 +1022,10 @@ extern "C" kns_status kns_render_noalloc(kns_ctx *ctx, const kns_grid *grid, con
     a.fill[1] = cellbuf + 3 * (NC + 1);
     a.off = cellbuf + 4 * (NC + 1);
     a.tile_off = cellbuf + 5 * (NC + 1);
-    a.W = W;
-    a.H = H;
-    a.n_cams = n_cams;
+    a.n_views = n_cams;
+    a.max_W = W;
+    a.max_H = H;
+    a.views = d_views;
     a.max_steps = max_steps;
     a.eps = eps;
     a.NC = NC;
@@ -933,17 +1036,24 @@ extern "C" kns_status kns_render_noalloc(kns_ctx *ctx, const kns_grid *grid, con
     a.min_active = kRenderMinActive;
     a.static_tiles = kRenderStaticTiles == 1;
     a.status = ctx->d_status;
-    a.cams = d_cams;
     a.wt = grid->d_wt;
     a.wt_stride = grid->wt_stride;
-    a.rgb = out->rgb;
-    a.depth = out->depth;
-    a.normal = out->normal;
-    a.cell_out = out->cell;
-    a.steps_out = out->steps;
-    a.hit_out = out->hit;
+    kns::ViewDev hv[KNS_NOALLOC_MAX_CAMS];  // host staging of the view table (no allocation)
+    const int64_t hw = (int64_t)W * H;
+    for (int c = 0; c < n_cams; ++c) {
+        kns_frame f{};
+        f.rgb = out->rgb + 3 * c * hw;
+        f.depth = out->depth + c * hw;
+        f.normal = out->normal ? out->normal + 3 * c * hw : nullptr;
+        f.cell = out->cell ? out->cell + c * hw : nullptr;
+        f.steps = out->steps ? out->steps + c * hw : nullptr;
+        f.hit = out->hit ? out->hit + c * hw : nullptr;
+        hv[c] = make_view(cams[c], W, H, c * hw, f);
+    }
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    cudaError_t e = cudaMemcpyAsync(d_cams, cams, sizeof(kns_camera) * n_cams, cudaMemcpyHostToDevice, s);
+    // a copy from pageable host memory has read its source when the call returns, so the stack
+    // staging array may go out of scope afterwards
+    cudaError_t e = cudaMemcpyAsync(d_views, hv, sizeof(kns::ViewDev) * n_cams, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.ctrl, 0, sizeof(kns::WaveCtrl), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(cellbuf, 0, sizeof(int) * 4 * (NC + 1), s);
     if (e == cudaSuccess) e = kns::launch_wave_gen(grid->shape, grid->view, a, s);

@@ -26,9 +26,20 @@ struct WaveCtrl {
     unsigned long long samples_bf16;  // SDF evaluations in BF16 tiles
 };
 
+// One view of a render: its camera, image size, first ray id and output buffers (device, 128 B).
+struct ViewDev {
+    float cam[16];  // c2w[12], fx, fy, cx, cy
+    float *rgb, *depth, *normal;
+    int32_t *cell, *steps;
+    uint8_t *hit;
+    int W, H, ray_base, pad;
+};
+
 // Everything the wavefront kernels read and write (device pointers; passed by value).
 struct WaveArgs {
-    int W, H, n_cams, max_steps;
+    int n_views, max_W, max_H, max_steps;
+    const ViewDev *views;  // n_views entries; rays of view v are ray_base .. ray_base + W*H - 1
+    int *ray_view;         // view of each ray
     float eps;
     int NC;               // cells N^3
     int nkeys;            // sort keys: key = cell + NC * coarse (NC for FP32 renders, 2 NC for BF16)
@@ -43,13 +54,8 @@ struct WaveArgs {
     int min_active;       // warp tiles with fewer live rays hand them to the next round
     int static_tiles;     // 1: contiguous runs of tiles per block (weight reuse); 0: dynamic
     int *status;          // context status word (kns_status of a device-side failure, 0 = fine)
-    const float *cams;    // n_cams x 16 floats
     const float *wt;      // k-major trace weights (see kns_device.cuh)
     int wt_stride;        // floats per cell
-    // outputs, indexed by ray id r = cam*H*W + i*W + j
-    float *rgb, *depth, *normal;
-    int32_t *cell_out, *steps_out;
-    uint8_t *hit_out;
     // per-ray state
     float *t_ray;
     int *steps_ray, *cell_ray;

@@ -108,19 +108,22 @@ __device__ __forceinline__ float tile_sdf_f32(const float *__restrict__ wt, cons
     return acc;
 }
 
-// Wave 0: one thread per pixel (16x8 pixels per block, 8x4 per warp); clip, advance, emit.
+// Wave 0: one thread per pixel (16x8 pixels per block, 8x4 per warp, blockIdx.z = view); clip,
+// advance, emit.
 template <class C>
 __global__ void __launch_bounds__(128) wave_gen_kernel(GridView g, WaveArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int j = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
     const int i = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
-    const int cam = blockIdx.z;
-    const bool valid = i < a.H && j < a.W;
-    const int r = cam * a.W * a.H + i * a.W + j;
+    const int view = blockIdx.z;
+    const ViewDev &V = a.views[view];
+    const bool valid = i < V.H && j < V.W;
+    const int r = V.ray_base + i * V.W + j;
     bool alive = false;
     int cell = -1;
     if (valid) {
-        const Ray ray = make_ray(a.cams + 16 * cam, i, j);
+        a.ray_view[r] = view;
+        const Ray ray = make_ray(V.cam, i, j);
         float t0, tf;
         if (!clip_box(g, ray, t0, tf)) {
             write_miss(a, r, 0);
@@ -363,24 +366,26 @@ __global__ void __launch_bounds__(128) wave_shade_kernel(GridView g, WaveArgs a)
         nrm[1] = grad[1] * inv;
         nrm[2] = grad[2] * inv;
         colour_f32<C>(cw, feat, nrm, ray.wx, ray.wy, ray.wz, x, y, z, rgb);
-        a.rgb[3 * (int64_t)r + 0] = rgb[0];
-        a.rgb[3 * (int64_t)r + 1] = rgb[1];
-        a.rgb[3 * (int64_t)r + 2] = rgb[2];
-        a.depth[r] = t;
-        if (a.normal) {
-            a.normal[3 * (int64_t)r + 0] = nrm[0];
-            a.normal[3 * (int64_t)r + 1] = nrm[1];
-            a.normal[3 * (int64_t)r + 2] = nrm[2];
+        const ViewDev &V = a.views[cam];
+        const int64_t p = r - V.ray_base;
+        V.rgb[3 * p + 0] = rgb[0];
+        V.rgb[3 * p + 1] = rgb[1];
+        V.rgb[3 * p + 2] = rgb[2];
+        V.depth[p] = t;
+        if (V.normal) {
+            V.normal[3 * p + 0] = nrm[0];
+            V.normal[3 * p + 1] = nrm[1];
+            V.normal[3 * p + 2] = nrm[2];
         }
-        if (a.cell_out) a.cell_out[r] = c;
-        if (a.steps_out) a.steps_out[r] = a.steps_ray[r];
-        if (a.hit_out) a.hit_out[r] = 1;
+        if (V.cell) V.cell[p] = c;
+        if (V.steps) V.steps[p] = a.steps_ray[r];
+        if (V.hit) V.hit[p] = 1;
     }
 }
 
 template <class C>
 cudaError_t launch_wave_gen_cfg(const GridView &g, const WaveArgs &a, cudaStream_t s) {
-    dim3 grid((a.W + 15) / 16, (a.H + 7) / 8, a.n_cams);
+    dim3 grid((a.max_W + 15) / 16, (a.max_H + 7) / 8, a.n_views);
     wave_gen_kernel<C><<<grid, 128, 0, s>>>(g, a);
     return cudaGetLastError();
 }

@@ -80,27 +80,30 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
     return false;
 }
 
-__device__ __forceinline__ Ray ray_of(const WaveArgs &a, int r, int &cam) {
-    const int hw = a.W * a.H;
-    cam = r / hw;
-    const int pix = r - cam * hw;
-    const int i = pix / a.W, j = pix - i * a.W;
-    return make_ray(a.cams + 16 * cam, i, j);
+// The ray with id r: its view v, pixel index in the view, and world-space origin and direction.
+__device__ __forceinline__ Ray ray_of(const WaveArgs &a, int r, int &v) {
+    v = a.ray_view[r];
+    const ViewDev &V = a.views[v];
+    const int pix = r - V.ray_base;
+    const int i = pix / V.W, j = pix - i * V.W;
+    return make_ray(V.cam, i, j);
 }
 
 __device__ __forceinline__ void write_miss(const WaveArgs &a, int r, int steps) {
-    a.rgb[3 * (int64_t)r + 0] = 0.f;
-    a.rgb[3 * (int64_t)r + 1] = 0.f;
-    a.rgb[3 * (int64_t)r + 2] = 0.f;
-    a.depth[r] = INFINITY;
-    if (a.normal) {
-        a.normal[3 * (int64_t)r + 0] = 0.f;
-        a.normal[3 * (int64_t)r + 1] = 0.f;
-        a.normal[3 * (int64_t)r + 2] = 0.f;
+    const ViewDev &V = a.views[a.ray_view[r]];
+    const int64_t p = r - V.ray_base;
+    V.rgb[3 * p + 0] = 0.f;
+    V.rgb[3 * p + 1] = 0.f;
+    V.rgb[3 * p + 2] = 0.f;
+    V.depth[p] = INFINITY;
+    if (V.normal) {
+        V.normal[3 * p + 0] = 0.f;
+        V.normal[3 * p + 1] = 0.f;
+        V.normal[3 * p + 2] = 0.f;
     }
-    if (a.cell_out) a.cell_out[r] = -1;
-    if (a.steps_out) a.steps_out[r] = steps;
-    if (a.hit_out) a.hit_out[r] = 0;
+    if (V.cell) V.cell[p] = -1;
+    if (V.steps) V.steps[p] = steps;
+    if (V.hit) V.hit[p] = 0;
 }
 
 // Moves a ray at parameter t to its next sample: the cell at x(t), or, when x(t) lies in an empty
