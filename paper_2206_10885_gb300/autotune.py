@@ -18,11 +18,11 @@ DEFAULT_CACHE = os.path.join(_HERE, "_tune_cache.json")
 
 # candidate values of each knob (0 would mean the library default)
 SPACE = {
-    "inner_steps": (1, 4, 16),
+    "inner_steps": (1, 4),
     "min_active": (1, 8),
     "static_tiles": (1, 2),
     "blocks_per_sm": (8, 16, 32),
-    "tail_rays": (-1, 512, 4096),
+    "tail_rays": (-1, 4096, 32768, 131072),
 }
 
 

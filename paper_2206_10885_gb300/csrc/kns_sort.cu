@@ -62,8 +62,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) wave_scan_kernel(WaveArgs a, int
         a.ctrl->next_tile_bf = 0;
     }
     const int n_live = a.ctrl->n_live[cur];
+    // a small round is finished one thread per ray (still sorted, so a warp's rays share cells)
     if (threadIdx.x == 0) a.ctrl->tail = n_live <= a.tail_max ? 1 : 0;
-    if (n_live == 0 || n_live <= a.tail_max) {  // nothing to sort: empty, or finished per thread
+    if (n_live == 0) {
         if (threadIdx.x == 0) {
             a.ctrl->n_tiles = 0;
             a.ctrl->n_tiles_fine = 0;
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) wave_scan_kernel(WaveArgs a, int
 }
 
 __global__ void __launch_bounds__(256) wave_scatter_kernel(WaveArgs a, int cur) {
-    const int n = a.ctrl->tail ? 0 : a.ctrl->n_live[cur];
+    const int n = a.ctrl->n_live[cur];
     const int lane = threadIdx.x & 31;
     const int stride = gridDim.x * blockDim.x;
     const int bound = (n + 31) & ~31;  // warp-uniform loop bound

@@ -190,9 +190,10 @@ __device__ __noinline__ void finish_ray_f32(const GridView &g, const WaveArgs &a
     write_miss(a, r, steps);
 }
 
-// A tail round: one thread per ray, to the end.
+// A tail round: one thread per ray, to the end.  Rays are taken in cell-sorted order so that the
+// lanes of a warp mostly share a cell (uniform weight loads); a ray's cell is its sort key.
 template <class C>
-__global__ void __launch_bounds__(128) wave_tail_kernel(GridView g, WaveArgs a, int cur) {
+__global__ void __launch_bounds__(128, 4) wave_tail_kernel(GridView g, WaveArgs a, int cur) {
     if (!a.ctrl->tail) return;
     const int n = a.ctrl->n_live[cur];
     const int bound = (n + 31) & ~31;
@@ -200,8 +201,13 @@ __global__ void __launch_bounds__(128) wave_tail_kernel(GridView g, WaveArgs a, 
         bool hit = false;
         int r = 0;
         if (q < n) {
-            r = a.q[cur][q];
-            finish_ray_f32<C>(g, a, r, a.qcell[cur][q], hit);
+            r = a.sorted[q];
+            int lo = 0, hi = a.NC;  // the key with off[key] <= q < off[key+1]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(a.off + mid) <= q) lo = mid; else hi = mid;
+            }
+            finish_ray_f32<C>(g, a, r, lo, hit);
         }
         const int hp = warp_append(&a.ctrl->n_hits, hit);
         if (hit) a.hits[hp] = r;
@@ -397,7 +403,7 @@ cudaError_t launch_wave_eval_cfg(const GridView &g, const WaveArgs &a, int cur, 
     if (e != cudaSuccess) return e;
     wave_eval_kernel<C><<<blocks, 32, smem, s>>>(g, a, cur);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    wave_tail_kernel<C><<<blocks / 4 + 1, 128, 0, s>>>(g, a, cur);
+    wave_tail_kernel<C><<<blocks, 128, 0, s>>>(g, a, cur);
     return cudaGetLastError();
 }
 template <class C>
