@@ -109,9 +109,9 @@ typedef struct kns_frame {
  * the work, never a result; 0 selects the built-in default. */
 typedef struct kns_render_opts {
     int32_t precision;    /* KNS_FP32 or KNS_BF16 */
-    float eps_coarse;     /* KNS_BF16: hit threshold of the BF16 trace (<= 0: max(eps, 4e-3)) */
+    float eps_coarse;     /* KNS_BF16: hit threshold of the BF16 trace (<= 0: max(eps, 0.04)) */
     int32_t refine_steps; /* KNS_BF16: FP32 evaluations after the BF16 hit before the FP32 field decides
-                             (<= 0: 2); the ray is a hit at the first |d| < eps, or at the last of them if
+                             (<= 0: 64); the ray is a hit at the first |d| < eps, or at the last of them if
                              |d| < eps_coarse there, else a miss */
     /* tuning (0 = default) */
     int32_t inner_steps;   /* sphere steps a tile may take per round while its rays stay in its cells (1..1024) */
