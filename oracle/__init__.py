@@ -78,6 +78,11 @@ def lib():
             L.ko_march_roots.argtypes = [D, f, C.c_int64, d, d, d, d, C.c_double, C.c_double, d]
             L.ko_first_occupied.restype = C.c_int
             L.ko_first_occupied.argtypes = [D, u64, d, d, C.c_double, d, i32]
+            L.ko_train_loss.restype = C.c_double
+            L.ko_train_loss.argtypes = [D, f, C.c_double, C.c_double, C.c_int64, d, d, d, C.c_int, d, C.c_int, d,
+                                        C.c_int64, d, C.c_double, C.c_double, d, d, d]
+            L.ko_train_grad.restype = C.c_double
+            L.ko_train_grad.argtypes = L.ko_train_loss.argtypes
             L.ko_num_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -262,3 +267,45 @@ def robust_mask(margins: np.ndarray, delta_d: float, delta_x: float, delta_t: fl
     delta_t = delta_x if delta_t is None else delta_t
     return ((margins[:, 0] > delta_d) & (margins[:, 1] > delta_t) & (margins[:, 2] > delta_x)
             & (margins[:, 3] > delta_x))
+
+
+def train_loss(g, w, s: float, s_up: float, o, dirs, target, u_strat, u_imp, points, lam: float, h: float,
+               t_fixed=None, want_t: bool = False):
+    """NeuS-style training loss (see ko_train_loss in kns_oracle.c).  Returns (loss, parts, t)."""
+    w = _f32(w)
+    o = np.ascontiguousarray(o, dtype=np.float64).reshape(-1, 3)
+    dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+    target = np.ascontiguousarray(target, dtype=np.float64).reshape(-1, 3)
+    u_strat = np.ascontiguousarray(u_strat, dtype=np.float64)
+    u_imp = np.ascontiguousarray(u_imp, dtype=np.float64)
+    points = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    B, Ns, Ni = o.shape[0], u_strat.shape[1], u_imp.shape[1]
+    tf = None if t_fixed is None else np.ascontiguousarray(t_fixed, dtype=np.float64)
+    t_out = np.zeros((B, Ns + Ni)) if want_t else None
+    parts = np.zeros(2)
+    loss = lib().ko_train_loss(C.byref(_desc(g)), _p(w, C.c_float), float(s), float(s_up), B, _p(o, C.c_double),
+                               _p(dirs, C.c_double), _p(target, C.c_double), Ns, _p(u_strat, C.c_double), Ni,
+                               _p(u_imp, C.c_double), points.shape[0], _p(points, C.c_double), float(lam), float(h),
+                               _p(tf, C.c_double), _p(t_out, C.c_double), _p(parts, C.c_double))
+    return loss, parts, t_out
+
+
+def train_grad(g, w, s: float, s_up: float, o, dirs, target, u_strat, u_imp, points, lam: float, h: float,
+               t_fixed=None):
+    """Loss and its reverse-mode gradient over every weight (see ko_train_grad).  Returns (loss, parts, grad)."""
+    w = _f32(w)
+    o = np.ascontiguousarray(o, dtype=np.float64).reshape(-1, 3)
+    dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+    target = np.ascontiguousarray(target, dtype=np.float64).reshape(-1, 3)
+    u_strat = np.ascontiguousarray(u_strat, dtype=np.float64)
+    u_imp = np.ascontiguousarray(u_imp, dtype=np.float64)
+    points = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    tf = None if t_fixed is None else np.ascontiguousarray(t_fixed, dtype=np.float64)
+    grad = np.zeros(w.shape[0], dtype=np.float64)
+    parts = np.zeros(2)
+    loss = lib().ko_train_grad(C.byref(_desc(g)), _p(w, C.c_float), float(s), float(s_up), o.shape[0],
+                               _p(o, C.c_double), _p(dirs, C.c_double), _p(target, C.c_double), u_strat.shape[1],
+                               _p(u_strat, C.c_double), u_imp.shape[1], _p(u_imp, C.c_double), points.shape[0],
+                               _p(points, C.c_double), float(lam), float(h), _p(tf, C.c_double), _p(grad, C.c_double),
+                               _p(parts, C.c_double))
+    return loss, parts, grad

@@ -529,3 +529,351 @@ int ko_num_threads(void) {
     return 1;
 #endif
 }
+
+/* ---------------------------------------------------------------------------------------------
+ * NeuS-style training loss (Sec. 3.2.2: photometric L1 colour loss over sampled pixels, eikonal
+ * regulariser, total L = L_color + lambda L_eik), with the finite-difference gradients of Sec. 3.3.
+ *
+ * Per ray (origin o, unit direction w, target I): clip to the box; Ns stratified samples
+ * t_i = tn + (i + u_i)/Ns (tf - tn); a coarse pass evaluates d at them and forms the NeuS weights
+ * T_i alpha_i with alpha_i = max((Phi(d_i) - Phi(d_{i+1})) / Phi(d_i), 0), Phi(d) = sigmoid(s_up d),
+ * T_i = prod_{j<i} (1 - alpha_j); Ni importance samples are drawn by inverting the CDF of the
+ * piecewise-constant density (T_i alpha_i + 1e-5 on [t_i, t_{i+1}]) at the sorted uniforms u'.
+ * All Ns + Ni samples, merged in order, are rendered: d_i and z_i of the cell at x_i, the normal
+ * n_i = g_i / |g_i| with g_i the central difference (d(x+h e_k) - d(x-h e_k)) / 2h (each point
+ * evaluated in its own cell), colour c_i = sigmoid(colour MLP(z_i, n_i, gamma(w))), alpha_i with
+ * Phi(d) = sigmoid(s d), C = sum_i T_i alpha_i c_i.  L_color = (1/B) sum_rays sum_ch |C - I|.
+ * Eikonal on M points p: L_eik = (1/M) sum (|g(p)| - 1)^2 with the same central difference.
+ * Rays that miss the box render C = 0.  If t_fixed is given, the Ns + Ni sample positions of every
+ * ray are taken from it (positions are not differentiated: they are held fixed when the loss is
+ * differentiated).  t_out (nullable) receives them.
+ * ------------------------------------------------------------------------------------------- */
+static double sdf_at(const ko_desc *g, const float *weights, const double x[3], double *feat) {
+    return ko_sdf_eval(g, weights, ko_cell(g, x), x, feat, NULL);
+}
+
+static void fd_grad(const ko_desc *g, const float *weights, const double x[3], double h, double gr[3]) {
+    for (int k = 0; k < 3; k++) {
+        double xp[3] = {x[0], x[1], x[2]}, xm[3] = {x[0], x[1], x[2]};
+        xp[k] += h;
+        xm[k] -= h;
+        gr[k] = (sdf_at(g, weights, xp, NULL) - sdf_at(g, weights, xm, NULL)) / (2.0 * h);
+    }
+}
+
+double ko_train_loss(const ko_desc *g, const float *weights, double s, double s_up, int64_t B, const double *o,
+                     const double *w, const double *target, int Ns, const double *u_s, int Ni, const double *u_i,
+                     int64_t M, const double *P, double lambda, double h, const double *t_fixed, double *t_out,
+                     double *parts) {
+    const int S = Ns + Ni;
+    double l1 = 0.0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : l1)
+    for (int64_t r = 0; r < B; r++) {
+        const double *ro = o + 3 * r, *rw = w + 3 * r;
+        double tn, tf, margin = INFINITY, C[3] = {0, 0, 0};
+        double *ts = (double *)malloc(sizeof(double) * (size_t)S);
+        int ok = ko_clip(g, ro, rw, &tn, &tf, &margin);
+        if (ok) {
+            if (t_fixed) {
+                for (int i = 0; i < S; i++) ts[i] = t_fixed[r * S + i];
+            } else {
+                double *tc = (double *)malloc(sizeof(double) * (size_t)Ns);
+                double *dc = (double *)malloc(sizeof(double) * (size_t)Ns);
+                double *cdf = (double *)malloc(sizeof(double) * (size_t)Ns);
+                for (int i = 0; i < Ns; i++) {
+                    tc[i] = tn + ((double)i + u_s[r * Ns + i]) / Ns * (tf - tn);
+                    double x[3] = {ro[0] + tc[i] * rw[0], ro[1] + tc[i] * rw[1], ro[2] + tc[i] * rw[2]};
+                    dc[i] = sdf_at(g, weights, x, NULL);
+                }
+                /* coarse weights on the Ns-1 intervals, then their CDF */
+                double T = 1.0, tot = 0.0;
+                cdf[0] = 0.0;
+                for (int i = 0; i + 1 < Ns; i++) {
+                    double p0 = 1.0 / (1.0 + exp(-s_up * dc[i])), p1 = 1.0 / (1.0 + exp(-s_up * dc[i + 1]));
+                    double a = fmax((p0 - p1) / p0, 0.0);
+                    double wgt = T * a + 1e-5;
+                    T *= 1.0 - a;
+                    tot += wgt;
+                    cdf[i + 1] = tot;
+                }
+                for (int i = 1; i < Ns; i++) cdf[i] /= tot;
+                /* inverse CDF at the sorted uniforms, merged with the stratified samples */
+                int a = 0, b = 0, k = 0;
+                while (a < Ns || b < Ni) {
+                    double timp = INFINITY;
+                    if (b < Ni) {
+                        double u = u_i[r * Ni + b];
+                        int j = 0;
+                        while (j + 2 < Ns && cdf[j + 1] <= u) j++;
+                        double den = cdf[j + 1] - cdf[j];
+                        timp = tc[j] + (den > 0 ? (u - cdf[j]) / den : 0.0) * (tc[j + 1] - tc[j]);
+                    }
+                    if (a < Ns && (b >= Ni || tc[a] <= timp)) {
+                        ts[k++] = tc[a++];
+                    } else {
+                        ts[k++] = timp;
+                        b++;
+                    }
+                }
+                free(tc);
+                free(dc);
+                free(cdf);
+            }
+            if (t_out)
+                for (int i = 0; i < S; i++) t_out[r * S + i] = ts[i];
+            double *d = (double *)malloc(sizeof(double) * (size_t)S);
+            double (*col)[3] = malloc(sizeof(double) * 3 * (size_t)S);
+            for (int i = 0; i < S; i++) {
+                double x[3] = {ro[0] + ts[i] * rw[0], ro[1] + ts[i] * rw[1], ro[2] + ts[i] * rw[2]};
+                double feat[KO_MAXIN], gr[3], n[3];
+                int c = ko_cell(g, x);
+                d[i] = ko_sdf_eval(g, weights, c, x, feat, NULL);
+                fd_grad(g, weights, x, h, gr);
+                double gn = sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+                for (int q = 0; q < 3; q++) n[q] = gn > 0 ? gr[q] / gn : 0.0;
+                ko_colour_eval(g, weights, c, x, feat, n, rw, col[i]);
+            }
+            double T = 1.0;
+            for (int i = 0; i + 1 < S; i++) {
+                double p0 = 1.0 / (1.0 + exp(-s * d[i])), p1 = 1.0 / (1.0 + exp(-s * d[i + 1]));
+                double a = fmax((p0 - p1) / p0, 0.0);
+                for (int q = 0; q < 3; q++) C[q] += T * a * col[i][q];
+                T *= 1.0 - a;
+            }
+            free(d);
+            free(col);
+        } else if (t_out) {
+            for (int i = 0; i < S; i++) t_out[r * S + i] = 0.0;
+        }
+        free(ts);
+        for (int q = 0; q < 3; q++) l1 += fabs(C[q] - target[3 * r + q]);
+    }
+    double eik = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : eik)
+    for (int64_t m = 0; m < M; m++) {
+        double gr[3];
+        fd_grad(g, weights, P + 3 * m, h, gr);
+        double gn = sqrt(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+        eik += (gn - 1.0) * (gn - 1.0);
+    }
+    const double lc = B > 0 ? l1 / (double)B : 0.0, le = M > 0 ? eik / (double)M : 0.0;
+    if (parts) {
+        parts[0] = lc;
+        parts[1] = le;
+    }
+    return lc + lambda * le;
+}
+
+/* ---------------------------------------------------------------------------------------------
+ * Reverse-mode gradient of ko_train_loss with respect to every weight of the canonical array.
+ * The sample positions are held fixed (they are not differentiated).  |.| and max(., 0) take the
+ * derivative 0 at their kinks.  grad (n_cells x params_cell doubles) is overwritten.
+ * ------------------------------------------------------------------------------------------- */
+
+/* gradient of (dd * d + sum_k dz[k] z[k]) at x in `cell` with respect to the cell's SDF weights
+ * (accumulated into gw, which points at the cell's first weight) */
+static void sdf_backward(const ko_desc *g, const float *weights, int cell, const double x[3], double dd,
+                         const double *dz, double *gw) {
+    int dims[KO_MAXLAYERS + 2];
+    int nd = sdf_dims(g, dims);
+    int nl = nd - 1;
+    const float *w = weights + (int64_t)cell * ko_params_cell(g);
+    double act[KO_MAXLAYERS + 1][KO_MAXIN], pre[KO_MAXLAYERS][KO_MAXW];
+    int64_t offs[KO_MAXLAYERS];
+    int64_t off = 0;
+    for (int l = 0; l < nl; l++) {
+        offs[l] = off;
+        off += (int64_t)dims[l] * dims[l + 1] + dims[l + 1];
+    }
+    ko_pe(g->pe_pos_L, 3, x, act[0]);
+    for (int l = 0; l < nl; l++) {
+        const float *W = w + offs[l], *b = W + (int64_t)dims[l] * dims[l + 1];
+        for (int o = 0; o < dims[l + 1]; o++) {
+            double s = (double)b[o];
+            for (int i = 0; i < dims[l]; i++) s += (double)W[(int64_t)o * dims[l] + i] * act[l][i];
+            pre[l][o] = s;
+            act[l + 1][o] = (l + 1 < nl) ? ko_softplus(s, g->beta) : s;
+        }
+    }
+    /* delta = dL / d pre[l] */
+    double delta[KO_MAXIN], nxt[KO_MAXIN];
+    delta[0] = dd;
+    for (int k = 0; k < g->feat_dim; k++) delta[1 + k] = dz ? dz[k] : 0.0;
+    for (int l = nl - 1; l >= 0; l--) {
+        const float *W = w + offs[l];
+        double *gW = gw + offs[l], *gb = gW + (int64_t)dims[l] * dims[l + 1];
+        for (int o = 0; o < dims[l + 1]; o++) {
+            gb[o] += delta[o];
+            for (int i = 0; i < dims[l]; i++) gW[(int64_t)o * dims[l] + i] += delta[o] * act[l][i];
+        }
+        if (l == 0) break;
+        for (int i = 0; i < dims[l]; i++) {
+            double s = 0;
+            for (int o = 0; o < dims[l + 1]; o++) s += (double)W[(int64_t)o * dims[l] + i] * delta[o];
+            nxt[i] = s * dsoftplus(pre[l - 1][i], g->beta);
+        }
+        memcpy(delta, nxt, sizeof(double) * dims[l]);
+    }
+}
+
+/* gradient of drgb . rgb (rgb = colour MLP output) with respect to the cell's colour weights
+ * (accumulated into gw, which points at the cell's first colour weight) and to the inputs feat and n */
+static void colour_backward(const ko_desc *g, const float *weights, int cell, const double x[3], const double *feat,
+                            const double n[3], const double v[3], const double drgb[3], double *gw, double *dfeat,
+                            double dn[3]) {
+    int dims[KO_MAXLAYERS + 2];
+    int nd = col_dims(g, dims);
+    int nl = nd - 1;
+    const float *w = weights + (int64_t)cell * ko_params_cell(g) + ko_params_sdf(g);
+    double act[KO_MAXLAYERS + 1][KO_MAXIN], pre[KO_MAXLAYERS][KO_MAXW];
+    int64_t offs[KO_MAXLAYERS];
+    int64_t off = 0;
+    for (int l = 0; l < nl; l++) {
+        offs[l] = off;
+        off += (int64_t)dims[l] * dims[l + 1] + dims[l + 1];
+    }
+    int u = 0;
+    for (int k = 0; k < g->feat_dim; k++) act[0][u++] = feat[k];
+    for (int c = 0; c < 3; c++) act[0][u++] = n[c];
+    ko_pe(g->pe_dir_L, 3, v, act[0] + u);
+    u += 3 + 6 * g->pe_dir_L;
+    if (g->col_use_x)
+        for (int c = 0; c < 3; c++) act[0][u++] = x[c];
+    for (int l = 0; l < nl; l++) {
+        const float *W = w + offs[l], *b = W + (int64_t)dims[l] * dims[l + 1];
+        for (int o = 0; o < dims[l + 1]; o++) {
+            double s = (double)b[o];
+            for (int i = 0; i < dims[l]; i++) s += (double)W[(int64_t)o * dims[l] + i] * act[l][i];
+            pre[l][o] = s;
+            act[l + 1][o] = (l + 1 < nl) ? fmax(s, 0.0) : sigmoid(s);
+        }
+    }
+    double delta[KO_MAXIN], nxt[KO_MAXIN];
+    for (int c = 0; c < 3; c++) delta[c] = drgb[c] * act[nl][c] * (1.0 - act[nl][c]);
+    for (int l = nl - 1; l >= 0; l--) {
+        const float *W = w + offs[l];
+        double *gW = gw + offs[l], *gb = gW + (int64_t)dims[l] * dims[l + 1];
+        for (int o = 0; o < dims[l + 1]; o++) {
+            gb[o] += delta[o];
+            for (int i = 0; i < dims[l]; i++) gW[(int64_t)o * dims[l] + i] += delta[o] * act[l][i];
+        }
+        for (int i = 0; i < dims[l]; i++) {
+            double s = 0;
+            for (int o = 0; o < dims[l + 1]; o++) s += (double)W[(int64_t)o * dims[l] + i] * delta[o];
+            nxt[i] = (l > 0) ? (pre[l - 1][i] > 0 ? s : 0.0) : s;
+        }
+        memcpy(delta, nxt, sizeof(double) * dims[l]);
+    }
+    for (int k = 0; k < g->feat_dim; k++) dfeat[k] = delta[k];
+    for (int c = 0; c < 3; c++) dn[c] = delta[g->feat_dim + c];
+}
+
+/* the six central-difference points around x get upstream +-dgr[k] / 2h */
+static void fd_backward(const ko_desc *g, const float *weights, const double x[3], double h, const double dgr[3],
+                        double *grad, int64_t pc) {
+    for (int k = 0; k < 3; k++) {
+        double xp[3] = {x[0], x[1], x[2]}, xm[3] = {x[0], x[1], x[2]};
+        xp[k] += h;
+        xm[k] -= h;
+        int cp = ko_cell(g, xp), cm = ko_cell(g, xm);
+        sdf_backward(g, weights, cp, xp, dgr[k] / (2.0 * h), NULL, grad + (int64_t)cp * pc);
+        sdf_backward(g, weights, cm, xm, -dgr[k] / (2.0 * h), NULL, grad + (int64_t)cm * pc);
+    }
+}
+
+double ko_train_grad(const ko_desc *g, const float *weights, double s, double s_up, int64_t B, const double *o,
+                     const double *w, const double *target, int Ns, const double *u_s, int Ni, const double *u_i,
+                     int64_t M, const double *P, double lambda, double h, const double *t_fixed, double *grad,
+                     double *parts) {
+    const int S = Ns + Ni;
+    const int64_t pc = ko_params_cell(g), ncell = (int64_t)g->N * g->N * g->N, nw = pc * ncell;
+    const int64_t psdf = ko_params_sdf(g);
+    double *ts = (double *)malloc(sizeof(double) * (size_t)(B > 0 ? B : 1) * S);
+    double loss = ko_train_loss(g, weights, s, s_up, B, o, w, target, Ns, u_s, Ni, u_i, M, P, lambda, h, t_fixed,
+                                ts, parts);
+    memset(grad, 0, sizeof(double) * (size_t)nw);
+    /* serial accumulation keeps the oracle plain; it is sized for test problems */
+    for (int64_t r = 0; r < B; r++) {
+        const double *ro = o + 3 * r, *rw = w + 3 * r;
+        double tn, tf, margin = INFINITY;
+        if (!ko_clip(g, ro, rw, &tn, &tf, &margin)) continue;
+        const double *t = ts + r * S;
+        double *d = malloc(sizeof(double) * S), *Phi = malloc(sizeof(double) * S), *alpha = malloc(sizeof(double) * S);
+        double *Tr = malloc(sizeof(double) * S), (*col)[3] = malloc(sizeof(double) * 3 * S);
+        double (*feat)[KO_MAXIN] = malloc(sizeof(double) * KO_MAXIN * S), (*nrm)[3] = malloc(sizeof(double) * 3 * S);
+        double *gnorm = malloc(sizeof(double) * S), (*gr)[3] = malloc(sizeof(double) * 3 * S);
+        int *cell = malloc(sizeof(int) * S);
+        for (int i = 0; i < S; i++) {
+            double x[3] = {ro[0] + t[i] * rw[0], ro[1] + t[i] * rw[1], ro[2] + t[i] * rw[2]};
+            cell[i] = ko_cell(g, x);
+            d[i] = ko_sdf_eval(g, weights, cell[i], x, feat[i], NULL);
+            fd_grad(g, weights, x, h, gr[i]);
+            gnorm[i] = sqrt(gr[i][0] * gr[i][0] + gr[i][1] * gr[i][1] + gr[i][2] * gr[i][2]);
+            for (int q = 0; q < 3; q++) nrm[i][q] = gnorm[i] > 0 ? gr[i][q] / gnorm[i] : 0.0;
+            ko_colour_eval(g, weights, cell[i], x, feat[i], nrm[i], rw, col[i]);
+            Phi[i] = 1.0 / (1.0 + exp(-s * d[i]));
+        }
+        double T = 1.0, C[3] = {0, 0, 0};
+        for (int i = 0; i + 1 < S; i++) {
+            alpha[i] = fmax((Phi[i] - Phi[i + 1]) / Phi[i], 0.0);
+            Tr[i] = T;
+            for (int q = 0; q < 3; q++) C[q] += T * alpha[i] * col[i][q];
+            T *= 1.0 - alpha[i];
+        }
+        double gC[3];
+        for (int q = 0; q < 3; q++) {
+            double e = C[q] - target[3 * r + q];
+            gC[q] = (e > 0 ? 1.0 : (e < 0 ? -1.0 : 0.0)) / (double)B;
+        }
+        /* Chat = colour rendered from sample i+1 on with unit transmittance, built back to front */
+        double Chat[3] = {0, 0, 0};
+        double *dd = calloc((size_t)S, sizeof(double));
+        for (int i = S - 2; i >= 0; i--) {
+            double dalpha = 0.0;
+            for (int q = 0; q < 3; q++) dalpha += Tr[i] * gC[q] * (col[i][q] - Chat[q]);
+            if ((Phi[i] - Phi[i + 1]) / Phi[i] > 0) {
+                dd[i] += dalpha * s * Phi[i + 1] * (1.0 - Phi[i]) / Phi[i];
+                dd[i + 1] -= dalpha * s * Phi[i + 1] * (1.0 - Phi[i + 1]) / Phi[i];
+            }
+            for (int q = 0; q < 3; q++) Chat[q] = alpha[i] * col[i][q] + (1.0 - alpha[i]) * Chat[q];
+        }
+        for (int i = 0; i < S; i++) {
+            double x[3] = {ro[0] + t[i] * rw[0], ro[1] + t[i] * rw[1], ro[2] + t[i] * rw[2]};
+            double dz[KO_MAXIN] = {0}, dn[3] = {0, 0, 0};
+            if (i + 1 < S) {
+                double drgb[3];
+                for (int q = 0; q < 3; q++) drgb[q] = Tr[i] * alpha[i] * gC[q];
+                colour_backward(g, weights, cell[i], x, feat[i], nrm[i], rw, drgb, grad + cell[i] * pc + psdf, dz,
+                                dn);
+            }
+            sdf_backward(g, weights, cell[i], x, dd[i], dz, grad + cell[i] * pc);
+            if (gnorm[i] > 0) {
+                double nd = nrm[i][0] * dn[0] + nrm[i][1] * dn[1] + nrm[i][2] * dn[2], dgr[3];
+                for (int q = 0; q < 3; q++) dgr[q] = (dn[q] - nrm[i][q] * nd) / gnorm[i];
+                fd_backward(g, weights, x, h, dgr, grad, pc);
+            }
+        }
+        free(dd);
+        free(d);
+        free(Phi);
+        free(alpha);
+        free(Tr);
+        free(col);
+        free(feat);
+        free(nrm);
+        free(gnorm);
+        free(gr);
+        free(cell);
+    }
+    for (int64_t m = 0; m < M; m++) {
+        double gm[3];
+        fd_grad(g, weights, P + 3 * m, h, gm);
+        double gn = sqrt(gm[0] * gm[0] + gm[1] * gm[1] + gm[2] * gm[2]);
+        if (gn <= 0) continue;
+        double dgr[3];
+        for (int q = 0; q < 3; q++) dgr[q] = lambda / (double)M * 2.0 * (gn - 1.0) * gm[q] / gn;
+        fd_backward(g, weights, P + 3 * m, h, dgr, grad, pc);
+    }
+    free(ts);
+    return loss;
+}
