@@ -218,6 +218,59 @@ kns_status kns_render_views(kns_ctx *ctx, const kns_grid *grid, const kns_view *
 kns_status kns_sdf(kns_ctx *ctx, const kns_grid *grid, const float *pts, int64_t n, float *sdf,
                    float *feat, float *grad, void *cuda_stream);
 
+/* ------------------------------------------------------- training step */
+
+/* One batch of the fine-tuning loss of Sec. 3.2.2.  Device pointers, FP32, row-major.  Rays: origins
+ * and unit directions (n_rays x 3), target colours (n_rays x 3).  The random draws of the step are
+ * inputs: u_strat (n_rays x n_strat, in [0, 1)) jitters the stratified samples, u_imp (n_rays x
+ * n_imp, each row ascending in [0, 1)) places the importance samples; eik_points (n_eik x 3) are the
+ * eikonal points.  s: sharpness of the NeuS opacity Phi_s = sigmoid(s d) of the rendered samples;
+ * s_up: the same for the coarse pass that places the importance samples; lambda: eikonal weight;
+ * h: central-difference step of the SDF gradient (Sec. 3.3).  t_fixed (device, n_rays x (n_strat +
+ * n_imp), each row ascending, or NULL): sample positions to render instead of placing them (the
+ * coarse pass and u_strat, u_imp are then unused). */
+typedef struct {
+    int64_t n_rays;
+    const float *origins, *dirs, *target;
+    int32_t n_strat, n_imp; /* n_strat >= 2, n_strat + n_imp <= 256 */
+    const float *u_strat, *u_imp;
+    int64_t n_eik;
+    const float *eik_points;
+    float s, s_up, lambda, h;
+    const float *t_fixed;
+} kns_train_batch;
+
+/* Training loss (Sec. 3.2.2: L = L_color + lambda L_eikonal) of a Kilo-grid whose canonical FP32 weights
+ * `params` (device, N^3 x params-per-cell) the caller owns, e.g. a framework parameter tensor.
+ * Per ray (NeuS volume rendering with one importance pass): the box interval [t_n, t_f] gets n_strat
+ * samples t_i = t_n + (i + u_i)/n_strat (t_f - t_n); their SDF values give coarse weights T_i alpha_i
+ * (Phi_{s_up}); n_imp samples invert the CDF of those weights (+1e-5 per interval); all samples, merged
+ * in order, are rendered: alpha_i = max(1 - Phi_s(d_{i+1}) / Phi_s(d_i), 0), T_i = prod_{j<i} (1 -
+ * alpha_j), C = sum_i T_i alpha_i c_i (black background), with c_i the colour MLP on the cell's
+ * feature, the normal g/|g| and gamma(v), where g is the central difference of d with step h, each
+ * difference point evaluated in its own cell (Sec. 3.3).  L_color = mean over rays of |C - I|_1;
+ * L_eikonal = mean over points of (|g| - 1)^2.  Sample positions are not differentiated.
+ * loss: device, 3 floats written (L, L_color, L_eikonal).  rgb (device n_rays x 3) and t_samples
+ * (device n_rays x (n_strat + n_imp); 0 for rays that miss the box) are optional outputs.
+ * Supported shapes: sdf_width 32, sdf_hidden 2 or 3, pe_pos_L 4, pe_dir_L 2, col_use_x 0.
+ * The pass keeps its state in the context for kns_train_backward and returns a token for it; the
+ * next forward on the context replaces that state.  params and the batch arrays must stay valid and
+ * unchanged until the backward has run.  Errors: INVALID_ARG (NULL pointers, counts or sizes out of
+ * range, s, s_up, h <= 0, lambda < 0), UNSUPPORTED (grid shape), CUDA, OUT_OF_MEMORY. */
+kns_status kns_train_forward(kns_ctx *ctx, const kns_grid_desc *desc, const float *params,
+                             const kns_train_batch *batch, float *loss, float *rgb, float *t_samples,
+                             uint64_t *token, void *cuda_stream);
+
+/* Gradient of dloss * L (dloss: device scalar, NULL = 1) with respect to every weight of the forward
+ * pass `token`, written to grad (device, canonical layout, same size as params; overwritten).  The
+ * hand-written backward of the forward above: |.| and max(., 0) take derivative 0 at their kinks.
+ * Errors: INVALID_ARG (token not the context's latest forward, NULL grad), CUDA. */
+kns_status kns_train_backward(kns_ctx *ctx, uint64_t token, const float *dloss, float *grad, void *cuda_stream);
+
+/* kns_train_forward followed by kns_train_backward (grad NULL: forward only). */
+kns_status kns_train_step(kns_ctx *ctx, const kns_grid_desc *desc, const float *params,
+                          const kns_train_batch *batch, float *loss, float *grad, void *cuda_stream);
+
 /* ------------------------------------------------------- allocation-free render */
 
 /* Limits of kns_render_noalloc's built-in scratch. */

@@ -80,9 +80,9 @@ def lib():
             L.ko_first_occupied.argtypes = [D, u64, d, d, C.c_double, d, i32]
             L.ko_train_loss.restype = C.c_double
             L.ko_train_loss.argtypes = [D, f, C.c_double, C.c_double, C.c_int64, d, d, d, C.c_int, d, C.c_int, d,
-                                        C.c_int64, d, C.c_double, C.c_double, d, d, d]
+                                        C.c_int64, d, C.c_double, C.c_double, d, d, d, d]
             L.ko_train_grad.restype = C.c_double
-            L.ko_train_grad.argtypes = L.ko_train_loss.argtypes
+            L.ko_train_grad.argtypes = L.ko_train_loss.argtypes[:-1]
             L.ko_num_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -270,8 +270,8 @@ def robust_mask(margins: np.ndarray, delta_d: float, delta_x: float, delta_t: fl
 
 
 def train_loss(g, w, s: float, s_up: float, o, dirs, target, u_strat, u_imp, points, lam: float, h: float,
-               t_fixed=None, want_t: bool = False):
-    """NeuS-style training loss (see ko_train_loss in kns_oracle.c).  Returns (loss, parts, t)."""
+               t_fixed=None, want_t: bool = False, want_rgb: bool = False):
+    """NeuS-style training loss (see ko_train_loss in kns_oracle.c).  Returns (loss, parts, t[, rgb])."""
     w = _f32(w)
     o = np.ascontiguousarray(o, dtype=np.float64).reshape(-1, 3)
     dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
@@ -282,11 +282,14 @@ def train_loss(g, w, s: float, s_up: float, o, dirs, target, u_strat, u_imp, poi
     B, Ns, Ni = o.shape[0], u_strat.shape[1], u_imp.shape[1]
     tf = None if t_fixed is None else np.ascontiguousarray(t_fixed, dtype=np.float64)
     t_out = np.zeros((B, Ns + Ni)) if want_t else None
+    rgb = np.zeros((B, 3)) if want_rgb else None
     parts = np.zeros(2)
     loss = lib().ko_train_loss(C.byref(_desc(g)), _p(w, C.c_float), float(s), float(s_up), B, _p(o, C.c_double),
                                _p(dirs, C.c_double), _p(target, C.c_double), Ns, _p(u_strat, C.c_double), Ni,
                                _p(u_imp, C.c_double), points.shape[0], _p(points, C.c_double), float(lam), float(h),
-                               _p(tf, C.c_double), _p(t_out, C.c_double), _p(parts, C.c_double))
+                               _p(tf, C.c_double), _p(t_out, C.c_double), _p(parts, C.c_double), _p(rgb, C.c_double))
+    if want_rgb:
+        return loss, parts, t_out, rgb
     return loss, parts, t_out
 
 

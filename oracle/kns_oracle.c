@@ -546,7 +546,7 @@ int ko_num_threads(void) {
  * Eikonal on M points p: L_eik = (1/M) sum (|g(p)| - 1)^2 with the same central difference.
  * Rays that miss the box render C = 0.  If t_fixed is given, the Ns + Ni sample positions of every
  * ray are taken from it (positions are not differentiated: they are held fixed when the loss is
- * differentiated).  t_out (nullable) receives them.
+ * differentiated).  t_out and rgb_out (nullable) receive the positions and the rendered colours C.
  * ------------------------------------------------------------------------------------------- */
 static double sdf_at(const ko_desc *g, const float *weights, const double x[3], double *feat) {
     return ko_sdf_eval(g, weights, ko_cell(g, x), x, feat, NULL);
@@ -564,7 +564,7 @@ static void fd_grad(const ko_desc *g, const float *weights, const double x[3], d
 double ko_train_loss(const ko_desc *g, const float *weights, double s, double s_up, int64_t B, const double *o,
                      const double *w, const double *target, int Ns, const double *u_s, int Ni, const double *u_i,
                      int64_t M, const double *P, double lambda, double h, const double *t_fixed, double *t_out,
-                     double *parts) {
+                     double *parts, double *rgb_out) {
     const int S = Ns + Ni;
     double l1 = 0.0;
 #pragma omp parallel for schedule(dynamic, 4) reduction(+ : l1)
@@ -647,6 +647,8 @@ double ko_train_loss(const ko_desc *g, const float *weights, double s, double s_
         }
         free(ts);
         for (int q = 0; q < 3; q++) l1 += fabs(C[q] - target[3 * r + q]);
+        if (rgb_out)
+            for (int q = 0; q < 3; q++) rgb_out[3 * r + q] = C[q];
     }
     double eik = 0.0;
 #pragma omp parallel for schedule(static) reduction(+ : eik)
@@ -790,7 +792,7 @@ double ko_train_grad(const ko_desc *g, const float *weights, double s, double s_
     const int64_t psdf = ko_params_sdf(g);
     double *ts = (double *)malloc(sizeof(double) * (size_t)(B > 0 ? B : 1) * S);
     double loss = ko_train_loss(g, weights, s, s_up, B, o, w, target, Ns, u_s, Ni, u_i, M, P, lambda, h, t_fixed,
-                                ts, parts);
+                                ts, parts, NULL);
     memset(grad, 0, sizeof(double) * (size_t)nw);
     /* serial accumulation keeps the oracle plain; it is sized for test problems */
     for (int64_t r = 0; r < B; r++) {

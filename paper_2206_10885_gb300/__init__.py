@@ -9,9 +9,10 @@ from __future__ import annotations
 import numpy as np
 
 from . import _capi as capi
+from . import train
 from ._capi import KNS_BF16, KNS_FP32, KnsError
 
-__all__ = ["capi", "KnsError", "KNS_FP32", "KNS_BF16", "Context", "Grid", "alloc_frame", "render", "sdf"]
+__all__ = ["capi", "KnsError", "KNS_FP32", "KNS_BF16", "Context", "Grid", "alloc_frame", "render", "sdf", "train"]
 
 
 def _stream_ptr(stream) -> int:

@@ -55,6 +55,13 @@ class kns_view(C.Structure):
     _fields_ = [("cam", kns_camera), ("W", C.c_int32), ("H", C.c_int32), ("out", kns_frame)]
 
 
+class kns_train_batch(C.Structure):
+    _fields_ = [("n_rays", C.c_int64), ("origins", C.c_void_p), ("dirs", C.c_void_p), ("target", C.c_void_p),
+                ("n_strat", C.c_int32), ("n_imp", C.c_int32), ("u_strat", C.c_void_p), ("u_imp", C.c_void_p),
+                ("n_eik", C.c_int64), ("eik_points", C.c_void_p), ("s", C.c_float), ("s_up", C.c_float),
+                ("lambda_", C.c_float), ("h", C.c_float), ("t_fixed", C.c_void_p)]
+
+
 class kns_render_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("eps_coarse", C.c_float), ("refine_steps", C.c_int32),
                 ("inner_steps", C.c_int32), ("min_active", C.c_int32), ("tail_rays", C.c_int32),
@@ -113,6 +120,13 @@ def lib():
             L.kns_render_views.restype = st
             L.kns_get_render_stats.argtypes = [vp, C.POINTER(kns_render_stats)]
             L.kns_get_render_stats.restype = st
+            L.kns_train_forward.argtypes = [vp, C.POINTER(kns_grid_desc), vp, C.POINTER(kns_train_batch), vp, vp, vp,
+                                            C.POINTER(C.c_uint64), vp]
+            L.kns_train_forward.restype = st
+            L.kns_train_backward.argtypes = [vp, C.c_uint64, vp, vp, vp]
+            L.kns_train_backward.restype = st
+            L.kns_train_step.argtypes = [vp, C.POINTER(kns_grid_desc), vp, C.POINTER(kns_train_batch), vp, vp, vp]
+            L.kns_train_step.restype = st
             _lib = L
     return _lib
 
@@ -223,3 +237,22 @@ def kns_render_noalloc(ctx: int, grid: int, cams_host_ptr: int, n_cams: int, W: 
                        eps: float, frame: kns_frame = None, stream: int = 0) -> None:
     _check(lib().kns_render_noalloc(ctx, grid, cams_host_ptr, n_cams, W, H, max_steps, eps,
                                     C.byref(frame) if frame is not None else None, stream), ctx)
+
+
+def kns_train_forward(ctx: int, desc: kns_grid_desc, params_ptr: int, batch: kns_train_batch, loss_ptr: int,
+                      rgb_ptr: int = None, t_ptr: int = None, stream: int = 0) -> int:
+    tok = C.c_uint64(0)
+    desc = desc_struct(desc)
+    _check(lib().kns_train_forward(ctx, C.byref(desc), params_ptr, C.byref(batch), loss_ptr, rgb_ptr, t_ptr,
+                                   C.byref(tok), stream), ctx)
+    return tok.value
+
+
+def kns_train_backward(ctx: int, token: int, dloss_ptr: int, grad_ptr: int, stream: int = 0) -> None:
+    _check(lib().kns_train_backward(ctx, token, dloss_ptr, grad_ptr, stream), ctx)
+
+
+def kns_train_step(ctx: int, desc: kns_grid_desc, params_ptr: int, batch: kns_train_batch, loss_ptr: int,
+                   grad_ptr: int = None, stream: int = 0) -> None:
+    desc = desc_struct(desc)
+    _check(lib().kns_train_step(ctx, C.byref(desc), params_ptr, C.byref(batch), loss_ptr, grad_ptr, stream), ctx)

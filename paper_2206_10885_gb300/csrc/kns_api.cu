@@ -29,6 +29,23 @@ struct WaveScratch {
     kns::WaveCtrl *ctrl = nullptr;
 };
 
+// Device scratch and saved state of the training step, owned by the context and grown on demand.
+struct TrainScratch {
+    int64_t cap_B = 0, cap_M = 0;  // capacity: rays, eikonal points
+    int cap_S = 0, cap_Ns = 0, cap_keys = 0;
+    int64_t cap_rec = 0;           // sorted records
+    float *t = nullptr, *d_coarse = nullptr, *d_fd = nullptr, *g_fd = nullptr, *d_c = nullptr, *g_dc = nullptr;
+    float *rgb_c = nullptr, *g_rgb = nullptr, *C = nullptr;
+    uint8_t *valid = nullptr;
+    double *acc = nullptr;
+    int *keys = nullptr;           // count, off, fill, chunk_off (4 x (keys + 1))
+    float4 *sorted = nullptr;
+    // the forward pass whose state the scratch holds
+    uint64_t gen = 0;
+    bool pending = false;
+    kns::TrainArgs args{};
+};
+
 struct kns_ctx {
     int device = 0;
     int sm_count = 1;
@@ -36,6 +53,7 @@ struct kns_ctx {
     std::string err;
     int *d_status = nullptr;  // device status word written by kernels (0 = fine)
     WaveScratch ws;
+    TrainScratch ts;
     int *h_live = nullptr;                 // pinned: live-sample counts of recent rounds
     cudaEvent_t ev_live[4] = {nullptr, nullptr, nullptr, nullptr};
     // last render's statistics
@@ -352,6 +370,58 @@ kns_status ensure_scratch(kns_ctx *ctx, int64_t rays, int nc, int cams) {
     return KNS_OK;
 }
 
+void free_train_scratch(TrainScratch &t) {
+    void *ps[] = {t.t, t.d_coarse, t.d_fd, t.g_fd, t.d_c, t.g_dc, t.rgb_c, t.g_rgb, t.C, t.valid, t.acc, t.keys,
+                  t.sorted};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+    const uint64_t gen = t.gen;
+    t = TrainScratch{};
+    t.gen = gen;
+}
+
+// Grows the training scratch for B rays of S samples (Ns stratified), M eikonal points, nkeys keys.
+kns_status ensure_train_scratch(kns_ctx *ctx, int64_t B, int S, int Ns, int64_t M, int nkeys) {
+    TrainScratch &t = ctx->ts;
+    const int64_t nrec = std::max(B * Ns, 6 * (B * S + M) + B * S);
+    if (B <= t.cap_B && S <= t.cap_S && Ns <= t.cap_Ns && M <= t.cap_M && nkeys <= t.cap_keys && nrec <= t.cap_rec)
+        return KNS_OK;
+    cudaDeviceSynchronize();  // earlier steps may still use the old buffers
+    const int64_t cB = std::max(B, t.cap_B), cM = std::max(M, t.cap_M);
+    const int cS = std::max(S, t.cap_S), cNs = std::max(Ns, t.cap_Ns), cK = std::max(nkeys, t.cap_keys);
+    const int64_t cR = std::max(nrec, t.cap_rec);
+    free_train_scratch(t);
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](auto **p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc((void **)p, bytes > 0 ? bytes : 16);
+    };
+    const size_t bs = (size_t)cB * cS, fd = 6 * ((size_t)cB * cS + (size_t)cM);
+    alloc(&t.t, sizeof(float) * bs);
+    alloc(&t.d_coarse, sizeof(float) * (size_t)cB * cNs);
+    alloc(&t.d_fd, sizeof(float) * fd);
+    alloc(&t.g_fd, sizeof(float) * fd);
+    alloc(&t.d_c, sizeof(float) * bs);
+    alloc(&t.g_dc, sizeof(float) * bs);
+    alloc(&t.rgb_c, sizeof(float) * 3 * bs);
+    alloc(&t.g_rgb, sizeof(float) * 3 * bs);
+    alloc(&t.C, sizeof(float) * 3 * (size_t)cB);
+    alloc(&t.valid, (size_t)cB);
+    alloc(&t.acc, 2 * sizeof(double));
+    alloc(&t.keys, sizeof(int) * 4 * ((size_t)cK + 1));
+    alloc(&t.sorted, sizeof(float4) * (size_t)cR);
+    if (e != cudaSuccess) {
+        free_train_scratch(t);
+        return cuda_err(ctx, e, "training scratch");
+    }
+    t.cap_B = cB;
+    t.cap_S = cS;
+    t.cap_Ns = cNs;
+    t.cap_M = cM;
+    t.cap_keys = cK;
+    t.cap_rec = cR;
+    return KNS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -397,6 +467,7 @@ void kns_destroy(kns_ctx *ctx) {
         DeviceScope ds(ctx->device);
         cudaDeviceSynchronize();
         free_scratch(ctx->ws);
+        free_train_scratch(ctx->ts);
         cudaFree(ctx->d_status);
         cudaFreeHost(ctx->h_live);
         for (int i = 0; i < 4; ++i)
@@ -1077,3 +1148,154 @@ extern "C" kns_status kns_render_noalloc(kns_ctx *ctx, const kns_grid *grid, con
     if (e != cudaSuccess) return cuda_err(ctx, e, "render launch");
     return KNS_OK;
 }
+
+// ------------------------------------------------------------------ training step
+namespace {
+
+kns_status check_train(kns_ctx *ctx, const kns_grid_desc *desc, const float *params, const kns_train_batch *b) {
+    if (!desc || !params || !b) return set_err(ctx, KNS_ERR_INVALID_ARG, "NULL descriptor, params or batch");
+    kns_status st = check_desc(ctx, *desc);
+    if (st != KNS_OK) return st;
+    if (desc->sdf_width != 32 || (desc->sdf_hidden != 2 && desc->sdf_hidden != 3) || desc->pe_pos_L != 4 ||
+        desc->pe_dir_L != 2 || desc->col_use_x != 0)
+        return set_err(ctx, KNS_ERR_UNSUPPORTED,
+                       "training supports width 32, 2 or 3 SDF hidden layers, (L, Ld) = (4, 2), no x colour input");
+    if (b->n_rays < 0 || b->n_eik < 0) return set_err(ctx, KNS_ERR_INVALID_ARG, "negative ray or point count");
+    if (b->n_strat < 2 || b->n_imp < 0 || b->n_strat + b->n_imp > 256)
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "need n_strat >= 2, n_imp >= 0, n_strat + n_imp <= 256");
+    if (b->n_rays > 0 && (!b->origins || !b->dirs || !b->target ||
+                          (!b->t_fixed && (!b->u_strat || (b->n_imp > 0 && !b->u_imp)))))
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "NULL ray array");
+    if (b->n_eik > 0 && !b->eik_points) return set_err(ctx, KNS_ERR_INVALID_ARG, "NULL eikonal points");
+    if (!(b->s > 0.f) || !(b->s_up > 0.f) || !(b->h > 0.f) || !(b->lambda >= 0.f) || !std::isfinite(b->s) ||
+        !std::isfinite(b->s_up) || !std::isfinite(b->h) || !std::isfinite(b->lambda))
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "need s, s_up, h > 0 and lambda >= 0, all finite");
+    const int64_t S = b->n_strat + b->n_imp;
+    const int64_t nrec = 6 * (b->n_rays * S + b->n_eik) + b->n_rays * S;
+    if (b->n_rays > ((int64_t)1 << 26) || b->n_eik > ((int64_t)1 << 28) || nrec >= ((int64_t)1 << 31))
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "batch too large (records must stay below 2^31)");
+    return KNS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kns_status kns_train_forward(kns_ctx *ctx, const kns_grid_desc *desc, const float *params,
+                             const kns_train_batch *batch, float *loss, float *rgb, float *t_samples,
+                             uint64_t *token, void *cuda_stream) {
+    if (!ctx) return KNS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    kns_status st = check_train(ctx, desc, params, batch);
+    if (st != KNS_OK) return st;
+    if (!loss) return set_err(ctx, KNS_ERR_INVALID_ARG, "NULL loss");
+    DeviceScope ds(ctx->device);
+    const kns_train_batch &b = *batch;
+    const int S = b.n_strat + b.n_imp;
+    const int NC = desc->N * desc->N * desc->N;
+    ctx->ts.pending = false;
+    if ((st = ensure_train_scratch(ctx, b.n_rays, S, b.n_strat, b.n_eik, 2 * NC)) != KNS_OK) return st;
+    TrainScratch &t = ctx->ts;
+    kns::TrainArgs a{};
+    a.N = desc->N;
+    a.NC = NC;
+    a.H = desc->sdf_hidden;
+    for (int k = 0; k < 3; ++k) {
+        a.bmin[k] = desc->bbox_min[k];
+        a.bmax[k] = desc->bbox_max[k];
+        a.cscale[k] = (float)desc->N / (desc->bbox_max[k] - desc->bbox_min[k]);
+    }
+    a.beta = desc->softplus_beta;
+    a.inv_beta = 1.f / desc->softplus_beta;
+    a.p_sdf = (int)canon_sdf_params(*desc);
+    a.p_cell = a.p_sdf + (int)canon_col_params(*desc);
+    a.params = params;
+    a.B = b.n_rays;
+    a.o = b.origins;
+    a.w = b.dirs;
+    a.target = b.target;
+    a.Ns = b.n_strat;
+    a.Ni = b.n_imp;
+    a.S = S;
+    a.u_s = b.u_strat;
+    a.u_i = b.u_imp;
+    a.M = b.n_eik;
+    a.P = b.eik_points;
+    a.s = b.s;
+    a.s_up = b.s_up;
+    a.lambda = b.lambda;
+    a.h = b.h;
+    a.t = t.t;
+    a.valid = t.valid;
+    a.d_coarse = t.d_coarse;
+    a.d_fd = t.d_fd;
+    a.g_fd = t.g_fd;
+    a.d_c = t.d_c;
+    a.g_dc = t.g_dc;
+    a.rgb_c = t.rgb_c;
+    a.g_rgb = t.g_rgb;
+    a.C = t.C;
+    a.acc = t.acc;
+    a.loss = loss;
+    a.nkeys = NC;  // the coarse sort uses cell keys only
+    const size_t kk = (size_t)t.cap_keys + 1;
+    a.count = t.keys;
+    a.off = t.keys + kk;
+    a.fill = t.keys + 2 * kk;
+    a.chunk_off = t.keys + 3 * kk;
+    a.sorted = t.sorted;
+    a.status = ctx->d_status;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaSuccess;
+    if (a.B > 0 && b.t_fixed) {
+        a.t = const_cast<float *>(b.t_fixed);  // read only from here on
+        e = kns::train_valid(a, s);
+    } else if (a.B > 0) {
+        e = kns::train_sort(a, kns::TRAIN_COARSE, a.B * a.Ns, ctx->sm_count, s);
+        if (e == cudaSuccess) e = kns::train_coarse_eval(a, ctx->sm_count, s);
+        if (e == cudaSuccess) e = kns::train_importance(a, s);
+    }
+    a.nkeys = 2 * NC;
+    const int64_t nfine = 6 * (a.B * a.S + a.M) + a.B * a.S;
+    if (e == cudaSuccess && nfine > 0) e = kns::train_sort(a, kns::TRAIN_FINE, nfine, ctx->sm_count, s);
+    if (e == cudaSuccess && nfine > 0) e = kns::train_fine_forward(a, ctx->sm_count, s);
+    if (e == cudaSuccess) e = kns::train_loss_forward(a, s);
+    if (e == cudaSuccess && rgb) e = kns::train_rgb_out(a, rgb, s);
+    if (e == cudaSuccess && t_samples && a.B > 0)
+        e = cudaMemcpyAsync(t_samples, a.t, sizeof(float) * (size_t)a.B * a.S, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "training forward");
+    t.args = a;
+    t.pending = true;
+    t.gen += 1;
+    if (token) *token = t.gen;
+    return KNS_OK;
+}
+
+kns_status kns_train_backward(kns_ctx *ctx, uint64_t token, const float *dloss, float *grad, void *cuda_stream) {
+    if (!ctx) return KNS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    TrainScratch &t = ctx->ts;
+    if (!t.pending || token != t.gen)
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "no pending training forward with this token");
+    if (!grad) return set_err(ctx, KNS_ERR_INVALID_ARG, "NULL grad");
+    DeviceScope ds(ctx->device);
+    kns::TrainArgs a = t.args;
+    a.grad = grad;
+    a.dloss = dloss;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)a.NC * a.p_cell, s);
+    if (e == cudaSuccess) e = kns::train_backward(a, ctx->sm_count, s);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "training backward");
+    return KNS_OK;
+}
+
+kns_status kns_train_step(kns_ctx *ctx, const kns_grid_desc *desc, const float *params, const kns_train_batch *batch,
+                          float *loss, float *grad, void *cuda_stream) {
+    uint64_t token = 0;
+    kns_status st = kns_train_forward(ctx, desc, params, batch, loss, nullptr, nullptr, &token, cuda_stream);
+    if (st != KNS_OK) return st;
+    if (!grad) return KNS_OK;
+    return kns_train_backward(ctx, token, nullptr, grad, cuda_stream);
+}
+
+}  // extern "C"

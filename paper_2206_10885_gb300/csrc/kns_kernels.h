@@ -102,4 +102,53 @@ cudaError_t launch_sdf_f32(const Shape &sh, const GridView &g, const float *pts,
 cudaError_t launch_occupancy_f32(const Shape &sh, const GridView &g, float thresh, uint32_t *words,
                                  cudaStream_t s);
 
+// ------------------------------------------------------------------ training step
+// Everything the training kernels read and write (device pointers unless noted; passed by value).
+// Records: coarse samples (B x Ns), central-difference points (6 per fine sample and per eikonal
+// point) and fine-sample centres (B x S).  Records are counting-sorted by key: coarse records by
+// cell; fine records by cell (difference points) and NC + cell (centres).
+struct TrainArgs {
+    int N, NC, H;                      // cells per axis, N^3, SDF hidden layers (width 32)
+    float bmin[3], bmax[3], cscale[3];
+    float beta, inv_beta;
+    int p_cell, p_sdf;                 // canonical floats per cell and in its SDF part
+    const float *params;               // canonical weights
+    float *grad;                       // canonical gradient (accumulated; zeroed by the caller)
+    int64_t B;                         // rays
+    const float *o, *w, *target;       // B x 3
+    int Ns, Ni, S;                     // stratified, importance, total samples per ray
+    const float *u_s, *u_i;            // B x Ns, B x Ni
+    int64_t M;                         // eikonal points
+    const float *P;                    // M x 3
+    float s, s_up, lambda, h;
+    const float *dloss;                // upstream scalar (NULL = 1)
+    // scratch
+    float *t;                          // B x S sample positions
+    uint8_t *valid;                    // B: the ray meets the box
+    float *d_coarse;                   // B x Ns
+    float *d_fd, *g_fd;                // (B S + M) x 6: SDF at the difference points and its upstream
+    float *d_c, *g_dc;                 // B x S: SDF at the sample centres and its upstream
+    float *rgb_c, *g_rgb;              // B x S x 3: colour and its upstream
+    float *C;                          // B x 3 rendered colour
+    double *acc;                       // [0] sum |C - I|, [1] sum (|grad| - 1)^2
+    float *loss;                       // 3: total, colour, eikonal
+    int nkeys;
+    int *count, *off, *fill, *chunk_off;  // nkeys + 1 each
+    float4 *sorted;                    // x, y, z, record id (bit pattern)
+    int *status;
+};
+
+// record sets of the training sort
+enum TrainRecords { TRAIN_COARSE = 0, TRAIN_FINE = 1 };
+
+cudaError_t train_sort(const TrainArgs &a, int which, int64_t n_rec, int sm_count, cudaStream_t s);
+cudaError_t train_coarse_eval(const TrainArgs &a, int sm_count, cudaStream_t s);
+cudaError_t train_importance(const TrainArgs &a, cudaStream_t s);
+cudaError_t train_valid(const TrainArgs &a, cudaStream_t s);
+cudaError_t train_fine_forward(const TrainArgs &a, int sm_count, cudaStream_t s);
+cudaError_t train_loss_forward(const TrainArgs &a, cudaStream_t s);
+cudaError_t train_rgb_out(const TrainArgs &a, float *rgb, cudaStream_t s);
+cudaError_t train_backward(const TrainArgs &a, int sm_count, cudaStream_t s);
+int train_chunk_records();
+
 }  // namespace kns

@@ -43,6 +43,7 @@ STREAM_SDF_CELL = 2
 STREAM_COL_CELL = 3
 STREAM_CAMERA = 4
 STREAM_POINTS = 5
+STREAM_TRAIN = 7
 
 
 def _mix(z: np.ndarray) -> np.ndarray:
@@ -326,3 +327,40 @@ def write_kns(path: str, desc: GridDesc, weights: np.ndarray, occ_bits: np.ndarr
         f.write(weights.tobytes())
         if occ is not None:
             f.write(occ.tobytes())
+
+
+# ---------------------------------------------------------------- training batches
+# The fine-tuning workload: 2^18 rays through a 16^3 grid of width-32 MLPs (3 hidden layers), 64
+# stratified + 32 importance samples per ray, L1 colour + 0.1 x eikonal on 2^16 uniform points.  The
+# rays are random pixels of 8 orbit cameras at 800 x 800; the targets are renders of a perturbed
+# sphere grid (seed 3, per-cell perturbation std 1e-2); the trained weights start from the SAL grid.
+TRAIN_WORKLOAD = dict(grid="c2", n_rays=1 << 18, n_strat=64, n_imp=32, n_eik=1 << 16, s=20.0, s_up=64.0,
+                      lam=0.1, h=1e-2, n_cams=8, W=800, H=800, max_steps=128, eps=1e-4, target_seed=3,
+                      target_std=1e-2)
+
+
+def pixel_rays(cams: np.ndarray, W: int, H: int, sel: np.ndarray):
+    """Origins and unit directions (FP32, n x 3) of global pixel ids cam*H*W + i*W + j (pixel centres)."""
+    cams = np.asarray(cams, dtype=np.float64).reshape(-1, 16)
+    sel = np.asarray(sel, dtype=np.int64)
+    c = sel // (W * H)
+    i = (sel // W) % H
+    j = sel % W
+    cam = cams[c]
+    dx = (j + 0.5 - cam[:, 14]) / cam[:, 12]
+    dy = (i + 0.5 - cam[:, 15]) / cam[:, 13]
+    R = cam[:, :12].reshape(-1, 3, 4)
+    d = R[:, :, 0] * dx[:, None] + R[:, :, 1] * dy[:, None] + R[:, :, 2]
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    return R[:, :, 3].astype(np.float32), d.astype(np.float32)
+
+
+def train_draws(n_rays: int, n_strat: int, n_imp: int, n_eik: int, n_pix: int, seed: int):
+    """Seeded random draws of one training batch (FP32): pixel ids, stratified jitter (n_rays x n_strat),
+    ascending importance uniforms (n_rays x n_imp) and eikonal points uniform in [-1, 1]^3."""
+    sel = (uniform(stream_key(seed, STREAM_TRAIN, 0), n_rays) * n_pix).astype(np.int64)
+    u_s = uniform(stream_key(seed, STREAM_TRAIN, 1), n_rays * n_strat).reshape(n_rays, n_strat)
+    u_i = np.sort(uniform(stream_key(seed, STREAM_TRAIN, 2), n_rays * n_imp).reshape(n_rays, n_imp), axis=1)
+    pts = uniform(stream_key(seed, STREAM_TRAIN, 3), 3 * n_eik).reshape(n_eik, 3) * 2.0 - 1.0
+    # FP32 rounding can tie neighbours but keeps the rows ascending
+    return sel, u_s.astype(np.float32), u_i.astype(np.float32), pts.astype(np.float32)
