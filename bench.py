@@ -8,7 +8,12 @@ between steps a 512 MiB buffer is overwritten to flush the 126 MB L2 (the grid's
 in L2), outside the events.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16]
-                    [--workload c2|c3s|c3l|c1] [--impl kns|reference]
+                    [--workload c2|c3s|c3l|c1|train] [--impl kns|reference]
+
+--workload train times the NeuS-style training step instead (kns_train_step: loss and hand-written
+backward): 2^18 rays x (64 stratified + 32 importance samples) through the 16^3 grid (3 hidden
+layers of width 32), L1 colour + 0.1 x eikonal on 2^16 points; targets are renders of a perturbed
+sphere grid by the render path; metric Mrays/s through the step.
 
 Multi-GPU (torchrun): every rank renders its own batch on its own GPU (replicas, no
 collective on the data path); value = rays of all ranks / max-over-ranks time.
@@ -360,20 +365,267 @@ def run_kns(args, rank, world, local_rank):
     ctx.close()
 
 
+# ---------------------------------------------------------------- training step
+TRAIN_METRIC = "Mrays/s through the NeuS training step (loss + hand-written backward)"
+
+
+def train_macs(desc):
+    """Algorithmic multiply-adds per record of the two backward kernels (16 outputs of the SDF MLP;
+    biases and activations not counted): a difference point needs d, its input-gradient and the
+    weight gradient; a sample centre needs d and z, the colour MLP and both backward passes."""
+    IN = 3 + 6 * desc.pe_pos_L
+    Wd, Hd = desc.sdf_width, desc.sdf_hidden
+    fwd_d = IN * Wd + (Hd - 1) * Wd * Wd + Wd
+    fwd_full = IN * Wd + (Hd - 1) * Wd * Wd + Wd * (1 + desc.feat_dim)
+    back_in_d = Wd + (Hd - 1) * Wd * Wd
+    back_in_full = Wd * (1 + desc.feat_dim) + (Hd - 1) * Wd * Wd
+    cin = desc.feat_dim + 3 + 3 + 6 * desc.pe_dir_L
+    col = cin * desc.col_width + desc.col_width * 3
+    col_back_in = desc.col_width * 3 + (desc.feat_dim + 3) * desc.col_width
+    fd = fwd_d + back_in_d + fwd_d
+    centre = fwd_full + col + col_back_in + col + back_in_full + fwd_full
+    return fd, centre, fwd_d, fwd_full + col
+
+
+def train_setup(torch, kns, S, ctx, dev, seed):
+    wl = S.TRAIN_WORKLOAD
+    desc = S.config_desc(wl["grid"])
+    W, H, n_cams = wl["W"], wl["H"], wl["n_cams"]
+    cams = S.orbit_cameras(n_cams, W, H, seed=1)
+    tw = S.sal_sphere_grid(desc, seed=wl["target_seed"], perturb_std=wl["target_std"])
+    tgrid = kns.Grid.load(ctx, desc, tw)
+    img = kns.render(ctx, tgrid, cams, W, H, wl["max_steps"], wl["eps"])["rgb"]
+    sel, u_s, u_i, P = S.train_draws(wl["n_rays"], wl["n_strat"], wl["n_imp"], wl["n_eik"], n_cams * W * H, seed)
+    o, d = S.pixel_rays(cams, W, H, sel)
+    tgt = img[torch.from_numpy(sel).to(dev)].contiguous()
+    torch.cuda.synchronize()
+    tgrid.free()
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    host = dict(o=o, d=d, target=tgt.cpu().numpy(), u_s=u_s, u_i=u_i, P=P)
+    batch = kns.train.TrainBatch(f(o), f(d), tgt, f(u_s), f(u_i), f(P), s=wl["s"], s_up=wl["s_up"], lam=wl["lam"],
+                                 h=wl["h"])
+    params = f(S.sal_sphere_grid(desc, seed=0))
+    return wl, desc, batch, params, host
+
+
+def train_config(wl, desc, dtype_note):
+    return {"workload": "train: NeuS training step on a %d^3 Kilo-grid (SDF MLP %d hidden x %d, softplus beta=%g, "
+                        "PE L=%d; colour MLP %d x %d); %d rays x (%d stratified + %d importance) samples, L1 colour "
+                        "+ %g x eikonal on %d points, s=%g, s_up=%g, central-difference step h=%g; %s"
+                        % (desc.N, desc.sdf_hidden, desc.sdf_width, desc.softplus_beta, desc.pe_pos_L,
+                           desc.col_hidden, desc.col_width, wl["n_rays"], wl["n_strat"], wl["n_imp"], wl["lam"],
+                           wl["n_eik"], wl["s"], wl["s_up"], wl["h"], dtype_note),
+            "rays_per_step": wl["n_rays"], "samples_per_ray": wl["n_strat"] + wl["n_imp"],
+            "eikonal_points": wl["n_eik"], "grid": "%d^3" % desc.N,
+            "l2": "flushed between steps (512 MiB write outside the timed events); step scratch ~5 GB > L2",
+            "inputs": "synthetic: rays at seeded random pixels of 8 orbit cameras at 800x800, targets rendered "
+                      "from a perturbed sphere grid (seed 3, std 1e-2), trained weights = SAL grid seed 0"}
+
+
+def oracle_train_rate(desc, w, host, wl, seconds: float, seed: int = 0):
+    """Times the FP64 oracle's loss + gradient (as it stands) on seeded random subsets of the batch."""
+    import oracle as O
+    rng = np.random.default_rng(seed)
+    B, M = wl["n_rays"], wl["n_eik"]
+    done, elapsed, n = 0, 0.0, 8
+    while elapsed < seconds:
+        r = rng.choice(B, n, replace=False)
+        m = rng.choice(M, max(1, n * M // B), replace=False)
+        args = (wl["s"], wl["s_up"], host["o"][r].astype(np.float64), host["d"][r].astype(np.float64),
+                host["target"][r].astype(np.float64), host["u_s"][r].astype(np.float64),
+                host["u_i"][r].astype(np.float64), host["P"][m].astype(np.float64), wl["lam"], wl["h"])
+        t0 = time.perf_counter()
+        O.train_grad(desc, w, *args)
+        dt = time.perf_counter() - t0
+        elapsed += dt
+        done += n
+        if dt < seconds / 8:
+            n *= 2
+    return done / elapsed / 1e6, done, elapsed, O.num_threads()
+
+
+def oracle_train_inputs(S, wl, desc, n: int = 4096):
+    """The first n rays of the training batch (the GPU arm's draws) with targets rendered by the oracle."""
+    import oracle as O
+    cams = S.orbit_cameras(wl["n_cams"], wl["W"], wl["H"], seed=1)
+    sel, u_s, u_i, P = S.train_draws(wl["n_rays"], wl["n_strat"], wl["n_imp"], wl["n_eik"],
+                                     wl["n_cams"] * wl["W"] * wl["H"], 0)
+    o, d = S.pixel_rays(cams, wl["W"], wl["H"], sel[:n])
+    tw = S.sal_sphere_grid(desc, seed=wl["target_seed"], perturb_std=wl["target_std"])
+    tgt = O.render(desc, tw, None, cams, wl["W"], wl["H"], wl["max_steps"], wl["eps"], sel=sel[:n])["rgb"]
+    m = max(1, n * wl["n_eik"] // wl["n_rays"])  # the batch's share of eikonal points
+    return dict(o=o, d=d, target=tgt, u_s=u_s[:n], u_i=u_i[:n], P=P[:m]), dict(wl, n_rays=n, n_eik=m)
+
+
+def run_train_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2206_10885_gb300 import synth as S
+    wl = S.TRAIN_WORKLOAD
+    desc = S.config_desc(wl["grid"])
+    host, wl_sub = oracle_train_inputs(S, wl, desc)
+    w = S.sal_sphere_grid(desc, seed=0)
+    per_step = max(1.0, args.cpu_seconds / max(1, args.steps))
+    for _ in range(args.warmup):
+        oracle_train_rate(desc, w, host, wl_sub, 0.2)
+    total, total_s, cores = 0, 0.0, 1
+    for k in range(args.steps):
+        v, n, s, cores = oracle_train_rate(desc, w, host, wl_sub, per_step, seed=k + 1)
+        total += n
+        total_s += s
+    value = total / total_s / 1e6
+    line = {"impl": "reference", "metric": TRAIN_METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wl["n_rays"] / (value * 1e6),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": train_config(wl, desc, "fp64 oracle"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d seeded random rays of the first 4096 of the batch, with their share of "
+                                       "eikonal points, over %d steps (%.1f s)" % (total, args.steps, total_s)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_train(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2206_10885_gb300 as kns
+    from paper_2206_10885_gb300 import build as kbuild
+    from paper_2206_10885_gb300 import synth as S
+
+    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_2206_10885_gb300", "libkns.so")):
+        kbuild.build()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    ctx = kns.Context(local_rank)
+    wl, desc, batch, params, host = train_setup(torch, kns, S, ctx, dev, seed=rank)
+    stream = torch.cuda.current_stream()
+    loss = torch.empty(3, dtype=torch.float32, device=dev)
+    grad = torch.empty_like(params)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        kns.train.step(ctx, desc, params, batch, stream=stream, loss_out=loss, grad_out=grad)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    # per-phase device time and record counts from a step timed with CUDA events
+    batch.timing = True
+    step()
+    st = kns.train.stats(ctx)
+    batch.timing = False
+    fd_mac, centre_mac, coarse_mac, _ = train_macs(desc)
+
+    clocks = ClockSampler(local_rank).start() if rank == 0 else None
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    times = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(times)
+    # e2e through the public API: the batch's inputs copied from pinned host memory every step, the
+    # loss read back
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v, dtype=np.float32)).pin_memory() for k, v in host.items()}
+    dev_in = {"o": batch.origins, "d": batch.dirs, "target": batch.target, "u_s": batch.u_strat,
+              "u_i": batch.u_imp, "P": batch.eik_points}
+    loss_host = torch.empty(3, dtype=torch.float32, pin_memory=True)
+    h2d = sum(v.numel() * v.element_size() for v in pin.values())
+    d2h = loss_host.numel() * 4
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for k, v in pin.items():
+            dev_in[k].copy_(v, non_blocking=True)
+        step()
+        loss_host.copy_(loss, non_blocking=True)
+        stream.synchronize()
+    e2e_s = time.perf_counter() - t0
+    clock_info = clocks.stop() if clocks else None
+
+    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    e_max = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+        dist.all_reduce(e_max, op=dist.ReduceOp.MAX)
+    total_ms, e2e_s = float(t_max.item()), float(e_max.item())
+    n_rays = wl["n_rays"]
+    value = world * n_rays * args.steps / (total_ms * 1e-3) / 1e6
+    if rank == 0:
+        peaks = load_peaks()
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+        flops = 2.0 * st["records_fd"] * fd_mac
+        kms = st["ms_fd_backward"]
+        achieved = flops / (kms * 1e-3) / 1e12 if kms > 0 else 0.0
+        roof = {"bound": "alu", "peak": fp32_peak, "unit": "TFLOP/s", "kernel": "k_backward (difference points)",
+                "peak_source": FP32_PEAK_NOTE, "achieved": achieved, "frac": achieved / fp32_peak,
+                "traffic": profile_traffic("k_backward_fd_train"), "algorithmic_flop_per_launch": flops,
+                "kernel_ms_per_launch": kms, "flop_per_record": 2 * fd_mac, "records_per_launch": st["records_fd"]}
+        phases = {k: st[k] for k in st if k.startswith("ms_")}
+        counts = {k: st[k] for k in ("rays", "samples_per_ray", "eik_points", "records_coarse", "records_fd",
+                                     "records_centre")}
+        work = {"fp32_flop_algorithmic": 2.0 * (st["records_fd"] * (fd_mac + coarse_mac) +
+                                                st["records_centre"] * centre_mac +
+                                                st["records_coarse"] * coarse_mac)}
+        work["fp32_tflops_whole_step"] = work["fp32_flop_algorithmic"] / (total_ms / args.steps * 1e-3) / 1e12
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            o_host, wl_sub = oracle_train_inputs(S, wl, desc)
+            v, n, s, cores = oracle_train_rate(desc, params.cpu().numpy(), o_host, wl_sub, args.cpu_seconds)
+            cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": "%d seeded random rays of the first 4096 of the %d-ray batch with their share of the "
+                             "eikonal points (%.1f s of FP64 oracle loss + gradient)" % (n, n_rays, s)}
+        line = {"metric": TRAIN_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(train_config(wl, desc, "fp32"),
+                               parallelism="replicas" if world > 1 else "single GPU"),
+                "roofline": roof, "cpu_baseline": cpu, "phases_ms_per_step": phases, "counts_per_step": counts,
+                "work_per_step": work,
+                "e2e": {"value": world * n_rays * args.steps / e2e_s / 1e6, "unit": UNIT,
+                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+                "clocks": clock_info, "gpu_launches": args.steps * 17,
+                "launch_count_source": "fixed kernel sequence of kns_train_step: coarse hist/scan/scatter/eval, "
+                                       "importance, fine hist/scan/scatter, difference and centre forward, "
+                                       "composite, eikonal, finalize, composite and eikonal upstream, centre and "
+                                       "difference backward (memsets and copies not counted)",
+                "step_ms_min": min(times), "step_ms_median": statistics.median(times),
+                "final_loss": [float(x) for x in loss.cpu()]}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
-        run_reference(args, rank, world)
+        if args.workload == "train":
+            run_train_reference(args, rank, world)
+        else:
+            run_reference(args, rank, world)
         return
     if world > 1:
         import torch
         import torch.distributed as dist
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    run_kns(args, rank, world, local_rank)
+    if args.workload == "train":
+        run_train(args, rank, world, local_rank)
+    else:
+        run_kns(args, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

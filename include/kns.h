@@ -238,7 +238,19 @@ typedef struct {
     const float *eik_points;
     float s, s_up, lambda, h;
     const float *t_fixed;
+    int32_t timing; /* 1: time the phases with CUDA events (kns_train_get_stats) */
 } kns_train_batch;
+
+/* Work counts and, when the forward ran with timing = 1, per-phase device milliseconds of the latest
+ * training forward (and its backward, once run).  Records are SDF evaluations: coarse samples,
+ * central-difference points (6 per sample and per eikonal point) and sample centres. */
+typedef struct {
+    int64_t rays, eik_points;
+    int32_t samples_per_ray, pad;
+    int64_t records_coarse, records_fd, records_centre;
+    float ms_coarse, ms_sort, ms_fd_forward, ms_centre_forward, ms_loss;
+    float ms_upstream, ms_centre_backward, ms_fd_backward, ms_total;
+} kns_train_stats;
 
 /* Training loss (Sec. 3.2.2: L = L_color + lambda L_eikonal) of a Kilo-grid whose canonical FP32 weights
  * `params` (device, N^3 x params-per-cell) the caller owns, e.g. a framework parameter tensor.
@@ -266,6 +278,10 @@ kns_status kns_train_forward(kns_ctx *ctx, const kns_grid_desc *desc, const floa
  * hand-written backward of the forward above: |.| and max(., 0) take derivative 0 at their kinks.
  * Errors: INVALID_ARG (token not the context's latest forward, NULL grad), CUDA. */
 kns_status kns_train_backward(kns_ctx *ctx, uint64_t token, const float *dloss, float *grad, void *cuda_stream);
+
+/* Statistics of the latest training forward/backward on the context (waits for its timing events).
+ * Errors: INVALID_ARG (no forward yet), CUDA. */
+kns_status kns_train_get_stats(kns_ctx *ctx, kns_train_stats *out);
 
 /* kns_train_forward followed by kns_train_backward (grad NULL: forward only). */
 kns_status kns_train_step(kns_ctx *ctx, const kns_grid_desc *desc, const float *params,

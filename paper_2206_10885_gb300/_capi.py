@@ -59,7 +59,15 @@ class kns_train_batch(C.Structure):
     _fields_ = [("n_rays", C.c_int64), ("origins", C.c_void_p), ("dirs", C.c_void_p), ("target", C.c_void_p),
                 ("n_strat", C.c_int32), ("n_imp", C.c_int32), ("u_strat", C.c_void_p), ("u_imp", C.c_void_p),
                 ("n_eik", C.c_int64), ("eik_points", C.c_void_p), ("s", C.c_float), ("s_up", C.c_float),
-                ("lambda_", C.c_float), ("h", C.c_float), ("t_fixed", C.c_void_p)]
+                ("lambda_", C.c_float), ("h", C.c_float), ("t_fixed", C.c_void_p), ("timing", C.c_int32)]
+
+
+class kns_train_stats(C.Structure):
+    _fields_ = [("rays", C.c_int64), ("eik_points", C.c_int64), ("samples_per_ray", C.c_int32), ("pad", C.c_int32),
+                ("records_coarse", C.c_int64), ("records_fd", C.c_int64), ("records_centre", C.c_int64),
+                ("ms_coarse", C.c_float), ("ms_sort", C.c_float), ("ms_fd_forward", C.c_float),
+                ("ms_centre_forward", C.c_float), ("ms_loss", C.c_float), ("ms_upstream", C.c_float),
+                ("ms_centre_backward", C.c_float), ("ms_fd_backward", C.c_float), ("ms_total", C.c_float)]
 
 
 class kns_render_opts(C.Structure):
@@ -127,6 +135,8 @@ def lib():
             L.kns_train_backward.restype = st
             L.kns_train_step.argtypes = [vp, C.POINTER(kns_grid_desc), vp, C.POINTER(kns_train_batch), vp, vp, vp]
             L.kns_train_step.restype = st
+            L.kns_train_get_stats.argtypes = [vp, C.POINTER(kns_train_stats)]
+            L.kns_train_get_stats.restype = st
             _lib = L
     return _lib
 
@@ -256,3 +266,9 @@ def kns_train_step(ctx: int, desc: kns_grid_desc, params_ptr: int, batch: kns_tr
                    grad_ptr: int = None, stream: int = 0) -> None:
     desc = desc_struct(desc)
     _check(lib().kns_train_step(ctx, C.byref(desc), params_ptr, C.byref(batch), loss_ptr, grad_ptr, stream), ctx)
+
+
+def kns_train_get_stats(ctx: int) -> dict:
+    st = kns_train_stats()
+    _check(lib().kns_train_get_stats(ctx, C.byref(st)), ctx)
+    return {k: getattr(st, k) for k, _ in kns_train_stats._fields_ if k != "pad"}

@@ -40,9 +40,13 @@ struct TrainScratch {
     double *acc = nullptr;
     int *keys = nullptr;           // count, off, fill, chunk_off (4 x (keys + 1))
     float4 *sorted = nullptr;
+    int *d_counts = nullptr;       // records: coarse, difference points, centres
+    // phase timing (events created on first use)
+    cudaEvent_t ev[2 * 8] = {};
+    bool timed = false;
     // the forward pass whose state the scratch holds
     uint64_t gen = 0;
-    bool pending = false;
+    bool pending = false, backward_done = false;
     kns::TrainArgs args{};
 };
 
@@ -372,12 +376,15 @@ kns_status ensure_scratch(kns_ctx *ctx, int64_t rays, int nc, int cams) {
 
 void free_train_scratch(TrainScratch &t) {
     void *ps[] = {t.t, t.d_coarse, t.d_fd, t.g_fd, t.d_c, t.g_dc, t.rgb_c, t.g_rgb, t.C, t.valid, t.acc, t.keys,
-                  t.sorted};
+                  t.sorted, t.d_counts};
     for (void *p : ps)
         if (p) cudaFree(p);
     const uint64_t gen = t.gen;
+    cudaEvent_t ev[16];
+    for (int i = 0; i < 16; ++i) ev[i] = t.ev[i];
     t = TrainScratch{};
     t.gen = gen;
+    for (int i = 0; i < 16; ++i) t.ev[i] = ev[i];
 }
 
 // Grows the training scratch for B rays of S samples (Ns stratified), M eikonal points, nkeys keys.
@@ -409,6 +416,7 @@ kns_status ensure_train_scratch(kns_ctx *ctx, int64_t B, int S, int Ns, int64_t 
     alloc(&t.acc, 2 * sizeof(double));
     alloc(&t.keys, sizeof(int) * 4 * ((size_t)cK + 1));
     alloc(&t.sorted, sizeof(float4) * (size_t)cR);
+    alloc(&t.d_counts, 4 * sizeof(int));
     if (e != cudaSuccess) {
         free_train_scratch(t);
         return cuda_err(ctx, e, "training scratch");
@@ -468,6 +476,8 @@ void kns_destroy(kns_ctx *ctx) {
         cudaDeviceSynchronize();
         free_scratch(ctx->ws);
         free_train_scratch(ctx->ts);
+        for (cudaEvent_t ev : ctx->ts.ev)
+            if (ev) cudaEventDestroy(ev);
         cudaFree(ctx->d_status);
         cudaFreeHost(ctx->h_live);
         for (int i = 0; i < 4; ++i)
@@ -1247,25 +1257,50 @@ kns_status kns_train_forward(kns_ctx *ctx, const kns_grid_desc *desc, const floa
     a.status = ctx->d_status;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     cudaError_t e = cudaSuccess;
+    t.timed = b.timing != 0;
+    if (t.timed)
+        for (int i = 0; i < 16 && e == cudaSuccess; ++i)
+            if (!t.ev[i]) e = cudaEventCreate(&t.ev[i]);
+    auto mark = [&](int i) {
+        if (t.timed && e == cudaSuccess) e = cudaEventRecord(t.ev[i], s);
+    };
+    if (e == cudaSuccess) e = cudaMemsetAsync(t.d_counts, 0, 4 * sizeof(int), s);
+    mark(0);
     if (a.B > 0 && b.t_fixed) {
         a.t = const_cast<float *>(b.t_fixed);  // read only from here on
-        e = kns::train_valid(a, s);
+        if (e == cudaSuccess) e = kns::train_valid(a, s);
     } else if (a.B > 0) {
-        e = kns::train_sort(a, kns::TRAIN_COARSE, a.B * a.Ns, ctx->sm_count, s);
+        if (e == cudaSuccess) e = kns::train_sort(a, kns::TRAIN_COARSE, a.B * a.Ns, ctx->sm_count, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(t.d_counts, a.off + NC, sizeof(int), cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess) e = kns::train_coarse_eval(a, ctx->sm_count, s);
         if (e == cudaSuccess) e = kns::train_importance(a, s);
     }
+    mark(1);
     a.nkeys = 2 * NC;
     const int64_t nfine = 6 * (a.B * a.S + a.M) + a.B * a.S;
+    mark(2);
     if (e == cudaSuccess && nfine > 0) e = kns::train_sort(a, kns::TRAIN_FINE, nfine, ctx->sm_count, s);
-    if (e == cudaSuccess && nfine > 0) e = kns::train_fine_forward(a, ctx->sm_count, s);
+    if (e == cudaSuccess && nfine > 0)
+        e = cudaMemcpyAsync(t.d_counts + 1, a.off + NC, sizeof(int), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && nfine > 0)
+        e = cudaMemcpyAsync(t.d_counts + 2, a.off + 2 * NC, sizeof(int), cudaMemcpyDeviceToDevice, s);
+    mark(3);
+    mark(4);
+    if (e == cudaSuccess && nfine > 0) e = kns::train_fd_forward(a, ctx->sm_count, s);
+    mark(5);
+    mark(6);
+    if (e == cudaSuccess && nfine > 0) e = kns::train_centre_forward(a, ctx->sm_count, s);
+    mark(7);
+    mark(8);
     if (e == cudaSuccess) e = kns::train_loss_forward(a, s);
+    mark(9);
     if (e == cudaSuccess && rgb) e = kns::train_rgb_out(a, rgb, s);
     if (e == cudaSuccess && t_samples && a.B > 0)
         e = cudaMemcpyAsync(t_samples, a.t, sizeof(float) * (size_t)a.B * a.S, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_err(ctx, e, "training forward");
     t.args = a;
     t.pending = true;
+    t.backward_done = false;
     t.gen += 1;
     if (token) *token = t.gen;
     return KNS_OK;
@@ -1283,9 +1318,54 @@ kns_status kns_train_backward(kns_ctx *ctx, uint64_t token, const float *dloss, 
     a.grad = grad;
     a.dloss = dloss;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    cudaError_t e = cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)a.NC * a.p_cell, s);
-    if (e == cudaSuccess) e = kns::train_backward(a, ctx->sm_count, s);
+    cudaError_t e = cudaSuccess;
+    auto mark = [&](int i) {
+        if (t.timed && e == cudaSuccess) e = cudaEventRecord(t.ev[i], s);
+    };
+    mark(10);
+    e = cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)a.NC * a.p_cell, s);
+    if (e == cudaSuccess) e = kns::train_upstream(a, s);
+    mark(11);
+    mark(12);
+    if (e == cudaSuccess) e = kns::train_centre_backward(a, ctx->sm_count, s);
+    mark(13);
+    mark(14);
+    if (e == cudaSuccess) e = kns::train_fd_backward(a, ctx->sm_count, s);
+    mark(15);
+    t.backward_done = true;
     if (e != cudaSuccess) return cuda_err(ctx, e, "training backward");
+    return KNS_OK;
+}
+
+kns_status kns_train_get_stats(kns_ctx *ctx, kns_train_stats *out) {
+    if (!ctx || !out) return ctx ? set_err(ctx, KNS_ERR_INVALID_ARG, "NULL out") : KNS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    TrainScratch &t = ctx->ts;
+    if (!t.pending) return set_err(ctx, KNS_ERR_INVALID_ARG, "no training forward on this context");
+    DeviceScope ds(ctx->device);
+    kns_train_stats st{};
+    const kns::TrainArgs &a = t.args;
+    st.rays = a.B;
+    st.samples_per_ray = a.S;
+    st.eik_points = a.M;
+    int cnt[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpy(cnt, t.d_counts, sizeof(cnt), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "training stats");
+    st.records_coarse = cnt[0];
+    st.records_fd = cnt[1];
+    st.records_centre = cnt[2] - cnt[1];  // off[2 NC] - off[NC]
+    if (t.timed) {
+        float *dst[8] = {&st.ms_coarse, &st.ms_sort, &st.ms_fd_forward, &st.ms_centre_forward, &st.ms_loss,
+                         &st.ms_upstream, &st.ms_centre_backward, &st.ms_fd_backward};
+        const int n = t.backward_done ? 8 : 5;
+        for (int k = 0; k < n; ++k) {
+            if (cudaEventSynchronize(t.ev[2 * k + 1]) != cudaSuccess ||
+                cudaEventElapsedTime(dst[k], t.ev[2 * k], t.ev[2 * k + 1]) != cudaSuccess)
+                *dst[k] = 0.f;
+            st.ms_total += *dst[k];
+        }
+    }
+    *out = st;
     return KNS_OK;
 }
 

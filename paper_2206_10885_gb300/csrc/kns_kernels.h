@@ -145,10 +145,13 @@ cudaError_t train_sort(const TrainArgs &a, int which, int64_t n_rec, int sm_coun
 cudaError_t train_coarse_eval(const TrainArgs &a, int sm_count, cudaStream_t s);
 cudaError_t train_importance(const TrainArgs &a, cudaStream_t s);
 cudaError_t train_valid(const TrainArgs &a, cudaStream_t s);
-cudaError_t train_fine_forward(const TrainArgs &a, int sm_count, cudaStream_t s);
+cudaError_t train_fd_forward(const TrainArgs &a, int sm_count, cudaStream_t s);
+cudaError_t train_centre_forward(const TrainArgs &a, int sm_count, cudaStream_t s);
 cudaError_t train_loss_forward(const TrainArgs &a, cudaStream_t s);
 cudaError_t train_rgb_out(const TrainArgs &a, float *rgb, cudaStream_t s);
-cudaError_t train_backward(const TrainArgs &a, int sm_count, cudaStream_t s);
+cudaError_t train_upstream(const TrainArgs &a, cudaStream_t s);
+cudaError_t train_centre_backward(const TrainArgs &a, int sm_count, cudaStream_t s);
+cudaError_t train_fd_backward(const TrainArgs &a, int sm_count, cudaStream_t s);
 int train_chunk_records();
 
 }  // namespace kns

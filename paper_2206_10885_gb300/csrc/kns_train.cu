@@ -973,11 +973,13 @@ cudaError_t train_valid(const TrainArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t train_fine_forward(const TrainArgs &a, int sm_count, cudaStream_t s) {
+cudaError_t train_fd_forward(const TrainArgs &a, int sm_count, cudaStream_t s) {
     const int64_t fd_chunks = 6 * (a.B * a.S + a.M) / CHUNK + a.NC + 1;
-    cudaError_t e = a.H == 3 ? eval_d_h<3>(a, 0, a.NC, a.d_fd, grid_for(sm_count, 4, fd_chunks), s)
-                             : eval_d_h<2>(a, 0, a.NC, a.d_fd, grid_for(sm_count, 4, fd_chunks), s);
-    if (e != cudaSuccess) return e;
+    return a.H == 3 ? eval_d_h<3>(a, 0, a.NC, a.d_fd, grid_for(sm_count, 4, fd_chunks), s)
+                    : eval_d_h<2>(a, 0, a.NC, a.d_fd, grid_for(sm_count, 4, fd_chunks), s);
+}
+
+cudaError_t train_centre_forward(const TrainArgs &a, int sm_count, cudaStream_t s) {
     const int64_t c_chunks = a.B * a.S / CHUNK + a.NC + 1;
     const int blocks = grid_for(sm_count, 4, c_chunks);
     return a.H == 3 ? centre_fwd_h<3>(a, blocks, s) : centre_fwd_h<2>(a, blocks, s);
@@ -997,15 +999,19 @@ cudaError_t train_rgb_out(const TrainArgs &a, float *rgb, cudaStream_t s) {
     return cudaSuccess;
 }
 
-cudaError_t train_backward(const TrainArgs &a, int sm_count, cudaStream_t s) {
+cudaError_t train_upstream(const TrainArgs &a, cudaStream_t s) {
     if (a.B > 0) k_composite_bwd<<<(unsigned)((a.B + 127) / 128), 128, 0, s>>>(a);
     if (a.M > 0) k_eik_bwd<<<(unsigned)((a.M + 127) / 128), 128, 0, s>>>(a);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t train_centre_backward(const TrainArgs &a, int sm_count, cudaStream_t s) {
     const int64_t c_chunks = a.B * a.S / CHUNK + a.NC + 1;
-    e = a.H == 3 ? backward_h<3, true>(a, grid_for(sm_count, 1, c_chunks), s)
-                 : backward_h<2, true>(a, grid_for(sm_count, 1, c_chunks), s);
-    if (e != cudaSuccess) return e;
+    return a.H == 3 ? backward_h<3, true>(a, grid_for(sm_count, 1, c_chunks), s)
+                    : backward_h<2, true>(a, grid_for(sm_count, 1, c_chunks), s);
+}
+
+cudaError_t train_fd_backward(const TrainArgs &a, int sm_count, cudaStream_t s) {
     const int64_t fd_chunks = 6 * (a.B * a.S + a.M) / CHUNK + a.NC + 1;
     return a.H == 3 ? backward_h<3, false>(a, grid_for(sm_count, 1, fd_chunks), s)
                     : backward_h<2, false>(a, grid_for(sm_count, 1, fd_chunks), s);

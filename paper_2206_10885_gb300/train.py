@@ -31,6 +31,7 @@ class TrainBatch:
     lam: float = 0.1
     h: float = 1e-2
     t_fixed: "torch.Tensor" = None  # (B, Ns + Ni) sample positions to use instead of placing them
+    timing: bool = False            # time the phases with CUDA events (stats())
 
     def __post_init__(self):
         for k in ("origins", "dirs", "target", "u_strat", "u_imp", "eik_points", "t_fixed"):
@@ -60,6 +61,7 @@ class TrainBatch:
         b.eik_points = self.eik_points.data_ptr() if self.eik_points.numel() else None
         b.s, b.s_up, b.lambda_, b.h = float(self.s), float(self.s_up), float(self.lam), float(self.h)
         b.t_fixed = self.t_fixed.data_ptr() if self.t_fixed is not None else None
+        b.timing = 1 if self.timing else 0
         return b
 
 
@@ -94,10 +96,21 @@ def backward(ctx, token: int, params, dloss=None, stream=None):
     return grad
 
 
-def step(ctx, desc, params, batch: TrainBatch, stream=None):
-    """One fused training step: (loss parts tensor, gradient tensor)."""
-    loss, tok, _, _ = forward(ctx, desc, params, batch, stream=stream)
-    return loss, backward(ctx, tok, params, stream=stream)
+def step(ctx, desc, params, batch: TrainBatch, stream=None, loss_out=None, grad_out=None):
+    """One fused training step (kns_train_step): (loss parts tensor, gradient tensor).
+
+    loss_out (3 floats) and grad_out (params' shape) may be given to reuse buffers."""
+    import torch
+    loss = loss_out if loss_out is not None else torch.empty(3, dtype=torch.float32, device=params.device)
+    grad = grad_out if grad_out is not None else torch.empty_like(params)
+    capi.kns_train_step(ctx.handle, desc, params.data_ptr(), batch.c_struct(), loss.data_ptr(), grad.data_ptr(),
+                        _stream(stream))
+    return loss, grad
+
+
+def stats(ctx) -> dict:
+    """Record counts and per-phase device ms (batches built with timing=True) of the latest step."""
+    return capi.kns_train_get_stats(ctx.handle)
 
 
 def _function():

@@ -54,7 +54,8 @@ int main(void) {
          offsetof(kns_camera, cy));
   printf("%zu %zu\\n", offsetof(kns_frame, hit), offsetof(kns_render_opts, refine_steps));
   printf("%zu %zu %zu %zu\\n", sizeof(kns_train_batch), offsetof(kns_train_batch, n_eik),
-         offsetof(kns_train_batch, s), offsetof(kns_train_batch, h));
+         offsetof(kns_train_batch, s), offsetof(kns_train_batch, timing));
+  printf("%zu %zu\\n", sizeof(kns_train_stats), offsetof(kns_train_stats, ms_fd_backward));
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -64,7 +65,8 @@ int main(void) {
             C.sizeof(capi.kns_render_opts), capi.kns_grid_desc.softplus_beta.offset,
             capi.kns_grid_desc.bbox_max.offset, capi.kns_camera.cy.offset, capi.kns_frame.hit.offset,
             capi.kns_render_opts.refine_steps.offset, C.sizeof(capi.kns_train_batch),
-            capi.kns_train_batch.n_eik.offset, capi.kns_train_batch.s.offset, capi.kns_train_batch.h.offset]
+            capi.kns_train_batch.n_eik.offset, capi.kns_train_batch.s.offset, capi.kns_train_batch.timing.offset,
+            C.sizeof(capi.kns_train_stats), capi.kns_train_stats.ms_fd_backward.offset]
     assert vals == want
 
 
