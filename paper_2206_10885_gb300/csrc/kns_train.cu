@@ -8,203 +8,30 @@
 //   C = sum_i T_i alpha_i c_i; L = mean |C - I|_1 + lambda mean (|grad d| - 1)^2 over eikonal points,
 //   the gradient again by central differences.  Sample positions are not differentiated.
 //
-// How: every SDF evaluation is a record (a point and an id).  Records are counting-sorted by the
-// cell that evaluates them, and cut into chunks of at most CHUNK records of one cell.  A block takes
-// a chunk, stages the cell's weights in shared memory and gives each thread one record at a time:
-// the forward pass runs in registers with weights read as warp-uniform float4 broadcasts.  In the
-// backward kernels each thread also writes its record's layer inputs and output deltas as one
-// column of a shared-memory tile (128 records), and the block then forms the weight gradient of
-// the tile as outer-product sums: thread-owned 4x4 blocks of (output, input) entries accumulate in
-// registers over every tile of the chunk and are added to the global gradient once per chunk.
-// Bias gradients come out of the same sums through a constant-one input row.
+// How: every SDF evaluation is a record (a point and an id).  This file makes the records and
+// counting-sorts them by the cell that evaluates them (chunks of at most CHUNK records of one cell
+// are what the grouped MLP kernels of kns_train_tile.cu take), places the importance samples, and
+// does the per-ray volume rendering, the loss and the upstream gradients of the rendered samples.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "kns_device.cuh"
 #include "kns_kernels.h"
+#include "kns_train.cuh"
 
 namespace kns {
 namespace {
 
-constexpr int PE_L = 4;                   // encoding frequencies of x
-constexpr int A0ROWS = 28;                // 27 encoded inputs + the constant-one row
-constexpr int TILE = 128;                 // records per tile = threads per block
-constexpr int RS = TILE + 4;              // shared row stride (floats): 16-byte rows, shifted banks
-constexpr int CHUNK = 4096;               // records per work chunk
-constexpr int MAXS = 256;                 // samples per ray
+using train::CHUNK;
+using train::MAXS;
+using train::fd_normal;
+using train::grid_for;
+using train::load3;
 
-// Shared-memory weight layout (rows padded to 4 floats) and the canonical layout, per cell.
-template <int H>
-struct TL {
-    static constexpr int sW0 = 0, sb0 = 32 * 28, sH = sb0 + 32;
-    static constexpr int HS = 32 * 32 + 32;  // one hidden layer (W, b)
-    static constexpr int sWo = sH + (H - 1) * HS, sbo = sWo + 16 * 32, SDF = sbo + 16;
-    static constexpr int sC0 = SDF, sc0 = sC0 + 32 * 36, sC1 = sc0 + 32, sc1 = sC1 + 4 * 32, ALL = sc1 + 4;
-    static constexpr int cW0 = 0, cb0 = 32 * 27, cH = cb0 + 32;
-    static constexpr int cWo = cH + (H - 1) * HS, cbo = cWo + 16 * 32, PSDF = cbo + 16;
-    static constexpr int cC0 = PSDF, cc0 = cC0 + 32 * 33, cC1 = cc0 + 32, cc1 = cC1 + 3 * 32;
-    // tile rows: A0 (28), A_l (36 each: 32 + one + 3 zero), D_l (32 each), Dout, then the colour rows
-    static constexpr int rA0 = 0;
-    __host__ __device__ static constexpr int rA(int l) { return A0ROWS + (l - 1) * 36; }  // l = 1..H
-    __host__ __device__ static constexpr int rD(int l) { return A0ROWS + H * 36 + (l - 1) * 32; }
-    static constexpr int rDout = A0ROWS + H * 36 + H * 32;
-    static constexpr int ROWS_FD = rDout + 4;
-    static constexpr int rU = rDout + 16, rHc = rU + 36, rDh = rHc + 36, rDc = rDh + 32;
-    static constexpr int ROWS_C = rDc + 4;
-};
-
-// canonical index of shared weight slot j (-1: zero pad)
-template <int H>
-__device__ __forceinline__ int canon_of(int j) {
-    using T = TL<H>;
-    if (j < T::sb0) {
-        const int o = j / 28, i = j - o * 28;
-        return i < 27 ? o * 27 + i : -1;
-    }
-    if (j < T::sH) return T::cb0 + (j - T::sb0);
-    if (j < T::SDF) return T::cH + (j - T::sH);  // hidden and output layers: same order, no padding
-    j -= T::SDF;
-    if (j < 32 * 36) {
-        const int o = j / 36, i = j - o * 36;
-        return i < 33 ? T::cC0 + o * 33 + i : -1;
-    }
-    j -= 32 * 36;
-    if (j < 32) return T::cc0 + j;
-    j -= 32;
-    if (j < 128) {
-        const int o = j >> 5, i = j & 31;
-        return o < 3 ? T::cC1 + o * 32 + i : -1;
-    }
-    j -= 128;
-    return j < 3 ? T::cc1 + j : -1;
-}
-
-template <int H>
-__device__ __forceinline__ void load_weights(const float *__restrict__ cw, float *sw, int n) {
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const int c = canon_of<H>(j);
-        sw[j] = c >= 0 ? __ldg(cw + c) : 0.f;
-    }
-}
-
-// ------------------------------------------------------------------ activations (accurate forms)
-__device__ __forceinline__ float sp(float s, float beta, float inv_beta) {
-    return fmaxf(s, 0.f) + log1pf(expf(-beta * fabsf(s))) * inv_beta;
-}
-// softplus_beta'(s) = sigmoid(beta s) = 1 - exp(-beta softplus_beta(s)), from the activation a
-__device__ __forceinline__ float dsp_from_act(float a, float beta) { return -expm1f(-beta * a); }
+// ------------------------------------------------------------------ activations
 __device__ __forceinline__ float sigm(float s) { return 1.f / (1.f + expf(-s)); }
 // log sigmoid(x), stable for any x
 __device__ __forceinline__ float log_sigm(float x) {
     return x < 0.f ? x - log1pf(expf(x)) : -log1pf(expf(-x));
-}
-
-// shared-memory float4 load kept in program order, so that unrolled layers do not hoist every
-// weight load ahead of its use (which spills)
-__device__ __forceinline__ float4 lds4(const float *p) {
-    float4 v;
-    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
-    return v;
-}
-// y = b + W x, W[OUT][RSTR] row-major in shared memory (RSTR % 4 == 0, IN <= RSTR, IN % 4 == 0)
-template <int IN, int OUT, int RSTR>
-__device__ __forceinline__ void lin(const float *W, const float *b, const float (&x)[IN], float (&y)[OUT]) {
-#pragma unroll
-    for (int o = 0; o < OUT; ++o) {
-        float acc = b[o];
-#pragma unroll
-        for (int i = 0; i < IN; i += 4) {
-            const float4 w4 = lds4(W + o * RSTR + i);
-            acc = fmaf(w4.x, x[i], acc);
-            acc = fmaf(w4.y, x[i + 1], acc);
-            acc = fmaf(w4.z, x[i + 2], acc);
-            acc = fmaf(w4.w, x[i + 3], acc);
-        }
-        y[o] = acc;
-    }
-}
-
-// SDF forward: out = [d, z]; with STORE, the layer inputs go to column `col` of the tile rows.
-template <int H, bool STORE>
-__device__ __forceinline__ void sdf_forward(const float *sw, float px, float py, float pz, float beta,
-                                            float inv_beta, float (&out)[16], float *rows, int col) {
-    using T = TL<H>;
-    float a0[28];
-    encode3<PE_L, 28>(px, py, pz, a0);
-    if (STORE) {
-#pragma unroll
-        for (int i = 0; i < 27; ++i) rows[(T::rA0 + i) * RS + col] = a0[i];
-    }
-    float h[32];
-    lin<28, 32, 28>(sw + T::sW0, sw + T::sb0, a0, h);
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        h[j] = sp(h[j], beta, inv_beta);
-        if (STORE) rows[(T::rA(1) + j) * RS + col] = h[j];
-    }
-#pragma unroll
-    for (int l = 1; l < H; ++l) {
-        float hn[32];
-        lin<32, 32, 32>(sw + T::sH + (l - 1) * T::HS, sw + T::sH + (l - 1) * T::HS + 1024, h, hn);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            h[j] = sp(hn[j], beta, inv_beta);
-            if (STORE) rows[(T::rA(l + 1) + j) * RS + col] = h[j];
-        }
-    }
-    lin<32, 16, 32>(sw + T::sWo, sw + T::sbo, h, out);
-}
-
-// SDF backward from the output deltas dout[0..NO) (rows written: Dout, D_H .. D_1).
-template <int H, int NO>
-__device__ __forceinline__ void sdf_backward(const float *sw, const float (&dout)[NO], float beta, float *rows,
-                                             int col) {
-    using T = TL<H>;
-#pragma unroll
-    for (int o = 0; o < NO; ++o) rows[(T::rDout + o) * RS + col] = dout[o];
-    float dl[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) dl[j] = 0.f;
-#pragma unroll
-    for (int o = 0; o < NO; ++o) {
-#pragma unroll
-        for (int j = 0; j < 32; j += 4) {
-            const float4 w4 = lds4(sw + T::sWo + o * 32 + j);
-            dl[j] = fmaf(w4.x, dout[o], dl[j]);
-            dl[j + 1] = fmaf(w4.y, dout[o], dl[j + 1]);
-            dl[j + 2] = fmaf(w4.z, dout[o], dl[j + 2]);
-            dl[j + 3] = fmaf(w4.w, dout[o], dl[j + 3]);
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        dl[j] *= dsp_from_act(rows[(T::rA(H) + j) * RS + col], beta);
-        rows[(T::rD(H) + j) * RS + col] = dl[j];
-    }
-#pragma unroll
-    for (int l = H - 1; l >= 1; --l) {
-        const float *Wl = sw + T::sH + (l - 1) * T::HS;  // maps A_l -> pre-activation of layer l + 1
-        float dn[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) dn[j] = 0.f;
-#pragma unroll
-        for (int o = 0; o < 32; ++o) {
-#pragma unroll
-            for (int j = 0; j < 32; j += 4) {
-                const float4 w4 = lds4(Wl + o * 32 + j);
-                dn[j] = fmaf(w4.x, dl[o], dn[j]);
-                dn[j + 1] = fmaf(w4.y, dl[o], dn[j + 1]);
-                dn[j + 2] = fmaf(w4.z, dl[o], dn[j + 2]);
-                dn[j + 3] = fmaf(w4.w, dl[o], dn[j + 3]);
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            dl[j] = dn[j] * dsp_from_act(rows[(T::rA(l) + j) * RS + col], beta);
-            rows[(T::rD(l) + j) * RS + col] = dl[j];
-        }
-    }
 }
 
 // ------------------------------------------------------------------ geometry
@@ -234,11 +61,6 @@ __device__ __forceinline__ bool clip_ray(const TrainArgs &a, const float *o, con
     tn = fmaxf(lo, 0.f);
     tf = hi;
     return true;
-}
-__device__ __forceinline__ void load3(const float *p, float *v) {
-    v[0] = __ldg(p);
-    v[1] = __ldg(p + 1);
-    v[2] = __ldg(p + 2);
 }
 __device__ __forceinline__ float strat_t(float tn, float tf, int i, float u, int Ns) {
     return tn + ((float)i + u) / (float)Ns * (tf - tn);
@@ -380,40 +202,6 @@ __global__ void __launch_bounds__(256) k_scatter(TrainArgs a, int64_t n) {
     }
 }
 
-// chunk c of keys [k0, k1): its key (largest k with chunk_off[k] <= c) and record range
-__device__ __forceinline__ int chunk_key(const int *chunk_off, int k0, int k1, int c) {
-    int lo = k0, hi = k1;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(chunk_off + mid) <= c) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
-
-// ------------------------------------------------------------------ forward: d at sorted records
-// out[rec] = d(x_rec) for the records of keys [k0, k1) (key = cell)
-template <int H>
-__global__ void __launch_bounds__(TILE, 4) k_eval_d(TrainArgs a, int k0, int k1, float *out) {
-    extern __shared__ float4 smem4[];
-    float *sw = reinterpret_cast<float *>(smem4);
-    const int c0 = a.chunk_off[k0], total = a.chunk_off[k1] - c0;
-    for (int ci = blockIdx.x; ci < total; ci += gridDim.x) {
-        const int key = chunk_key(a.chunk_off, k0, k1, c0 + ci);
-        const int j = c0 + ci - a.chunk_off[key];
-        const int beg = a.off[key] + j * CHUNK, end = min(beg + CHUNK, a.off[key + 1]);
-        __syncthreads();
-        load_weights<H>(a.params + (int64_t)key * a.p_cell, sw, TL<H>::SDF);
-        __syncthreads();
-        for (int i = beg + (int)threadIdx.x; i < end; i += TILE) {
-            const float4 r = a.sorted[i];
-            float y[16];
-            sdf_forward<H, false>(sw, r.x, r.y, r.z, a.beta, a.inv_beta, y, nullptr, 0);
-            out[__float_as_int(r.w)] = y[0];
-        }
-    }
-}
-
 // ------------------------------------------------------------------ importance sampling
 __global__ void __launch_bounds__(128) k_importance(TrainArgs a) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -474,71 +262,6 @@ __global__ void __launch_bounds__(128) k_valid(TrainArgs a) {
     load3(a.o + 3 * r, o);
     load3(a.w + 3 * r, w);
     a.valid[r] = clip_ray(a, o, w, tn, tf) ? 1 : 0;
-}
-
-// ------------------------------------------------------------------ sample centres: SDF, normal, colour
-// normal from the six difference records of centre q; returns |g| (n = 0 when |g| = 0)
-__device__ __forceinline__ float fd_normal(const TrainArgs &a, int64_t q, float (&g)[3], float (&n)[3]) {
-    const float inv2h = 1.f / (2.f * a.h);
-    const float *d = a.d_fd + 6 * q;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) g[k] = (d[2 * k] - d[2 * k + 1]) * inv2h;
-    const float gn = sqrtf(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-    const float ig = gn > 0.f ? 1.f / gn : 0.f;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) n[k] = g[k] * ig;
-    return gn;
-}
-
-// colour input u = [z (15), n (3), gamma_2(v) (15), 0 0 0]
-__device__ __forceinline__ void colour_input(const float (&y)[16], const float (&n)[3], const float *v,
-                                             float (&u)[36]) {
-#pragma unroll
-    for (int k = 0; k < 15; ++k) u[k] = y[1 + k];
-    u[15] = n[0];
-    u[16] = n[1];
-    u[17] = n[2];
-    float e[16];
-    encode3<2, 16>(v[0], v[1], v[2], e);
-#pragma unroll
-    for (int k = 0; k < 15; ++k) u[18 + k] = e[k];
-    u[33] = u[34] = u[35] = 0.f;
-}
-
-template <int H>
-__global__ void __launch_bounds__(TILE, 4) k_centre_fwd(TrainArgs a) {
-    using T = TL<H>;
-    extern __shared__ float4 smem4[];
-    float *sw = reinterpret_cast<float *>(smem4);
-    const int k0 = a.NC, k1 = 2 * a.NC;
-    const int64_t nfd = 6 * (a.B * a.S + a.M);
-    const int c0 = a.chunk_off[k0], total = a.chunk_off[k1] - c0;
-    for (int ci = blockIdx.x; ci < total; ci += gridDim.x) {
-        const int key = chunk_key(a.chunk_off, k0, k1, c0 + ci);
-        const int j = c0 + ci - a.chunk_off[key];
-        const int beg = a.off[key] + j * CHUNK, end = min(beg + CHUNK, a.off[key + 1]);
-        __syncthreads();
-        load_weights<H>(a.params + (int64_t)(key - a.NC) * a.p_cell, sw, T::ALL);
-        __syncthreads();
-        for (int i = beg + (int)threadIdx.x; i < end; i += TILE) {
-            const float4 rr = a.sorted[i];
-            const int64_t q = (int64_t)__float_as_int(rr.w) - nfd;
-            const int64_t r = q / a.S;
-            float y[16], g[3], n[3], v[3], u[36], hid[32], lg[4];
-            sdf_forward<H, false>(sw, rr.x, rr.y, rr.z, a.beta, a.inv_beta, y, nullptr, 0);
-            fd_normal(a, q, g, n);
-            load3(a.w + 3 * r, v);
-            colour_input(y, n, v, u);
-            lin<36, 32, 36>(sw + T::sC0, sw + T::sc0, u, hid);
-#pragma unroll
-            for (int k = 0; k < 32; ++k) hid[k] = fmaxf(hid[k], 0.f);
-            lin<32, 4, 32>(sw + T::sC1, sw + T::sc1, hid, lg);
-            a.d_c[q] = y[0];
-            a.rgb_c[3 * q] = sigm(lg[0]);
-            a.rgb_c[3 * q + 1] = sigm(lg[1]);
-            a.rgb_c[3 * q + 2] = sigm(lg[2]);
-        }
-    }
 }
 
 // ------------------------------------------------------------------ volume rendering and loss
@@ -672,273 +395,6 @@ __global__ void __launch_bounds__(128) k_eik_bwd(TrainArgs a) {
     }
 }
 
-// ------------------------------------------------------------------ backward: weight gradients
-// One (output rows) x (input rows) layer of the tile GEMM: thread blocks of 4 x 4 entries with rows
-// ob + OB jo and ib + IB ji.
-struct GemmLayer {
-    int drow, OB, arow, IB, out_real, in_real, cW, cb;
-};
-
-template <int H, bool CENTRE>
-struct GemmPlan {
-    static constexpr int NL = H + 1 + (CENTRE ? 2 : 0);
-    __device__ static GemmLayer layer(int l) {
-        using T = TL<H>;
-        if (l == 0) return {T::rD(1), 8, T::rA0, 7, 32, 27, T::cW0, T::cb0};
-        if (l < H) return {T::rD(l + 1), 8, T::rA(l), 9, 32, 32, T::cH + (l - 1) * T::HS, T::cH + (l - 1) * T::HS + 1024};
-        if (l == H) return {T::rDout, CENTRE ? 4 : 1, T::rA(H), 9, CENTRE ? 16 : 1, 32, T::cWo, T::cbo};
-        if (l == H + 1) return {T::rDh, 8, T::rU, 9, 32, 33, T::cC0, T::cc0};
-        return {T::rDc, 1, T::rHc, 9, 3, 32, T::cC1, T::cc1};
-    }
-    __host__ __device__ static constexpr int blocks() {
-        return 56 + 72 * (H - 1) + (CENTRE ? 36 + 72 + 9 : 9);
-    }
-    static constexpr int NB = (blocks() + TILE - 1) / TILE;
-};
-
-struct Blk {
-    int drow, OB, arow, IB, out_real, in_real, cW, cb, ob, ib;
-};
-
-template <class Plan>
-__device__ __forceinline__ Blk block_of(int b) {
-    Blk k{};
-    k.drow = -1;
-    if (b >= Plan::blocks()) return k;
-#pragma unroll 1
-    for (int l = 0; l < Plan::NL; ++l) {
-        const GemmLayer L = Plan::layer(l);
-        const int n = L.OB * L.IB;
-        if (b < n) {
-            k.drow = L.drow;
-            k.OB = L.OB;
-            k.arow = L.arow;
-            k.IB = L.IB;
-            k.out_real = L.out_real;
-            k.in_real = L.in_real;
-            k.cW = L.cW;
-            k.cb = L.cb;
-            k.ob = b / L.IB;
-            k.ib = b - k.ob * L.IB;
-            return k;
-        }
-        b -= n;
-    }
-    return k;
-}
-
-template <class Plan>
-__device__ __forceinline__ void gemm_tile(const float *rows, int b, float (&acc)[16]) {
-    const Blk k = block_of<Plan>(b);
-    if (k.drow < 0) return;
-    const float *D = rows + (k.drow + k.ob) * RS;
-    const float *A = rows + (k.arow + k.ib) * RS;
-    const int sd = k.OB * RS, sa = k.IB * RS;
-#pragma unroll 2
-    for (int r = 0; r < TILE; r += 4) {
-        float4 dv[4], av[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            dv[q] = *reinterpret_cast<const float4 *>(D + q * sd + r);
-            av[q] = *reinterpret_cast<const float4 *>(A + q * sa + r);
-        }
-#pragma unroll
-        for (int jo = 0; jo < 4; ++jo)
-#pragma unroll
-            for (int ji = 0; ji < 4; ++ji) {
-                float s = acc[jo * 4 + ji];
-                s = fmaf(dv[jo].x, av[ji].x, s);
-                s = fmaf(dv[jo].y, av[ji].y, s);
-                s = fmaf(dv[jo].z, av[ji].z, s);
-                s = fmaf(dv[jo].w, av[ji].w, s);
-                acc[jo * 4 + ji] = s;
-            }
-    }
-}
-
-template <class Plan>
-__device__ __forceinline__ void flush_block(float *gcell, int b, float (&acc)[16]) {
-    const Blk k = block_of<Plan>(b);
-    if (k.drow < 0) return;
-#pragma unroll
-    for (int jo = 0; jo < 4; ++jo)
-#pragma unroll
-        for (int ji = 0; ji < 4; ++ji) {
-            const int o = k.ob + k.OB * jo, i = k.ib + k.IB * ji;
-            const float v = acc[jo * 4 + ji];
-            acc[jo * 4 + ji] = 0.f;
-            if (v == 0.f || o >= k.out_real || i > k.in_real) continue;
-            atomicAdd(gcell + (i < k.in_real ? k.cW + o * k.in_real + i : k.cb + o), v);
-        }
-}
-
-// CENTRE: sample-centre records (colour MLP + SDF with upstream on d and z; writes the difference
-// records' upstream).  Otherwise: difference records (SDF with upstream on d only).
-template <int H, bool CENTRE>
-__global__ void __launch_bounds__(TILE, 1) k_backward(TrainArgs a) {
-    using T = TL<H>;
-    using Plan = GemmPlan<H, CENTRE>;
-    constexpr int NROWS = CENTRE ? T::ROWS_C : T::ROWS_FD;
-    constexpr int NW = CENTRE ? T::ALL : T::SDF;
-    extern __shared__ float4 smem4[];
-    float *rows = reinterpret_cast<float *>(smem4);
-    float *sw = rows + NROWS * RS;
-    const int tid = threadIdx.x;
-    // zero every row once (stale columns of later partial tiles stay finite), then the one-rows
-    for (int i = tid; i < NROWS * RS; i += TILE) rows[i] = 0.f;
-    __syncthreads();
-    for (int c = tid; c < RS; c += TILE) {
-        rows[(T::rA0 + 27) * RS + c] = 1.f;
-        for (int l = 1; l <= H; ++l) rows[(T::rA(l) + 32) * RS + c] = 1.f;
-        if (CENTRE) {
-            rows[(T::rU + 33) * RS + c] = 1.f;
-            rows[(T::rHc + 32) * RS + c] = 1.f;
-        }
-    }
-    float acc[Plan::NB][16];
-#pragma unroll
-    for (int k = 0; k < Plan::NB; ++k)
-#pragma unroll
-        for (int e = 0; e < 16; ++e) acc[k][e] = 0.f;
-    const int k0 = CENTRE ? a.NC : 0, k1 = CENTRE ? 2 * a.NC : a.NC;
-    const int64_t nfd = 6 * (a.B * a.S + a.M);
-    const int c0 = a.chunk_off[k0], total = a.chunk_off[k1] - c0;
-    const float inv2h = 1.f / (2.f * a.h);
-    for (int ci = blockIdx.x; ci < total; ci += gridDim.x) {
-        const int key = chunk_key(a.chunk_off, k0, k1, c0 + ci);
-        const int cell = key - k0;
-        const int j = c0 + ci - a.chunk_off[key];
-        const int beg = a.off[key] + j * CHUNK, end = min(beg + CHUNK, a.off[key + 1]);
-        __syncthreads();
-        load_weights<H>(a.params + (int64_t)cell * a.p_cell, sw, NW);
-        __syncthreads();
-        for (int tb = beg; tb < end; tb += TILE) {
-            const int i = tb + tid;
-            if (i < end) {
-                const float4 rr = a.sorted[i];
-                const int64_t rec = (int64_t)__float_as_int(rr.w);
-                float y[16];
-                sdf_forward<H, true>(sw, rr.x, rr.y, rr.z, a.beta, a.inv_beta, y, rows, tid);
-                if (CENTRE) {
-                    const int64_t q = rec - nfd, r = q / a.S;
-                    float g[3], n[3], v[3], u[36], hid[32], lg[4];
-                    const float gn = fd_normal(a, q, g, n);
-                    load3(a.w + 3 * r, v);
-                    colour_input(y, n, v, u);
-#pragma unroll
-                    for (int k = 0; k < 33; ++k) rows[(T::rU + k) * RS + tid] = u[k];
-                    lin<36, 32, 36>(sw + T::sC0, sw + T::sc0, u, hid);
-#pragma unroll
-                    for (int k = 0; k < 32; ++k) {
-                        hid[k] = fmaxf(hid[k], 0.f);
-                        rows[(T::rHc + k) * RS + tid] = hid[k];
-                    }
-                    lin<32, 4, 32>(sw + T::sC1, sw + T::sc1, hid, lg);
-                    // colour backward: logits, hidden (ReLU), inputs z and n
-                    float dc[3];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const float rgb = sigm(lg[c]);
-                        dc[c] = a.g_rgb[3 * q + c] * rgb * (1.f - rgb);
-                        rows[(T::rDc + c) * RS + tid] = dc[c];
-                    }
-                    float dh[32];
-#pragma unroll
-                    for (int k = 0; k < 32; ++k) {
-                        float s = sw[T::sC1 + k] * dc[0];
-                        s = fmaf(sw[T::sC1 + 32 + k], dc[1], s);
-                        s = fmaf(sw[T::sC1 + 64 + k], dc[2], s);
-                        dh[k] = hid[k] > 0.f ? s : 0.f;
-                        rows[(T::rDh + k) * RS + tid] = dh[k];
-                    }
-                    float gu[20];
-#pragma unroll
-                    for (int k = 0; k < 20; ++k) gu[k] = 0.f;
-#pragma unroll
-                    for (int o = 0; o < 32; ++o) {
-#pragma unroll
-                        for (int k = 0; k < 20; k += 4) {
-                            const float4 w4 = lds4(sw + T::sC0 + o * 36 + k);
-                            gu[k] = fmaf(w4.x, dh[o], gu[k]);
-                            gu[k + 1] = fmaf(w4.y, dh[o], gu[k + 1]);
-                            gu[k + 2] = fmaf(w4.z, dh[o], gu[k + 2]);
-                            gu[k + 3] = fmaf(w4.w, dh[o], gu[k + 3]);
-                        }
-                    }
-                    // normal n = g / |g|: dL/dg = (dL/dn - n (n . dL/dn)) / |g|; g_k = (d+ - d-) / 2h
-                    const float nd = n[0] * gu[15] + n[1] * gu[16] + n[2] * gu[17];
-                    const float ig = gn > 0.f ? 1.f / gn : 0.f;
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        const float dg = (gu[15 + k] - n[k] * nd) * ig * inv2h;
-                        a.g_fd[6 * q + 2 * k] = dg;
-                        a.g_fd[6 * q + 2 * k + 1] = -dg;
-                    }
-                    float dout[16];
-                    dout[0] = a.g_dc[q];
-#pragma unroll
-                    for (int k = 0; k < 15; ++k) dout[1 + k] = gu[k];
-                    sdf_backward<H, 16>(sw, dout, a.beta, rows, tid);
-                } else {
-                    const float dout[1] = {a.g_fd[rec]};
-                    sdf_backward<H, 1>(sw, dout, a.beta, rows, tid);
-                }
-            } else {
-                // no record: zero deltas
-                for (int l = 1; l <= H; ++l)
-                    for (int k = 0; k < 32; ++k) rows[(T::rD(l) + k) * RS + tid] = 0.f;
-                for (int k = 0; k < (CENTRE ? 16 : 1); ++k) rows[(T::rDout + k) * RS + tid] = 0.f;
-                if (CENTRE) {
-                    for (int k = 0; k < 32; ++k) rows[(T::rDh + k) * RS + tid] = 0.f;
-                    for (int k = 0; k < 3; ++k) rows[(T::rDc + k) * RS + tid] = 0.f;
-                }
-            }
-            __syncthreads();
-#pragma unroll
-            for (int k = 0; k < Plan::NB; ++k) gemm_tile<Plan>(rows, tid + k * TILE, acc[k]);
-            __syncthreads();
-        }
-        float *gcell = a.grad + (int64_t)cell * a.p_cell;
-#pragma unroll
-        for (int k = 0; k < Plan::NB; ++k) flush_block<Plan>(gcell, tid + k * TILE, acc[k]);
-    }
-}
-
-template <int H>
-size_t backward_smem(bool centre) {
-    using T = TL<H>;
-    return ((size_t)(centre ? T::ROWS_C : T::ROWS_FD) * RS + (centre ? T::ALL : T::SDF)) * sizeof(float);
-}
-
-int grid_for(int sm_count, int per_sm, int64_t work_upper) {
-    int64_t b = (int64_t)sm_count * per_sm;
-    if (work_upper < b) b = work_upper;
-    return (int)(b > 0 ? b : 1);
-}
-
-template <int H>
-cudaError_t eval_d_h(const TrainArgs &a, int k0, int k1, float *out, int blocks, cudaStream_t s) {
-    const size_t sm = TL<H>::SDF * sizeof(float);
-    k_eval_d<H><<<blocks, TILE, sm, s>>>(a, k0, k1, out);
-    return cudaGetLastError();
-}
-
-template <int H>
-cudaError_t centre_fwd_h(const TrainArgs &a, int blocks, cudaStream_t s) {
-    const size_t sm = TL<H>::ALL * sizeof(float);
-    k_centre_fwd<H><<<blocks, TILE, sm, s>>>(a);
-    return cudaGetLastError();
-}
-
-template <int H, bool CENTRE>
-cudaError_t backward_h(const TrainArgs &a, int blocks, cudaStream_t s) {
-    const size_t sm = backward_smem<H>(CENTRE);
-    cudaError_t e = cudaFuncSetAttribute(k_backward<H, CENTRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    k_backward<H, CENTRE><<<blocks, TILE, sm, s>>>(a);
-    return cudaGetLastError();
-}
-
 }  // namespace
 
 int train_chunk_records() { return CHUNK; }
@@ -955,12 +411,6 @@ cudaError_t train_sort(const TrainArgs &a, int which, int64_t n_rec, int sm_coun
     return cudaGetLastError();
 }
 
-cudaError_t train_coarse_eval(const TrainArgs &a, int sm_count, cudaStream_t s) {
-    const int64_t chunks = a.B * a.Ns / CHUNK + a.NC + 1;
-    const int blocks = grid_for(sm_count, 4, chunks);
-    return a.H == 3 ? eval_d_h<3>(a, 0, a.NC, a.d_coarse, blocks, s) : eval_d_h<2>(a, 0, a.NC, a.d_coarse, blocks, s);
-}
-
 cudaError_t train_importance(const TrainArgs &a, cudaStream_t s) {
     if (a.B == 0) return cudaSuccess;
     k_importance<<<(unsigned)((a.B + 127) / 128), 128, 0, s>>>(a);
@@ -971,18 +421,6 @@ cudaError_t train_valid(const TrainArgs &a, cudaStream_t s) {
     if (a.B == 0) return cudaSuccess;
     k_valid<<<(unsigned)((a.B + 127) / 128), 128, 0, s>>>(a);
     return cudaGetLastError();
-}
-
-cudaError_t train_fd_forward(const TrainArgs &a, int sm_count, cudaStream_t s) {
-    const int64_t fd_chunks = 6 * (a.B * a.S + a.M) / CHUNK + a.NC + 1;
-    return a.H == 3 ? eval_d_h<3>(a, 0, a.NC, a.d_fd, grid_for(sm_count, 4, fd_chunks), s)
-                    : eval_d_h<2>(a, 0, a.NC, a.d_fd, grid_for(sm_count, 4, fd_chunks), s);
-}
-
-cudaError_t train_centre_forward(const TrainArgs &a, int sm_count, cudaStream_t s) {
-    const int64_t c_chunks = a.B * a.S / CHUNK + a.NC + 1;
-    const int blocks = grid_for(sm_count, 4, c_chunks);
-    return a.H == 3 ? centre_fwd_h<3>(a, blocks, s) : centre_fwd_h<2>(a, blocks, s);
 }
 
 cudaError_t train_loss_forward(const TrainArgs &a, cudaStream_t s) {
@@ -1003,18 +441,6 @@ cudaError_t train_upstream(const TrainArgs &a, cudaStream_t s) {
     if (a.B > 0) k_composite_bwd<<<(unsigned)((a.B + 127) / 128), 128, 0, s>>>(a);
     if (a.M > 0) k_eik_bwd<<<(unsigned)((a.M + 127) / 128), 128, 0, s>>>(a);
     return cudaGetLastError();
-}
-
-cudaError_t train_centre_backward(const TrainArgs &a, int sm_count, cudaStream_t s) {
-    const int64_t c_chunks = a.B * a.S / CHUNK + a.NC + 1;
-    return a.H == 3 ? backward_h<3, true>(a, grid_for(sm_count, 1, c_chunks), s)
-                    : backward_h<2, true>(a, grid_for(sm_count, 1, c_chunks), s);
-}
-
-cudaError_t train_fd_backward(const TrainArgs &a, int sm_count, cudaStream_t s) {
-    const int64_t fd_chunks = 6 * (a.B * a.S + a.M) / CHUNK + a.NC + 1;
-    return a.H == 3 ? backward_h<3, false>(a, grid_for(sm_count, 1, fd_chunks), s)
-                    : backward_h<2, false>(a, grid_for(sm_count, 1, fd_chunks), s);
 }
 
 }  // namespace kns
