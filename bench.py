@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--cams", type=int, default=0, help="use only the first N cameras (small profiling cases)")
+    ap.add_argument("--train-rays", type=int, default=0,
+                    help="train workload: rays per step (eikonal points scale along; small profiling cases)")
     ap.add_argument("--tune", default="cache", choices=["cache", "force", "off"],
                     help="schedule autotuning before timing: use the cached best (tuning once if absent), "
                          "re-tune, or use the library defaults")
@@ -388,8 +390,10 @@ def train_macs(desc):
     return {"fwd_d": fwd_d, "fwd_full": sdf_full + col, "bwd_d": bwd_d, "bwd_full": bwd_full}
 
 
-def train_setup(torch, kns, S, ctx, dev, seed):
-    wl = S.TRAIN_WORKLOAD
+def train_setup(torch, kns, S, ctx, dev, seed, n_rays=0):
+    wl = dict(S.TRAIN_WORKLOAD)
+    if n_rays:
+        wl.update(n_rays=n_rays, n_eik=max(1, n_rays * wl["n_eik"] // wl["n_rays"]))
     desc = S.config_desc(wl["grid"])
     W, H, n_cams = wl["W"], wl["H"], wl["n_cams"]
     cams = S.orbit_cameras(n_cams, W, H, seed=1)
@@ -448,6 +452,7 @@ def oracle_train_rate(desc, w, host, wl, seconds: float, seed: int = 0):
 def oracle_train_inputs(S, wl, desc, n: int = 4096):
     """The first n rays of the training batch (the GPU arm's draws) with targets rendered by the oracle."""
     import oracle as O
+    n = min(n, wl["n_rays"])
     cams = S.orbit_cameras(wl["n_cams"], wl["W"], wl["H"], seed=1)
     sel, u_s, u_i, P = S.train_draws(wl["n_rays"], wl["n_strat"], wl["n_imp"], wl["n_eik"],
                                      wl["n_cams"] * wl["W"] * wl["H"], 0)
@@ -501,7 +506,7 @@ def run_train(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     ctx = kns.Context(local_rank)
-    wl, desc, batch, params, host = train_setup(torch, kns, S, ctx, dev, seed=rank)
+    wl, desc, batch, params, host = train_setup(torch, kns, S, ctx, dev, seed=rank, n_rays=args.train_rays)
     stream = torch.cuda.current_stream()
     loss = torch.empty(3, dtype=torch.float32, device=dev)
     grad = torch.empty_like(params)

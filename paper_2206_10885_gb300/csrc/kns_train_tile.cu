@@ -222,12 +222,27 @@ __device__ __forceinline__ void hidden_layer(const float *Wk, const float *b, fl
     store_rows(rows, dst, acc);
 }
 
-// encoding of the tile's records (threads 0..127, one record each) into rows A0 .. A0+26
-__device__ __forceinline__ void encode_column(float *rows, int a0, int col, float x, float y, float z) {
-    float e[28];
-    encode3<PE_L, 28>(x, y, z, e);
+// encoding of record column col into rows A0 .. A0+26, split between two threads: half 0 writes x
+// and frequencies 0, 1; half 1 frequencies 2, 3 (rows 3 + 6k + c: sin, 3 + 6k + 3 + c: cos)
+__device__ __forceinline__ void encode_half(float *rows, int a0, int col, int half, float x, float y, float z) {
+    const float p[3] = {x, y, z};
+    if (half == 0) {
+        rows[(a0 + 0) * RS + col] = x;
+        rows[(a0 + 1) * RS + col] = y;
+        rows[(a0 + 2) * RS + col] = z;
+    }
 #pragma unroll
-    for (int i = 0; i < 27; ++i) rows[(a0 + i) * RS + col] = e[i];
+    for (int kk = 0; kk < 2; ++kk) {
+        const int k = 2 * half + kk;
+        const float f = (float)(1 << k);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float sn, cs;
+            sincospif(f * p[c], &sn, &cs);
+            rows[(a0 + 3 + 6 * k + c) * RS + col] = sn;
+            rows[(a0 + 6 + 6 * k + c) * RS + col] = cs;
+        }
+    }
 }
 
 // ------------------------------------------------------------------ forward: d at records
@@ -249,12 +264,12 @@ __global__ void __launch_bounds__(TPB, 3) k_tile_eval_d(TrainArgs a, int k0, int
         __syncthreads();
         load_slots<H>(a.params + (int64_t)key * a.p_cell, sw, 0, L::FS);
         for (int tb = beg; tb < end; tb += TILE) {
-            if (tid < TILE) {
-                const int i = tb + tid;
+            {
+                const int col = tid & (TILE - 1), i = tb + col;
                 float4 r = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
                 if (i < end) r = a.sorted[i];
-                s_rec[tid] = __float_as_int(r.w);
-                encode_column(rows, R::A0, tid, r.x, r.y, r.z);
+                if (tid < TILE) s_rec[tid] = __float_as_int(r.w);
+                encode_half(rows, R::A0, col, tid >> 7, r.x, r.y, r.z);
             }
             __syncthreads();
             hidden_layer<27>(sw + L::T0, sw + L::b0, rows, R::A0, R::P, a.beta, a.inv_beta);
@@ -361,17 +376,19 @@ __global__ void __launch_bounds__(TPB, 2) k_tile_centre_fwd(TrainArgs a) {
         __syncthreads();
         load_slots<H>(a.params + (int64_t)(key - a.NC) * a.p_cell, sw, 0, L::FC);
         for (int tb = beg; tb < end; tb += TILE) {
-            if (tid < TILE) {
-                const int i = tb + tid;
+            {
+                const int col = tid & (TILE - 1), i = tb + col;
                 float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
                 long long q = -1;
                 if (i < end) {
                     r = a.sorted[i];
                     q = (long long)__float_as_int(r.w) - nfd;
                 }
-                s_q[tid] = q;
-                encode_column(rows, R::A0, tid, r.x, r.y, r.z);
-                if (q >= 0) centre_inputs(a, rows, R::FU, tid, q);
+                encode_half(rows, R::A0, col, tid >> 7, r.x, r.y, r.z);
+                if (tid < TILE) {
+                    s_q[tid] = q;
+                    if (q >= 0) centre_inputs(a, rows, R::FU, tid, q);
+                }
             }
             __syncthreads();
             hidden_layer<27>(sw + L::T0, sw + L::b0, rows, R::A0, R::P, a.beta, a.inv_beta);
@@ -444,8 +461,21 @@ __device__ __forceinline__ Blk block_of(int b) {
             k.in_real = G.in_real;
             k.cW = G.cW;
             k.cb = G.cb;
-            k.ob = b / G.IB;
-            k.ib = b - k.ob * G.IB;
+            if (G.IB == 9) {
+                // eight consecutive lanes (one shared-memory phase of a 16-byte load) take input rows
+                // ib = 0..7 of one output group, so their rows fall in distinct bank groups; the
+                // ib = 8 blocks follow, one per output group
+                if (b < 8 * G.OB) {
+                    k.ob = b >> 3;
+                    k.ib = b & 7;
+                } else {
+                    k.ob = b - 8 * G.OB;
+                    k.ib = 8;
+                }
+            } else {
+                k.ob = b / G.IB;
+                k.ib = b - k.ob * G.IB;
+            }
             return k;
         }
         b -= n;
@@ -562,20 +592,22 @@ __global__ void __launch_bounds__(TPB, 1) k_tile_backward(TrainArgs a) {
         else load_slots<H>(cw, sw, L::FC, L::BS);
         for (int tb = beg; tb < end; tb += TILE) {
             // records: encoding, and the upstream of d (difference points) or the colour inputs (centres)
-            if (tid < TILE) {
-                const int i = tb + tid;
+            {
+                const int col = tid & (TILE - 1), i = tb + col;
                 float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
                 long long q = -1;
                 if (i < end) {
                     r = a.sorted[i];
                     q = (long long)__float_as_int(r.w) - (CENTRE ? nfd : 0);
                 }
-                s_q[tid] = q;
-                encode_column(rows, R::A0, tid, r.x, r.y, r.z);
-                if (CENTRE) {
-                    if (q >= 0) centre_inputs(a, rows, R::U, tid, q);
-                } else {
-                    rows[R::Dout * RS + tid] = q >= 0 ? a.g_fd[q] : 0.f;
+                encode_half(rows, R::A0, col, tid >> 7, r.x, r.y, r.z);
+                if (tid < TILE) {
+                    s_q[tid] = q;
+                    if (CENTRE) {
+                        if (q >= 0) centre_inputs(a, rows, R::U, tid, q);
+                    } else {
+                        rows[R::Dout * RS + tid] = q >= 0 ? a.g_fd[q] : 0.f;
+                    }
                 }
             }
             __syncthreads();
