@@ -73,7 +73,8 @@ class kns_train_stats(C.Structure):
 class kns_render_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("eps_coarse", C.c_float), ("refine_steps", C.c_int32),
                 ("inner_steps", C.c_int32), ("min_active", C.c_int32), ("tail_rays", C.c_int32),
-                ("blocks_per_sm", C.c_int32), ("static_tiles", C.c_int32), ("timing", C.c_int32)]
+                ("blocks_per_sm", C.c_int32), ("static_tiles", C.c_int32), ("timing", C.c_int32),
+                ("block_tiles", C.c_int32)]
 
 
 class kns_render_stats(C.Structure):

@@ -18,17 +18,18 @@ DEFAULT_CACHE = os.path.join(_HERE, "_tune_cache.json")
 
 # candidate values of each knob (0 would mean the library default)
 SPACE = {
+    "block_tiles": (1, 2, 3),
     "inner_steps": (1, 4),
     "min_active": (1, 8),
     "static_tiles": (1, 2),
     "blocks_per_sm": (8, 16, 32),
-    "tail_rays": (-1, 4096, 32768, 131072),
+    "tail_rays": (-1, 32768, 65536, 131072),
 }
 
 
 def _key(grid, n_cams, W, H, max_steps, precision, device_name):
     d = grid.desc
-    return "|".join(str(v) for v in (device_name, d.N, d.sdf_width, d.sdf_hidden, d.pe_pos_L, d.occ_res,
+    return "|".join(str(v) for v in ("v2", device_name, d.N, d.sdf_width, d.sdf_hidden, d.pe_pos_L, d.occ_res,
                                       n_cams, W, H, max_steps, precision))
 
 
@@ -58,11 +59,23 @@ def _store(key, value):
     os.replace(tmp, path)
 
 
+# knobs that only the 16-sample warp tiles read (block tiles take one sphere step per round and size
+# their own grid)
+WARP_ONLY = {"inner_steps": 1, "min_active": 1, "blocks_per_sm": 16}
+
+
 def candidates(space=None):
     space = space or SPACE
     keys = sorted(space)
+    seen = set()
     for vals in itertools.product(*(space[k] for k in keys)):
-        yield dict(zip(keys, vals))
+        cand = dict(zip(keys, vals))
+        if cand.get("block_tiles") in (1, 3):
+            cand.update({k: v for k, v in WARP_ONLY.items() if k in cand})
+        key = tuple(sorted(cand.items()))
+        if key not in seen:
+            seen.add(key)
+            yield cand
 
 
 def time_setting(kns, ctx, grid, cams, W, H, max_steps, eps, precision, tuning, out, flush, reps=2):

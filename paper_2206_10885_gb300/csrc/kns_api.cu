@@ -21,6 +21,7 @@ struct WaveScratch {
     int nc = 0;        // capacity in cells
     int cams = 0;      // capacity in cameras
     float *t_ray = nullptr;
+    float4 *t_hist = nullptr;  // last evaluated positions of each ray (cycle test)
     int *steps_ray = nullptr, *cell_ray = nullptr, *q[2] = {nullptr, nullptr}, *qcell[2] = {nullptr, nullptr};
     int *sorted = nullptr, *hits = nullptr;
     int *cellbuf = nullptr;  // count[2], fill[2], off, tile_off (6 * (nc + 1) ints)
@@ -293,6 +294,7 @@ void fill_view(kns_grid *g) {
 
 void free_scratch(WaveScratch &w) {
     cudaFree(w.t_ray);
+    cudaFree(w.t_hist);
     cudaFree(w.steps_ray);
     cudaFree(w.cell_ray);
     cudaFree(w.q[0]);
@@ -308,12 +310,13 @@ void free_scratch(WaveScratch &w) {
     w = WaveScratch{};
 }
 
-// Render tiling: samples per tile (one warp evaluates one tile).
-constexpr int kRenderBlockTile = 16;
+// Render tiling: samples per tile (a warp tile, or a 256-thread block tile).
+constexpr int kRenderBlockTile = 16;        // samples per warp tile
+constexpr int kRenderBlockTiles = 1;        // FP32 renders use block tiles by default
 // Defaults picked by the autotuner on the 16^3 / width-32 grid at 8 x 800x800.
 constexpr int kRenderInnerSteps = 4;
 constexpr int kRenderMinActive = 8;
-constexpr int kRenderTailRays = 4096;  // rounds this small finish one thread per ray
+constexpr int kRenderTailRays = 65536;  // rounds this small finish one thread per ray
 constexpr int kRenderBlocksPerSM = 16;
 constexpr int kRenderStaticTiles = 2;
 
@@ -352,6 +355,7 @@ kns_status ensure_scratch(kns_ctx *ctx, int64_t rays, int nc, int cams) {
         if (e == cudaSuccess) e = cudaMalloc((void **)p, bytes);
     };
     alloc(&w.t_ray, sizeof(float) * R);
+    alloc(&w.t_hist, sizeof(float4) * R);
     alloc(&w.steps_ray, sizeof(int) * R);
     alloc(&w.cell_ray, sizeof(int) * R);
     alloc(&w.q[0], sizeof(int) * R);
@@ -726,6 +730,7 @@ struct RenderCfg {
     float eps_coarse = 4e-3f;
     int refine_steps = 2, inner_steps = kRenderInnerSteps, min_active = kRenderMinActive,
         tail_rays = kRenderTailRays, blocks_per_sm = kRenderBlocksPerSM, static_tiles = 1;
+    int block_mode = 1;  // FP32 renders: 0 = 16-sample warp tiles, 1 = 128-sample, 3 = 256-sample block tiles
 };
 
 kns_status resolve_opts(kns_ctx *ctx, const kns_render_opts *opts, float eps, RenderCfg &c) {
@@ -746,8 +751,11 @@ kns_status resolve_opts(kns_ctx *ctx, const kns_render_opts *opts, float eps, Re
     c.blocks_per_sm = opts ? knob(opts->blocks_per_sm, kRenderBlocksPerSM) : kRenderBlocksPerSM;
     c.static_tiles = (opts ? knob(opts->static_tiles, kRenderStaticTiles) : kRenderStaticTiles) == 1;
     if (c.inner_steps < 1 || c.inner_steps > 1024 || c.min_active < 1 || c.min_active > 16 || c.tail_rays < -1 ||
-        c.blocks_per_sm < 1 || c.blocks_per_sm > 64 || (opts && (opts->static_tiles < 0 || opts->static_tiles > 2)))
+        c.blocks_per_sm < 1 || c.blocks_per_sm > 64 || (opts && (opts->static_tiles < 0 || opts->static_tiles > 2)) ||
+        (opts && (opts->block_tiles < 0 || opts->block_tiles > 3)))
         return set_err(ctx, KNS_ERR_INVALID_ARG, "render tuning field out of range");
+    const int bt = opts ? knob(opts->block_tiles, kRenderBlockTiles) : kRenderBlockTiles;
+    c.block_mode = c.bf16 || bt == 2 ? 0 : bt;
     if (c.tail_rays < 0) c.tail_rays = 0;
     if (c.bf16) c.tail_rays = 0;  // the per-thread tail evaluator is FP32 only
     c.timing = opts && opts->timing == 1;
@@ -804,6 +812,7 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
     a.wt = grid->d_wt;
     a.wt_stride = grid->wt_stride;
     a.t_ray = w.t_ray;
+    a.t_hist = w.t_hist;
     a.steps_ray = w.steps_ray;
     a.cell_ray = w.cell_ray;
     a.q[0] = w.q[0];
@@ -838,6 +847,9 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
             if (e != cudaSuccess || ctx->h_live[(k - 2) & 3] == 0) break;
         }
         ++ctx->stats.rounds;
+        // block tiles: the sort cuts tiles of the size the evaluation kernel takes
+        if (cfg.block_mode == 1) a.btile = 128;
+        else if (cfg.block_mode == 3) a.btile = 256;
         int tm = timing_begin(ctx, cfg.timing, kTSort, s);
         e = kns::launch_wave_scan(a, cur, s);
         if (e == cudaSuccess)
@@ -846,7 +858,9 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
         if (e == cudaSuccess) e = kns::launch_wave_scatter(a, cur, scatter_blocks, s);
         timing_end(ctx, tm, s);
         tm = timing_begin(ctx, cfg.timing, kTEvalF32, s);
-        if (e == cudaSuccess) e = kns::launch_wave_eval(grid->shape, grid->view, a, cur, eval_blocks, s);
+        if (e == cudaSuccess)
+            e = kns::launch_wave_eval(grid->shape, grid->view, a, cur, eval_blocks, cfg.block_mode ? 1 : 0,
+                                      ctx->sm_count, s);
         timing_end(ctx, tm, s);
         if (e == cudaSuccess && cfg.bf16) {
             tm = timing_begin(ctx, cfg.timing, kTEvalBF16, s);
@@ -1152,7 +1166,7 @@ extern "C" kns_status kns_render_noalloc(kns_ctx *ctx, const kns_grid *grid, con
             e = cudaMemcpyAsync(ctx->h_live + (k & 3), &a.ctrl->n_live[cur], sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_live[k & 3], s);
         if (e == cudaSuccess) e = kns::launch_wave_scatter(a, cur, scatter_blocks, s);
-        if (e == cudaSuccess) e = kns::launch_wave_eval(grid->shape, grid->view, a, cur, eval_blocks, s);
+        if (e == cudaSuccess) e = kns::launch_wave_eval(grid->shape, grid->view, a, cur, eval_blocks, 0, ctx->sm_count, s);
     }
     if (e == cudaSuccess) e = kns::launch_wave_shade(grid->shape, grid->view, a, ctx->sm_count * 8, s);
     if (e != cudaSuccess) return cuda_err(ctx, e, "render launch");

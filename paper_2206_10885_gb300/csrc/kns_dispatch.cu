@@ -33,8 +33,10 @@ cudaError_t launch_wave_gen(const Shape &sh, const GridView &g, const WaveArgs &
     return dispatch(sh, [&](auto c) { return launch_wave_gen_cfg<decltype(c)>(g, a, s); });
 }
 cudaError_t launch_wave_eval(const Shape &sh, const GridView &g, const WaveArgs &a, int cur, int blocks,
-                             cudaStream_t s) {
-    return dispatch(sh, [&](auto c) { return launch_wave_eval_cfg<decltype(c)>(g, a, cur, blocks, s); });
+                             int block_tiles, int sm_count, cudaStream_t s) {
+    return dispatch(sh, [&](auto c) {
+        return launch_wave_eval_cfg<decltype(c)>(g, a, cur, blocks, block_tiles, sm_count, s);
+    });
 }
 cudaError_t launch_wave_shade(const Shape &sh, const GridView &g, const WaveArgs &a, int blocks, cudaStream_t s) {
     return dispatch(sh, [&](auto c) { return launch_wave_shade_cfg<decltype(c)>(g, a, blocks, s); });

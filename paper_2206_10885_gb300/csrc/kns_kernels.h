@@ -58,6 +58,7 @@ struct WaveArgs {
     int wt_stride;        // floats per cell
     // per-ray state
     float *t_ray;
+    float4 *t_hist;       // the ray's last four evaluated positions, newest first (NULL: no cycle test)
     int *steps_ray, *cell_ray;
     // wave queues (double-buffered), cell-sorted samples, hits
     int *q[2], *qcell[2];
@@ -71,7 +72,8 @@ struct WaveArgs {
 template <class C>
 cudaError_t launch_wave_gen_cfg(const GridView &g, const WaveArgs &a, cudaStream_t s);
 template <class C>
-cudaError_t launch_wave_eval_cfg(const GridView &g, const WaveArgs &a, int cur, int blocks, cudaStream_t s);
+cudaError_t launch_wave_eval_cfg(const GridView &g, const WaveArgs &a, int cur, int blocks, int block_tiles,
+                                 int sm_count, cudaStream_t s);
 template <class C>
 cudaError_t launch_wave_shade_cfg(const GridView &g, const WaveArgs &a, int blocks, cudaStream_t s);
 template <class C>
@@ -89,7 +91,7 @@ int bf16_cell_bytes(const Shape &sh, int *k0p);
 
 cudaError_t launch_wave_gen(const Shape &sh, const GridView &g, const WaveArgs &a, cudaStream_t s);
 cudaError_t launch_wave_eval(const Shape &sh, const GridView &g, const WaveArgs &a, int cur, int blocks,
-                             cudaStream_t s);
+                             int block_tiles, int sm_count, cudaStream_t s);
 cudaError_t launch_wave_shade(const Shape &sh, const GridView &g, const WaveArgs &a, int blocks, cudaStream_t s);
 cudaError_t launch_wave_eval_bf16(const Shape &sh, const GridView &g, const WaveArgs &a, int cur, int blocks,
                                   cudaStream_t s);

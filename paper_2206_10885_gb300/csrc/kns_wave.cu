@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(128) wave_gen_kernel(GridView g, WaveArgs a) {
                 alive = true;
                 a.t_ray[r] = t;
                 a.steps_ray[r] = 0;
+                if (a.t_hist) a.t_hist[r] = no_history();
             }
         }
     }
@@ -160,6 +161,245 @@ __host__ __device__ constexpr int eval_smem_bytes() {
     return (C::TSIZE + TILE * (act_stride(C::INP) + 2 * act_stride(C::W))) * (int)sizeof(float);
 }
 
+// ---------------------------------------------------------------- block tiles (FP32 renders)
+// Round k with tiles of up to 128 samples of one cell (sort granularity 128): a block of 256
+// threads stages the cell's k-major trace weights with one TMA bulk copy (kept while consecutive
+// tiles share the cell), encodes the samples into shared rows h[k][s] (row stride 132 floats, two
+// threads per sample), and runs each layer as a [W x K] by [K x 128] block GEMM: warp w owns output
+// units w*W/8 .. w*W/8 + W/8 - 1, lane l owns samples 4l .. 4l+3, so per input k one warp-uniform
+// float4 (or two) of weights and one float4 of activations feed 4*W/8 FMAs per thread.  Every output
+// is its bias followed by one FMA per input in ascending order and the d row is one sequential FMA
+// chain, the order of the per-thread evaluator, so d does not depend on the tile shape.  Threads
+// 0..127 then advance their sample (hit, miss, or emit to round k+1 with its next cell).
+constexpr int BTHREADS = 256;
+// shared row stride (floats) of a BT-sample tile: row r starts in bank group r mod 8
+__host__ __device__ constexpr int block_rs(int BT) { return BT + 4; }
+
+template <class C, int BT>
+__host__ __device__ constexpr int block_eval_smem_bytes() {
+    return (C::TSIZE + (C::INP + 2 * C::W) * block_rs(BT)) * (int)sizeof(float);
+}
+
+// encoding of sample column s (Eq. 1) split into NH parts (1 or 2 threads per sample): part 0
+// writes x, part h frequencies [h L/NH, (h+1) L/NH); values as encode3
+template <int L, int NH, int BRS>
+__device__ __forceinline__ void encode_split(float *rows, int s, int half, float px, float py, float pz) {
+    const float p[3] = {px, py, pz};
+    if (half == 0) {
+        rows[0 * BRS + s] = px;
+        rows[1 * BRS + s] = py;
+        rows[2 * BRS + s] = pz;
+    }
+#pragma unroll
+    for (int kk = 0; kk < L / NH; ++kk) {
+        const int k = half * (L / NH) + kk;
+        const float f = (float)(1 << k);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float sn, cs;
+            sincospif(f * p[c], &sn, &cs);
+            rows[(3 + 6 * k + c) * BRS + s] = sn;
+            rows[(3 + 6 * k + 3 + c) * BRS + s] = cs;
+        }
+    }
+}
+
+// out[o][s] = softplus(b[o] + sum_{k < K} Wt[k][o] in[k][s]) for this thread's W/8 outputs x BT/32
+// samples
+template <int K, int W, int BT>
+__device__ __forceinline__ void block_layer(const float *Wt, const float *b, const float *in, float *out,
+                                            float beta, float inv_beta) {
+    constexpr int NO = W / 8, NS = BT / 32, BRS = block_rs(BT);
+    const int o0 = (threadIdx.x >> 5) * NO, s0 = (threadIdx.x & 31) * NS;
+    float acc[NO][NS];
+#pragma unroll
+    for (int i = 0; i < NO; ++i) {
+        const float bi = b[o0 + i];
+#pragma unroll
+        for (int j = 0; j < NS; ++j) acc[i][j] = bi;
+    }
+#pragma unroll 2
+    for (int k = 0; k < K; ++k) {
+        float xa[NS];
+#pragma unroll
+        for (int j4 = 0; j4 < NS; j4 += 4) {
+            const float4 x = *reinterpret_cast<const float4 *>(in + k * BRS + s0 + j4);
+            xa[j4] = x.x;
+            xa[j4 + 1] = x.y;
+            xa[j4 + 2] = x.z;
+            xa[j4 + 3] = x.w;
+        }
+#pragma unroll
+        for (int i4 = 0; i4 < NO; i4 += 4) {
+            const float4 w = *reinterpret_cast<const float4 *>(Wt + k * W + o0 + i4);
+            const float wa[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < NS; ++j) acc[i4 + i][j] = fmaf(wa[i], xa[j], acc[i4 + i][j]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NO; ++i)
+#pragma unroll
+        for (int j4 = 0; j4 < NS; j4 += 4)
+            *reinterpret_cast<float4 *>(out + (o0 + i) * BRS + s0 + j4) = make_float4(
+                softplus_f32(acc[i][j4], beta, inv_beta), softplus_f32(acc[i][j4 + 1], beta, inv_beta),
+                softplus_f32(acc[i][j4 + 2], beta, inv_beta), softplus_f32(acc[i][j4 + 3], beta, inv_beta));
+}
+
+template <class C, int BT>
+__global__ void __launch_bounds__(BTHREADS) wave_eval_block_kernel(GridView g, WaveArgs a, int cur) {
+    constexpr int BRS = block_rs(BT), NH = BTHREADS / BT;  // NH threads encode one sample
+    extern __shared__ __align__(128) float dyn[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_tile[4];  // cell, start, len, fresh
+    __shared__ float s_x[3][BT];
+    if (a.ctrl->tail) return;  // finished one thread per ray by wave_tail_kernel
+    const int n_tiles = a.ctrl->n_tiles_fine;
+    if (n_tiles <= 0) return;
+    const int tid = threadIdx.x, nxt = cur ^ 1;
+    float *wsm = dyn;
+    float *A0 = dyn + C::TSIZE, *P = A0 + C::INP * BRS, *Q = P + C::W * BRS;
+    // encoding pad rows stay zero
+    for (int i = tid; i < (C::INP - C::IN) * BRS; i += BTHREADS) A0[C::IN * BRS + i] = 0.f;
+    if (tid == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    const int per = (n_tiles + gridDim.x - 1) / gridDim.x;
+    int next_static = blockIdx.x * per;
+    const int end_static = min(n_tiles, next_static + per);
+    int cached = -1;
+    uint32_t phase = 0;
+    for (;;) {
+        if (tid == 0) {
+            int tile = a.static_tiles ? (next_static < end_static ? next_static : n_tiles)
+                                      : atomicAdd(&a.ctrl->next_tile, 1);
+            int c = -1, start = 0, len = 0;
+            if (tile < n_tiles) {
+                int lo = 0, hi = a.NC;  // the cell c with tile_off[c] <= tile < tile_off[c+1]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (__ldg(a.tile_off + mid) <= tile) lo = mid; else hi = mid;
+                }
+                c = lo;
+                start = __ldg(a.off + lo) + (tile - __ldg(a.tile_off + lo)) * BT;
+                len = min(BT, __ldg(a.off + lo + 1) - start);
+                if (c != cached) bulk_load(wsm, a.wt + (int64_t)c * a.wt_stride, C::TSIZE * sizeof(float), &bar);
+            }
+            s_tile[0] = c;
+            s_tile[1] = start;
+            s_tile[2] = len;
+            s_tile[3] = c != cached;
+        }
+        ++next_static;
+        __syncthreads();
+        const int c = s_tile[0], start = s_tile[1], len = s_tile[2];
+        const bool fresh = s_tile[3] != 0;
+        if (c < 0) break;
+        cached = c;
+        // samples: threads 0..127 own sample s = tid
+        bool active = tid < len;
+        int r = 0, steps = 0, switched = 0;
+        float t = 0.f, t0 = 0.f, tf = 0.f;
+        float4 hist = no_history();
+        const bool cycles = a.t_hist != nullptr && !a.coarse;
+        Ray ray{};
+        if (active) {
+            r = a.sorted[start + tid];
+            t = a.t_ray[r];
+            if (cycles) hist = a.t_hist[r];
+            steps = a.steps_ray[r];
+            if (a.coarse) switched = a.cell_ray[r];
+            int cam;
+            ray = ray_of(a, r, cam);
+            clip_box(g, ray, t0, tf);
+        }
+        if (tid < BT) {
+            s_x[0][tid] = active ? fmaf(t, ray.wx, ray.ox) : 0.f;
+            s_x[1][tid] = active ? fmaf(t, ray.wy, ray.oy) : 0.f;
+            s_x[2][tid] = active ? fmaf(t, ray.wz, ray.oz) : 0.f;
+        }
+        __syncthreads();
+        {
+            const int s = tid & (BT - 1);
+            encode_split<C::L, NH, BRS>(A0, s, tid / BT, s_x[0][s], s_x[1][s], s_x[2][s]);
+        }
+        if (fresh) {
+            const bool ok = mbar_wait(&bar, phase, 1u << 26);
+            phase ^= 1u;
+            if (__syncthreads_or(!ok)) {  // the weights never landed: report and leave
+                if (tid == 0) atomicCAS(a.status, 0, (int)6 /* KNS_ERR_TIMEOUT */);
+                return;
+            }
+        } else {
+            __syncthreads();
+        }
+        block_layer<C::INP, C::W, BT>(wsm + C::tW0, wsm + C::tb0, A0, P, g.beta, g.inv_beta);
+        float *src = P, *dst = Q;
+#pragma unroll
+        for (int l = 1; l < C::H; ++l) {
+            __syncthreads();
+            block_layer<C::W, C::W, BT>(wsm + C::tWl(l), wsm + C::tbl(l), src, dst, g.beta, g.inv_beta);
+            float *tmp = src;
+            src = dst;
+            dst = tmp;
+        }
+        __syncthreads();
+        if (tid < BT) {
+            // the d row: bias first, then one sequential FMA chain over k
+            float d = wsm[C::tbL];
+#pragma unroll 8
+            for (int k = 0; k < C::W; ++k) d = fmaf(wsm[C::tdL + k], src[k * BRS + tid], d);
+            {
+                const unsigned n = __popc(__ballot_sync(FULL, active));
+                if ((tid & 31) == 0 && n) atomicAdd(&a.ctrl->samples_f32, (unsigned long long)n);
+            }
+            bool hit = false, emit = false;
+            int ncell = -1;
+            if (active) {
+                ++steps;
+                const bool last_refine = a.coarse && steps - switched >= a.refine_steps;
+                if (fabsf(d) < a.eps || (last_refine && fabsf(d) < a.eps_coarse)) {
+                    hit = true;
+                    a.cell_ray[r] = c;
+                    a.t_ray[r] = t;
+                    a.steps_ray[r] = steps;
+                } else if (last_refine) {
+                    write_miss(a, r, steps);
+                } else {
+                    const float t_eval = t;
+                    t += d;
+                    if (t > tf || t < t0 || steps >= a.max_steps) {
+                        write_miss(a, r, steps);
+                    } else {
+                        ncell = advance_ray(g, ray, t, tf);
+                        if (ncell < 0) {
+                            write_miss(a, r, steps);
+                        } else if (cycles && cycle_step(hist, t_eval, t)) {
+                            write_miss(a, r, a.max_steps);
+                            ncell = -1;
+                        } else {
+                            emit = true;
+                            a.t_ray[r] = t;
+                            a.steps_ray[r] = steps;
+                            if (cycles) a.t_hist[r] = hist;
+                        }
+                    }
+                }
+            }
+            const int hp = warp_append(&a.ctrl->n_hits, hit);
+            if (hit) a.hits[hp] = r;
+            const int qp = warp_append(&a.ctrl->n_live[nxt], emit);
+            if (emit) {
+                a.q[nxt][qp] = r;
+                a.qcell[nxt][qp] = ncell;
+            }
+            warp_count_cells(a.count[nxt], emit, ncell);
+        }
+        __syncthreads();
+    }
+}
+
 // Tail: one thread runs one ray to its end with the per-thread evaluator (weights via L1).
 template <class C>
 __device__ __noinline__ void finish_ray_f32(const GridView &g, const WaveArgs &a, int r, int cell, bool &hit_out) {
@@ -169,6 +409,8 @@ __device__ __noinline__ void finish_ray_f32(const GridView &g, const WaveArgs &a
     clip_box(g, ray, t0, tf);
     float t = a.t_ray[r];
     int steps = a.steps_ray[r];
+    const bool cycles = a.t_hist != nullptr;  // the tail runs in FP32 renders only
+    float4 hist = cycles ? a.t_hist[r] : no_history();
     hit_out = false;
     for (;;) {
         const float d = sdf_trace_f32<C>(g.w + (int64_t)cell * g.cell_stride, fmaf(t, ray.wx, ray.ox),
@@ -182,10 +424,15 @@ __device__ __noinline__ void finish_ray_f32(const GridView &g, const WaveArgs &a
             hit_out = true;
             return;
         }
+        const float t_eval = t;
         t += d;
         if (t > tf || t < t0 || steps >= a.max_steps) break;
         cell = advance_ray(g, ray, t, tf);
         if (cell < 0) break;
+        if (cycles && cycle_step(hist, t_eval, t)) {
+            steps = a.max_steps;
+            break;
+        }
     }
     write_miss(a, r, steps);
 }
@@ -264,10 +511,13 @@ __global__ void __launch_bounds__(32) wave_eval_kernel(GridView g, WaveArgs a, i
         bool active = lane < TILE && s < len;
         int r = 0, steps = 0, switched = 0;
         float t = 0.f, t0 = 0.f, tf = 0.f;
+        float4 hist = no_history();
+        const bool cycles = a.t_hist != nullptr && !a.coarse;
         Ray ray{};
         if (active) {
             r = a.sorted[start + s];
             t = a.t_ray[r];
+            if (cycles) hist = a.t_hist[r];
             steps = a.steps_ray[r];
             if (a.coarse) switched = a.cell_ray[r];  // step count at the BF16 -> FP32 switch
             int cam;
@@ -322,6 +572,7 @@ __global__ void __launch_bounds__(32) wave_eval_kernel(GridView g, WaveArgs a, i
                     write_miss(a, r, steps);
                     active = false;
                 } else {
+                    const float t_eval = t;
                     t += d;
                     if (t > tf || t < t0 || steps >= a.max_steps) {
                         write_miss(a, r, steps);
@@ -331,10 +582,15 @@ __global__ void __launch_bounds__(32) wave_eval_kernel(GridView g, WaveArgs a, i
                         if (ncell < 0) {
                             write_miss(a, r, steps);
                             active = false;
+                        } else if (cycles && cycle_step(hist, t_eval, t)) {
+                            write_miss(a, r, a.max_steps);
+                            active = false;
+                            ncell = -1;
                         } else if (ncell != c || it + 1 >= a.inner_steps || sparse) {
                             emit = true;
                             a.t_ray[r] = t;
                             a.steps_ray[r] = steps;
+                            if (cycles) a.t_hist[r] = hist;
                             active = false;
                         }
                     }
@@ -395,13 +651,40 @@ cudaError_t launch_wave_gen_cfg(const GridView &g, const WaveArgs &a, cudaStream
     wave_gen_kernel<C><<<grid, 128, 0, s>>>(g, a);
     return cudaGetLastError();
 }
-template <class C>
-cudaError_t launch_wave_eval_cfg(const GridView &g, const WaveArgs &a, int cur, int blocks, cudaStream_t s) {
-    constexpr int smem = eval_smem_bytes<C>();
-    static_assert(smem <= 200 * 1024, "eval tile does not fit in shared memory");
-    cudaError_t e = cudaFuncSetAttribute(wave_eval_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+template <class C, int BT>
+int block_eval_per_sm() {
+    constexpr int smem = block_eval_smem_bytes<C, BT>();
+    const int by_smem = (228 * 1024) / (smem + 2048);
+    return by_smem < 1 ? 1 : (by_smem > 3 ? 3 : by_smem);
+}
+
+template <class C, int BT>
+cudaError_t launch_block_eval(const GridView &g, const WaveArgs &a, int cur, int sm_count, cudaStream_t s) {
+    constexpr int smem = block_eval_smem_bytes<C, BT>();
+    static_assert(smem <= 220 * 1024, "block tile does not fit in shared memory");
+    cudaError_t e =
+        cudaFuncSetAttribute(wave_eval_block_kernel<C, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    wave_eval_kernel<C><<<blocks, 32, smem, s>>>(g, a, cur);
+    wave_eval_block_kernel<C, BT><<<sm_count * block_eval_per_sm<C, BT>(), BTHREADS, smem, s>>>(g, a, cur);
+    return cudaGetLastError();
+}
+
+template <class C>
+cudaError_t launch_wave_eval_cfg(const GridView &g, const WaveArgs &a, int cur, int blocks, int block_tiles,
+                                 int sm_count, cudaStream_t s) {
+    cudaError_t e;
+    if (block_tiles) {
+        // the sort's tile size decides the kernel: 256- or 128-sample block tiles
+        e = a.btile == 256 ? launch_block_eval<C, 256>(g, a, cur, sm_count, s)
+                           : launch_block_eval<C, 128>(g, a, cur, sm_count, s);
+        if (e != cudaSuccess) return e;
+    } else {
+        constexpr int smem = eval_smem_bytes<C>();
+        static_assert(smem <= 200 * 1024, "eval tile does not fit in shared memory");
+        e = cudaFuncSetAttribute(wave_eval_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        wave_eval_kernel<C><<<blocks, 32, smem, s>>>(g, a, cur);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     wave_tail_kernel<C><<<blocks, 128, 0, s>>>(g, a, cur);
     return cudaGetLastError();
@@ -415,7 +698,8 @@ cudaError_t launch_wave_shade_cfg(const GridView &g, const WaveArgs &a, int bloc
 #ifdef KNS_W
 using InstCfg = Cfg<KNS_W, KNS_H, KNS_L, KNS_LD>;
 template cudaError_t launch_wave_gen_cfg<InstCfg>(const GridView &, const WaveArgs &, cudaStream_t);
-template cudaError_t launch_wave_eval_cfg<InstCfg>(const GridView &, const WaveArgs &, int, int, cudaStream_t);
+template cudaError_t launch_wave_eval_cfg<InstCfg>(const GridView &, const WaveArgs &, int, int, int, int,
+                                                   cudaStream_t);
 template cudaError_t launch_wave_shade_cfg<InstCfg>(const GridView &, const WaveArgs &, int, cudaStream_t);
 #endif
 

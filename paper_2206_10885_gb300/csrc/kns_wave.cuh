@@ -106,6 +106,19 @@ __device__ __forceinline__ void write_miss(const WaveArgs &a, int r, int steps) 
     if (V.hit) V.hit[p] = 0;
 }
 
+// Cycle test.  A ray's next sample position is a deterministic function of its current position
+// (the cell's d, the step, the occupancy skip), so a ray whose next position t_next equals one it
+// evaluated before repeats those evaluations for ever: none of them met |d| < eps or left the
+// interval, so the ray ends as a miss when its step budget runs out, with steps = max_steps.  hist
+// holds the four positions evaluated before t_eval (newest first; NaN where none): a match finds
+// cycles of period 2 to 5.  Returns true for a cycle; otherwise shifts t_eval into hist.
+__device__ __forceinline__ bool cycle_step(float4 &hist, float t_eval, float t_next) {
+    if (t_next == hist.x || t_next == hist.y || t_next == hist.z || t_next == hist.w) return true;
+    hist = make_float4(t_eval, hist.x, hist.y, hist.z);
+    return false;
+}
+__device__ __forceinline__ float4 no_history() { return make_float4(NAN, NAN, NAN, NAN); }
+
 // Moves a ray at parameter t to its next sample: the cell at x(t), or, when x(t) lies in an empty
 // occupancy voxel, the entry face of the next occupied voxel (t moves there; the voxel fixes the
 // cell exactly).  Returns the cell, or -1 when the ray leaves the grid (a miss).

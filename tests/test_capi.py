@@ -52,7 +52,8 @@ int main(void) {
   printf("%zu %zu %zu %zu\\n", sizeof(kns_grid_desc), sizeof(kns_camera), sizeof(kns_frame), sizeof(kns_render_opts));
   printf("%zu %zu %zu\\n", offsetof(kns_grid_desc, softplus_beta), offsetof(kns_grid_desc, bbox_max),
          offsetof(kns_camera, cy));
-  printf("%zu %zu\\n", offsetof(kns_frame, hit), offsetof(kns_render_opts, refine_steps));
+  printf("%zu %zu %zu\\n", offsetof(kns_frame, hit), offsetof(kns_render_opts, refine_steps),
+         offsetof(kns_render_opts, block_tiles));
   printf("%zu %zu %zu %zu\\n", sizeof(kns_train_batch), offsetof(kns_train_batch, n_eik),
          offsetof(kns_train_batch, s), offsetof(kns_train_batch, timing));
   printf("%zu %zu\\n", sizeof(kns_train_stats), offsetof(kns_train_stats, ms_fd_backward));
@@ -64,7 +65,8 @@ int main(void) {
     want = [C.sizeof(capi.kns_grid_desc), C.sizeof(capi.kns_camera), C.sizeof(capi.kns_frame),
             C.sizeof(capi.kns_render_opts), capi.kns_grid_desc.softplus_beta.offset,
             capi.kns_grid_desc.bbox_max.offset, capi.kns_camera.cy.offset, capi.kns_frame.hit.offset,
-            capi.kns_render_opts.refine_steps.offset, C.sizeof(capi.kns_train_batch),
+            capi.kns_render_opts.refine_steps.offset, capi.kns_render_opts.block_tiles.offset,
+            C.sizeof(capi.kns_train_batch),
             capi.kns_train_batch.n_eik.offset, capi.kns_train_batch.s.offset, capi.kns_train_batch.timing.offset,
             C.sizeof(capi.kns_train_stats), capi.kns_train_stats.ms_fd_backward.offset]
     assert vals == want

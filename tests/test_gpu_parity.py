@@ -312,13 +312,20 @@ def test_schedule_knobs_do_not_change_results(kns, ctx):
     grid = kns.Grid.load(ctx, desc, w)
     try:
         ref = gpu_render(kns, ctx, grid, cams, 160, 120, 128, 1e-4)
-        for tuning in [dict(inner_steps=1, min_active=1, static_tiles=2, tail_rays=-1),
-                       dict(inner_steps=64, min_active=16, static_tiles=1, blocks_per_sm=2, tail_rays=4096),
-                       dict(inner_steps=7, min_active=3, static_tiles=2, blocks_per_sm=16, tail_rays=100000)]:
+        for tuning in [dict(block_tiles=2, inner_steps=1, min_active=1, static_tiles=2, tail_rays=-1),
+                       dict(block_tiles=2, inner_steps=64, min_active=16, static_tiles=1, blocks_per_sm=2,
+                            tail_rays=4096),
+                       dict(block_tiles=2, inner_steps=7, min_active=3, static_tiles=2, blocks_per_sm=16,
+                            tail_rays=100000),
+                       dict(block_tiles=1, static_tiles=1, tail_rays=-1),
+                       dict(block_tiles=3, static_tiles=2, tail_rays=4096),
+                       dict(block_tiles=3, static_tiles=1, tail_rays=-1)]:
             got = gpu_render(kns, ctx, grid, cams, 160, 120, 128, 1e-4, tuning=tuning)
             for k in ref:
                 assert np.array_equal(ref[k], got[k]), (k, tuning)
         with pytest.raises(kns.KnsError):
             kns.render(ctx, grid, cams, 160, 120, 128, 1e-4, tuning=dict(min_active=17))
+        with pytest.raises(kns.KnsError):
+            kns.render(ctx, grid, cams, 160, 120, 128, 1e-4, tuning=dict(block_tiles=4))
     finally:
         grid.free()
