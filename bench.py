@@ -324,11 +324,15 @@ def run_kns(args, rank, world, local_rank):
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
         if precision == kns.KNS_FP32:
-            # dominant kernel: the FP32 tile evaluation (wave_eval_kernel), FMA-bound
+            # dominant kernel class: the FP32 evaluation (block or warp tiles, plus the per-thread tail
+            # that finishes the last rays; the library times them as one class), FMA-bound
             flops = 2.0 * st["samples_fp32"] * mac_trace
             kms = st["ms_eval_fp32"]
-            roof = {"bound": "alu", "peak": fp32_peak, "unit": "TFLOP/s", "kernel": "wave_eval_kernel",
-                    "peak_source": FP32_PEAK_NOTE}
+            warp_tiles = bool(tuning) and tuning.get("block_tiles") == 2
+            roof = {"bound": "alu", "peak": fp32_peak, "unit": "TFLOP/s",
+                    "kernel": "wave_eval_kernel" if warp_tiles else "wave_eval_block_kernel",
+                    "kernel_class_note": "time and samples of the evaluation class: tile rounds plus the "
+                                         "per-thread tail kernel", "peak_source": FP32_PEAK_NOTE}
         else:
             # dominant kernel: the BF16 tensor-core tile evaluation (wave_eval_bf16_kernel)
             flops = 2.0 * st["samples_bf16"] * mac_trace
