@@ -755,7 +755,7 @@ kns_status resolve_opts(kns_ctx *ctx, const kns_render_opts *opts, float eps, Re
         (opts && (opts->block_tiles < 0 || opts->block_tiles > 3)))
         return set_err(ctx, KNS_ERR_INVALID_ARG, "render tuning field out of range");
     const int bt = opts ? knob(opts->block_tiles, kRenderBlockTiles) : kRenderBlockTiles;
-    c.block_mode = c.bf16 || bt == 2 ? 0 : bt;
+    c.block_mode = bt == 2 ? 0 : bt;  // BF16 renders: the FP32 refinement tiles
     if (c.tail_rays < 0) c.tail_rays = 0;
     if (c.bf16) c.tail_rays = 0;  // the per-thread tail evaluator is FP32 only
     c.timing = opts && opts->timing == 1;
@@ -804,6 +804,7 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
     a.wb = grid->d_wb;
     a.wb_stride = grid->wb_stride;
     a.btile = kRenderBlockTile;
+    a.btile_bf = kRenderBlockTile;
     a.inner_steps = cfg.inner_steps;
     a.tail_max = cfg.tail_rays;
     a.min_active = cfg.min_active;
@@ -1128,6 +1129,7 @@ extern "C" kns_status kns_render_noalloc(kns_ctx *ctx, const kns_grid *grid, con
     a.NC = NC;
     a.nkeys = NC;
     a.btile = kRenderBlockTile;
+    a.btile_bf = kRenderBlockTile;
     a.inner_steps = kRenderInnerSteps;
     a.tail_max = kRenderTailRays;
     a.min_active = kRenderMinActive;

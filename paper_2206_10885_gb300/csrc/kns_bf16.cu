@@ -184,11 +184,16 @@ __global__ void __launch_bounds__(32) wave_eval_bf16_kernel(GridView g, WaveArgs
         bool active = lane < TILE && s < len;
         int r = 0, steps = 0;
         float t = 0.f, t0 = 0.f, tf = 0.f;
+        // cycle test of the BF16 phase: its positions and d values come from this one evaluator, and a
+        // cycle never meets |d| < eps_coarse, so it ends as a budget miss (the FP32 phase keeps none)
+        const bool cycles = a.t_hist != nullptr;
+        float4 hist = no_history();
         Ray ray{};
         if (active) {
             r = a.sorted[start + s];
             t = a.t_ray[r];
             steps = a.steps_ray[r];
+            if (cycles) hist = a.t_hist[r];
             int cam;
             ray = ray_of(a, r, cam);
             clip_box(g, ray, t0, tf);
@@ -240,6 +245,7 @@ __global__ void __launch_bounds__(32) wave_eval_bf16_kernel(GridView g, WaveArgs
                     }
                     active = false;
                 } else {
+                    const float t_eval = t;
                     t += d;
                     if (t > tf || t < t0 || steps >= a.max_steps) {
                         write_miss(a, r, steps);
@@ -249,11 +255,15 @@ __global__ void __launch_bounds__(32) wave_eval_bf16_kernel(GridView g, WaveArgs
                         if (ncell < 0) {
                             write_miss(a, r, steps);
                             active = false;
+                        } else if (cycles && cycle_step(hist, t_eval, t)) {
+                            write_miss(a, r, a.max_steps);
+                            active = false;
                         } else if (ncell != c || it + 1 >= a.inner_steps || sparse) {
                             emit = true;
                             nkey = ncell + a.NC;
                             a.t_ray[r] = t;
                             a.steps_ray[r] = steps;
+                            if (cycles) a.t_hist[r] = hist;
                             active = false;
                         }
                     }

@@ -48,7 +48,8 @@ struct WaveArgs {
     int refine_steps;     // FP32 evaluations after a BF16 hit before the final decision
     const unsigned char *wb;  // BF16 mma fragment trace weights
     int wb_stride;            // bytes per cell
-    int btile;            // samples per block tile (cell-sorted samples are cut into such tiles)
+    int btile;            // samples per FP32 tile (cell-sorted samples are cut into such tiles)
+    int btile_bf;         // samples per BF16 tile (keys >= NC)
     int inner_steps;      // sphere steps a tile may take in one round while its rays stay in its cells
     int tail_max;         // a round with at most this many rays is finished one thread per ray
     int min_active;       // warp tiles with fewer live rays hand them to the next round

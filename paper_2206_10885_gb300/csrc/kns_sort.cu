@@ -77,8 +77,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) wave_scan_kernel(WaveArgs a, int
     int sum = 0, tiles = 0;
     for (int c = c0; c < c1; ++c) {
         const int n = a.count[cur][c];
+        const int bt = c < a.NC ? a.btile : a.btile_bf;  // FP32 keys, then BF16 keys
         sum += n;
-        tiles += (n + a.btile - 1) / a.btile;
+        tiles += (n + bt - 1) / bt;
     }
     int incl_s = sum, incl_t = tiles;
     block_scan2(incl_s, incl_t, wa, wb);
@@ -89,7 +90,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) wave_scan_kernel(WaveArgs a, int
         a.tile_off[c] = run_t;
         if (c == a.NC) a.ctrl->n_tiles_fine = run_t;  // first BF16 key: FP32 tiles end here
         run_s += n;
-        run_t += (n + a.btile - 1) / a.btile;
+        run_t += (n + (c < a.NC ? a.btile : a.btile_bf) - 1) / (c < a.NC ? a.btile : a.btile_bf);
     }
     if (threadIdx.x == SCAN_THREADS - 1) {
         a.off[NC] = incl_s;
