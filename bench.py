@@ -169,6 +169,21 @@ def kernel_source_hash() -> str:
     return h.hexdigest()
 
 
+def max_over_ranks(vals, device, world: int):
+    """Element-wise maximum of per-rank values (the slowest rank's times); identity for one rank."""
+    import torch
+    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(units_per_rank: int, world: int, steps: int, total_ms: float) -> float:
+    """Units of all ranks per second (millions) over the slowest rank's time: weak-scaling value."""
+    return world * units_per_rank * steps / (total_ms * 1e-3) / 1e6
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -309,15 +324,10 @@ def run_kns(args, rank, world, local_rank):
     e2e_s = time.perf_counter() - t0
     clock_info = clocks.stop() if clocks else None
 
-    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    e_max = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-        dist.all_reduce(e_max, op=dist.ReduceOp.MAX)
-    total_ms, e2e_s = float(t_max.item()), float(e_max.item())
+    total_ms, e2e_s = max_over_ranks([total_ms, e2e_s], dev, world)
     ms_per_step = total_ms / args.steps
-    value = world * n_rays * args.steps / (total_ms * 1e-3) / 1e6
-    e2e_value = world * n_rays * args.steps / e2e_s / 1e6
+    value = whole_job_rate(n_rays, world, args.steps, total_ms)
+    e2e_value = whole_job_rate(n_rays, world, args.steps, e2e_s * 1e3)
 
     if rank == 0:
         peaks = load_peaks()
@@ -563,14 +573,9 @@ def run_train(args, rank, world, local_rank):
     e2e_s = time.perf_counter() - t0
     clock_info = clocks.stop() if clocks else None
 
-    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    e_max = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-        dist.all_reduce(e_max, op=dist.ReduceOp.MAX)
-    total_ms, e2e_s = float(t_max.item()), float(e_max.item())
+    total_ms, e2e_s = max_over_ranks([total_ms, e2e_s], dev, world)
     n_rays = wl["n_rays"]
-    value = world * n_rays * args.steps / (total_ms * 1e-3) / 1e6
+    value = whole_job_rate(n_rays, world, args.steps, total_ms)
     if rank == 0:
         peaks = load_peaks()
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -607,7 +612,7 @@ def run_train(args, rank, world, local_rank):
                                parallelism="replicas" if world > 1 else "single GPU"),
                 "roofline": roof, "cpu_baseline": cpu, "phases_ms_per_step": phases, "counts_per_step": counts,
                 "work_per_step": work,
-                "e2e": {"value": world * n_rays * args.steps / e2e_s / 1e6, "unit": UNIT,
+                "e2e": {"value": whole_job_rate(n_rays, world, args.steps, e2e_s * 1e3), "unit": UNIT,
                         "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
                 "clocks": clock_info, "gpu_launches": args.steps * 17,
                 "launch_count_source": "fixed kernel sequence of kns_train_step: coarse hist/scan/scatter/eval, "
