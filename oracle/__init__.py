@@ -83,6 +83,14 @@ def lib():
                                         C.c_int64, d, C.c_double, C.c_double, d, d, d, d]
             L.ko_train_grad.restype = C.c_double
             L.ko_train_grad.argtypes = L.ko_train_loss.argtypes[:-1]
+            L.ko_splitmix64.restype = C.c_uint64
+            L.ko_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
+            L.ko_pt_uniform.restype = C.c_double
+            L.ko_pt_uniform.argtypes = [C.c_uint64, C.c_int64, C.c_int, C.c_int]
+            L.ko_cosine_dir.argtypes = [d, C.c_double, C.c_double, d]
+            L.ko_sky.argtypes = [d, d, d, d]
+            L.ko_path_trace.argtypes = [D, f, u64, f, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                        C.c_double, C.c_double, C.c_uint64, d, d, C.c_int64, i64, d, d, i32]
             L.ko_num_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -312,3 +320,43 @@ def train_grad(g, w, s: float, s_up: float, o, dirs, target, u_strat, u_imp, poi
                                _p(points, C.c_double), float(lam), float(h), _p(tf, C.c_double), _p(grad, C.c_double),
                                _p(parts, C.c_double))
     return loss, parts, grad
+
+
+def splitmix64(seed: int, k: int) -> int:
+    return int(lib().ko_splitmix64(seed & 0xFFFFFFFFFFFFFFFF, k))
+
+
+def pt_uniform(seed: int, path: int, depth: int, dim: int) -> float:
+    return float(lib().ko_pt_uniform(seed, path, depth, dim))
+
+
+def cosine_dir(n, u1: float, u2: float) -> np.ndarray:
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    w = np.zeros(3)
+    lib().ko_cosine_dir(_p(n, C.c_double), float(u1), float(u2), _p(w, C.c_double))
+    return w
+
+
+def sky(w, horizon, zenith) -> np.ndarray:
+    out = np.zeros(3)
+    args = [np.ascontiguousarray(v, dtype=np.float64) for v in (w, horizon, zenith)]
+    lib().ko_sky(*[_p(v, C.c_double) for v in args], _p(out, C.c_double))
+    return out
+
+
+def path_trace(g, w, occ, cams, W: int, H: int, spp: int, max_depth: int, max_steps: int, eps: float,
+               offset: float, seed: int, horizon, zenith, sel=None):
+    """Lambertian path tracing (see ko_path_trace).  Returns dict(rgb per pixel, L per path, traces per path)."""
+    w = _f32(w)
+    cams = _f32(cams).reshape(-1, 16)
+    occ = None if occ is None else np.ascontiguousarray(occ, dtype=np.uint64)
+    sel = np.arange(cams.shape[0] * W * H, dtype=np.int64) if sel is None else np.ascontiguousarray(sel, np.int64)
+    n = sel.size
+    hz = np.ascontiguousarray(horizon, dtype=np.float64)
+    zn = np.ascontiguousarray(zenith, dtype=np.float64)
+    out = dict(rgb=np.zeros((n, 3)), L=np.zeros((n, spp, 3)), traces=np.zeros((n, spp), np.int32))
+    lib().ko_path_trace(C.byref(_desc(g)), _p(w, C.c_float), _p(occ, C.c_uint64), _p(cams, C.c_float),
+                        cams.shape[0], W, H, spp, max_depth, max_steps, float(eps), float(offset), seed,
+                        _p(hz, C.c_double), _p(zn, C.c_double), n, _p(sel, C.c_int64),
+                        _p(out["rgb"], C.c_double), _p(out["L"], C.c_double), _p(out["traces"], C.c_int32))
+    return out

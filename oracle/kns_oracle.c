@@ -879,3 +879,109 @@ double ko_train_grad(const ko_desc *g, const float *weights, double s, double s_
     free(ts);
     return loss;
 }
+
+/* ---------------------------------------------------------------------------------------------
+ * Lambertian path tracing of the KiloNeuS surface (Sec. 3.4: the path tracer treats the surface as
+ * Lambertian; the colour network gives its albedo, the normalised SDF gradient its normal).
+ *
+ * Random numbers: SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): the k-th output of the generator
+ * seeded with s is mix(s + (k + 1) * 0x9E3779B97F4A7C15); a uniform in [0, 1) is its top 24 bits
+ * times 2^-24 (exact in float and double).  Path p, trace depth t, dimension i use k = (p * 16 + t)
+ * * 4 + i.
+ * Path p of pixel (c, i, j) and sample s: p = ((c * H + i) * W + j) * spp + s.  Its primary ray goes
+ * through the point (j + u_0, i + u_1) of the image plane (u from depth 0).  At each depth the ray is
+ * sphere-traced (ko_trace); a miss adds beta * E(w) and ends the path, E(w) = (1 - a) horizon +
+ * a zenith with a = (w_z + 1) / 2; a hit multiplies beta by the albedo (the colour MLP at the hit,
+ * seen from the ray) and, below the last depth, continues from x + offset * n in a cosine-weighted
+ * direction about n (u_2, u_3 of this depth; orthonormal basis of Duff et al., JCGT 2017); a hit at
+ * the last depth ends the path with no light.  Pixel value = mean over its spp paths.
+ * ------------------------------------------------------------------------------------------- */
+#define KO_PT_MAXDEPTH 16
+
+uint64_t ko_splitmix64(uint64_t seed, uint64_t k) {
+    uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+double ko_pt_uniform(uint64_t seed, int64_t path, int depth, int dim) {
+    uint64_t k = ((uint64_t)path * KO_PT_MAXDEPTH + (uint64_t)depth) * 4u + (uint64_t)dim;
+    return (double)(ko_splitmix64(seed, k) >> 40) * 0x1p-24;
+}
+
+/* cosine-weighted unit direction about the unit normal n */
+void ko_cosine_dir(const double n[3], double u1, double u2, double w[3]) {
+    double sign = n[2] >= 0 ? 1.0 : -1.0;
+    double a = -1.0 / (sign + n[2]);
+    double b = n[0] * n[1] * a;
+    double t[3] = {1.0 + sign * n[0] * n[0] * a, sign * b, -sign * n[0]};
+    double bb[3] = {b, sign + n[1] * n[1] * a, -n[1]};
+    double r = sqrt(u2), phi = 2.0 * M_PI * u1, z = sqrt(1.0 - u2);
+    for (int k = 0; k < 3; k++) w[k] = r * cos(phi) * t[k] + r * sin(phi) * bb[k] + z * n[k];
+}
+
+void ko_sky(const double w[3], const double horizon[3], const double zenith[3], double out[3]) {
+    double a = 0.5 * (w[2] + 1.0);
+    for (int k = 0; k < 3; k++) out[k] = (1.0 - a) * horizon[k] + a * zenith[k];
+}
+
+/* path tracing of the selected pixels; L (n_sel * spp * 3) and traces (n_sel * spp) per path are
+ * optional outputs */
+void ko_path_trace(const ko_desc *g, const float *weights, const uint64_t *occ, const float *cams, int n_cams,
+                   int W, int H, int spp, int max_depth, int max_steps, double eps, double offset, uint64_t seed,
+                   const double *horizon, const double *zenith, int64_t n_sel, const int64_t *sel, double *rgb,
+                   double *L_out, int32_t *traces_out) {
+    if (max_depth > KO_PT_MAXDEPTH) max_depth = KO_PT_MAXDEPTH;
+    (void)n_cams;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t q = 0; q < n_sel; q++) {
+        const int64_t pix = sel[q];
+        const int c = (int)(pix / ((int64_t)W * H));
+        const int i = (int)((pix / W) % H), j = (int)(pix % W);
+        const float *cam = cams + 16 * c;
+        double acc[3] = {0, 0, 0};
+        for (int s = 0; s < spp; s++) {
+            const int64_t path = pix * spp + s;
+            double o[3], w[3], beta[3] = {1, 1, 1}, L[3] = {0, 0, 0};
+            {
+                double u0 = ko_pt_uniform(seed, path, 0, 0), u1 = ko_pt_uniform(seed, path, 0, 1);
+                double dc[3] = {((double)j + u0 - cam[14]) / cam[12], ((double)i + u1 - cam[15]) / cam[13], 1.0};
+                double nrm = 0;
+                for (int r = 0; r < 3; r++) {
+                    w[r] = cam[4 * r + 0] * dc[0] + cam[4 * r + 1] * dc[1] + cam[4 * r + 2] * dc[2];
+                    nrm += w[r] * w[r];
+                    o[r] = cam[4 * r + 3];
+                }
+                nrm = sqrt(nrm);
+                for (int r = 0; r < 3; r++) w[r] /= nrm;
+            }
+            int traces = 0;
+            for (int depth = 0; depth < max_depth; depth++) {
+                ko_ray_out r;
+                ko_trace(g, weights, occ, o, w, max_steps, eps, &r);
+                traces++;
+                if (!r.hit) {
+                    double e[3];
+                    ko_sky(w, horizon, zenith, e);
+                    for (int k = 0; k < 3; k++) L[k] += beta[k] * e[k];
+                    break;
+                }
+                for (int k = 0; k < 3; k++) beta[k] *= r.rgb[k];
+                if (depth + 1 == max_depth) break;
+                double x[3], nw[3];
+                for (int k = 0; k < 3; k++) x[k] = o[k] + r.depth * w[k] + offset * r.normal[k];
+                ko_cosine_dir(r.normal, ko_pt_uniform(seed, path, depth, 2), ko_pt_uniform(seed, path, depth, 3), nw);
+                for (int k = 0; k < 3; k++) {
+                    o[k] = x[k];
+                    w[k] = nw[k];
+                }
+            }
+            for (int k = 0; k < 3; k++) acc[k] += L[k];
+            if (L_out)
+                for (int k = 0; k < 3; k++) L_out[3 * (q * spp + s) + k] = L[k];
+            if (traces_out) traces_out[q * spp + s] = traces;
+        }
+        for (int k = 0; k < 3; k++) rgb[3 * q + k] = acc[k] / spp;
+    }
+}
