@@ -214,6 +214,39 @@ typedef struct kns_view {
 kns_status kns_render_views(kns_ctx *ctx, const kns_grid *grid, const kns_view *views, int n_views, int max_steps,
                             float eps, const kns_render_opts *opts, void *cuda_stream);
 
+/* Sphere-trace and shade explicit rays (Sec. 3.4.1 for arbitrary rays, e.g. the bounce rays of a path
+ * tracer): origins and unit directions (device, n x 3 FP32); ray k writes element k of every output
+ * of `out` (device buffers of n elements; rgb and depth required, the rest nullable) exactly as
+ * kns_render writes a pixel.  n = 0 is a successful no-op.  Errors: INVALID_ARG (NULL grid, rays or
+ * rgb/depth, n out of [0, 2^31 - 4097], max_steps < 1, eps <= 0, bad opts), CUDA, OUT_OF_MEMORY. */
+kns_status kns_trace_rays(kns_ctx *ctx, const kns_grid *grid, const float *origins, const float *dirs, int64_t n,
+                          int max_steps, float eps, const kns_frame *out, const kns_render_opts *opts,
+                          void *cuda_stream);
+
+/* Lambertian path tracing (Sec. 3.4: the surface is treated as Lambertian; the colour network gives
+ * its albedo, the normalised SDF gradient its normal).  Per path: a primary ray through the point
+ * (j + u0, i + u1) of pixel (i, j); at each of at most max_depth traces a miss adds beta * E(w) and
+ * ends the path, E(w) = (1 - a) horizon + a zenith with a = (w_z + 1) / 2; a hit multiplies beta by
+ * the albedo and, below the last depth, continues from hit + offset * normal in a cosine-weighted
+ * direction about the normal (a hit at the last depth gathers no light).  Random numbers: SplitMix64
+ * outputs k = (path * 16 + depth) * 4 + dim of the generator seeded with `seed`, top 24 bits / 2^24;
+ * path = pixel * spp + sample, pixel = (cam * H + i) * W + j. */
+typedef struct {
+    int32_t spp;          /* paths per pixel (>= 1) */
+    int32_t max_depth;    /* traces per path (1..16) */
+    uint64_t seed;
+    float offset;         /* bounce origin offset along the normal (>= 0) */
+    float horizon[3], zenith[3];
+} kns_pt_opts;
+
+/* Path-traced image: rgb_out (device, n_cams x H x W x 3, camera-major, row-major) gets the mean of
+ * each pixel's spp paths.  cams: host array.  Tracing uses kns_render's sphere tracer with max_steps,
+ * eps and opts.  Errors: INVALID_ARG (NULL grid/opts/cams/rgb_out, sizes or pt fields out of range,
+ * more than 2^31 - 4097 paths), CUDA, OUT_OF_MEMORY. */
+kns_status kns_path_trace(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams, int n_cams, int W, int H,
+                          const kns_pt_opts *pt, int max_steps, float eps, float *rgb_out,
+                          const kns_render_opts *opts, void *cuda_stream);
+
 /* Batch field query (the vectorised per-cell MLP query of Sec. 3.3): for n points (device,
  * n x 3 FP32, row-major) evaluate the SDF MLP of cell m(x): sdf (device, n floats), feat (device,
  * n x feat_dim, or NULL), grad (device, n x 3 analytic input gradient, or NULL).

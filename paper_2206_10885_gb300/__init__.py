@@ -12,7 +12,8 @@ from . import _capi as capi
 from . import train
 from ._capi import KNS_BF16, KNS_FP32, KnsError
 
-__all__ = ["capi", "KnsError", "KNS_FP32", "KNS_BF16", "Context", "Grid", "alloc_frame", "render", "sdf", "train"]
+__all__ = ["capi", "KnsError", "KNS_FP32", "KNS_BF16", "Context", "Grid", "alloc_frame", "render", "sdf", "train",
+           "trace_rays", "path_trace"]
 
 
 def _stream_ptr(stream) -> int:
@@ -154,3 +155,34 @@ def sdf(ctx: Context, grid: Grid, pts, want_feat: bool = True, want_grad: bool =
     capi.kns_sdf(ctx.handle, grid.handle, pts.data_ptr(), n, d.data_ptr(), feat.data_ptr() if want_feat else None,
                  grad.data_ptr() if want_grad else None, _stream_ptr(stream))
     return d, feat, grad
+
+
+def trace_rays(ctx: Context, grid: Grid, origins, dirs, max_steps: int, eps: float, tuning=None, stream=None):
+    """kns_trace_rays on (n, 3) float32 CUDA tensors; returns the dict of per-ray output tensors."""
+    origins, dirs = origins.contiguous(), dirs.contiguous()
+    n = origins.shape[0]
+    t, f = alloc_frame(n, origins.device)
+    capi.kns_trace_rays(ctx.handle, grid.handle, origins.data_ptr(), dirs.data_ptr(), n, max_steps, eps, f,
+                        render_opts(KNS_FP32, tuning=tuning), _stream_ptr(stream))
+    return t
+
+
+SKY_HORIZON = (1.0, 1.0, 1.0)
+SKY_ZENITH = (0.5, 0.7, 1.0)
+
+
+def path_trace(ctx: Context, grid: Grid, cams: np.ndarray, W: int, H: int, spp: int = 16, max_depth: int = 4,
+               seed: int = 0, offset: float = 1e-2, horizon=SKY_HORIZON, zenith=SKY_ZENITH, max_steps: int = 128,
+               eps: float = 1e-4, tuning=None, stream=None):
+    """kns_path_trace: Lambertian path-traced image as an (n_cams * H * W, 3) float32 CUDA tensor."""
+    import torch
+    cams = np.ascontiguousarray(cams, dtype=np.float32).reshape(-1, 16)
+    rgb = torch.empty((cams.shape[0] * W * H, 3), dtype=torch.float32, device="cuda:%d" % ctx.device)
+    pt = capi.kns_pt_opts()
+    pt.spp, pt.max_depth, pt.seed, pt.offset = spp, max_depth, seed, offset
+    for k in range(3):
+        pt.horizon[k] = horizon[k]
+        pt.zenith[k] = zenith[k]
+    capi.kns_path_trace(ctx.handle, grid.handle, cams.ctypes.data, cams.shape[0], W, H, pt, max_steps, eps,
+                        rgb.data_ptr(), render_opts(KNS_FP32, tuning=tuning), _stream_ptr(stream))
+    return rgb

@@ -70,6 +70,11 @@ class kns_train_stats(C.Structure):
                 ("ms_centre_backward", C.c_float), ("ms_fd_backward", C.c_float), ("ms_total", C.c_float)]
 
 
+class kns_pt_opts(C.Structure):
+    _fields_ = [("spp", C.c_int32), ("max_depth", C.c_int32), ("seed", C.c_uint64), ("offset", C.c_float),
+                ("horizon", C.c_float * 3), ("zenith", C.c_float * 3)]
+
+
 class kns_render_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("eps_coarse", C.c_float), ("refine_steps", C.c_int32),
                 ("inner_steps", C.c_int32), ("min_active", C.c_int32), ("tail_rays", C.c_int32),
@@ -129,6 +134,12 @@ def lib():
             L.kns_render_views.restype = st
             L.kns_get_render_stats.argtypes = [vp, C.POINTER(kns_render_stats)]
             L.kns_get_render_stats.restype = st
+            L.kns_trace_rays.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_int, C.c_float, C.POINTER(kns_frame),
+                                         C.POINTER(kns_render_opts), vp]
+            L.kns_trace_rays.restype = st
+            L.kns_path_trace.argtypes = [vp, vp, vp, C.c_int, C.c_int, C.c_int, C.POINTER(kns_pt_opts), C.c_int,
+                                         C.c_float, vp, C.POINTER(kns_render_opts), vp]
+            L.kns_path_trace.restype = st
             L.kns_train_forward.argtypes = [vp, C.POINTER(kns_grid_desc), vp, C.POINTER(kns_train_batch), vp, vp, vp,
                                             C.POINTER(C.c_uint64), vp]
             L.kns_train_forward.restype = st
@@ -273,3 +284,15 @@ def kns_train_get_stats(ctx: int) -> dict:
     st = kns_train_stats()
     _check(lib().kns_train_get_stats(ctx, C.byref(st)), ctx)
     return {k: getattr(st, k) for k, _ in kns_train_stats._fields_ if k != "pad"}
+
+
+def kns_trace_rays(ctx: int, grid: int, origins_ptr: int, dirs_ptr: int, n: int, max_steps: int, eps: float,
+                   frame: kns_frame, opts: kns_render_opts = None, stream: int = 0) -> None:
+    _check(lib().kns_trace_rays(ctx, grid, origins_ptr, dirs_ptr, n, max_steps, eps, C.byref(frame),
+                                C.byref(opts) if opts is not None else None, stream), ctx)
+
+
+def kns_path_trace(ctx: int, grid: int, cams_host_ptr: int, n_cams: int, W: int, H: int, pt: kns_pt_opts,
+                   max_steps: int, eps: float, rgb_ptr: int, opts: kns_render_opts = None, stream: int = 0) -> None:
+    _check(lib().kns_path_trace(ctx, grid, cams_host_ptr, n_cams, W, H, C.byref(pt), max_steps, eps, rgb_ptr,
+                                C.byref(opts) if opts is not None else None, stream), ctx)

@@ -30,6 +30,15 @@ struct WaveScratch {
     kns::WaveCtrl *ctrl = nullptr;
 };
 
+// Device scratch of the path tracer (per path: ray, throughput, radiance, trace outputs).
+struct PtScratch {
+    int64_t cap = 0;  // paths
+    int cap_cams = 0;
+    float *o = nullptr, *w = nullptr, *beta = nullptr, *L = nullptr, *rgb = nullptr, *depth = nullptr,
+          *normal = nullptr, *cams = nullptr;
+    uint8_t *alive = nullptr, *hit = nullptr;
+};
+
 // Device scratch and saved state of the training step, owned by the context and grown on demand.
 struct TrainScratch {
     int64_t cap_B = 0, cap_M = 0;  // capacity: rays, eikonal points
@@ -59,6 +68,7 @@ struct kns_ctx {
     int *d_status = nullptr;  // device status word written by kernels (0 = fine)
     WaveScratch ws;
     TrainScratch ts;
+    PtScratch ps;
     int *h_live = nullptr;                 // pinned: live-sample counts of recent rounds
     cudaEvent_t ev_live[4] = {nullptr, nullptr, nullptr, nullptr};
     // last render's statistics
@@ -378,6 +388,44 @@ kns_status ensure_scratch(kns_ctx *ctx, int64_t rays, int nc, int cams) {
     return KNS_OK;
 }
 
+void free_pt_scratch(PtScratch &p) {
+    void *ps[] = {p.o, p.w, p.beta, p.L, p.rgb, p.depth, p.normal, p.cams, p.alive, p.hit};
+    for (void *q : ps)
+        if (q) cudaFree(q);
+    p = PtScratch{};
+}
+
+kns_status ensure_pt_scratch(kns_ctx *ctx, int64_t n, int cams) {
+    PtScratch &p = ctx->ps;
+    if (n <= p.cap && cams <= p.cap_cams) return KNS_OK;
+    cudaDeviceSynchronize();
+    const int64_t N = std::max(n, p.cap);
+    const int NC = std::max(cams, p.cap_cams);
+    free_pt_scratch(p);
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](auto **q, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc((void **)q, bytes);
+    };
+    const size_t v3 = sizeof(float) * 3 * (size_t)N;
+    alloc(&p.o, v3);
+    alloc(&p.w, v3);
+    alloc(&p.beta, v3);
+    alloc(&p.L, v3);
+    alloc(&p.rgb, v3);
+    alloc(&p.normal, v3);
+    alloc(&p.depth, sizeof(float) * (size_t)N);
+    alloc(&p.cams, sizeof(float) * 16 * (size_t)NC);
+    alloc(&p.alive, (size_t)N);
+    alloc(&p.hit, (size_t)N);
+    if (e != cudaSuccess) {
+        free_pt_scratch(p);
+        return cuda_err(ctx, e, "path-tracing scratch");
+    }
+    p.cap = N;
+    p.cap_cams = NC;
+    return KNS_OK;
+}
+
 void free_train_scratch(TrainScratch &t) {
     void *ps[] = {t.t, t.d_coarse, t.d_fd, t.g_fd, t.d_c, t.g_dc, t.rgb_c, t.g_rgb, t.C, t.valid, t.acc, t.keys,
                   t.sorted, t.d_counts};
@@ -480,6 +528,7 @@ void kns_destroy(kns_ctx *ctx) {
         cudaDeviceSynchronize();
         free_scratch(ctx->ws);
         free_train_scratch(ctx->ts);
+        free_pt_scratch(ctx->ps);
         for (cudaEvent_t ev : ctx->ts.ev)
             if (ev) cudaEventDestroy(ev);
         cudaFree(ctx->d_status);
@@ -776,7 +825,8 @@ void begin_stats(kns_ctx *ctx, cudaStream_t s, int64_t rays) {
 // whose device counters kns_get_render_stats reads later; earlier batches add theirs here.
 kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vector<kns::ViewDev> &views,
                              int64_t rays, int max_steps, float eps, const RenderCfg &cfg, cudaStream_t s,
-                             bool last) {
+                             bool last, const float *ray_o = nullptr, const float *ray_w = nullptr,
+                             int64_t n_table = 0) {
     const int NC = grid->desc.N * grid->desc.N * grid->desc.N;
     const int nkeys = cfg.bf16 ? 2 * NC : NC;
     const int nv = (int)views.size();
@@ -794,6 +844,9 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
     a.max_H = max_H;
     a.views = w.d_views;
     a.ray_view = w.ray_view;
+    a.ray_o = ray_o;
+    a.ray_w = ray_w;
+    a.n_table = ray_o ? (int)n_table : 0;
     a.max_steps = max_steps;
     a.eps = eps;
     a.NC = NC;
@@ -979,6 +1032,107 @@ kns_status kns_render_views(kns_ctx *ctx, const kns_grid *grid, const kns_view *
     begin_stats(ctx, s, rays);
     st = render_views_impl(ctx, grid, dv, rays, max_steps, eps, cfg, s, true);
     if (st != KNS_OK) return st;
+    ctx->have_stats = true;
+    return KNS_OK;
+}
+
+kns_status kns_trace_rays(kns_ctx *ctx, const kns_grid *grid, const float *origins, const float *dirs, int64_t n,
+                          int max_steps, float eps, const kns_frame *out, const kns_render_opts *opts,
+                          void *cuda_stream) {
+    if (!ctx) return KNS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!grid) return set_err(ctx, KNS_ERR_INVALID_ARG, "NULL grid");
+    if (n < 0 || n > INT32_MAX - 4096) return set_err(ctx, KNS_ERR_INVALID_ARG, "n out of range");
+    if (n == 0) return KNS_OK;
+    if (!origins || !dirs || !out || !out->rgb || !out->depth)
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "NULL rays or rgb/depth outputs");
+    if (max_steps < 1) return set_err(ctx, KNS_ERR_INVALID_ARG, "max_steps=%d < 1", max_steps);
+    if (!(eps > 0.f) || !std::isfinite(eps)) return set_err(ctx, KNS_ERR_INVALID_ARG, "eps must be > 0 and finite");
+    RenderCfg cfg;
+    kns_status st = resolve_opts(ctx, opts, eps, cfg);
+    if (st != KNS_OK) return st;
+    DeviceScope ds(ctx->device);
+    // one view of rows of 4096 rays; rays past n in the last row are skipped
+    const int Wv = (int)std::min<int64_t>(n, 4096), Hv = (int)((n + Wv - 1) / Wv);
+    kns_camera cam{};
+    std::vector<kns::ViewDev> dv{make_view(cam, Wv, Hv, 0, *out)};
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    begin_stats(ctx, s, n);
+    st = render_views_impl(ctx, grid, dv, (int64_t)Wv * Hv, max_steps, eps, cfg, s, true, origins, dirs, n);
+    if (st != KNS_OK) return st;
+    ctx->have_stats = true;
+    return KNS_OK;
+}
+
+kns_status kns_path_trace(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams, int n_cams, int W, int H,
+                          const kns_pt_opts *pt, int max_steps, float eps, float *rgb_out,
+                          const kns_render_opts *opts, void *cuda_stream) {
+    if (!ctx) return KNS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!grid || !pt || (n_cams > 0 && !cams)) return set_err(ctx, KNS_ERR_INVALID_ARG, "NULL grid, opts or cams");
+    if (n_cams < 0 || W < 0 || H < 0) return set_err(ctx, KNS_ERR_INVALID_ARG, "negative size");
+    if (pt->spp < 1 || pt->max_depth < 1 || pt->max_depth > kns::pt_max_depth())
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "need spp >= 1 and 1 <= max_depth <= %d", kns::pt_max_depth());
+    if (!(pt->offset >= 0.f) || !std::isfinite(pt->offset))
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "offset must be finite and >= 0");
+    const int64_t n_pix = (int64_t)n_cams * W * H, n = n_pix * pt->spp;
+    if (n == 0) return KNS_OK;
+    if (!rgb_out) return set_err(ctx, KNS_ERR_INVALID_ARG, "NULL rgb_out");
+    if (n > INT32_MAX - 4096) return set_err(ctx, KNS_ERR_INVALID_ARG, "more than 2^31 - 4097 paths");
+    if (max_steps < 1) return set_err(ctx, KNS_ERR_INVALID_ARG, "max_steps=%d < 1", max_steps);
+    if (!(eps > 0.f) || !std::isfinite(eps)) return set_err(ctx, KNS_ERR_INVALID_ARG, "eps must be > 0 and finite");
+    RenderCfg cfg;
+    kns_status st = resolve_opts(ctx, opts, eps, cfg);
+    if (st != KNS_OK) return st;
+    DeviceScope ds(ctx->device);
+    if ((st = ensure_pt_scratch(ctx, n, n_cams)) != KNS_OK) return st;
+    PtScratch &p = ctx->ps;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    kns::PtArgs a{};
+    a.n_cams = n_cams;
+    a.W = W;
+    a.H = H;
+    a.spp = pt->spp;
+    a.max_depth = pt->max_depth;
+    a.n_paths = n;
+    a.cams = p.cams;
+    a.seed = pt->seed;
+    a.offset = pt->offset;
+    for (int k = 0; k < 3; ++k) {
+        a.horizon[k] = pt->horizon[k];
+        a.zenith[k] = pt->zenith[k];
+        a.bmax[k] = grid->desc.bbox_max[k];
+    }
+    a.o = p.o;
+    a.w = p.w;
+    a.beta = p.beta;
+    a.L = p.L;
+    a.alive = p.alive;
+    a.t_rgb = p.rgb;
+    a.t_depth = p.depth;
+    a.t_normal = p.normal;
+    a.t_hit = p.hit;
+    a.rgb_out = rgb_out;
+    cudaError_t e = cudaMemcpyAsync(p.cams, cams, sizeof(kns_camera) * n_cams, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = kns::pt_primary(a, s);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "path-tracing launch");
+    // each depth traces every path's ray (finished paths carry a ray that misses the box at once)
+    const int Wv = (int)std::min<int64_t>(n, 4096), Hv = (int)((n + Wv - 1) / Wv);
+    kns_frame fr{};
+    fr.rgb = p.rgb;
+    fr.depth = p.depth;
+    fr.normal = p.normal;
+    fr.hit = p.hit;
+    kns_camera cam0{};
+    std::vector<kns::ViewDev> dv{make_view(cam0, Wv, Hv, 0, fr)};
+    begin_stats(ctx, s, n);
+    for (int depth = 0; depth < pt->max_depth; ++depth) {
+        st = render_views_impl(ctx, grid, dv, (int64_t)Wv * Hv, max_steps, eps, cfg, s,
+                               depth + 1 == pt->max_depth, p.o, p.w, n);
+        if (st != KNS_OK) return st;
+        if ((e = kns::pt_bounce(a, depth, s)) != cudaSuccess) return cuda_err(ctx, e, "path-tracing launch");
+    }
+    if ((e = kns::pt_resolve(a, s)) != cudaSuccess) return cuda_err(ctx, e, "path-tracing launch");
     ctx->have_stats = true;
     return KNS_OK;
 }

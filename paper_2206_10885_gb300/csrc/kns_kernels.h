@@ -39,6 +39,8 @@ struct ViewDev {
 struct WaveArgs {
     int n_views, max_W, max_H, max_steps;
     const ViewDev *views;  // n_views entries; rays of view v are ray_base .. ray_base + W*H - 1
+    const float *ray_o, *ray_w;  // explicit rays (n_table x 3 each) instead of camera pixels, or NULL
+    int n_table;
     int *ray_view;         // view of each ray
     float eps;
     int NC;               // cells N^3
@@ -104,6 +106,26 @@ cudaError_t launch_sdf_f32(const Shape &sh, const GridView &g, const float *pts,
                            float *feat, float *grad, cudaStream_t s);
 cudaError_t launch_occupancy_f32(const Shape &sh, const GridView &g, float thresh, uint32_t *words,
                                  cudaStream_t s);
+
+// ------------------------------------------------------------------ path tracing
+struct PtArgs {
+    int n_cams, W, H, spp, max_depth;
+    int64_t n_paths;            // n_cams * W * H * spp
+    const float *cams;          // device, n_cams x 16
+    uint64_t seed;
+    float offset;               // bounce origin = hit + offset * normal
+    float horizon[3], zenith[3];
+    float bmax[3];              // box corner (dead paths get a ray that misses the box)
+    float *o, *w, *beta, *L;    // per path x 3
+    uint8_t *alive;
+    const float *t_rgb, *t_depth, *t_normal;  // the current depth's trace results
+    const uint8_t *t_hit;
+    float *rgb_out;             // per pixel x 3
+};
+int pt_max_depth();
+cudaError_t pt_primary(const PtArgs &a, cudaStream_t s);
+cudaError_t pt_bounce(const PtArgs &a, int depth, cudaStream_t s);
+cudaError_t pt_resolve(const PtArgs &a, cudaStream_t s);
 
 // ------------------------------------------------------------------ training step
 // Everything the training kernels read and write (device pointers unless noted; passed by value).

@@ -117,13 +117,13 @@ __global__ void __launch_bounds__(128) wave_gen_kernel(GridView g, WaveArgs a) {
     const int i = blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
     const int view = blockIdx.z;
     const ViewDev &V = a.views[view];
-    const bool valid = i < V.H && j < V.W;
     const int r = V.ray_base + i * V.W + j;
+    const bool valid = i < V.H && j < V.W && (a.ray_o == nullptr || r < a.n_table);
     bool alive = false;
     int cell = -1;
     if (valid) {
         a.ray_view[r] = view;
-        const Ray ray = make_ray(V.cam, i, j);
+        const Ray ray = a.ray_o ? table_ray(a, r) : make_ray(V.cam, i, j);
         float t0, tf;
         if (!clip_box(g, ray, t0, tf)) {
             write_miss(a, r, 0);

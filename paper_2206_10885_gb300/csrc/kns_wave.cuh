@@ -80,9 +80,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
     return false;
 }
 
-// The ray with id r: its view v, pixel index in the view, and world-space origin and direction.
+// The ray with id r: its view v, pixel index in the view, and world-space origin and direction (a
+// camera pixel, or row r of the explicit ray table).
+__device__ __forceinline__ Ray table_ray(const WaveArgs &a, int r) {
+    Ray ray;
+    ray.ox = __ldg(a.ray_o + 3 * r);
+    ray.oy = __ldg(a.ray_o + 3 * r + 1);
+    ray.oz = __ldg(a.ray_o + 3 * r + 2);
+    ray.wx = __ldg(a.ray_w + 3 * r);
+    ray.wy = __ldg(a.ray_w + 3 * r + 1);
+    ray.wz = __ldg(a.ray_w + 3 * r + 2);
+    return ray;
+}
+
 __device__ __forceinline__ Ray ray_of(const WaveArgs &a, int r, int &v) {
     v = a.ray_view[r];
+    if (a.ray_o) return table_ray(a, r);
     const ViewDev &V = a.views[v];
     const int pix = r - V.ray_base;
     const int i = pix / V.W, j = pix - i * V.W;

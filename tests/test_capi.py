@@ -57,6 +57,7 @@ int main(void) {
   printf("%zu %zu %zu %zu\\n", sizeof(kns_train_batch), offsetof(kns_train_batch, n_eik),
          offsetof(kns_train_batch, s), offsetof(kns_train_batch, timing));
   printf("%zu %zu\\n", sizeof(kns_train_stats), offsetof(kns_train_stats, ms_fd_backward));
+  printf("%zu %zu %zu\\n", sizeof(kns_pt_opts), offsetof(kns_pt_opts, seed), offsetof(kns_pt_opts, zenith));
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -68,7 +69,8 @@ int main(void) {
             capi.kns_render_opts.refine_steps.offset, capi.kns_render_opts.block_tiles.offset,
             C.sizeof(capi.kns_train_batch),
             capi.kns_train_batch.n_eik.offset, capi.kns_train_batch.s.offset, capi.kns_train_batch.timing.offset,
-            C.sizeof(capi.kns_train_stats), capi.kns_train_stats.ms_fd_backward.offset]
+            C.sizeof(capi.kns_train_stats), capi.kns_train_stats.ms_fd_backward.offset,
+            C.sizeof(capi.kns_pt_opts), capi.kns_pt_opts.seed.offset, capi.kns_pt_opts.zenith.offset]
     assert vals == want
 
 
