@@ -8,12 +8,13 @@ between steps a 512 MiB buffer is overwritten to flush the 126 MB L2 (the grid's
 in L2), outside the events.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16]
-                    [--workload c2|c3s|c3l|c1|train] [--impl kns|reference]
+                    [--workload c2|c3s|c3l|c1|train|pt] [--impl kns|reference]
 
 --workload train times the NeuS-style training step instead (kns_train_step: loss and hand-written
 backward): 2^18 rays x (64 stratified + 32 importance samples) through the 16^3 grid (3 hidden
 layers of width 32), L1 colour + 0.1 x eikonal on 2^16 points; targets are renders of a perturbed
-sphere grid by the render path; metric Mrays/s through the step.
+sphere grid by the render path; metric Mrays/s through the step.  --workload pt times Lambertian path
+tracing (kns_path_trace) of the 16^3 grid: 800x800, 16 paths per pixel, up to 4 traces per path.
 
 Multi-GPU (torchrun): every rank renders its own batch on its own GPU (replicas, no
 collective on the data path); value = rays of all ranks / max-over-ranks time.
@@ -381,6 +382,134 @@ def run_kns(args, rank, world, local_rank):
     ctx.close()
 
 
+# ---------------------------------------------------------------- path tracing
+PT_METRIC = "Mpaths/s Lambertian path tracing (sphere-traced bounces)"
+PT_WORKLOAD = dict(grid="c2", n_cams=1, W=800, H=800, spp=16, max_depth=4, offset=1e-2, max_steps=128, eps=1e-4)
+
+
+def oracle_pt_rate(desc, w, occ, cams, seconds: float, seed: int = 0):
+    """Times the FP64 oracle's path tracer (as it stands) on seeded random pixels of the workload."""
+    import oracle as O
+    wl = PT_WORKLOAD
+    rng = np.random.default_rng(seed)
+    n_pix = wl["n_cams"] * wl["W"] * wl["H"]
+    done, elapsed, batch = 0, 0.0, 64
+    while elapsed < seconds:
+        sel = np.sort(rng.integers(0, n_pix, batch))
+        t0 = time.perf_counter()
+        O.path_trace(desc, w, occ, cams, wl["W"], wl["H"], wl["spp"], wl["max_depth"], wl["max_steps"], wl["eps"],
+                     wl["offset"], seed, (1.0, 1.0, 1.0), (0.5, 0.7, 1.0), sel=sel)
+        dt = time.perf_counter() - t0
+        elapsed += dt
+        done += batch * wl["spp"]
+        if dt < seconds / 8:
+            batch *= 2
+    return done / elapsed / 1e6, done, elapsed, O.num_threads()
+
+
+def run_pt_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2206_10885_gb300 import synth as S
+    wl = PT_WORKLOAD
+    desc = S.config_desc(wl["grid"])
+    w = S.sal_sphere_grid(desc, seed=0)
+    occ = O.occupancy(desc, w)
+    cams = S.orbit_cameras(wl["n_cams"], wl["W"], wl["H"], seed=1)
+    per_step = max(1.0, args.cpu_seconds / max(1, args.steps))
+    for _ in range(args.warmup):
+        oracle_pt_rate(desc, w, occ, cams, 0.2)
+    total, total_s, cores = 0, 0.0, 1
+    for k in range(args.steps):
+        v, n, s, cores = oracle_pt_rate(desc, w, occ, cams, per_step, seed=k + 1)
+        total += n
+        total_s += s
+    value = total / total_s / 1e6
+    n_paths = wl["n_cams"] * wl["W"] * wl["H"] * wl["spp"]
+    line = {"impl": "reference", "metric": PT_METRIC, "value": value, "unit": "Mpaths/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n_paths / (value * 1e6),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "pt (FP64 oracle)", "paths_per_step": n_paths},
+            "cpu_baseline": {"value": value, "unit": "Mpaths/s", "cores": cores, "kind": "oracle",
+                             "sample": "%d paths of seeded random pixels over %d steps (%.1f s)"
+                                       % (total, args.steps, total_s)},
+            "e2e": {"value": value, "unit": "Mpaths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_pt(args, rank, world, local_rank):
+    import torch
+
+    import paper_2206_10885_gb300 as kns
+    from paper_2206_10885_gb300 import build as kbuild
+    from paper_2206_10885_gb300 import synth as S
+    if rank == 0 or not os.path.exists(os.path.join(ROOT, "paper_2206_10885_gb300", "libkns.so")):
+        kbuild.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wl = PT_WORKLOAD
+    desc = S.config_desc(wl["grid"])
+    w = S.sal_sphere_grid(desc, seed=0)
+    cams = S.orbit_cameras(wl["n_cams"], wl["W"], wl["H"], seed=1)
+    ctx = kns.Context(local_rank)
+    grid = kns.Grid.load(ctx, desc, w)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    n_paths = wl["n_cams"] * wl["W"] * wl["H"] * wl["spp"]
+
+    def step(k):
+        return kns.path_trace(ctx, grid, cams, wl["W"], wl["H"], spp=wl["spp"], max_depth=wl["max_depth"], seed=k,
+                              offset=wl["offset"], max_steps=wl["max_steps"], eps=wl["eps"])
+
+    for k in range(max(3, args.warmup)):
+        step(k)
+    torch.cuda.synchronize()
+    st = ctx.render_stats()
+    clocks = ClockSampler(local_rank).start() if rank == 0 else None
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        evs[k][0].record(stream)
+        step(100 + k)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    times = [a.elapsed_time(b) for a, b in evs]
+    clock_info = clocks.stop() if clocks else None
+    total_ms, = max_over_ranks([sum(times)], dev, world)
+    value = whole_job_rate(n_paths, world, args.steps, total_ms)
+    # e2e: cameras from host memory every step, the image read back to pinned host memory
+    host = torch.empty((wl["n_cams"] * wl["W"] * wl["H"], 3), dtype=torch.float32, pin_memory=True)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        host.copy_(step(200 + k), non_blocking=True)
+        stream.synchronize()
+    e2e_s, = max_over_ranks([time.perf_counter() - t0], dev, world)
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            import oracle as O
+            v, n, s_, cores = oracle_pt_rate(desc, w, O.occupancy(desc, w), cams, args.cpu_seconds)
+            cpu = {"value": v, "unit": "Mpaths/s", "cores": cores, "kind": "oracle",
+                   "sample": "%d paths of seeded random pixels (%.1f s of FP64 oracle work)" % (n, s_)}
+        line = {"metric": PT_METRIC, "value": value, "unit": "Mpaths/s", "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "pt: Lambertian path tracing of the 16^3 Kilo-grid (3 hidden x 32), 1 orbit "
+                                       "camera at 800x800, 16 paths per pixel, up to 4 traces per path, sky "
+                                       "gradient; every trace is a wavefront sphere trace (max 128 steps, eps 1e-4)",
+                           "paths_per_step": n_paths, "l2": "flushed between steps (512 MiB write)",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "counts_last_warmup_step": {k: st[k] for k in ("rays", "hits", "samples_fp32")},
+                "cpu_baseline": cpu,
+                "e2e": {"value": whole_job_rate(n_paths, world, args.steps, e2e_s * 1e3), "unit": "Mpaths/s",
+                        "h2d_bytes_per_step": int(cams.nbytes), "d2h_bytes_per_step": int(host.numel() * 4)},
+                "clocks": clock_info, "step_ms_min": min(times), "step_ms_median": statistics.median(times)}
+        print(json.dumps(line), flush=True)
+    grid.free()
+    ctx.close()
+
+
 # ---------------------------------------------------------------- training step
 TRAIN_METRIC = "Mrays/s through the NeuS training step (loss + hand-written backward)"
 
@@ -633,6 +762,8 @@ def main():
     if args.impl == "reference":
         if args.workload == "train":
             run_train_reference(args, rank, world)
+        elif args.workload == "pt":
+            run_pt_reference(args, rank, world)
         else:
             run_reference(args, rank, world)
         return
@@ -643,6 +774,8 @@ def main():
         dist.init_process_group("nccl")
     if args.workload == "train":
         run_train(args, rank, world, local_rank)
+    elif args.workload == "pt":
+        run_pt(args, rank, world, local_rank)
     else:
         run_kns(args, rank, world, local_rank)
     if world > 1:
