@@ -121,8 +121,9 @@ typedef struct kns_render_opts {
     int32_t static_tiles;  /* 1: each block takes a contiguous run of tiles; 2: tiles handed out dynamically */
     int32_t timing;        /* 1: time each kernel class with CUDA events for kns_get_render_stats (adds host work) */
     int32_t block_tiles;   /* FP32 evaluation (also the refinement phase of KNS_BF16): 1 = 128-sample tiles per
-                              256-thread block (block GEMMs); 3 = 256-sample block tiles; 2 = 16-sample tiles per
-                              warp (in-tile stepping, min_active); 0 = default (1) */
+                              256-thread block (block GEMMs); 3 = 256-sample tiles per 256 threads; 4 = 128-sample
+                              tiles per 128 threads; 2 = 16-sample tiles per warp (in-tile stepping, min_active);
+                              0 = default (1) */
 } kns_render_opts;
 
 /* Counters of the last kns_render on a context (kns_get_render_stats). */

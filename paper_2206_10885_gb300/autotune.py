@@ -18,7 +18,7 @@ DEFAULT_CACHE = os.path.join(_HERE, "_tune_cache.json")
 
 # candidate values of each knob (0 would mean the library default)
 SPACE = {
-    "block_tiles": (1, 2, 3),
+    "block_tiles": (1, 2, 3, 4),
     "inner_steps": (1, 4),
     "min_active": (1, 8),
     "static_tiles": (1, 2),
@@ -70,7 +70,7 @@ def candidates(space=None):
     seen = set()
     for vals in itertools.product(*(space[k] for k in keys)):
         cand = dict(zip(keys, vals))
-        if cand.get("block_tiles") in (1, 3):
+        if cand.get("block_tiles") in (1, 3, 4):
             cand.update({k: v for k, v in WARP_ONLY.items() if k in cand})
         key = tuple(sorted(cand.items()))
         if key not in seen:

@@ -779,7 +779,8 @@ struct RenderCfg {
     float eps_coarse = 4e-3f;
     int refine_steps = 2, inner_steps = kRenderInnerSteps, min_active = kRenderMinActive,
         tail_rays = kRenderTailRays, blocks_per_sm = kRenderBlocksPerSM, static_tiles = 1;
-    int block_mode = 1;  // FP32 renders: 0 = 16-sample warp tiles, 1 = 128-sample, 3 = 256-sample block tiles
+    int block_mode = 1;  // 0 = 16-sample warp tiles; block tiles: 1 = 128 samples x 256 threads,
+                         // 3 = 256 x 256, 4 = 128 x 128
 };
 
 kns_status resolve_opts(kns_ctx *ctx, const kns_render_opts *opts, float eps, RenderCfg &c) {
@@ -801,7 +802,7 @@ kns_status resolve_opts(kns_ctx *ctx, const kns_render_opts *opts, float eps, Re
     c.static_tiles = (opts ? knob(opts->static_tiles, kRenderStaticTiles) : kRenderStaticTiles) == 1;
     if (c.inner_steps < 1 || c.inner_steps > 1024 || c.min_active < 1 || c.min_active > 16 || c.tail_rays < -1 ||
         c.blocks_per_sm < 1 || c.blocks_per_sm > 64 || (opts && (opts->static_tiles < 0 || opts->static_tiles > 2)) ||
-        (opts && (opts->block_tiles < 0 || opts->block_tiles > 3)))
+        (opts && (opts->block_tiles < 0 || opts->block_tiles > 4)))
         return set_err(ctx, KNS_ERR_INVALID_ARG, "render tuning field out of range");
     const int bt = opts ? knob(opts->block_tiles, kRenderBlockTiles) : kRenderBlockTiles;
     c.block_mode = bt == 2 ? 0 : bt;  // BF16 renders: the FP32 refinement tiles
@@ -902,7 +903,7 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
         }
         ++ctx->stats.rounds;
         // block tiles: the sort cuts tiles of the size the evaluation kernel takes
-        if (cfg.block_mode == 1) a.btile = 128;
+        if (cfg.block_mode == 1 || cfg.block_mode == 4) a.btile = 128;
         else if (cfg.block_mode == 3) a.btile = 256;
         int tm = timing_begin(ctx, cfg.timing, kTSort, s);
         e = kns::launch_wave_scan(a, cur, s);
@@ -913,8 +914,7 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
         timing_end(ctx, tm, s);
         tm = timing_begin(ctx, cfg.timing, kTEvalF32, s);
         if (e == cudaSuccess)
-            e = kns::launch_wave_eval(grid->shape, grid->view, a, cur, eval_blocks, cfg.block_mode ? 1 : 0,
-                                      ctx->sm_count, s);
+            e = kns::launch_wave_eval(grid->shape, grid->view, a, cur, eval_blocks, cfg.block_mode, ctx->sm_count, s);
         timing_end(ctx, tm, s);
         if (e == cudaSuccess && cfg.bf16) {
             tm = timing_begin(ctx, cfg.timing, kTEvalBF16, s);

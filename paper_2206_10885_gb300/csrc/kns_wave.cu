@@ -171,7 +171,7 @@ __host__ __device__ constexpr int eval_smem_bytes() {
 // is its bias followed by one FMA per input in ascending order and the d row is one sequential FMA
 // chain, the order of the per-thread evaluator, so d does not depend on the tile shape.  Threads
 // 0..127 then advance their sample (hit, miss, or emit to round k+1 with its next cell).
-constexpr int BTHREADS = 256;
+constexpr int BTHREADS = 256;  // default threads per block tile (two per sample in the encoding)
 // shared row stride (floats) of a BT-sample tile: row r starts in bank group r mod 8
 __host__ __device__ constexpr int block_rs(int BT) { return BT + 4; }
 
@@ -206,10 +206,10 @@ __device__ __forceinline__ void encode_split(float *rows, int s, int half, float
 
 // out[o][s] = softplus(b[o] + sum_{k < K} Wt[k][o] in[k][s]) for this thread's W/8 outputs x BT/32
 // samples
-template <int K, int W, int BT>
+template <int K, int W, int BT, int NT>
 __device__ __forceinline__ void block_layer(const float *Wt, const float *b, const float *in, float *out,
                                             float beta, float inv_beta) {
-    constexpr int NO = W / 8, NS = BT / 32, BRS = block_rs(BT);
+    constexpr int NO = W / (NT / 32), NS = BT / 32, BRS = block_rs(BT);
     const int o0 = (threadIdx.x >> 5) * NO, s0 = (threadIdx.x & 31) * NS;
     float acc[NO][NS];
 #pragma unroll
@@ -248,9 +248,9 @@ __device__ __forceinline__ void block_layer(const float *Wt, const float *b, con
                 softplus_f32(acc[i][j4 + 2], beta, inv_beta), softplus_f32(acc[i][j4 + 3], beta, inv_beta));
 }
 
-template <class C, int BT>
-__global__ void __launch_bounds__(BTHREADS) wave_eval_block_kernel(GridView g, WaveArgs a, int cur) {
-    constexpr int BRS = block_rs(BT), NH = BTHREADS / BT;  // NH threads encode one sample
+template <class C, int BT, int NT>
+__global__ void __launch_bounds__(NT) wave_eval_block_kernel(GridView g, WaveArgs a, int cur) {
+    constexpr int BRS = block_rs(BT), NH = NT / BT;  // NH threads encode one sample
     extern __shared__ __align__(128) float dyn[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_tile[4];  // cell, start, len, fresh
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(BTHREADS) wave_eval_block_kernel(GridView g, W
     float *wsm = dyn;
     float *A0 = dyn + C::TSIZE, *P = A0 + C::INP * BRS, *Q = P + C::W * BRS;
     // encoding pad rows stay zero
-    for (int i = tid; i < (C::INP - C::IN) * BRS; i += BTHREADS) A0[C::IN * BRS + i] = 0.f;
+    for (int i = tid; i < (C::INP - C::IN) * BRS; i += NT) A0[C::IN * BRS + i] = 0.f;
     if (tid == 0) mbar_init(&bar, 1);
     __syncthreads();
     const int per = (n_tiles + gridDim.x - 1) / gridDim.x;
@@ -334,12 +334,12 @@ __global__ void __launch_bounds__(BTHREADS) wave_eval_block_kernel(GridView g, W
         } else {
             __syncthreads();
         }
-        block_layer<C::INP, C::W, BT>(wsm + C::tW0, wsm + C::tb0, A0, P, g.beta, g.inv_beta);
+        block_layer<C::INP, C::W, BT, NT>(wsm + C::tW0, wsm + C::tb0, A0, P, g.beta, g.inv_beta);
         float *src = P, *dst = Q;
 #pragma unroll
         for (int l = 1; l < C::H; ++l) {
             __syncthreads();
-            block_layer<C::W, C::W, BT>(wsm + C::tWl(l), wsm + C::tbl(l), src, dst, g.beta, g.inv_beta);
+            block_layer<C::W, C::W, BT, NT>(wsm + C::tWl(l), wsm + C::tbl(l), src, dst, g.beta, g.inv_beta);
             float *tmp = src;
             src = dst;
             dst = tmp;
@@ -658,14 +658,14 @@ int block_eval_per_sm() {
     return by_smem < 1 ? 1 : (by_smem > 3 ? 3 : by_smem);
 }
 
-template <class C, int BT>
+template <class C, int BT, int NT>
 cudaError_t launch_block_eval(const GridView &g, const WaveArgs &a, int cur, int sm_count, cudaStream_t s) {
     constexpr int smem = block_eval_smem_bytes<C, BT>();
     static_assert(smem <= 220 * 1024, "block tile does not fit in shared memory");
-    cudaError_t e =
-        cudaFuncSetAttribute(wave_eval_block_kernel<C, BT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(wave_eval_block_kernel<C, BT, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    wave_eval_block_kernel<C, BT><<<sm_count * block_eval_per_sm<C, BT>(), BTHREADS, smem, s>>>(g, a, cur);
+    wave_eval_block_kernel<C, BT, NT><<<sm_count * block_eval_per_sm<C, BT>(), NT, smem, s>>>(g, a, cur);
     return cudaGetLastError();
 }
 
@@ -674,9 +674,11 @@ cudaError_t launch_wave_eval_cfg(const GridView &g, const WaveArgs &a, int cur, 
                                  int sm_count, cudaStream_t s) {
     cudaError_t e;
     if (block_tiles) {
-        // the sort's tile size decides the kernel: 256- or 128-sample block tiles
-        e = a.btile == 256 ? launch_block_eval<C, 256>(g, a, cur, sm_count, s)
-                           : launch_block_eval<C, 128>(g, a, cur, sm_count, s);
+        // the sort's tile size decides the kernel: 256- or 128-sample block tiles, the latter with 256
+        // threads (two per sample in the encoding) or 128 (block_tiles == 4: one thread per sample)
+        e = a.btile == 256 ? launch_block_eval<C, 256, 256>(g, a, cur, sm_count, s)
+            : block_tiles == 4 ? launch_block_eval<C, 128, 128>(g, a, cur, sm_count, s)
+                               : launch_block_eval<C, 128, 256>(g, a, cur, sm_count, s);
         if (e != cudaSuccess) return e;
     } else {
         constexpr int smem = eval_smem_bytes<C>();
