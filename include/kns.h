@@ -116,7 +116,7 @@ typedef struct kns_render_opts {
     /* tuning (0 = default) */
     int32_t inner_steps;   /* sphere steps a tile may take per round while its rays stay in its cells (1..1024) */
     int32_t min_active;    /* a 16-ray warp tile with fewer live rays hands them to the next round (1..16) */
-    int32_t tail_rays;     /* a round with at most this many rays is finished one thread per ray (>= 0; -1: never) */
+    int32_t tail_rays;     /* a round with at most this many rays is finished one warp per ray (>= 0; -1: never) */
     int32_t blocks_per_sm; /* evaluation blocks (one warp each) launched per SM (1..64) */
     int32_t static_tiles;  /* 1: each block takes a contiguous run of tiles; 2: tiles handed out dynamically */
     int32_t timing;        /* 1: time each kernel class with CUDA events for kns_get_render_stats (adds host work) */

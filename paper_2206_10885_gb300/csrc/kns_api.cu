@@ -326,7 +326,7 @@ constexpr int kRenderBlockTiles = 1;        // FP32 renders use block tiles by d
 // Defaults picked by the autotuner on the 16^3 / width-32 grid at 8 x 800x800.
 constexpr int kRenderInnerSteps = 4;
 constexpr int kRenderMinActive = 8;
-constexpr int kRenderTailRays = 65536;  // rounds this small finish one thread per ray
+constexpr int kRenderTailRays = 65536;  // rounds this small finish one warp per ray
 constexpr int kRenderBlocksPerSM = 16;
 constexpr int kRenderStaticTiles = 2;
 

@@ -19,7 +19,7 @@ struct WaveCtrl {
     int n_hits;     // rays that converged (queued for shading)
     int n_tiles;    // block tiles of the current round
     int next_tile;     // dynamic tile counter of the current round (FP32 tiles)
-    int tail;          // 1: the current round is small enough to finish one thread per ray
+    int tail;          // 1: the current round is small enough to finish one warp per ray
     int n_tiles_fine;  // tiles of FP32 samples (keys < NC); BF16 tiles follow them
     int next_tile_bf;  // dynamic tile counter of the BF16 tiles
     unsigned long long samples_f32;   // SDF evaluations in FP32 tiles and the per-thread tail
@@ -53,7 +53,7 @@ struct WaveArgs {
     int btile;            // samples per FP32 tile (cell-sorted samples are cut into such tiles)
     int btile_bf;         // samples per BF16 tile (keys >= NC)
     int inner_steps;      // sphere steps a tile may take in one round while its rays stay in its cells
-    int tail_max;         // a round with at most this many rays is finished one thread per ray
+    int tail_max;         // a round with at most this many rays is finished one warp per ray
     int min_active;       // warp tiles with fewer live rays hand them to the next round
     int static_tiles;     // 1: contiguous runs of tiles per block (weight reuse); 0: dynamic
     int *status;          // context status word (kns_status of a device-side failure, 0 = fine)

@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) wave_scan_kernel(WaveArgs a, int
         a.ctrl->next_tile_bf = 0;
     }
     const int n_live = a.ctrl->n_live[cur];
-    // a small round is finished one thread per ray (still sorted, so a warp's rays share cells)
+    // a small round is finished one warp per ray (in cell-sorted order)
     if (threadIdx.x == 0) a.ctrl->tail = n_live <= a.tail_max ? 1 : 0;
     if (n_live == 0) {
         if (threadIdx.x == 0) {

@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(128) wave_gen_kernel(GridView g, WaveArgs a) {
 // sample lies in the same cell keeps stepping inside the tile (up to inner_steps evaluations this
 // round, while at least min_active rays remain); the others are emitted to round k+1 with their
 // next cell, converge (hit list) or terminate (miss written).  A round with few rays (tail) is
-// finished one thread per ray by wave_tail_kernel.
+// finished one warp per ray by wave_tail_warp_kernel.
 template <class C>
 __host__ __device__ constexpr int eval_smem_bytes() {
     return (C::TSIZE + TILE * (act_stride(C::INP) + 2 * act_stride(C::W))) * (int)sizeof(float);
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(NT) wave_eval_block_kernel(GridView g, WaveArg
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_tile[4];  // cell, start, len, fresh
     __shared__ float s_x[3][BT];
-    if (a.ctrl->tail) return;  // finished one thread per ray by wave_tail_kernel
+    if (a.ctrl->tail) return;  // finished one warp per ray by wave_tail_warp_kernel
     const int n_tiles = a.ctrl->n_tiles_fine;
     if (n_tiles <= 0) return;
     const int tid = threadIdx.x, nxt = cur ^ 1;
@@ -400,64 +400,120 @@ __global__ void __launch_bounds__(NT) wave_eval_block_kernel(GridView g, WaveArg
     }
 }
 
-// Tail: one thread runs one ray to its end with the per-thread evaluator (weights via L1).
-template <class C>
-__device__ __noinline__ void finish_ray_f32(const GridView &g, const WaveArgs &a, int r, int cell, bool &hit_out) {
-    int cam;
-    const Ray ray = ray_of(a, r, cam);
-    float t0, tf;
-    clip_box(g, ray, t0, tf);
-    float t = a.t_ray[r];
-    int steps = a.steps_ray[r];
-    const bool cycles = a.t_hist != nullptr;  // the tail runs in FP32 renders only
-    float4 hist = cycles ? a.t_hist[r] : no_history();
-    hit_out = false;
-    for (;;) {
-        const float d = sdf_trace_f32<C>(g.w + (int64_t)cell * g.cell_stride, fmaf(t, ray.wx, ray.ox),
-                                         fmaf(t, ray.wy, ray.oy), fmaf(t, ray.wz, ray.oz), g.beta, g.inv_beta);
-        ++steps;
-        atomicAdd(&a.ctrl->samples_f32, 1ull);
-        if (fabsf(d) < a.eps) {
-            a.cell_ray[r] = cell;
-            a.t_ray[r] = t;
-            a.steps_ray[r] = steps;
-            hit_out = true;
-            return;
-        }
-        const float t_eval = t;
-        t += d;
-        if (t > tf || t < t0 || steps >= a.max_steps) break;
-        cell = advance_ray(g, ray, t, tf);
-        if (cell < 0) break;
-        if (cycles && cycle_step(hist, t_eval, t)) {
-            steps = a.max_steps;
-            break;
-        }
-    }
-    write_miss(a, r, steps);
+// Tail: a warp runs one ray to its end; lane o computes output unit o (and o + 32 for width 64) of
+// each layer from the cell's k-major trace weights, which the warp reads as coalesced 128-byte rows,
+// with the layer inputs broadcast by shuffles.  Every output is its bias followed by one FMA per
+// input in ascending order and every lane forms the d row as one sequential chain, the order of the
+// tile evaluators, so d is bit-identical to theirs.  (One thread per ray would have the lanes of a
+// warp read 32 different cells' weights.)
+
+// input k of the encoding (Eq. 1): x, y, z, then per frequency sin x, sin y, sin z, cos x, cos y, cos z
+__device__ __forceinline__ float encoding_entry(int k, float px, float py, float pz) {
+    if (k < 3) return k == 0 ? px : (k == 1 ? py : pz);
+    const int f = (k - 3) / 6, c = (k - 3) % 6;
+    const float p = (c % 3) == 0 ? px : ((c % 3) == 1 ? py : pz);
+    float sn, cs;
+    sincospif((float)(1 << f) * p, &sn, &cs);
+    return c < 3 ? sn : cs;
 }
 
-// A tail round: one thread per ray, to the end.  Rays are taken in cell-sorted order so that the
-// lanes of a warp mostly share a cell (uniform weight loads); a ray's cell is its sort key.
 template <class C>
-__global__ void __launch_bounds__(128, 4) wave_tail_kernel(GridView g, WaveArgs a, int cur) {
+__device__ __forceinline__ float warp_sdf_trace(const float *__restrict__ wt, float px, float py, float pz,
+                                                int lane, float beta, float inv_beta) {
+    constexpr int NPL = C::W / 32, NIN = (C::INP + 31) / 32;
+    float in[NIN];  // lane k holds inputs k, k + 32 (zero past IN)
+#pragma unroll
+    for (int j = 0; j < NIN; ++j) {
+        const int k = lane + 32 * j;
+        in[j] = k < C::IN ? encoding_entry(k, px, py, pz) : 0.f;
+    }
+    float h[NPL], g[NPL];
+#pragma unroll
+    for (int u = 0; u < NPL; ++u) {
+        const int o = lane + 32 * u;
+        float acc = __ldg(wt + C::tb0 + o);
+#pragma unroll 4
+        for (int k = 0; k < C::INP; ++k)
+            acc = fmaf(__ldg(wt + C::tW0 + k * C::W + o), __shfl_sync(FULL, in[k >> 5], k & 31), acc);
+        h[u] = softplus_f32(acc, beta, inv_beta);
+    }
+#pragma unroll
+    for (int l = 1; l < C::H; ++l) {
+#pragma unroll
+        for (int u = 0; u < NPL; ++u) {
+            const int o = lane + 32 * u;
+            float acc = __ldg(wt + C::tbl(l) + o);
+#pragma unroll 4
+            for (int k = 0; k < C::W; ++k)
+                acc = fmaf(__ldg(wt + C::tWl(l) + k * C::W + o), __shfl_sync(FULL, h[k >> 5], k & 31), acc);
+            g[u] = softplus_f32(acc, beta, inv_beta);
+        }
+#pragma unroll
+        for (int u = 0; u < NPL; ++u) h[u] = g[u];
+    }
+    float d = __ldg(wt + C::tbL);
+#pragma unroll 4
+    for (int k = 0; k < C::W; ++k) d = fmaf(__ldg(wt + C::tdL + k), __shfl_sync(FULL, h[k >> 5], k & 31), d);
+    return d;
+}
+
+// A tail round: one warp per ray, to the end.  Rays come in cell-sorted order (the cell of a ray's
+// position is its sort key).
+template <class C>
+__global__ void __launch_bounds__(256) wave_tail_warp_kernel(GridView g, WaveArgs a, int cur) {
     if (!a.ctrl->tail) return;
     const int n = a.ctrl->n_live[cur];
-    const int bound = (n + 31) & ~31;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < bound; q += gridDim.x * blockDim.x) {
-        bool hit = false;
-        int r = 0;
-        if (q < n) {
-            r = a.sorted[q];
-            int lo = 0, hi = a.NC;  // the key with off[key] <= q < off[key+1]
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (__ldg(a.off + mid) <= q) lo = mid; else hi = mid;
-            }
-            finish_ray_f32<C>(g, a, r, lo, hit);
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < n; q += warps) {
+        const int r = a.sorted[q];
+        int lo = 0, hi = a.NC;  // the key with off[key] <= q < off[key+1]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(a.off + mid) <= q) lo = mid; else hi = mid;
         }
-        const int hp = warp_append(&a.ctrl->n_hits, hit);
-        if (hit) a.hits[hp] = r;
+        int cell = lo;
+        int cam;
+        const Ray ray = ray_of(a, r, cam);
+        float t0, tf;
+        clip_box(g, ray, t0, tf);
+        float t = a.t_ray[r];
+        int steps = a.steps_ray[r];
+        const bool cycles = a.t_hist != nullptr;  // the tail runs in FP32 renders only
+        float4 hist = cycles ? a.t_hist[r] : no_history();
+        bool hit = false;
+        int nsamples = 0;
+        for (;;) {
+            const float d = warp_sdf_trace<C>(a.wt + (int64_t)cell * a.wt_stride, fmaf(t, ray.wx, ray.ox),
+                                              fmaf(t, ray.wy, ray.oy), fmaf(t, ray.wz, ray.oz), lane, g.beta,
+                                              g.inv_beta);
+            ++steps;
+            ++nsamples;
+            if (fabsf(d) < a.eps) {
+                hit = true;
+                break;
+            }
+            const float t_eval = t;
+            t += d;
+            if (t > tf || t < t0 || steps >= a.max_steps) break;
+            cell = advance_ray(g, ray, t, tf);
+            if (cell < 0) break;
+            if (cycles && cycle_step(hist, t_eval, t)) {
+                steps = a.max_steps;
+                break;
+            }
+        }
+        if (lane == 0) {
+            atomicAdd(&a.ctrl->samples_f32, (unsigned long long)nsamples);
+            if (hit) {
+                a.cell_ray[r] = cell;
+                a.t_ray[r] = t;
+                a.steps_ray[r] = steps;
+                a.hits[atomicAdd(&a.ctrl->n_hits, 1)] = r;
+            } else {
+                write_miss(a, r, steps);
+            }
+        }
     }
 }
 
@@ -465,7 +521,7 @@ template <class C>
 __global__ void __launch_bounds__(32) wave_eval_kernel(GridView g, WaveArgs a, int cur) {
     extern __shared__ __align__(128) float dyn[];
     __shared__ __align__(8) uint64_t bar;
-    if (a.ctrl->tail) return;  // finished one thread per ray by wave_tail_kernel
+    if (a.ctrl->tail) return;  // finished one warp per ray by wave_tail_warp_kernel
     const int lane = threadIdx.x;
     const int nxt = cur ^ 1;
     float *wsm = dyn;
@@ -688,7 +744,7 @@ cudaError_t launch_wave_eval_cfg(const GridView &g, const WaveArgs &a, int cur, 
         wave_eval_kernel<C><<<blocks, 32, smem, s>>>(g, a, cur);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    wave_tail_kernel<C><<<blocks, 128, 0, s>>>(g, a, cur);
+    wave_tail_warp_kernel<C><<<sm_count * 8, 256, 0, s>>>(g, a, cur);
     return cudaGetLastError();
 }
 template <class C>
