@@ -38,6 +38,9 @@ cudaError_t launch_wave_eval(const Shape &sh, const GridView &g, const WaveArgs 
         return launch_wave_eval_cfg<decltype(c)>(g, a, cur, blocks, block_tiles, sm_count, s);
     });
 }
+cudaError_t launch_shade_block(const Shape &sh, const GridView &g, const WaveArgs &a, int sm_count, cudaStream_t s) {
+    return dispatch(sh, [&](auto c) { return launch_shade_block_cfg<decltype(c)>(g, a, sm_count, s); });
+}
 cudaError_t launch_wave_shade(const Shape &sh, const GridView &g, const WaveArgs &a, int blocks, cudaStream_t s) {
     return dispatch(sh, [&](auto c) { return launch_wave_shade_cfg<decltype(c)>(g, a, blocks, s); });
 }

@@ -156,4 +156,78 @@ cudaError_t launch_wave_scatter(const WaveArgs &a, int cur, int blocks, cudaStre
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- hits by cell (shading tiles)
+// After the last round: the hit list is counting-sorted by the cell of each hit into `sorted`, with
+// off[c] / tile_off[c] (tiles of HIT_TILE hits) and the tile count in ctrl->n_tiles.  Uses the wave's
+// count[0], fill[0], off, tile_off and sorted buffers, which the rounds no longer need.
+constexpr int HIT_TILE = 128;
+
+__global__ void __launch_bounds__(256) wave_hit_count_kernel(WaveArgs a) {
+    const int n = a.ctrl->n_hits;
+    const int bound = (n + 31) & ~31;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < bound; i += gridDim.x * blockDim.x) {
+        const bool pred = i < n;
+        const int c = pred ? a.cell_ray[a.hits[i]] : 0;
+        warp_count_cells(a.count[0], pred, c);
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) wave_hit_scan_kernel(WaveArgs a) {
+    __shared__ int wa[32], wb[32];
+    const int NC = a.NC;
+    const int per = (NC + SCAN_THREADS - 1) / SCAN_THREADS;
+    const int c0 = threadIdx.x * per, c1 = min(NC, c0 + per);
+    int sum = 0, tiles = 0;
+    for (int c = c0; c < c1; ++c) {
+        const int n = a.count[0][c];
+        sum += n;
+        tiles += (n + HIT_TILE - 1) / HIT_TILE;
+    }
+    int incl_s = sum, incl_t = tiles;
+    block_scan2(incl_s, incl_t, wa, wb);
+    int run_s = incl_s - sum, run_t = incl_t - tiles;
+    for (int c = c0; c < c1; ++c) {
+        const int n = a.count[0][c];
+        a.off[c] = run_s;
+        a.tile_off[c] = run_t;
+        a.fill[0][c] = 0;
+        run_s += n;
+        run_t += (n + HIT_TILE - 1) / HIT_TILE;
+    }
+    if (threadIdx.x == SCAN_THREADS - 1) {
+        a.off[NC] = incl_s;
+        a.tile_off[NC] = incl_t;
+        a.ctrl->n_tiles = incl_t;
+    }
+}
+
+__global__ void __launch_bounds__(256) wave_hit_scatter_kernel(WaveArgs a) {
+    const int n = a.ctrl->n_hits;
+    const int lane = threadIdx.x & 31;
+    const int bound = (n + 31) & ~31;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < bound; i += gridDim.x * blockDim.x) {
+        const bool pred = i < n;
+        const int r = pred ? a.hits[i] : 0;
+        const int c = pred ? a.cell_ray[r] : 0;
+        const unsigned m = __ballot_sync(FULL, pred);
+        if (pred) {
+            const unsigned grp = __match_any_sync(m, c);
+            const int leader = __ffs(grp) - 1;
+            int base = 0;
+            if (lane == leader) base = atomicAdd(a.fill[0] + c, __popc(grp));
+            base = __shfl_sync(grp, base, leader);
+            a.sorted[a.off[c] + base + __popc(grp & lanemask_lt())] = r;
+        }
+    }
+}
+
+cudaError_t launch_hit_sort(const WaveArgs &a, int sm_count, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(a.count[0], 0, sizeof(int) * (a.NC + 1), s);
+    if (e != cudaSuccess) return e;
+    wave_hit_count_kernel<<<sm_count * 4, 256, 0, s>>>(a);
+    wave_hit_scan_kernel<<<1, SCAN_THREADS, 0, s>>>(a);
+    wave_hit_scatter_kernel<<<sm_count * 4, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace kns
