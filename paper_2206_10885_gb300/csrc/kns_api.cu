@@ -924,12 +924,9 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
     }
     if (e == cudaSuccess) {
         const int tm = timing_begin(ctx, cfg.timing, kTShade, s);
-        if (grid->desc.sdf_width == 32) {  // hits sorted by cell, shaded on block tiles
-            e = kns::launch_hit_sort(a, ctx->sm_count, s);
-            if (e == cudaSuccess) e = kns::launch_shade_block(grid->shape, grid->view, a, ctx->sm_count, s);
-        } else {
-            e = kns::launch_wave_shade(grid->shape, grid->view, a, ctx->sm_count * 8, s);
-        }
+        // hits sorted by cell, shaded on block tiles
+        e = kns::launch_hit_sort(a, kns::shade_hit_tile(grid->desc.sdf_width), ctx->sm_count, s);
+        if (e == cudaSuccess) e = kns::launch_shade_block(grid->shape, grid->view, a, ctx->sm_count, s);
         timing_end(ctx, tm, s);
     }
     if (e != cudaSuccess) return cuda_err(ctx, e, "render launch");
@@ -1330,12 +1327,9 @@ extern "C" kns_status kns_render_noalloc(kns_ctx *ctx, const kns_grid *grid, con
         if (e == cudaSuccess) e = kns::launch_wave_eval(grid->shape, grid->view, a, cur, eval_blocks, 0, ctx->sm_count, s);
     }
     if (e == cudaSuccess) {
-        if (grid->desc.sdf_width == 32) {  // the same shading as kns_render (hits sorted by cell, block tiles)
-            e = kns::launch_hit_sort(a, ctx->sm_count, s);
-            if (e == cudaSuccess) e = kns::launch_shade_block(grid->shape, grid->view, a, ctx->sm_count, s);
-        } else {
-            e = kns::launch_wave_shade(grid->shape, grid->view, a, ctx->sm_count * 8, s);
-        }
+        // the same shading as kns_render (hits sorted by cell, block tiles)
+        e = kns::launch_hit_sort(a, kns::shade_hit_tile(grid->desc.sdf_width), ctx->sm_count, s);
+        if (e == cudaSuccess) e = kns::launch_shade_block(grid->shape, grid->view, a, ctx->sm_count, s);
     }
     if (e != cudaSuccess) return cuda_err(ctx, e, "render launch");
     return KNS_OK;

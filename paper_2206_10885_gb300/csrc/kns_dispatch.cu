@@ -41,9 +41,6 @@ cudaError_t launch_wave_eval(const Shape &sh, const GridView &g, const WaveArgs 
 cudaError_t launch_shade_block(const Shape &sh, const GridView &g, const WaveArgs &a, int sm_count, cudaStream_t s) {
     return dispatch(sh, [&](auto c) { return launch_shade_block_cfg<decltype(c)>(g, a, sm_count, s); });
 }
-cudaError_t launch_wave_shade(const Shape &sh, const GridView &g, const WaveArgs &a, int blocks, cudaStream_t s) {
-    return dispatch(sh, [&](auto c) { return launch_wave_shade_cfg<decltype(c)>(g, a, blocks, s); });
-}
 
 cudaError_t launch_wave_eval_bf16(const Shape &sh, const GridView &g, const WaveArgs &a, int cur, int blocks,
                                   cudaStream_t s) {

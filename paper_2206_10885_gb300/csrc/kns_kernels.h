@@ -78,8 +78,6 @@ template <class C>
 cudaError_t launch_wave_eval_cfg(const GridView &g, const WaveArgs &a, int cur, int blocks, int block_tiles,
                                  int sm_count, cudaStream_t s);
 template <class C>
-cudaError_t launch_wave_shade_cfg(const GridView &g, const WaveArgs &a, int blocks, cudaStream_t s);
-template <class C>
 cudaError_t launch_shade_block_cfg(const GridView &g, const WaveArgs &a, int sm_count, cudaStream_t s);
 template <class C>
 cudaError_t launch_wave_eval_bf16_cfg(const GridView &g, const WaveArgs &a, int cur, int blocks, cudaStream_t s);
@@ -97,12 +95,12 @@ int bf16_cell_bytes(const Shape &sh, int *k0p);
 cudaError_t launch_wave_gen(const Shape &sh, const GridView &g, const WaveArgs &a, cudaStream_t s);
 cudaError_t launch_wave_eval(const Shape &sh, const GridView &g, const WaveArgs &a, int cur, int blocks,
                              int block_tiles, int sm_count, cudaStream_t s);
-cudaError_t launch_wave_shade(const Shape &sh, const GridView &g, const WaveArgs &a, int blocks, cudaStream_t s);
 cudaError_t launch_wave_eval_bf16(const Shape &sh, const GridView &g, const WaveArgs &a, int cur, int blocks,
                                   cudaStream_t s);
 cudaError_t launch_wave_scan(const WaveArgs &a, int cur, cudaStream_t s);
-cudaError_t launch_hit_sort(const WaveArgs &a, int sm_count, cudaStream_t s);
+cudaError_t launch_hit_sort(const WaveArgs &a, int tile, int sm_count, cudaStream_t s);  // tile: shade_hit_tile
 cudaError_t launch_shade_block(const Shape &sh, const GridView &g, const WaveArgs &a, int sm_count, cudaStream_t s);
+inline int shade_hit_tile(int sdf_width) { return 4096 / sdf_width; }  // hits per shading tile
 cudaError_t launch_coarse_occupancy(const uint32_t *occ, int res, uint32_t *coarse, cudaStream_t s);
 cudaError_t launch_wave_scatter(const WaveArgs &a, int cur, int blocks, cudaStream_t s);
 

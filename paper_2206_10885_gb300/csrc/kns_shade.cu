@@ -2,28 +2,29 @@
 // analytic input gradient as the normal, the colour MLP of Eq. 3 at the hit).
 // kns:instantiate (compiled once per grid configuration)
 //
-// The hits of a render are counting-sorted by cell and cut into tiles of up to 128 same-cell hits.
-// A block of 256 threads stages the cell's weights in shared memory (forward layers k-major, the
-// layers the gradient runs back through row-major) and evaluates the tile as block GEMMs on rows of
-// 128 hits (row stride 132 floats): thread (warp w, lane l) owns 4 output units x 4 hits.  Forward:
+// The hits of a render are counting-sorted by cell and cut into tiles of 4096 / W same-cell hits (128
+// for width 32, 64 for width 64).  A block of 256 threads stages the cell's weights in shared memory
+// (forward layers k-major, the layers the gradient runs back through row-major) and evaluates the
+// tile as block GEMMs on rows of hits (row stride tile + 4 floats): thread (warp w, lane l) owns W/8
+// output units x tile/32 hits.  Forward:
 // A_l = softplus(W_l A_{l-1} + b_l), the 16 outputs [d, z].  Reverse mode in place: A_H becomes
 // D_H = w_d . softplus'(A_H), each A_l becomes D_l = (W_l^T D_{l+1}) . softplus'(A_l), and the
 // encoding rows become W_0^T D_1; the chain rule through the encoding (d sin(fx) = f cos(fx) dx,
 // d cos(fx) = -f sin(fx) dx) gives grad d, normalised to n.  The colour MLP then runs on
-// u = [z, n, gamma(v), x].  Width-32 grids; the per-thread shade in kns_wave.cu serves width 64.
+// u = [z, n, gamma(v), x].
 #include "kns_wave.cuh"
 
 namespace kns {
 namespace {
 
-constexpr int ST = 128;        // hits per tile
-constexpr int SRS = ST + 4;    // shared row stride (floats)
 constexpr int STHREADS = 256;
 
-// shared layout of one width-32 cell (floats, 16-byte aligned blocks)
+// shared layout of one cell and of a tile (floats, 16-byte aligned blocks)
 template <class C>
 struct SL {
-    static constexpr int W = 32, R0 = (C::INP + 31) / 32 * 32;  // encoding rows, padded to 32
+    static constexpr int W = C::W, R0 = (C::INP + 31) / 32 * 32;  // encoding rows, padded to 32
+    static constexpr int ST = 4096 / W, SRS = ST + 4;              // hits per tile (shade_hit_tile), row stride
+    static constexpr int OPT = W / 8, SPT = ST / 32;               // outputs x hits per thread
     // forward, k-major
     static constexpr int T0 = 0, b0 = T0 + C::INP * W, HL = W * W + W;
     __host__ __device__ static constexpr int Tl(int l) { return b0 + W + (l - 1) * HL; }
@@ -45,7 +46,7 @@ struct SL {
 template <class C>
 __device__ int src_of(int j) {
     using L = SL<C>;
-    constexpr int W = 32;
+    constexpr int W = C::W;
     if (j < L::b0) {
         const int k = j / W, o = j % W;
         return C::oW0 + o * C::INP + k;
@@ -87,55 +88,93 @@ __device__ __forceinline__ float dsoftplus_from_act(float a, float beta) {
     return x < 1e-2f ? x * (1.f - x * (0.5f - x * (1.f / 6.f))) : 1.f - __expf(-x);
 }
 
-__device__ __forceinline__ int o0_of() { return (threadIdx.x >> 5) * 4; }
-__device__ __forceinline__ int s0_of() { return (threadIdx.x & 31) * 4; }
+template <class L>
+__device__ __forceinline__ int o0_of() { return (threadIdx.x >> 5) * L::OPT; }
+template <class L>
+__device__ __forceinline__ int s0_of() { return (threadIdx.x & 31) * L::SPT; }
+
+template <int N>
+__device__ __forceinline__ void load_n(const float *p, float (&v)[N]) {
+    if constexpr (N == 4) {
+        const float4 x = *reinterpret_cast<const float4 *>(p);
+        v[0] = x.x;
+        v[1] = x.y;
+        v[2] = x.z;
+        v[3] = x.w;
+    } else if constexpr (N == 2) {
+        const float2 x = *reinterpret_cast<const float2 *>(p);
+        v[0] = x.x;
+        v[1] = x.y;
+    } else {
+#pragma unroll
+        for (int i = 0; i < N; i += 4) {
+            const float4 x = *reinterpret_cast<const float4 *>(p + i);
+            v[i] = x.x;
+            v[i + 1] = x.y;
+            v[i + 2] = x.z;
+            v[i + 3] = x.w;
+        }
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void store_n(float *p, const float (&v)[N]) {
+    if constexpr (N == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    }
+}
 
 // acc[i][j] += sum_{k < K} Wk[k WS + o0 + i] X[k SRS + s0 + j]
-template <int K, int WS>
-__device__ __forceinline__ void mm(const float *Wk, const float *X, float (&acc)[4][4]) {
-    const float *w = Wk + o0_of();
-    const float *x = X + s0_of();
+template <class L, int K, int WS>
+__device__ __forceinline__ void mm(const float *Wk, const float *X, float (&acc)[L::OPT][L::SPT]) {
+    const float *w = Wk + o0_of<L>();
+    const float *x = X + s0_of<L>();
 #pragma unroll 4
     for (int k = 0; k < K; ++k) {
-        const float4 wv = *reinterpret_cast<const float4 *>(w + k * WS);
-        const float4 xv = *reinterpret_cast<const float4 *>(x + k * SRS);
-        const float wa[4] = {wv.x, wv.y, wv.z, wv.w}, xa[4] = {xv.x, xv.y, xv.z, xv.w};
+        float wa[L::OPT], xa[L::SPT];
+        load_n<L::OPT>(w + k * WS, wa);
+        load_n<L::SPT>(x + k * L::SRS, xa);
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < L::OPT; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(wa[i], xa[j], acc[i][j]);
+            for (int j = 0; j < L::SPT; ++j) acc[i][j] = fmaf(wa[i], xa[j], acc[i][j]);
     }
 }
 
-__device__ __forceinline__ void bias4(const float *b, float (&acc)[4][4]) {
+template <class L>
+__device__ __forceinline__ void bias_n(const float *b, float (&acc)[L::OPT][L::SPT]) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < L::OPT; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = b[o0_of() + i];
+        for (int j = 0; j < L::SPT; ++j) acc[i][j] = b[o0_of<L>() + i];
 }
 
-__device__ __forceinline__ void put4(float *rows, int row0, const float (&v)[4][4]) {
+template <class L>
+__device__ __forceinline__ void zero_n(float (&acc)[L::OPT][L::SPT]) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-        *reinterpret_cast<float4 *>(rows + (row0 + o0_of() + i) * SRS + s0_of()) =
-            make_float4(v[i][0], v[i][1], v[i][2], v[i][3]);
+    for (int i = 0; i < L::OPT; ++i)
+#pragma unroll
+        for (int j = 0; j < L::SPT; ++j) acc[i][j] = 0.f;
 }
 
-__device__ __forceinline__ void get4(const float *rows, int row0, float (&v)[4][4]) {
+template <class L>
+__device__ __forceinline__ void put_n(float *rows, int row0, const float (&v)[L::OPT][L::SPT]) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float4 x = *reinterpret_cast<const float4 *>(rows + (row0 + o0_of() + i) * SRS + s0_of());
-        v[i][0] = x.x;
-        v[i][1] = x.y;
-        v[i][2] = x.z;
-        v[i][3] = x.w;
-    }
+    for (int i = 0; i < L::OPT; ++i) store_n<L::SPT>(rows + (row0 + o0_of<L>() + i) * L::SRS + s0_of<L>(), v[i]);
+}
+
+template <class L>
+__device__ __forceinline__ void get_n(const float *rows, int row0, float (&v)[L::OPT][L::SPT]) {
+#pragma unroll
+    for (int i = 0; i < L::OPT; ++i) load_n<L::SPT>(rows + (row0 + o0_of<L>() + i) * L::SRS + s0_of<L>(), v[i]);
 }
 
 template <class C>
 __global__ void __launch_bounds__(STHREADS) shade_block_kernel(GridView g, WaveArgs a) {
     using L = SL<C>;
-    constexpr int W = 32;
+    constexpr int W = C::W, ST = L::ST, SRS = L::SRS, OPT = L::OPT, SPT = L::SPT;
     extern __shared__ __align__(16) float sdyn[];
     float *sw = sdyn;
     float *rows = sdyn + L::END;
@@ -194,8 +233,8 @@ __global__ void __launch_bounds__(STHREADS) shade_block_kernel(GridView g, WaveA
             s_r[tid] = r;
         }
         __syncthreads();
-        {  // encoding (Eq. 1), two threads per hit: x and frequencies [0, L/2) | [L/2, L)
-            const int s = tid & (ST - 1), half = tid >> 7;
+        if (tid < 2 * ST) {  // encoding (Eq. 1), two threads per hit: x and frequencies [0, L/2) | [L/2, L)
+            const int s = tid % ST, half = tid / ST;
             const float p[3] = {s_x[0][s], s_x[1][s], s_x[2][s]};
             if (half == 0)
                 for (int k = 0; k < 3; ++k) rows[(L::A0 + k) * SRS + s] = p[k];
@@ -213,32 +252,32 @@ __global__ void __launch_bounds__(STHREADS) shade_block_kernel(GridView g, WaveA
             }
         }
         __syncthreads();
-        float acc[4][4];
+        float acc[OPT][SPT];
         // forward
-        bias4(sw + L::b0, acc);
-        mm<C::INP, W>(sw + L::T0, rows + L::A0 * SRS, acc);
+        bias_n<L>(sw + L::b0, acc);
+        mm<L, C::INP, W>(sw + L::T0, rows + L::A0 * SRS, acc);
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < OPT; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = softplus_f32(acc[i][j], g.beta, g.inv_beta);
-        put4(rows, L::A(1), acc);
+            for (int j = 0; j < SPT; ++j) acc[i][j] = softplus_f32(acc[i][j], g.beta, g.inv_beta);
+        put_n<L>(rows, L::A(1), acc);
 #pragma unroll
         for (int l = 1; l < C::H; ++l) {
             __syncthreads();
-            bias4(sw + L::bl(l), acc);
-            mm<W, W>(sw + L::Tl(l), rows + L::A(l) * SRS, acc);
+            bias_n<L>(sw + L::bl(l), acc);
+            mm<L, W, W>(sw + L::Tl(l), rows + L::A(l) * SRS, acc);
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < OPT; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = softplus_f32(acc[i][j], g.beta, g.inv_beta);
-            put4(rows, L::A(l + 1), acc);
+                for (int j = 0; j < SPT; ++j) acc[i][j] = softplus_f32(acc[i][j], g.beta, g.inv_beta);
+            put_n<L>(rows, L::A(l + 1), acc);
         }
         __syncthreads();
         {  // outputs [d, z]: 16 rows from Ud (z lands in U rows 0..14); warp w owns outputs 2w, 2w+1
-            const int o0 = (tid >> 5) * 2, s0 = s0_of();
-            float out[2][4];
+            const int o0 = (tid >> 5) * 2, s0 = s0_of<L>();
+            float out[2][SPT];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < SPT; ++j) {
                 out[0][j] = sw[L::bo + o0];
                 out[1][j] = sw[L::bo + o0 + 1];
             }
@@ -246,57 +285,49 @@ __global__ void __launch_bounds__(STHREADS) shade_block_kernel(GridView g, WaveA
 #pragma unroll 4
             for (int k = 0; k < W; ++k) {
                 const float2 wv = *reinterpret_cast<const float2 *>(sw + L::To + k * 16 + o0);
-                const float4 xv = *reinterpret_cast<const float4 *>(X + k * SRS);
-                const float xa[4] = {xv.x, xv.y, xv.z, xv.w};
+                float xa[SPT];
+                load_n<SPT>(X + k * SRS, xa);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < SPT; ++j) {
                     out[0][j] = fmaf(wv.x, xa[j], out[0][j]);
                     out[1][j] = fmaf(wv.y, xa[j], out[1][j]);
                 }
             }
 #pragma unroll
-            for (int i = 0; i < 2; ++i)
-                *reinterpret_cast<float4 *>(rows + (L::Ud + o0 + i) * SRS + s0) =
-                    make_float4(out[i][0], out[i][1], out[i][2], out[i][3]);
+            for (int i = 0; i < 2; ++i) store_n<SPT>(rows + (L::Ud + o0 + i) * SRS + s0, out[i]);
         }
         __syncthreads();
         // reverse mode, in place: D_H = w_d . softplus'(A_H)
         {
-            float act[4][4];
-            get4(rows, L::A(C::H), act);
+            float act[OPT][SPT];
+            get_n<L>(rows, L::A(C::H), act);
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < OPT; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) act[i][j] = sw[L::wd + o0_of() + i] * dsoftplus_from_act(act[i][j], g.beta);
-            put4(rows, L::A(C::H), act);
+                for (int j = 0; j < SPT; ++j)
+                    act[i][j] = sw[L::wd + o0_of<L>() + i] * dsoftplus_from_act(act[i][j], g.beta);
+            put_n<L>(rows, L::A(C::H), act);
         }
 #pragma unroll
         for (int l = C::H - 1; l >= 1; --l) {
             __syncthreads();
-            float act[4][4];
+            float act[OPT][SPT];
+            zero_n<L>(acc);
+            mm<L, W, W>(sw + L::Wlr(l), rows + L::A(l + 1) * SRS, acc);
+            get_n<L>(rows, L::A(l), act);
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < OPT; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-            mm<W, W>(sw + L::Wlr(l), rows + L::A(l + 1) * SRS, acc);
-            get4(rows, L::A(l), act);
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] *= dsoftplus_from_act(act[i][j], g.beta);
-            __syncthreads();  // every thread has read A_l before any overwrites it
-            put4(rows, L::A(l), acc);
+                for (int j = 0; j < SPT; ++j) acc[i][j] *= dsoftplus_from_act(act[i][j], g.beta);
+            put_n<L>(rows, L::A(l), acc);  // each thread reads and writes only its own block of A_l
         }
         __syncthreads();
-        // encoding rows <- W_0^T D_1 (groups of 32 inputs)
+        // encoding rows <- W_0^T D_1, in groups of W outputs (the thread's outputs o0 .. o0 + OPT - 1)
 #pragma unroll
-        for (int grp = 0; grp < L::R0 / 32; ++grp) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-            mm<W, L::R0>(sw + L::W0r + 32 * grp, rows + L::A(1) * SRS, acc);
-            put4(rows, L::A0 + 32 * grp, acc);
+        for (int grp = 0; grp < (L::R0 + W - 1) / W; ++grp) {
+            zero_n<L>(acc);
+            mm<L, W, L::R0>(sw + L::W0r + W * grp, rows + L::A(1) * SRS, acc);
+            if (W * grp + o0_of<L>() < L::R0) put_n<L>(rows, L::A0 + W * grp, acc);
         }
         __syncthreads();
         // per hit: grad d through the encoding, the normal, the colour inputs and the geometry outputs
@@ -348,13 +379,13 @@ __global__ void __launch_bounds__(STHREADS) shade_block_kernel(GridView g, WaveA
         }
         __syncthreads();
         // colour hidden layer (ReLU)
-        bias4(sw + L::c0, acc);
-        mm<C::CINP, W>(sw + L::C0t, rows + L::U * SRS, acc);
+        bias_n<L>(sw + L::c0, acc);
+        mm<L, C::CINP, W>(sw + L::C0t, rows + L::U * SRS, acc);
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < OPT; ++i)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fmaxf(acc[i][j], 0.f);
-        put4(rows, L::Hc, acc);
+            for (int j = 0; j < SPT; ++j) acc[i][j] = fmaxf(acc[i][j], 0.f);
+        put_n<L>(rows, L::Hc, acc);
         __syncthreads();
         if (tid < ST && s_r[tid] >= 0) {
             const int s = tid;
@@ -382,17 +413,12 @@ __global__ void __launch_bounds__(STHREADS) shade_block_kernel(GridView g, WaveA
 
 template <class C>
 cudaError_t launch_shade_block_cfg(const GridView &g, const WaveArgs &a, int sm_count, cudaStream_t s) {
-    if constexpr (C::W != 32) {
-        return cudaErrorNotSupported;
-    } else {
-        constexpr int smem = (SL<C>::END + SL<C>::ROWS * SRS) * (int)sizeof(float);
-        static_assert(smem <= 200 * 1024, "shade tile does not fit in shared memory");
-        cudaError_t e =
-            cudaFuncSetAttribute(shade_block_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        shade_block_kernel<C><<<sm_count, STHREADS, smem, s>>>(g, a);
-        return cudaGetLastError();
-    }
+    constexpr int smem = (SL<C>::END + SL<C>::ROWS * SL<C>::SRS) * (int)sizeof(float);
+    static_assert(smem <= 220 * 1024, "shade tile does not fit in shared memory");
+    cudaError_t e = cudaFuncSetAttribute(shade_block_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    shade_block_kernel<C><<<sm_count, STHREADS, smem, s>>>(g, a);
+    return cudaGetLastError();
 }
 
 #ifdef KNS_W

@@ -158,10 +158,9 @@ cudaError_t launch_wave_scatter(const WaveArgs &a, int cur, int blocks, cudaStre
 
 // ---------------------------------------------------------------- hits by cell (shading tiles)
 // After the last round: the hit list is counting-sorted by the cell of each hit into `sorted`, with
-// off[c] / tile_off[c] (tiles of HIT_TILE hits) and the tile count in ctrl->n_tiles.  Uses the wave's
-// count[0], fill[0], off, tile_off and sorted buffers, which the rounds no longer need.
-constexpr int HIT_TILE = 128;
-
+// off[c] / tile_off[c] (tiles of `tile` hits, the shading kernel's tile) and the tile count in
+// ctrl->n_tiles.  Uses the wave's count[0], fill[0], off, tile_off and sorted buffers, which the
+// rounds no longer need.
 __global__ void __launch_bounds__(256) wave_hit_count_kernel(WaveArgs a) {
     const int n = a.ctrl->n_hits;
     const int bound = (n + 31) & ~31;
@@ -172,7 +171,7 @@ __global__ void __launch_bounds__(256) wave_hit_count_kernel(WaveArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) wave_hit_scan_kernel(WaveArgs a) {
+__global__ void __launch_bounds__(SCAN_THREADS) wave_hit_scan_kernel(WaveArgs a, int tile) {
     __shared__ int wa[32], wb[32];
     const int NC = a.NC;
     const int per = (NC + SCAN_THREADS - 1) / SCAN_THREADS;
@@ -181,7 +180,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) wave_hit_scan_kernel(WaveArgs a)
     for (int c = c0; c < c1; ++c) {
         const int n = a.count[0][c];
         sum += n;
-        tiles += (n + HIT_TILE - 1) / HIT_TILE;
+        tiles += (n + tile - 1) / tile;
     }
     int incl_s = sum, incl_t = tiles;
     block_scan2(incl_s, incl_t, wa, wb);
@@ -192,7 +191,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) wave_hit_scan_kernel(WaveArgs a)
         a.tile_off[c] = run_t;
         a.fill[0][c] = 0;
         run_s += n;
-        run_t += (n + HIT_TILE - 1) / HIT_TILE;
+        run_t += (n + tile - 1) / tile;
     }
     if (threadIdx.x == SCAN_THREADS - 1) {
         a.off[NC] = incl_s;
@@ -221,11 +220,11 @@ __global__ void __launch_bounds__(256) wave_hit_scatter_kernel(WaveArgs a) {
     }
 }
 
-cudaError_t launch_hit_sort(const WaveArgs &a, int sm_count, cudaStream_t s) {
+cudaError_t launch_hit_sort(const WaveArgs &a, int tile, int sm_count, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(a.count[0], 0, sizeof(int) * (a.NC + 1), s);
     if (e != cudaSuccess) return e;
     wave_hit_count_kernel<<<sm_count * 4, 256, 0, s>>>(a);
-    wave_hit_scan_kernel<<<1, SCAN_THREADS, 0, s>>>(a);
+    wave_hit_scan_kernel<<<1, SCAN_THREADS, 0, s>>>(a, tile);
     wave_hit_scatter_kernel<<<sm_count * 4, 256, 0, s>>>(a);
     return cudaGetLastError();
 }

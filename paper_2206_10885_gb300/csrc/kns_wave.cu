@@ -664,43 +664,6 @@ __global__ void __launch_bounds__(32) wave_eval_kernel(GridView g, WaveArgs a, i
     }
 }
 
-// Shading of converged rays: full SDF MLP with its input gradient (normal), colour MLP (Eq. 3).
-template <class C>
-__global__ void __launch_bounds__(128) wave_shade_kernel(GridView g, WaveArgs a) {
-    const int n = a.ctrl->n_hits;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-        const int r = a.hits[q];
-        const int c = a.cell_ray[r];
-        const float t = a.t_ray[r];
-        int cam;
-        const Ray ray = ray_of(a, r, cam);
-        const float x = fmaf(t, ray.wx, ray.ox), y = fmaf(t, ray.wy, ray.oy), z = fmaf(t, ray.wz, ray.oz);
-        const float *cw = g.w + (int64_t)c * g.cell_stride;
-        float feat[FEAT], grad[3], nrm[3], rgb[3];
-        sdf_full_f32<C>(cw, x, y, z, g.beta, g.inv_beta, feat, grad);
-        const float gn = sqrtf(fmaf(grad[0], grad[0], fmaf(grad[1], grad[1], grad[2] * grad[2])));
-        const float inv = gn > 0.f ? 1.f / gn : 0.f;
-        nrm[0] = grad[0] * inv;
-        nrm[1] = grad[1] * inv;
-        nrm[2] = grad[2] * inv;
-        colour_f32<C>(cw, feat, nrm, ray.wx, ray.wy, ray.wz, x, y, z, rgb);
-        const ViewDev &V = a.views[cam];
-        const int64_t p = r - V.ray_base;
-        V.rgb[3 * p + 0] = rgb[0];
-        V.rgb[3 * p + 1] = rgb[1];
-        V.rgb[3 * p + 2] = rgb[2];
-        V.depth[p] = t;
-        if (V.normal) {
-            V.normal[3 * p + 0] = nrm[0];
-            V.normal[3 * p + 1] = nrm[1];
-            V.normal[3 * p + 2] = nrm[2];
-        }
-        if (V.cell) V.cell[p] = c;
-        if (V.steps) V.steps[p] = a.steps_ray[r];
-        if (V.hit) V.hit[p] = 1;
-    }
-}
-
 template <class C>
 cudaError_t launch_wave_gen_cfg(const GridView &g, const WaveArgs &a, cudaStream_t s) {
     dim3 grid((a.max_W + 15) / 16, (a.max_H + 7) / 8, a.n_views);
@@ -747,18 +710,12 @@ cudaError_t launch_wave_eval_cfg(const GridView &g, const WaveArgs &a, int cur, 
     wave_tail_warp_kernel<C><<<sm_count * 8, 256, 0, s>>>(g, a, cur);
     return cudaGetLastError();
 }
-template <class C>
-cudaError_t launch_wave_shade_cfg(const GridView &g, const WaveArgs &a, int blocks, cudaStream_t s) {
-    wave_shade_kernel<C><<<blocks, 128, 0, s>>>(g, a);
-    return cudaGetLastError();
-}
 
 #ifdef KNS_W
 using InstCfg = Cfg<KNS_W, KNS_H, KNS_L, KNS_LD>;
 template cudaError_t launch_wave_gen_cfg<InstCfg>(const GridView &, const WaveArgs &, cudaStream_t);
 template cudaError_t launch_wave_eval_cfg<InstCfg>(const GridView &, const WaveArgs &, int, int, int, int,
                                                    cudaStream_t);
-template cudaError_t launch_wave_shade_cfg<InstCfg>(const GridView &, const WaveArgs &, int, cudaStream_t);
 #endif
 
 }  // namespace kns
