@@ -288,7 +288,8 @@ def run_kns(args, rank, world, local_rank):
     mac_trace, mac_hit = mac_counts(desc)
     # kernels one render launches: generate, per round scan + scatter + FP32 eval + FP32 tail
     # (+ BF16 eval), shade; counted from the library's round counter
-    launches_per_step = 2 + st["rounds"] * (4 + (1 if precision == kns.KNS_BF16 else 0))
+    # gen + rounds x (scan, scatter, eval, tail[, bf16 eval]) + hit count/scan/scatter + shade
+    launches_per_step = 5 + st["rounds"] * (4 + (1 if precision == kns.KNS_BF16 else 0))
 
     clocks = ClockSampler(local_rank).start() if rank == 0 else None
     if world > 1:
@@ -335,7 +336,7 @@ def run_kns(args, rank, world, local_rank):
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
         if precision == kns.KNS_FP32:
-            # dominant kernel class: the FP32 evaluation (block or warp tiles, plus the per-thread tail
+            # dominant kernel class: the FP32 evaluation (block or warp tiles, plus the warp-per-ray tail
             # that finishes the last rays; the library times them as one class), FMA-bound
             flops = 2.0 * st["samples_fp32"] * mac_trace
             kms = st["ms_eval_fp32"]
@@ -343,7 +344,7 @@ def run_kns(args, rank, world, local_rank):
             roof = {"bound": "alu", "peak": fp32_peak, "unit": "TFLOP/s",
                     "kernel": "wave_eval_kernel" if warp_tiles else "wave_eval_block_kernel",
                     "kernel_class_note": "time and samples of the evaluation class: tile rounds plus the "
-                                         "per-thread tail kernel", "peak_source": FP32_PEAK_NOTE}
+                                         "warp-per-ray tail kernel", "peak_source": FP32_PEAK_NOTE}
         else:
             # dominant kernel: the BF16 tensor-core tile evaluation (wave_eval_bf16_kernel)
             flops = 2.0 * st["samples_bf16"] * mac_trace
@@ -358,7 +359,7 @@ def run_kns(args, rank, world, local_rank):
                      "kernel_ms_per_render": kms, "flop_per_sample": 2 * mac_trace})
         phases = {k: st[k] for k in ("ms_generate", "ms_sort", "ms_eval_fp32", "ms_eval_bf16", "ms_shade",
                                      "ms_total")}
-        counts = {k: st[k] for k in ("rounds", "rays", "hits", "samples_fp32", "samples_bf16")}
+        counts = {k: st[k] for k in ("rounds", "rays", "hits", "samples_fp32", "samples_bf16", "samples_tail")}
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             v, n, s, cores = oracle_rate(desc, w, cams, W, H, ms, eps, args.cpu_seconds)
@@ -375,7 +376,8 @@ def run_kns(args, rank, world, local_rank):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
                 "clocks": clock_info, "gpu_launches": args.steps * launches_per_step, "tuning": tuning,
-                "launch_count_source": "library round counter: 2 + rounds x (scan, scatter, eval, tail[, bf16 eval])",
+                "launch_count_source": "library round counter: gen + rounds x (scan, scatter, eval, tail[, bf16 eval]) + "
+                                      "hit sort (3) + shade",
                 "step_ms_min": min(times), "step_ms_median": statistics.median(times)}
         print(json.dumps(line), flush=True)
     grid.free()

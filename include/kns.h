@@ -135,6 +135,7 @@ typedef struct kns_render_stats {
     int64_t samples_bf16;  /* SDF evaluations in BF16 */
     /* device time (ms) per kernel class, summed over the render's launches; 0 unless opts->timing */
     float ms_generate, ms_sort, ms_eval_fp32, ms_eval_bf16, ms_shade, ms_total;
+    int64_t samples_tail;  /* the part of samples_fp32 evaluated one warp per ray (rounds of <= tail_rays rays) */
 } kns_render_stats;
 
 /* ---------------------------------------------------------------- context */

@@ -86,7 +86,7 @@ class kns_render_stats(C.Structure):
     _fields_ = [("rounds", C.c_int32), ("rays", C.c_int64), ("hits", C.c_int64), ("samples_fp32", C.c_int64),
                 ("samples_bf16", C.c_int64), ("ms_generate", C.c_float), ("ms_sort", C.c_float),
                 ("ms_eval_fp32", C.c_float), ("ms_eval_bf16", C.c_float), ("ms_shade", C.c_float),
-                ("ms_total", C.c_float)]
+                ("ms_total", C.c_float), ("samples_tail", C.c_int64)]
 
 
 _lib = None

@@ -938,6 +938,7 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
         ctx->stats.hits += hc.n_hits;
         ctx->stats.samples_fp32 += (int64_t)hc.samples_f32;
         ctx->stats.samples_bf16 += (int64_t)hc.samples_bf16;
+        ctx->stats.samples_tail += (int64_t)hc.samples_tail;
     }
     return KNS_OK;
 }
@@ -1154,6 +1155,7 @@ kns_status kns_get_render_stats(kns_ctx *ctx, kns_render_stats *out) {
     st.hits += hc.n_hits;
     st.samples_fp32 += (int64_t)hc.samples_f32;
     st.samples_bf16 += (int64_t)hc.samples_bf16;
+    st.samples_tail += (int64_t)hc.samples_tail;
     float *dst[5] = {&st.ms_generate, &st.ms_sort, &st.ms_eval_fp32, &st.ms_eval_bf16, &st.ms_shade};
     for (const auto &m : ctx->ev_marks) {
         float ms = 0.f;

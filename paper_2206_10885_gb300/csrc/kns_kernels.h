@@ -18,12 +18,13 @@ struct WaveCtrl {
     int n_live[2];  // samples queued for the current / next round
     int n_hits;     // rays that converged (queued for shading)
     int n_tiles;    // block tiles of the current round
-    int next_tile;     // dynamic tile counter of the current round (FP32 tiles)
+    int next_tile;     // dynamic tile counter of the current round (FP32 tiles; rays in a tail round)
     int tail;          // 1: the current round is small enough to finish one warp per ray
     int n_tiles_fine;  // tiles of FP32 samples (keys < NC); BF16 tiles follow them
     int next_tile_bf;  // dynamic tile counter of the BF16 tiles
-    unsigned long long samples_f32;   // SDF evaluations in FP32 tiles and the per-thread tail
+    unsigned long long samples_f32;   // SDF evaluations in FP32 (tiles and the tail)
     unsigned long long samples_bf16;  // SDF evaluations in BF16 tiles
+    unsigned long long samples_tail;  // the part of samples_f32 evaluated by the one-warp-per-ray tail
 };
 
 // One view of a render: its camera, image size, first ray id and output buffers (device, 128 B).

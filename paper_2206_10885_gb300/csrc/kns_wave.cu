@@ -6,6 +6,8 @@
 // h[k][s] (k = input unit, s = sample); lane (sg, ng) = (lane / 8, lane % 8) accumulates samples
 // 4sg..4sg+3 against output units ng*W/8 .. ng*W/8 + W/8 - 1, so each shared-memory float4 of
 // activations and each float4 of k-major weights feed 16 (W = 32) or 32 (W = 64) FMAs.
+#include <atomic>
+
 #include "kns_wave.cuh"
 
 namespace kns {
@@ -400,12 +402,14 @@ __global__ void __launch_bounds__(NT) wave_eval_block_kernel(GridView g, WaveArg
     }
 }
 
-// Tail: a warp runs one ray to its end; lane o computes output unit o (and o + 32 for width 64) of
-// each layer from the cell's k-major trace weights, which the warp reads as coalesced 128-byte rows,
-// with the layer inputs broadcast by shuffles.  Every output is its bias followed by one FMA per
-// input in ascending order and every lane forms the d row as one sequential chain, the order of the
-// tile evaluators, so d is bit-identical to theirs.  (One thread per ray would have the lanes of a
-// warp read 32 different cells' weights.)
+// Tail: a warp runs one ray to its end.  The warp keeps the k-major trace weights of its ray's
+// current cell in a shared-memory slot of its own (one bulk copy per change of cell: the rays left
+// for the tail are mostly grazing rays that take many small steps inside one cell) and evaluates a
+// sample as one matrix-vector product per layer: lane o computes output unit o (and o + 32 for width
+// 64) with its weights read conflict-free from the slot and the layer input broadcast from a
+// shared-memory row.  Every output is its bias followed by one FMA per input in ascending order and
+// every lane forms the d row as one sequential chain -- the order of the tile evaluators, so d is
+// bit-identical to theirs.  Rays are handed out one at a time in cell-sorted order.
 
 // input k of the encoding (Eq. 1): x, y, z, then per frequency sin x, sin y, sin z, cos x, cos y, cos z
 __device__ __forceinline__ float encoding_entry(int k, float px, float py, float pz) {
@@ -417,55 +421,85 @@ __device__ __forceinline__ float encoding_entry(int k, float px, float py, float
     return c < 3 ? sn : cs;
 }
 
+// shared memory of a tail warp: the weight slot, the encoded input row, two activation rows
 template <class C>
-__device__ __forceinline__ float warp_sdf_trace(const float *__restrict__ wt, float px, float py, float pz,
-                                                int lane, float beta, float inv_beta) {
-    constexpr int NPL = C::W / 32, NIN = (C::INP + 31) / 32;
-    float in[NIN];  // lane k holds inputs k, k + 32 (zero past IN)
+constexpr int tail_smem_floats() { return C::TSIZE + C::INP + 2 * C::W; }
+
+// one layer of the warp product: out[o] = softplus(b[o] + sum_k Wt[k][o] in[k]), k ascending
+template <int K, int W>
+__device__ __forceinline__ void warp_layer(const float *__restrict__ Wt, const float *__restrict__ b,
+                                           const float *in, float *out, int lane, float beta, float inv_beta) {
+    constexpr int NPL = W / 32;
+    float acc[NPL];
 #pragma unroll
-    for (int j = 0; j < NIN; ++j) {
-        const int k = lane + 32 * j;
-        in[j] = k < C::IN ? encoding_entry(k, px, py, pz) : 0.f;
-    }
-    float h[NPL], g[NPL];
-#pragma unroll
-    for (int u = 0; u < NPL; ++u) {
-        const int o = lane + 32 * u;
-        float acc = __ldg(wt + C::tb0 + o);
+    for (int u = 0; u < NPL; ++u) acc[u] = b[lane + 32 * u];
 #pragma unroll 4
-        for (int k = 0; k < C::INP; ++k)
-            acc = fmaf(__ldg(wt + C::tW0 + k * C::W + o), __shfl_sync(FULL, in[k >> 5], k & 31), acc);
-        h[u] = softplus_f32(acc, beta, inv_beta);
-    }
-#pragma unroll
-    for (int l = 1; l < C::H; ++l) {
+    for (int k = 0; k < K; k += 4) {
+        const float4 x = *reinterpret_cast<const float4 *>(in + k);
 #pragma unroll
         for (int u = 0; u < NPL; ++u) {
-            const int o = lane + 32 * u;
-            float acc = __ldg(wt + C::tbl(l) + o);
-#pragma unroll 4
-            for (int k = 0; k < C::W; ++k)
-                acc = fmaf(__ldg(wt + C::tWl(l) + k * C::W + o), __shfl_sync(FULL, h[k >> 5], k & 31), acc);
-            g[u] = softplus_f32(acc, beta, inv_beta);
+            const float *w = Wt + k * W + lane + 32 * u;
+            acc[u] = fmaf(w[0], x.x, acc[u]);
+            acc[u] = fmaf(w[W], x.y, acc[u]);
+            acc[u] = fmaf(w[2 * W], x.z, acc[u]);
+            acc[u] = fmaf(w[3 * W], x.w, acc[u]);
         }
-#pragma unroll
-        for (int u = 0; u < NPL; ++u) h[u] = g[u];
     }
-    float d = __ldg(wt + C::tbL);
-#pragma unroll 4
-    for (int k = 0; k < C::W; ++k) d = fmaf(__ldg(wt + C::tdL + k), __shfl_sync(FULL, h[k >> 5], k & 31), d);
+#pragma unroll
+    for (int u = 0; u < NPL; ++u) out[lane + 32 * u] = softplus_f32(acc[u], beta, inv_beta);
+    __syncwarp();
+}
+
+template <class C>
+__device__ __forceinline__ float warp_sdf_trace(const float *__restrict__ wsm, float *xin, float *h0, float *h1,
+                                                float px, float py, float pz, int lane, float beta,
+                                                float inv_beta) {
+    for (int k = lane; k < C::IN; k += 32) xin[k] = encoding_entry(k, px, py, pz);
+    __syncwarp();
+    warp_layer<C::INP, C::W>(wsm + C::tW0, wsm + C::tb0, xin, h0, lane, beta, inv_beta);
+    float *src = h0, *dst = h1;
+#pragma unroll
+    for (int l = 1; l < C::H; ++l) {
+        warp_layer<C::W, C::W>(wsm + C::tWl(l), wsm + C::tbl(l), src, dst, lane, beta, inv_beta);
+        float *tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+    float d = wsm[C::tbL];
+#pragma unroll
+    for (int k = 0; k < C::W; k += 4) {
+        const float4 w = *reinterpret_cast<const float4 *>(wsm + C::tdL + k);
+        const float4 h = *reinterpret_cast<const float4 *>(src + k);
+        d = fmaf(w.x, h.x, d);
+        d = fmaf(w.y, h.y, d);
+        d = fmaf(w.z, h.z, d);
+        d = fmaf(w.w, h.w, d);
+    }
     return d;
 }
 
-// A tail round: one warp per ray, to the end.  Rays come in cell-sorted order (the cell of a ray's
-// position is its sort key).
+// A tail round: one warp (one block) per ray, to the end.  Rays come in cell-sorted order (the cell
+// of a ray's position is its sort key); the round's tile counter hands them out.
 template <class C>
-__global__ void __launch_bounds__(256) wave_tail_warp_kernel(GridView g, WaveArgs a, int cur) {
+__global__ void __launch_bounds__(32) wave_tail_warp_kernel(GridView g, WaveArgs a, int cur) {
+    extern __shared__ __align__(128) float dyn[];
+    __shared__ __align__(8) uint64_t bar;
     if (!a.ctrl->tail) return;
     const int n = a.ctrl->n_live[cur];
-    const int lane = threadIdx.x & 31;
-    const int warps = gridDim.x * (blockDim.x >> 5);
-    for (int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < n; q += warps) {
+    const int lane = threadIdx.x;
+    float *wsm = dyn, *xin = dyn + C::TSIZE, *h0 = xin + C::INP, *h1 = h0 + C::W;
+    for (int k = C::IN + lane; k < C::INP; k += 32) xin[k] = 0.f;  // encoding pad stays zero
+    if (lane == 0) mbar_init(&bar, 1);
+    __syncwarp();
+    const bool cycles = a.t_hist != nullptr;  // the tail runs in FP32 renders only
+    int cached = -1;
+    uint32_t phase = 0;
+    unsigned long long nsamples = 0;
+    for (;;) {
+        int q = 0;
+        if (lane == 0) q = atomicAdd(&a.ctrl->next_tile, 1);
+        q = __shfl_sync(FULL, q, 0);
+        if (q >= n) break;
         const int r = a.sorted[q];
         int lo = 0, hi = a.NC;  // the key with off[key] <= q < off[key+1]
         while (hi - lo > 1) {
@@ -479,14 +513,22 @@ __global__ void __launch_bounds__(256) wave_tail_warp_kernel(GridView g, WaveArg
         clip_box(g, ray, t0, tf);
         float t = a.t_ray[r];
         int steps = a.steps_ray[r];
-        const bool cycles = a.t_hist != nullptr;  // the tail runs in FP32 renders only
         float4 hist = cycles ? a.t_hist[r] : no_history();
         bool hit = false;
-        int nsamples = 0;
         for (;;) {
-            const float d = warp_sdf_trace<C>(a.wt + (int64_t)cell * a.wt_stride, fmaf(t, ray.wx, ray.ox),
-                                              fmaf(t, ray.wy, ray.oy), fmaf(t, ray.wz, ray.oz), lane, g.beta,
-                                              g.inv_beta);
+            if (cell != cached) {
+                __syncwarp();  // every lane is done with the slot's previous cell
+                if (lane == 0) bulk_load(wsm, a.wt + (int64_t)cell * a.wt_stride, C::TSIZE * sizeof(float), &bar);
+                const bool ok = mbar_wait(&bar, phase, 1u << 26);
+                phase ^= 1u;
+                if (!__all_sync(FULL, ok)) {  // the weights never landed: report and leave
+                    if (lane == 0) atomicCAS(a.status, 0, (int)6 /* KNS_ERR_TIMEOUT */);
+                    return;
+                }
+                cached = cell;
+            }
+            const float d = warp_sdf_trace<C>(wsm, xin, h0, h1, fmaf(t, ray.wx, ray.ox), fmaf(t, ray.wy, ray.oy),
+                                              fmaf(t, ray.wz, ray.oz), lane, g.beta, g.inv_beta);
             ++steps;
             ++nsamples;
             if (fabsf(d) < a.eps) {
@@ -504,7 +546,6 @@ __global__ void __launch_bounds__(256) wave_tail_warp_kernel(GridView g, WaveArg
             }
         }
         if (lane == 0) {
-            atomicAdd(&a.ctrl->samples_f32, (unsigned long long)nsamples);
             if (hit) {
                 a.cell_ray[r] = cell;
                 a.t_ray[r] = t;
@@ -514,6 +555,10 @@ __global__ void __launch_bounds__(256) wave_tail_warp_kernel(GridView g, WaveArg
                 write_miss(a, r, steps);
             }
         }
+    }
+    if (lane == 0 && nsamples) {
+        atomicAdd(&a.ctrl->samples_f32, nsamples);
+        atomicAdd(&a.ctrl->samples_tail, nsamples);
     }
 }
 
@@ -707,7 +752,23 @@ cudaError_t launch_wave_eval_cfg(const GridView &g, const WaveArgs &a, int cur, 
         wave_eval_kernel<C><<<blocks, 32, smem, s>>>(g, a, cur);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    wave_tail_warp_kernel<C><<<sm_count * 8, 256, 0, s>>>(g, a, cur);
+    // one-warp blocks, as many as fit on the SMs at once (each holds one cell's weights)
+    constexpr int tsmem = tail_smem_floats<C>() * (int)sizeof(float);
+    static_assert(tsmem <= 64 * 1024, "tail weight slot does not fit");
+    static std::atomic<int> tail_blocks_per_sm{0};  // the same for every launch
+    int tail_blocks = tail_blocks_per_sm.load();
+    if (tail_blocks == 0) {
+        if ((e = cudaFuncSetAttribute(wave_tail_warp_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      tsmem)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(wave_tail_warp_kernel<C>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      100)) != cudaSuccess ||
+            (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tail_blocks, wave_tail_warp_kernel<C>, 32,
+                                                               tsmem)) != cudaSuccess)
+            return e;
+        if (tail_blocks < 1) tail_blocks = 1;
+        tail_blocks_per_sm.store(tail_blocks);
+    }
+    wave_tail_warp_kernel<C><<<sm_count * tail_blocks, 32, tsmem, s>>>(g, a, cur);
     return cudaGetLastError();
 }
 
