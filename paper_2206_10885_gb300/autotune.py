@@ -23,7 +23,7 @@ SPACE = {
     "min_active": (1, 8),
     "static_tiles": (1, 2),
     "blocks_per_sm": (8, 16, 32),
-    "tail_rays": (-1, 32768, 65536, 131072),
+    "tail_rays": (-1, 131072, 262144, 524288),
 }
 
 

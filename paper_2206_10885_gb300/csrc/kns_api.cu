@@ -25,6 +25,9 @@ struct WaveScratch {
     int *steps_ray = nullptr, *cell_ray = nullptr, *q[2] = {nullptr, nullptr}, *qcell[2] = {nullptr, nullptr};
     int *sorted = nullptr, *hits = nullptr;
     int *cellbuf = nullptr;  // count[2], fill[2], off, tile_off (6 * (nc + 1) ints)
+    int4 *tiles = nullptr;   // tile descriptors of a round (max_tiles(rays, 2 nc))
+    int *pend_r = nullptr;   // rays waiting for the occupancy DDA
+    float *pend_t = nullptr;
     int *ray_view = nullptr;
     kns::ViewDev *d_views = nullptr;
     kns::WaveCtrl *ctrl = nullptr;
@@ -314,6 +317,9 @@ void free_scratch(WaveScratch &w) {
     cudaFree(w.sorted);
     cudaFree(w.hits);
     cudaFree(w.cellbuf);
+    cudaFree(w.tiles);
+    cudaFree(w.pend_r);
+    cudaFree(w.pend_t);
     cudaFree(w.ray_view);
     cudaFree(w.d_views);
     cudaFree(w.ctrl);
@@ -326,7 +332,7 @@ constexpr int kRenderBlockTiles = 1;        // FP32 renders use block tiles by d
 // Defaults picked by the autotuner on the 16^3 / width-32 grid at 8 x 800x800.
 constexpr int kRenderInnerSteps = 4;
 constexpr int kRenderMinActive = 8;
-constexpr int kRenderTailRays = 65536;  // rounds this small finish one warp per ray
+constexpr int kRenderTailRays = 262144;  // rounds this small finish one warp per ray
 constexpr int kRenderBlocksPerSM = 16;
 constexpr int kRenderStaticTiles = 2;
 
@@ -375,6 +381,9 @@ kns_status ensure_scratch(kns_ctx *ctx, int64_t rays, int nc, int cams) {
     alloc(&w.sorted, sizeof(int) * R);
     alloc(&w.hits, sizeof(int) * R);
     alloc(&w.cellbuf, sizeof(int) * 6 * (size_t)(NC + 1));
+    alloc(&w.tiles, sizeof(int4) * (size_t)kns::max_tiles(R, 2 * NC));
+    alloc(&w.pend_r, sizeof(int) * R);
+    alloc(&w.pend_t, sizeof(float) * R);
     alloc(&w.ray_view, sizeof(int) * R);
     alloc(&w.d_views, sizeof(kns::ViewDev) * NCAM);
     alloc(&w.ctrl, sizeof(kns::WaveCtrl));
@@ -876,6 +885,9 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
     a.qcell[1] = w.qcell[1];
     a.sorted = w.sorted;
     a.hits = w.hits;
+    a.tiles = w.tiles;
+    a.pend_r = w.pend_r;
+    a.pend_t = w.pend_t;
     a.count[0] = w.cellbuf;
     a.count[1] = w.cellbuf + (nkeys + 1);
     a.fill[0] = w.cellbuf + 2 * (nkeys + 1);
@@ -1201,8 +1213,12 @@ constexpr size_t kNoAllocRayBuf = align_up(sizeof(int) * (size_t)KNS_NOALLOC_MAX
 constexpr size_t kNoAllocCellBuf = align_up(sizeof(int) * 6 * (size_t)(KNS_NOALLOC_MAX_CELLS + 1));
 constexpr size_t kNoAllocViewBuf = align_up(sizeof(kns::ViewDev) * (size_t)KNS_NOALLOC_MAX_CAMS);
 constexpr size_t kNoAllocCtrlBuf = align_up(sizeof(kns::WaveCtrl));
-// t_ray, steps_ray, cell_ray, q[2], qcell[2], sorted, hits, ray_view: ten per-ray int/float buffers
-constexpr size_t kNoAllocBytes = 10 * kNoAllocRayBuf + kNoAllocCellBuf + kNoAllocViewBuf + kNoAllocCtrlBuf;
+constexpr size_t kNoAllocTileBuf =
+    align_up(sizeof(int4) * (size_t)(KNS_NOALLOC_MAX_RAYS / 16 + KNS_NOALLOC_MAX_CELLS + 1));
+// t_ray, steps_ray, cell_ray, q[2], qcell[2], sorted, hits, ray_view, pend_r, pend_t: twelve per-ray
+// int/float buffers
+constexpr size_t kNoAllocBytes =
+    12 * kNoAllocRayBuf + kNoAllocCellBuf + kNoAllocViewBuf + kNoAllocCtrlBuf + kNoAllocTileBuf;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -1272,6 +1288,9 @@ extern "C" kns_status kns_render_noalloc(kns_ctx *ctx, const kns_grid *grid, con
     int *cellbuf = (int *)take(kNoAllocCellBuf);
     kns::ViewDev *d_views = (kns::ViewDev *)take(kNoAllocViewBuf);
     a.ctrl = (kns::WaveCtrl *)take(kNoAllocCtrlBuf);
+    a.tiles = (int4 *)take(kNoAllocTileBuf);
+    a.pend_r = (int *)take(kNoAllocRayBuf);
+    a.pend_t = (float *)take(kNoAllocRayBuf);
     a.count[0] = cellbuf;
     a.count[1] = cellbuf + (NC + 1);
     a.fill[0] = cellbuf + 2 * (NC + 1);

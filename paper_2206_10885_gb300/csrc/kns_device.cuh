@@ -378,12 +378,10 @@ __device__ __forceinline__ bool clip_box(const GridView &g, const Ray &r, float 
     return true;
 }
 
-// Integer 3D-DDA (Amanatides & Woo) from voxel (vx, vy, vz) to the entry of the next occupied voxel.
-// Returns true with te and the voxel updated; false when the ray leaves the grid or passes tf.
-// The crossing parameter of each axis is (face - o) / w with the face coordinate exact; after a
-// step only the crossed axis' value changes, so only it is recomputed.
-__device__ __forceinline__ float dda_face_t(float bmin, int v, bool up, float vox, float o, float w) {
-    return w == 0.f ? INFINITY : (bmin + (float)(v + (up ? 1 : 0)) * vox - o) / w;
+// Crossing parameter of a voxel face on one axis: (face - o) times 1/w (inv_w, computed once per
+// walk), the face coordinate exact; a ray parallel to the axis never crosses.
+__device__ __forceinline__ float dda_face_t(float bmin, int v, bool up, float vox, float o, float inv_w) {
+    return isinf(inv_w) ? INFINITY : (bmin + (float)(v + (up ? 1 : 0)) * vox - o) * inv_w;
 }
 __device__ __forceinline__ bool coarse_empty(const GridView &g, int vx, int vy, int vz) {
     if (!g.occ_coarse) return false;
@@ -401,8 +399,8 @@ __device__ __forceinline__ int unambiguous_index(float o, float w, float t, floa
 
 // Integer 3D-DDA (Amanatides & Woo) from voxel (vx, vy, vz) to the entry of the next occupied voxel.
 // Returns true with te and the voxel updated; false when the ray leaves the grid or passes tf.
-// The crossing parameter of each axis is (face - o) / w with the face coordinate exact; after a
-// step only the crossed axis' value changes, so only it is recomputed.  Blocks of 8^3 voxels that
+// The crossing parameter of each axis is (face - o) / w (dda_face_t, by the reciprocal of w); after
+// a step only the crossed axis' value changes, so only it is recomputed.  Blocks of 8^3 voxels that
 // the coarse mask marks empty are crossed in one step: the exit face is found among the block's
 // faces with the same formula and tie rule, and the other two voxel indices at the exit are taken
 // from the position there unless it lies within 1e-3 voxel of a face, in which case the block is
@@ -411,17 +409,18 @@ __device__ __forceinline__ bool dda_next(const GridView &g, const Ray &r, int &v
                                          float &te) {
     const int res = g.occ_res;
     const bool ux = r.wx > 0.f, uy = r.wy > 0.f, uz = r.wz > 0.f;
-    float tx = dda_face_t(g.bmin[0], vx, ux, g.ovox[0], r.ox, r.wx);
-    float ty = dda_face_t(g.bmin[1], vy, uy, g.ovox[1], r.oy, r.wy);
-    float tz = dda_face_t(g.bmin[2], vz, uz, g.ovox[2], r.oz, r.wz);
+    const float ix = 1.f / r.wx, iy = 1.f / r.wy, iz = 1.f / r.wz;
+    float tx = dda_face_t(g.bmin[0], vx, ux, g.ovox[0], r.ox, ix);
+    float ty = dda_face_t(g.bmin[1], vy, uy, g.ovox[1], r.oy, iy);
+    float tz = dda_face_t(g.bmin[2], vz, uz, g.ovox[2], r.oz, iz);
     // at most 3*res voxel crossings before the ray leaves the grid
     for (int guard = 0; guard < 3 * res + 3; ++guard) {
         if (coarse_empty(g, vx, vy, vz)) {
             // the last voxel of this block along each axis in the direction of travel
             const int bx = ux ? (vx | 7) : (vx & ~7), by = uy ? (vy | 7) : (vy & ~7), bz = uz ? (vz | 7) : (vz & ~7);
-            const float Tx = dda_face_t(g.bmin[0], bx, ux, g.ovox[0], r.ox, r.wx);
-            const float Ty = dda_face_t(g.bmin[1], by, uy, g.ovox[1], r.oy, r.wy);
-            const float Tz = dda_face_t(g.bmin[2], bz, uz, g.ovox[2], r.oz, r.wz);
+            const float Tx = dda_face_t(g.bmin[0], bx, ux, g.ovox[0], r.ox, ix);
+            const float Ty = dda_face_t(g.bmin[1], by, uy, g.ovox[1], r.oy, iy);
+            const float Tz = dda_face_t(g.bmin[2], bz, uz, g.ovox[2], r.oz, iz);
             int nx, ny, nz, va;
             float T;
             if (Tx <= Ty && Tx <= Tz) {
@@ -453,9 +452,9 @@ __device__ __forceinline__ bool dda_next(const GridView &g, const Ray &r, int &v
                     te = T;
                     return true;
                 }
-                tx = dda_face_t(g.bmin[0], vx, ux, g.ovox[0], r.ox, r.wx);
-                ty = dda_face_t(g.bmin[1], vy, uy, g.ovox[1], r.oy, r.wy);
-                tz = dda_face_t(g.bmin[2], vz, uz, g.ovox[2], r.oz, r.wz);
+                tx = dda_face_t(g.bmin[0], vx, ux, g.ovox[0], r.ox, ix);
+                ty = dda_face_t(g.bmin[1], vy, uy, g.ovox[1], r.oy, iy);
+                tz = dda_face_t(g.bmin[2], vz, uz, g.ovox[2], r.oz, iz);
                 continue;
             }
             // ambiguous exit: walk this block voxel by voxel
@@ -466,17 +465,17 @@ __device__ __forceinline__ bool dda_next(const GridView &g, const Ray &r, int &v
             tm = tx;
             vx += ux ? 1 : -1;
             va = vx;
-            tx = dda_face_t(g.bmin[0], vx, ux, g.ovox[0], r.ox, r.wx);
+            tx = dda_face_t(g.bmin[0], vx, ux, g.ovox[0], r.ox, ix);
         } else if (ty <= tz) {
             tm = ty;
             vy += uy ? 1 : -1;
             va = vy;
-            ty = dda_face_t(g.bmin[1], vy, uy, g.ovox[1], r.oy, r.wy);
+            ty = dda_face_t(g.bmin[1], vy, uy, g.ovox[1], r.oy, iy);
         } else {
             tm = tz;
             vz += uz ? 1 : -1;
             va = vz;
-            tz = dda_face_t(g.bmin[2], vz, uz, g.ovox[2], r.oz, r.wz);
+            tz = dda_face_t(g.bmin[2], vz, uz, g.ovox[2], r.oz, iz);
         }
         if (va < 0 || va >= res) return false;
         if (tm > tf) return false;

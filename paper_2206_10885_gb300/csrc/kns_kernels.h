@@ -22,6 +22,7 @@ struct WaveCtrl {
     int tail;          // 1: the current round is small enough to finish one warp per ray
     int n_tiles_fine;  // tiles of FP32 samples (keys < NC); BF16 tiles follow them
     int next_tile_bf;  // dynamic tile counter of the BF16 tiles
+    int n_pend;        // rays of the current round whose next position lies in an empty voxel
     unsigned long long samples_f32;   // SDF evaluations in FP32 (tiles and the tail)
     unsigned long long samples_bf16;  // SDF evaluations in BF16 tiles
     unsigned long long samples_tail;  // the part of samples_f32 evaluated by the one-warp-per-ray tail
@@ -37,6 +38,9 @@ struct ViewDev {
 };
 
 // Everything the wavefront kernels read and write (device pointers; passed by value).
+// Tile descriptors a round can need: every key's partial tile plus full tiles of the smallest size.
+inline int64_t max_tiles(int64_t rays, int nkeys) { return rays / 16 + nkeys + 1; }
+
 struct WaveArgs {
     int n_views, max_W, max_H, max_steps;
     const ViewDev *views;  // n_views entries; rays of view v are ray_base .. ray_base + W*H - 1
@@ -69,12 +73,17 @@ struct WaveArgs {
     int *sorted, *hits;
     int *count[2], *fill[2];  // per-cell sample counts and scatter cursors
     int *off, *tile_off;      // NC+1 exclusive scans: samples and tiles per cell
+    int4 *tiles;              // per tile of the round: key, first sorted sample, samples (max_tiles entries)
+    int *pend_r;              // rays waiting for the occupancy DDA (n_pend of them) ...
+    float *pend_t;            // ... and the position each was last evaluated at
     WaveCtrl *ctrl;
 };
 
 // Per-configuration launchers (explicitly instantiated, one object file per configuration).
 template <class C>
 cudaError_t launch_wave_gen_cfg(const GridView &g, const WaveArgs &a, cudaStream_t s);
+// After a round's evaluation: the rays it left in empty voxels walk to their next occupied voxel.
+cudaError_t launch_wave_advance(const GridView &g, const WaveArgs &a, int cur, int sm_count, cudaStream_t s);
 template <class C>
 cudaError_t launch_wave_eval_cfg(const GridView &g, const WaveArgs &a, int cur, int blocks, int block_tiles,
                                  int sm_count, cudaStream_t s);

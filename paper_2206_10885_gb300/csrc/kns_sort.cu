@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) wave_scan_kernel(WaveArgs a, int
         a.ctrl->n_live[nxt] = 0;
         a.ctrl->next_tile = 0;
         a.ctrl->next_tile_bf = 0;
+        a.ctrl->n_pend = 0;
     }
     const int n_live = a.ctrl->n_live[cur];
     // a small round is finished one warp per ray (in cell-sorted order)
@@ -86,11 +87,12 @@ __global__ void __launch_bounds__(SCAN_THREADS) wave_scan_kernel(WaveArgs a, int
     int run_s = incl_s - sum, run_t = incl_t - tiles;
     for (int c = c0; c < c1; ++c) {
         const int n = a.count[cur][c];
+        const int bt = c < a.NC ? a.btile : a.btile_bf;
         a.off[c] = run_s;
         a.tile_off[c] = run_t;
         if (c == a.NC) a.ctrl->n_tiles_fine = run_t;  // first BF16 key: FP32 tiles end here
+        for (int i = 0; i < n; i += bt) a.tiles[run_t++] = make_int4(c, run_s + i, min(bt, n - i), 0);
         run_s += n;
-        run_t += (n + (c < a.NC ? a.btile : a.btile_bf) - 1) / (c < a.NC ? a.btile : a.btile_bf);
     }
     if (threadIdx.x == SCAN_THREADS - 1) {
         a.off[NC] = incl_s;
@@ -226,6 +228,56 @@ cudaError_t launch_hit_sort(const WaveArgs &a, int tile, int sm_count, cudaStrea
     wave_hit_count_kernel<<<sm_count * 4, 256, 0, s>>>(a);
     wave_hit_scan_kernel<<<1, SCAN_THREADS, 0, s>>>(a, tile);
     wave_hit_scatter_kernel<<<sm_count * 4, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// Rays whose last step left them in an empty occupancy voxel: the DDA to the next occupied voxel (or
+// out of the grid: a miss), the cycle test on the position reached, and the emit to the next round --
+// what the tile kernels' advance_ray would have done in place.  One thread per ray: many independent
+// voxel walks hide each other's memory latency.
+__global__ void __launch_bounds__(256) wave_advance_kernel(GridView g, WaveArgs a, int cur) {
+    const int n = a.ctrl->n_pend;
+    const int nxt = cur ^ 1;
+    const bool cycles = a.t_hist != nullptr && !a.coarse;
+    const int stride = gridDim.x * blockDim.x;
+    const int bound = (n + 31) & ~31;  // warp-uniform loop bound
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < bound; i += stride) {
+        bool emit = false;
+        int ncell = -1, r = 0;
+        if (i < n) {
+            r = a.pend_r[i];
+            const float t_eval = a.pend_t[i];
+            int cam;
+            const Ray ray = ray_of(a, r, cam);
+            float t0, tf;
+            clip_box(g, ray, t0, tf);
+            float t = a.t_ray[r];
+            ncell = advance_ray(g, ray, t, tf);
+            if (ncell < 0) {
+                write_miss(a, r, a.steps_ray[r]);
+            } else {
+                float4 hist = cycles ? a.t_hist[r] : no_history();
+                if (cycles && cycle_step(hist, t_eval, t)) {
+                    write_miss(a, r, a.max_steps);
+                    ncell = -1;
+                } else {
+                    emit = true;
+                    a.t_ray[r] = t;
+                    if (cycles) a.t_hist[r] = hist;
+                }
+            }
+        }
+        const int qp = warp_append(&a.ctrl->n_live[nxt], emit);
+        if (emit) {
+            a.q[nxt][qp] = r;
+            a.qcell[nxt][qp] = ncell;
+        }
+        warp_count_cells(a.count[nxt], emit, ncell);
+    }
+}
+
+cudaError_t launch_wave_advance(const GridView &g, const WaveArgs &a, int cur, int sm_count, cudaStream_t s) {
+    wave_advance_kernel<<<sm_count * 4, 256, 0, s>>>(g, a, cur);
     return cudaGetLastError();
 }
 

@@ -177,9 +177,13 @@ constexpr int BTHREADS = 256;  // default threads per block tile (two per sample
 // shared row stride (floats) of a BT-sample tile: row r starts in bank group r mod 8
 __host__ __device__ constexpr int block_rs(int BT) { return BT + 4; }
 
+// rows of the buffer that holds the encoding and, after layer 0, the second activation buffer
+template <class C>
+__host__ __device__ constexpr int block_rows0() { return C::INP > C::W ? C::INP : C::W; }
+
 template <class C, int BT>
 __host__ __device__ constexpr int block_eval_smem_bytes() {
-    return (C::TSIZE + (C::INP + 2 * C::W) * block_rs(BT)) * (int)sizeof(float);
+    return (C::TSIZE + (block_rows0<C>() + C::W) * block_rs(BT)) * (int)sizeof(float);
 }
 
 // encoding of sample column s (Eq. 1) split into NH parts (1 or 2 threads per sample): part 0
@@ -250,8 +254,21 @@ __device__ __forceinline__ void block_layer(const float *Wt, const float *b, con
                 softplus_f32(acc[i][j4 + 2], beta, inv_beta), softplus_f32(acc[i][j4 + 3], beta, inv_beta));
 }
 
+// the block's next tile: the next of its own contiguous run (static), or the round's next (dynamic)
+__device__ __forceinline__ int claim_tile(const WaveArgs &a, int n_tiles, int &next_static, int end_static) {
+    if (a.static_tiles) return next_static < end_static ? next_static++ : n_tiles;
+    return atomicAdd(&a.ctrl->next_tile, 1);
+}
+
+// blocks of a tile kernel that fit on one SM by shared memory (at most 4): the register budget
+template <class C, int BT>
+__host__ __device__ constexpr int block_min_blocks() {
+    constexpr int by_smem = (227 * 1024) / (block_eval_smem_bytes<C, BT>() + 2048);
+    return by_smem < 1 ? 1 : (by_smem > 4 ? 4 : by_smem);
+}
+
 template <class C, int BT, int NT>
-__global__ void __launch_bounds__(NT) wave_eval_block_kernel(GridView g, WaveArgs a, int cur) {
+__global__ void __launch_bounds__(NT, block_min_blocks<C, BT>()) wave_eval_block_kernel(GridView g, WaveArgs a, int cur) {
     constexpr int BRS = block_rs(BT), NH = NT / BT;  // NH threads encode one sample
     extern __shared__ __align__(128) float dyn[];
     __shared__ __align__(8) uint64_t bar;
@@ -261,10 +278,9 @@ __global__ void __launch_bounds__(NT) wave_eval_block_kernel(GridView g, WaveArg
     const int n_tiles = a.ctrl->n_tiles_fine;
     if (n_tiles <= 0) return;
     const int tid = threadIdx.x, nxt = cur ^ 1;
+    // the encoding rows A0 are dead after layer 0, so the second activation buffer Q reuses them
     float *wsm = dyn;
-    float *A0 = dyn + C::TSIZE, *P = A0 + C::INP * BRS, *Q = P + C::W * BRS;
-    // encoding pad rows stay zero
-    for (int i = tid; i < (C::INP - C::IN) * BRS; i += NT) A0[C::IN * BRS + i] = 0.f;
+    float *A0 = dyn + C::TSIZE, *P = A0 + block_rows0<C>() * BRS, *Q = A0;
     if (tid == 0) mbar_init(&bar, 1);
     __syncthreads();
     const int per = (n_tiles + gridDim.x - 1) / gridDim.x;
@@ -272,28 +288,28 @@ __global__ void __launch_bounds__(NT) wave_eval_block_kernel(GridView g, WaveArg
     const int end_static = min(n_tiles, next_static + per);
     int cached = -1;
     uint32_t phase = 0;
+    // thread 0 keeps two tiles in flight: the descriptor of the next tile (loaded) and the index of
+    // the one after it (claimed), so that neither the claim nor the load waits at the tile's start
+    int4 nd = make_int4(-1, 0, 0, 0);
+    int nt = n_tiles;
+    unsigned n_eval = 0;  // samples this thread evaluated
+    if (tid == 0) {
+        const int t0 = claim_tile(a, n_tiles, next_static, end_static);
+        if (t0 < n_tiles) nd = a.tiles[t0];
+        nt = claim_tile(a, n_tiles, next_static, end_static);
+    }
     for (;;) {
         if (tid == 0) {
-            int tile = a.static_tiles ? (next_static < end_static ? next_static : n_tiles)
-                                      : atomicAdd(&a.ctrl->next_tile, 1);
-            int c = -1, start = 0, len = 0;
-            if (tile < n_tiles) {
-                int lo = 0, hi = a.NC;  // the cell c with tile_off[c] <= tile < tile_off[c+1]
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (__ldg(a.tile_off + mid) <= tile) lo = mid; else hi = mid;
-                }
-                c = lo;
-                start = __ldg(a.off + lo) + (tile - __ldg(a.tile_off + lo)) * BT;
-                len = min(BT, __ldg(a.off + lo + 1) - start);
-                if (c != cached) bulk_load(wsm, a.wt + (int64_t)c * a.wt_stride, C::TSIZE * sizeof(float), &bar);
-            }
-            s_tile[0] = c;
-            s_tile[1] = start;
-            s_tile[2] = len;
-            s_tile[3] = c != cached;
+            const int4 d = nd;
+            nd = nt < n_tiles ? a.tiles[nt] : make_int4(-1, 0, 0, 0);
+            if (d.x >= 0) nt = claim_tile(a, n_tiles, next_static, end_static);
+            if (d.x >= 0 && d.x != cached)
+                bulk_load(wsm, a.wt + (int64_t)d.x * a.wt_stride, C::TSIZE * sizeof(float), &bar);
+            s_tile[0] = d.x;
+            s_tile[1] = d.y;
+            s_tile[2] = d.z;
+            s_tile[3] = d.x != cached;
         }
-        ++next_static;
         __syncthreads();
         const int c = s_tile[0], start = s_tile[1], len = s_tile[2];
         const bool fresh = s_tile[3] != 0;
@@ -325,6 +341,9 @@ __global__ void __launch_bounds__(NT) wave_eval_block_kernel(GridView g, WaveArg
         {
             const int s = tid & (BT - 1);
             encode_split<C::L, NH, BRS>(A0, s, tid / BT, s_x[0][s], s_x[1][s], s_x[2][s]);
+            if (tid < BT)
+#pragma unroll
+                for (int k = C::IN; k < C::INP; ++k) A0[k * BRS + s] = 0.f;  // encoding pad
         }
         if (fresh) {
             const bool ok = mbar_wait(&bar, phase, 1u << 26);
@@ -352,12 +371,10 @@ __global__ void __launch_bounds__(NT) wave_eval_block_kernel(GridView g, WaveArg
             float d = wsm[C::tbL];
 #pragma unroll 8
             for (int k = 0; k < C::W; ++k) d = fmaf(wsm[C::tdL + k], src[k * BRS + tid], d);
-            {
-                const unsigned n = __popc(__ballot_sync(FULL, active));
-                if ((tid & 31) == 0 && n) atomicAdd(&a.ctrl->samples_f32, (unsigned long long)n);
-            }
-            bool hit = false, emit = false;
+            n_eval += active ? 1u : 0u;
+            bool hit = false, emit = false, pend = false;
             int ncell = -1;
+            float t_eval = t;
             if (active) {
                 ++steps;
                 const bool last_refine = a.coarse && steps - switched >= a.refine_steps;
@@ -369,14 +386,18 @@ __global__ void __launch_bounds__(NT) wave_eval_block_kernel(GridView g, WaveArg
                 } else if (last_refine) {
                     write_miss(a, r, steps);
                 } else {
-                    const float t_eval = t;
                     t += d;
                     if (t > tf || t < t0 || steps >= a.max_steps) {
                         write_miss(a, r, steps);
                     } else {
-                        ncell = advance_ray(g, ray, t, tf);
-                        if (ncell < 0) {
-                            write_miss(a, r, steps);
+                        // an occupied voxel gives the next cell at once; a ray that stepped into empty
+                        // space is left to wave_advance_kernel, so that no lane holds the block in a
+                        // long voxel walk
+                        ncell = advance_fast(g, ray, t);
+                        if (ncell == -2) {
+                            pend = true;
+                            a.t_ray[r] = t;
+                            a.steps_ray[r] = steps;
                         } else if (cycles && cycle_step(hist, t_eval, t)) {
                             write_miss(a, r, a.max_steps);
                             ncell = -1;
@@ -397,8 +418,17 @@ __global__ void __launch_bounds__(NT) wave_eval_block_kernel(GridView g, WaveArg
                 a.qcell[nxt][qp] = ncell;
             }
             warp_count_cells(a.count[nxt], emit, ncell);
+            const int pp = warp_append(&a.ctrl->n_pend, pend);
+            if (pend) {
+                a.pend_r[pp] = r;
+                a.pend_t[pp] = t_eval;
+            }
         }
         __syncthreads();
+    }
+    if (tid < BT) {  // evaluated samples, one atomic per warp
+        const unsigned long long n = warp_sum_u64(n_eval);
+        if ((tid & 31) == 0 && n) atomicAdd(&a.ctrl->samples_f32, n);
     }
 }
 
@@ -715,21 +745,31 @@ cudaError_t launch_wave_gen_cfg(const GridView &g, const WaveArgs &a, cudaStream
     wave_gen_kernel<C><<<grid, 128, 0, s>>>(g, a);
     return cudaGetLastError();
 }
-template <class C, int BT>
-int block_eval_per_sm() {
-    constexpr int smem = block_eval_smem_bytes<C, BT>();
-    const int by_smem = (228 * 1024) / (smem + 2048);
-    return by_smem < 1 ? 1 : (by_smem > 3 ? 3 : by_smem);
+// Resident blocks per SM of a kernel with `smem` bytes of dynamic shared memory (registers and shared
+// memory both count), after allowing it the largest shared-memory carve-out; asked once per kernel.
+template <class K>
+cudaError_t resident_blocks(K kernel, int threads, int smem, std::atomic<int> &cache, int &out) {
+    out = cache.load();
+    if (out > 0) return cudaSuccess;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out, kernel, threads, smem)) != cudaSuccess)
+        return e;
+    if (out < 1) out = 1;
+    cache.store(out);
+    return cudaSuccess;
 }
 
 template <class C, int BT, int NT>
 cudaError_t launch_block_eval(const GridView &g, const WaveArgs &a, int cur, int sm_count, cudaStream_t s) {
     constexpr int smem = block_eval_smem_bytes<C, BT>();
     static_assert(smem <= 220 * 1024, "block tile does not fit in shared memory");
-    cudaError_t e = cudaFuncSetAttribute(wave_eval_block_kernel<C, BT, NT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    static std::atomic<int> per_sm{0};
+    int nb = 0;
+    cudaError_t e = resident_blocks(wave_eval_block_kernel<C, BT, NT>, NT, smem, per_sm, nb);
     if (e != cudaSuccess) return e;
-    wave_eval_block_kernel<C, BT, NT><<<sm_count * block_eval_per_sm<C, BT>(), NT, smem, s>>>(g, a, cur);
+    wave_eval_block_kernel<C, BT, NT><<<sm_count * nb, NT, smem, s>>>(g, a, cur);
     return cudaGetLastError();
 }
 
@@ -755,21 +795,12 @@ cudaError_t launch_wave_eval_cfg(const GridView &g, const WaveArgs &a, int cur, 
     // one-warp blocks, as many as fit on the SMs at once (each holds one cell's weights)
     constexpr int tsmem = tail_smem_floats<C>() * (int)sizeof(float);
     static_assert(tsmem <= 64 * 1024, "tail weight slot does not fit");
-    static std::atomic<int> tail_blocks_per_sm{0};  // the same for every launch
-    int tail_blocks = tail_blocks_per_sm.load();
-    if (tail_blocks == 0) {
-        if ((e = cudaFuncSetAttribute(wave_tail_warp_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      tsmem)) != cudaSuccess ||
-            (e = cudaFuncSetAttribute(wave_tail_warp_kernel<C>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                      100)) != cudaSuccess ||
-            (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&tail_blocks, wave_tail_warp_kernel<C>, 32,
-                                                               tsmem)) != cudaSuccess)
-            return e;
-        if (tail_blocks < 1) tail_blocks = 1;
-        tail_blocks_per_sm.store(tail_blocks);
-    }
+    static std::atomic<int> tail_per_sm{0};
+    int tail_blocks = 0;
+    if ((e = resident_blocks(wave_tail_warp_kernel<C>, 32, tsmem, tail_per_sm, tail_blocks)) != cudaSuccess) return e;
     wave_tail_warp_kernel<C><<<sm_count * tail_blocks, 32, tsmem, s>>>(g, a, cur);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_wave_advance(g, a, cur, sm_count, s);
 }
 
 #ifdef KNS_W

@@ -27,6 +27,12 @@ __device__ __forceinline__ unsigned lanemask_lt() {
 
 // Appends the predicated lanes of a warp to a queue; returns this lane's slot (or -1).
 // Must be called by all 32 lanes.
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned v) {
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+    return x;
+}
 __device__ __forceinline__ int warp_append(int *counter, bool pred) {
     const unsigned m = __ballot_sync(FULL, pred);
     if (!m) return -1;
@@ -147,6 +153,20 @@ __device__ __forceinline__ int advance_ray(const GridView &g, const Ray &r, floa
             const int f = g.occ_per_cell;
             return vx / f + g.N * (vy / f + g.N * (vz / f));
         }
+    }
+    return cell_of(g, x, y, z);
+}
+
+// The first part of advance_ray: the cell of x(t) when its occupancy voxel is occupied (or there is no
+// mask), or -2 when the voxel is empty and the ray needs the DDA (advance_ray then gives the same
+// result as from the start).
+__device__ __forceinline__ int advance_fast(const GridView &g, const Ray &r, float t) {
+    const float x = fmaf(t, r.wx, r.ox), y = fmaf(t, r.wy, r.oy), z = fmaf(t, r.wz, r.oz);
+    if (g.occ) {
+        const int vx = grid_axis(x, g.bmin[0], g.oscale[0], g.occ_res),
+                  vy = grid_axis(y, g.bmin[1], g.oscale[1], g.occ_res),
+                  vz = grid_axis(z, g.bmin[2], g.oscale[2], g.occ_res);
+        if (!occ_test(g.occ, g.occ_res, vx, vy, vz)) return -2;
     }
     return cell_of(g, x, y, z);
 }
