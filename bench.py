@@ -342,9 +342,10 @@ def run_kns(args, rank, world, local_rank):
             kms = st["ms_eval_fp32"]
             warp_tiles = bool(tuning) and tuning.get("block_tiles") == 2
             roof = {"bound": "alu", "peak": fp32_peak, "unit": "TFLOP/s",
-                    "kernel": "wave_eval_kernel" if warp_tiles else "wave_eval_block_kernel",
-                    "kernel_class_note": "time and samples of the evaluation class: tile rounds plus the "
-                                         "warp-per-ray tail kernel", "peak_source": FP32_PEAK_NOTE}
+                    "kernel": ("wave_eval_kernel" if warp_tiles else "wave_eval_block_kernel")
+                              + " + wave_tail_warp_kernel + wave_advance_kernel",
+                    "kernel_class_note": "time and samples of the evaluation class: tile rounds, the "
+                                         "warp-per-ray tail and the empty-voxel advance kernel", "peak_source": FP32_PEAK_NOTE}
         else:
             # dominant kernel: the BF16 tensor-core tile evaluation (wave_eval_bf16_kernel)
             flops = 2.0 * st["samples_bf16"] * mac_trace
@@ -353,7 +354,7 @@ def run_kns(args, rank, world, local_rank):
                     "kernel": "wave_eval_bf16_kernel", "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured)"}
         achieved = flops / (kms * 1e-3) / 1e12 if kms > 0 else 0.0
         launches = st["rounds"]
-        kernel_tag = "%s_%s_%s" % (roof["kernel"], args.precision, args.workload)
+        kernel_tag = "%s_%s_%s" % (roof["kernel"].split()[0], args.precision, args.workload)
         roof.update({"achieved": achieved, "frac": achieved / roof["peak"], "traffic": profile_traffic(kernel_tag),
                      "launches_per_render": launches, "algorithmic_flop_per_render": flops,
                      "kernel_ms_per_render": kms, "flop_per_sample": 2 * mac_trace})
