@@ -26,8 +26,8 @@ struct WaveScratch {
     int *sorted = nullptr, *hits = nullptr;
     int *cellbuf = nullptr;  // count[2], fill[2], off, tile_off (6 * (nc + 1) ints)
     int4 *tiles = nullptr;   // tile descriptors of a round (max_tiles(rays, 2 nc))
-    int *pend_r = nullptr;   // rays waiting for the occupancy DDA
-    float *pend_t = nullptr;
+    int *pend_r[2] = {nullptr, nullptr};  // per round parity: rays waiting for the occupancy DDA
+    float *pend_t[2] = {nullptr, nullptr};
     int *ray_view = nullptr;
     kns::ViewDev *d_views = nullptr;
     kns::WaveCtrl *ctrl = nullptr;
@@ -72,8 +72,11 @@ struct kns_ctx {
     WaveScratch ws;
     TrainScratch ts;
     PtScratch ps;
-    int *h_live = nullptr;                 // pinned: live-sample counts of recent rounds
+    int *h_live = nullptr;                 // pinned: per recent round, its live samples and its
+                                           // predecessor's pending rays (2 ints per round, 4 rounds)
     cudaEvent_t ev_live[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t side = nullptr;           // the advance kernel of round k runs here beside round k + 1
+    cudaEvent_t ev_scan = nullptr, ev_adv[2] = {nullptr, nullptr};
     // last render's statistics
     bool have_stats = false;
     kns_render_stats stats{};
@@ -318,8 +321,10 @@ void free_scratch(WaveScratch &w) {
     cudaFree(w.hits);
     cudaFree(w.cellbuf);
     cudaFree(w.tiles);
-    cudaFree(w.pend_r);
-    cudaFree(w.pend_t);
+    for (int p = 0; p < 2; ++p) {
+        cudaFree(w.pend_r[p]);
+        cudaFree(w.pend_t[p]);
+    }
     cudaFree(w.ray_view);
     cudaFree(w.d_views);
     cudaFree(w.ctrl);
@@ -332,7 +337,7 @@ constexpr int kRenderBlockTiles = 1;        // FP32 renders use block tiles by d
 // Defaults picked by the autotuner on the 16^3 / width-32 grid at 8 x 800x800.
 constexpr int kRenderInnerSteps = 4;
 constexpr int kRenderMinActive = 8;
-constexpr int kRenderTailRays = 262144;  // rounds this small finish one warp per ray
+constexpr int kRenderTailRays = 131072;  // rounds this small finish one warp per ray
 constexpr int kRenderBlocksPerSM = 16;
 constexpr int kRenderStaticTiles = 2;
 
@@ -382,8 +387,10 @@ kns_status ensure_scratch(kns_ctx *ctx, int64_t rays, int nc, int cams) {
     alloc(&w.hits, sizeof(int) * R);
     alloc(&w.cellbuf, sizeof(int) * 6 * (size_t)(NC + 1));
     alloc(&w.tiles, sizeof(int4) * (size_t)kns::max_tiles(R, 2 * NC));
-    alloc(&w.pend_r, sizeof(int) * R);
-    alloc(&w.pend_t, sizeof(float) * R);
+    for (int p = 0; p < 2; ++p) {
+        alloc(&w.pend_r[p], sizeof(int) * R);
+        alloc(&w.pend_t[p], sizeof(float) * R);
+    }
     alloc(&w.ray_view, sizeof(int) * R);
     alloc(&w.d_views, sizeof(kns::ViewDev) * NCAM);
     alloc(&w.ctrl, sizeof(kns::WaveCtrl));
@@ -513,18 +520,23 @@ kns_status kns_create(int device, kns_ctx **out) {
         return cuda_err(nullptr, e, "cudaMalloc(status)");
     }
     if ((e = cudaMemset(c->d_status, 0, sizeof(int))) != cudaSuccess ||
-        (e = cudaHostAlloc((void **)&c->h_live, 4 * sizeof(int), cudaHostAllocDefault)) != cudaSuccess) {
+        (e = cudaHostAlloc((void **)&c->h_live, 8 * sizeof(int), cudaHostAllocDefault)) != cudaSuccess) {
         cudaFree(c->d_status);
         delete c;
         return cuda_err(nullptr, e, "context set-up");
     }
-    for (int i = 0; i < 4; ++i) {
-        if ((e = cudaEventCreateWithFlags(&c->ev_live[i], cudaEventDisableTiming)) != cudaSuccess) {
-            cudaFree(c->d_status);
-            cudaFreeHost(c->h_live);
-            delete c;
-            return cuda_err(nullptr, e, "cudaEventCreate");
-        }
+    cudaEvent_t *evs[7] = {&c->ev_live[0], &c->ev_live[1], &c->ev_live[2], &c->ev_live[3], &c->ev_scan,
+                           &c->ev_adv[0], &c->ev_adv[1]};
+    for (cudaEvent_t *ev : evs)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        for (cudaEvent_t *ev : evs)
+            if (*ev) cudaEventDestroy(*ev);
+        cudaFree(c->d_status);
+        cudaFreeHost(c->h_live);
+        delete c;
+        return cuda_err(nullptr, e, "context events and stream");
     }
     *out = c;
     return KNS_OK;
@@ -544,6 +556,10 @@ void kns_destroy(kns_ctx *ctx) {
         cudaFreeHost(ctx->h_live);
         for (int i = 0; i < 4; ++i)
             if (ctx->ev_live[i]) cudaEventDestroy(ctx->ev_live[i]);
+        if (ctx->ev_scan) cudaEventDestroy(ctx->ev_scan);
+        for (cudaEvent_t ev : ctx->ev_adv)
+            if (ev) cudaEventDestroy(ev);
+        if (ctx->side) cudaStreamDestroy(ctx->side);
         for (cudaEvent_t ev : ctx->ev_pool) cudaEventDestroy(ev);
     }
     delete ctx;
@@ -886,8 +902,10 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
     a.sorted = w.sorted;
     a.hits = w.hits;
     a.tiles = w.tiles;
-    a.pend_r = w.pend_r;
-    a.pend_t = w.pend_t;
+    for (int p = 0; p < 2; ++p) {
+        a.pend_r[p] = w.pend_r[p];
+        a.pend_t[p] = w.pend_t[p];
+    }
     a.count[0] = w.cellbuf;
     a.count[1] = w.cellbuf + (nkeys + 1);
     a.fill[0] = w.cellbuf + 2 * (nkeys + 1);
@@ -904,14 +922,23 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
         timing_end(ctx, tm, s);
     }
     const int eval_blocks = ctx->sm_count * cfg.blocks_per_sm, scatter_blocks = ctx->sm_count * 4;
-    // Rounds: at most max_steps (each live ray takes >= 1 step per round).  The host reads the
-    // live count of round k-2 before launching round k and stops once a round was empty, so it
-    // runs at most two rounds ahead of the device.
-    for (int k = 0; k < max_steps && e == cudaSuccess; ++k) {
+    // Rounds.  A ray takes one step per round, except that a step into an empty occupancy voxel
+    // puts it on its round's pending list: the advance kernel of round k walks those rays to their
+    // next occupied voxel on the side stream while round k + 1 runs (after round k + 1's scan has
+    // cleared the counters it adds to) and they rejoin in round k + 2, whose scan waits for it.  So a
+    // ray's budget of max_steps steps takes at most 2 max_steps rounds.  The host reads, for round
+    // k - 2, its live count and round k - 3's pending count before launching round k, and stops when
+    // both are zero (rounds k - 1 and k then hold nothing), so it runs at most two rounds ahead.
+    int last_adv = -1;  // the last round whose advance kernel was launched
+    for (int k = 0; k < 2 * max_steps + 2 && e == cudaSuccess; ++k) {
         const int cur = k & 1;
         if (k >= 2) {
             e = cudaEventSynchronize(ctx->ev_live[(k - 2) & 3]);
-            if (e != cudaSuccess || ctx->h_live[(k - 2) & 3] == 0) break;
+            const int *hl = ctx->h_live + 2 * ((k - 2) & 3);
+            if (e != cudaSuccess || (hl[0] == 0 && hl[1] == 0)) break;
+            // round k - 2's advance added to this round's counters
+            e = cudaStreamWaitEvent(s, ctx->ev_adv[k & 1], 0);
+            if (e != cudaSuccess) break;
         }
         ++ctx->stats.rounds;
         // block tiles: the sort cuts tiles of the size the evaluation kernel takes
@@ -919,9 +946,18 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
         else if (cfg.block_mode == 3) a.btile = 256;
         int tm = timing_begin(ctx, cfg.timing, kTSort, s);
         e = kns::launch_wave_scan(a, cur, s);
+        int *hl = ctx->h_live + 2 * (k & 3);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hl, &w.ctrl->n_live[cur], sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(ctx->h_live + (k & 3), &w.ctrl->n_live[cur], sizeof(int), cudaMemcpyDeviceToHost, s);
+            e = cudaMemcpyAsync(hl + 1, &w.ctrl->n_pend[cur ^ 1], sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_live[k & 3], s);
+        if (e == cudaSuccess && k >= 1) {  // round k - 1's pending rays, beside this round
+            e = cudaEventRecord(ctx->ev_scan, s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_scan, 0);
+            if (e == cudaSuccess) e = kns::launch_wave_advance(grid->view, a, cur ^ 1, ctx->sm_count, ctx->side);
+            if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_adv[cur ^ 1], ctx->side);
+            if (e == cudaSuccess) last_adv = k - 1;
+        }
         if (e == cudaSuccess) e = kns::launch_wave_scatter(a, cur, scatter_blocks, s);
         timing_end(ctx, tm, s);
         tm = timing_begin(ctx, cfg.timing, kTEvalF32, s);
@@ -934,6 +970,8 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
             timing_end(ctx, tm, s);
         }
     }
+    // the side stream's last advance joins before the shading (it found nothing: the rounds ended)
+    if (e == cudaSuccess && last_adv >= 0) e = cudaStreamWaitEvent(s, ctx->ev_adv[last_adv & 1], 0);
     if (e == cudaSuccess) {
         const int tm = timing_begin(ctx, cfg.timing, kTShade, s);
         // hits sorted by cell, shaded on block tiles
@@ -1289,8 +1327,10 @@ extern "C" kns_status kns_render_noalloc(kns_ctx *ctx, const kns_grid *grid, con
     kns::ViewDev *d_views = (kns::ViewDev *)take(kNoAllocViewBuf);
     a.ctrl = (kns::WaveCtrl *)take(kNoAllocCtrlBuf);
     a.tiles = (int4 *)take(kNoAllocTileBuf);
-    a.pend_r = (int *)take(kNoAllocRayBuf);
-    a.pend_t = (float *)take(kNoAllocRayBuf);
+    // warp tiles step every ray to its next occupied voxel themselves: nothing goes on the pending
+    // lists, which share one buffer pair
+    a.pend_r[0] = a.pend_r[1] = (int *)take(kNoAllocRayBuf);
+    a.pend_t[0] = a.pend_t[1] = (float *)take(kNoAllocRayBuf);
     a.count[0] = cellbuf;
     a.count[1] = cellbuf + (NC + 1);
     a.fill[0] = cellbuf + 2 * (NC + 1);
@@ -1338,11 +1378,12 @@ extern "C" kns_status kns_render_noalloc(kns_ctx *ctx, const kns_grid *grid, con
         const int cur = k & 1;
         if (k >= 2) {
             e = cudaEventSynchronize(ctx->ev_live[(k - 2) & 3]);
-            if (e != cudaSuccess || ctx->h_live[(k - 2) & 3] == 0) break;
+            if (e != cudaSuccess || ctx->h_live[2 * ((k - 2) & 3)] == 0) break;
         }
         e = kns::launch_wave_scan(a, cur, s);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(ctx->h_live + (k & 3), &a.ctrl->n_live[cur], sizeof(int), cudaMemcpyDeviceToHost, s);
+            e = cudaMemcpyAsync(ctx->h_live + 2 * (k & 3), &a.ctrl->n_live[cur], sizeof(int), cudaMemcpyDeviceToHost,
+                                s);
         if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_live[k & 3], s);
         if (e == cudaSuccess) e = kns::launch_wave_scatter(a, cur, scatter_blocks, s);
         if (e == cudaSuccess) e = kns::launch_wave_eval(grid->shape, grid->view, a, cur, eval_blocks, 0, ctx->sm_count, s);

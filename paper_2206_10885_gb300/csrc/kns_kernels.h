@@ -22,7 +22,7 @@ struct WaveCtrl {
     int tail;          // 1: the current round is small enough to finish one warp per ray
     int n_tiles_fine;  // tiles of FP32 samples (keys < NC); BF16 tiles follow them
     int next_tile_bf;  // dynamic tile counter of the BF16 tiles
-    int n_pend;        // rays of the current round whose next position lies in an empty voxel
+    int n_pend[2];     // rays a round (by parity) left in an empty voxel (its pending list)
     unsigned long long samples_f32;   // SDF evaluations in FP32 (tiles and the tail)
     unsigned long long samples_bf16;  // SDF evaluations in BF16 tiles
     unsigned long long samples_tail;  // the part of samples_f32 evaluated by the one-warp-per-ray tail
@@ -74,16 +74,18 @@ struct WaveArgs {
     int *count[2], *fill[2];  // per-cell sample counts and scatter cursors
     int *off, *tile_off;      // NC+1 exclusive scans: samples and tiles per cell
     int4 *tiles;              // per tile of the round: key, first sorted sample, samples (max_tiles entries)
-    int *pend_r;              // rays waiting for the occupancy DDA (n_pend of them) ...
-    float *pend_t;            // ... and the position each was last evaluated at
+    int *pend_r[2];           // per round parity: rays waiting for the occupancy DDA ...
+    float *pend_t[2];         // ... and the position each was last evaluated at
     WaveCtrl *ctrl;
 };
 
 // Per-configuration launchers (explicitly instantiated, one object file per configuration).
 template <class C>
 cudaError_t launch_wave_gen_cfg(const GridView &g, const WaveArgs &a, cudaStream_t s);
-// After a round's evaluation: the rays it left in empty voxels walk to their next occupied voxel.
-cudaError_t launch_wave_advance(const GridView &g, const WaveArgs &a, int cur, int sm_count, cudaStream_t s);
+// The rays round k left in empty voxels (pending list of parity p = k & 1) walk to their next
+// occupied voxel and join the queue, counts and live counter of parity p: round k + 2's input.  Runs
+// beside round k + 1, after round k + 1's scan has cleared those counters.
+cudaError_t launch_wave_advance(const GridView &g, const WaveArgs &a, int p, int sm_count, cudaStream_t s);
 template <class C>
 cudaError_t launch_wave_eval_cfg(const GridView &g, const WaveArgs &a, int cur, int blocks, int block_tiles,
                                  int sm_count, cudaStream_t s);

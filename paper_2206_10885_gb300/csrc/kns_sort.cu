@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) wave_scan_kernel(WaveArgs a, int
         a.ctrl->n_live[nxt] = 0;
         a.ctrl->next_tile = 0;
         a.ctrl->next_tile_bf = 0;
-        a.ctrl->n_pend = 0;
+        a.ctrl->n_pend[cur] = 0;  // this round's pending list (round k - 2's advance has read it)
     }
     const int n_live = a.ctrl->n_live[cur];
     // a small round is finished one warp per ray (in cell-sorted order)
@@ -232,12 +232,12 @@ cudaError_t launch_hit_sort(const WaveArgs &a, int tile, int sm_count, cudaStrea
 }
 
 // Rays whose last step left them in an empty occupancy voxel: the DDA to the next occupied voxel (or
-// out of the grid: a miss), the cycle test on the position reached, and the emit to the next round --
-// what the tile kernels' advance_ray would have done in place.  One thread per ray: many independent
-// voxel walks hide each other's memory latency.
-__global__ void __launch_bounds__(256) wave_advance_kernel(GridView g, WaveArgs a, int cur) {
-    const int n = a.ctrl->n_pend;
-    const int nxt = cur ^ 1;
+// out of the grid: a miss), the cycle test on the position reached, and the emit -- what the tile
+// kernels' advance_ray would have done in place, one round later.  One thread per ray: many
+// independent voxel walks hide each other's memory latency, and the kernel runs beside the next
+// round's tiles.
+__global__ void __launch_bounds__(256) wave_advance_kernel(GridView g, WaveArgs a, int p) {
+    const int n = a.ctrl->n_pend[p];
     const bool cycles = a.t_hist != nullptr && !a.coarse;
     const int stride = gridDim.x * blockDim.x;
     const int bound = (n + 31) & ~31;  // warp-uniform loop bound
@@ -245,8 +245,8 @@ __global__ void __launch_bounds__(256) wave_advance_kernel(GridView g, WaveArgs 
         bool emit = false;
         int ncell = -1, r = 0;
         if (i < n) {
-            r = a.pend_r[i];
-            const float t_eval = a.pend_t[i];
+            r = a.pend_r[p][i];
+            const float t_eval = a.pend_t[p][i];
             int cam;
             const Ray ray = ray_of(a, r, cam);
             float t0, tf;
@@ -267,17 +267,17 @@ __global__ void __launch_bounds__(256) wave_advance_kernel(GridView g, WaveArgs 
                 }
             }
         }
-        const int qp = warp_append(&a.ctrl->n_live[nxt], emit);
+        const int qp = warp_append(&a.ctrl->n_live[p], emit);
         if (emit) {
-            a.q[nxt][qp] = r;
-            a.qcell[nxt][qp] = ncell;
+            a.q[p][qp] = r;
+            a.qcell[p][qp] = ncell;
         }
-        warp_count_cells(a.count[nxt], emit, ncell);
+        warp_count_cells(a.count[p], emit, ncell);
     }
 }
 
-cudaError_t launch_wave_advance(const GridView &g, const WaveArgs &a, int cur, int sm_count, cudaStream_t s) {
-    wave_advance_kernel<<<sm_count * 4, 256, 0, s>>>(g, a, cur);
+cudaError_t launch_wave_advance(const GridView &g, const WaveArgs &a, int p, int sm_count, cudaStream_t s) {
+    wave_advance_kernel<<<sm_count * 4, 256, 0, s>>>(g, a, p);
     return cudaGetLastError();
 }
 

@@ -391,8 +391,8 @@ __global__ void __launch_bounds__(NT, block_min_blocks<C, BT>()) wave_eval_block
                         write_miss(a, r, steps);
                     } else {
                         // an occupied voxel gives the next cell at once; a ray that stepped into empty
-                        // space is left to wave_advance_kernel, so that no lane holds the block in a
-                        // long voxel walk
+                        // space goes on the round's pending list for wave_advance_kernel, so that no
+                        // lane holds the block in a long voxel walk
                         ncell = advance_fast(g, ray, t);
                         if (ncell == -2) {
                             pend = true;
@@ -418,10 +418,10 @@ __global__ void __launch_bounds__(NT, block_min_blocks<C, BT>()) wave_eval_block
                 a.qcell[nxt][qp] = ncell;
             }
             warp_count_cells(a.count[nxt], emit, ncell);
-            const int pp = warp_append(&a.ctrl->n_pend, pend);
+            const int pp = warp_append(&a.ctrl->n_pend[cur], pend);
             if (pend) {
-                a.pend_r[pp] = r;
-                a.pend_t[pp] = t_eval;
+                a.pend_r[cur][pp] = r;
+                a.pend_t[cur][pp] = t_eval;
             }
         }
         __syncthreads();
@@ -799,8 +799,7 @@ cudaError_t launch_wave_eval_cfg(const GridView &g, const WaveArgs &a, int cur, 
     int tail_blocks = 0;
     if ((e = resident_blocks(wave_tail_warp_kernel<C>, 32, tsmem, tail_per_sm, tail_blocks)) != cudaSuccess) return e;
     wave_tail_warp_kernel<C><<<sm_count * tail_blocks, 32, tsmem, s>>>(g, a, cur);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return launch_wave_advance(g, a, cur, sm_count, s);
+    return cudaGetLastError();
 }
 
 #ifdef KNS_W
