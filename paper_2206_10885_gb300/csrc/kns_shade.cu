@@ -186,17 +186,19 @@ __global__ void __launch_bounds__(STHREADS) shade_block_kernel(GridView g, WaveA
     for (int i = tid; i < L::ROWS * SRS; i += STHREADS) rows[i] = 0.f;
     __syncthreads();
     const int n_tiles = a.ctrl->n_tiles;
+    // a contiguous run of tiles per block, so consecutive tiles mostly share the cell's staged
+    // weights; thread 0 holds the next tile's descriptor (loaded a tile ahead)
+    const int per = (n_tiles + gridDim.x - 1) / gridDim.x;
+    const int t_begin = blockIdx.x * per, t_end = min(n_tiles, t_begin + per);
     int cached = -1;
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    int4 nd = make_int4(-1, 0, 0, 0);
+    if (tid == 0 && t_begin < t_end) nd = a.tiles[t_begin];
+    for (int tile = t_begin; tile < t_end; ++tile) {
         if (tid == 0) {
-            int lo = 0, hi = a.NC;  // the cell c with tile_off[c] <= tile < tile_off[c+1]
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (__ldg(a.tile_off + mid) <= tile) lo = mid; else hi = mid;
-            }
-            s_tile[0] = lo;
-            s_tile[1] = __ldg(a.off + lo) + (tile - __ldg(a.tile_off + lo)) * ST;
-            s_tile[2] = min(ST, __ldg(a.off + lo + 1) - s_tile[1]);
+            s_tile[0] = nd.x;
+            s_tile[1] = nd.y;
+            s_tile[2] = nd.z;
+            if (tile + 1 < t_end) nd = a.tiles[tile + 1];
         }
         __syncthreads();
         const int c = s_tile[0], start = s_tile[1], len = s_tile[2];

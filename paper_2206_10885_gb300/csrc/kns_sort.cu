@@ -160,8 +160,8 @@ cudaError_t launch_wave_scatter(const WaveArgs &a, int cur, int blocks, cudaStre
 
 // ---------------------------------------------------------------- hits by cell (shading tiles)
 // After the last round: the hit list is counting-sorted by the cell of each hit into `sorted`, with
-// off[c] / tile_off[c] (tiles of `tile` hits, the shading kernel's tile) and the tile count in
-// ctrl->n_tiles.  Uses the wave's count[0], fill[0], off, tile_off and sorted buffers, which the
+// off[c] / tile_off[c] (tiles of `tile` hits, the shading kernel's tile), one descriptor per tile in
+// `tiles` and the tile count in ctrl->n_tiles.  Uses the wave's count[0], fill[0], off, tile_off and sorted buffers, which the
 // rounds no longer need.
 __global__ void __launch_bounds__(256) wave_hit_count_kernel(WaveArgs a) {
     const int n = a.ctrl->n_hits;
@@ -192,8 +192,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) wave_hit_scan_kernel(WaveArgs a,
         a.off[c] = run_s;
         a.tile_off[c] = run_t;
         a.fill[0][c] = 0;
+        for (int i = 0; i < n; i += tile) a.tiles[run_t++] = make_int4(c, run_s + i, min(tile, n - i), 0);
         run_s += n;
-        run_t += (n + tile - 1) / tile;
     }
     if (threadIdx.x == SCAN_THREADS - 1) {
         a.off[NC] = incl_s;
