@@ -114,8 +114,10 @@ typedef struct kns_render_opts {
                              (<= 0: 64); the ray is a hit at the first |d| < eps, or at the last of them if
                              |d| < eps_coarse there, else a miss */
     /* tuning (0 = default) */
-    int32_t inner_steps;   /* sphere steps a tile may take per round while its rays stay in its cells (1..1024) */
-    int32_t min_active;    /* a 16-ray warp tile with fewer live rays hands them to the next round (1..16) */
+    int32_t inner_steps;   /* evaluations a tile may make per round while its rays stay in its cell (1..1024;
+                              default 4 for warp tiles, 2 for block tiles) */
+    int32_t min_active;    /* a tile continues only while at least this many of its rays stay in its cell
+                              (1..256; a warp tile holds 16; default 8 for warp tiles, 16 for block tiles) */
     int32_t tail_rays;     /* a round with at most this many rays is finished one warp per ray (>= 0; -1: never) */
     int32_t blocks_per_sm; /* evaluation blocks (one warp each) launched per SM (1..64) */
     int32_t static_tiles;  /* 1: each block takes a contiguous run of tiles; 2: tiles handed out dynamically */
@@ -123,7 +125,7 @@ typedef struct kns_render_opts {
     int32_t block_tiles;   /* FP32 evaluation (also the refinement phase of KNS_BF16): 1 = 128-sample tiles per
                               256-thread block (block GEMMs); 3 = 256-sample tiles per 256 threads; 4 = 128-sample
                               tiles per 128 threads; 2 = 16-sample tiles per warp (in-tile stepping, min_active);
-                              0 = default (1) */
+                              0 = default (4) */
 } kns_render_opts;
 
 /* Counters of the last kns_render on a context (kns_get_render_stats). */

@@ -19,8 +19,8 @@ DEFAULT_CACHE = os.path.join(_HERE, "_tune_cache.json")
 # candidate values of each knob (0 would mean the library default)
 SPACE = {
     "block_tiles": (1, 2, 3, 4),
-    "inner_steps": (1, 4),
-    "min_active": (1, 8),
+    "inner_steps": (1, 2, 4),
+    "min_active": (1, 8, 32),
     "static_tiles": (1, 2),
     "blocks_per_sm": (8, 16, 32),
     "tail_rays": (-1, 131072, 262144, 524288),
@@ -29,7 +29,7 @@ SPACE = {
 
 def _key(grid, n_cams, W, H, max_steps, precision, device_name):
     d = grid.desc
-    return "|".join(str(v) for v in ("v2", device_name, d.N, d.sdf_width, d.sdf_hidden, d.pe_pos_L, d.occ_res,
+    return "|".join(str(v) for v in ("v3", device_name, d.N, d.sdf_width, d.sdf_hidden, d.pe_pos_L, d.occ_res,
                                       n_cams, W, H, max_steps, precision))
 
 
@@ -59,9 +59,8 @@ def _store(key, value):
     os.replace(tmp, path)
 
 
-# knobs that only the 16-sample warp tiles read (block tiles take one sphere step per round and size
-# their own grid)
-WARP_ONLY = {"inner_steps": 1, "min_active": 1, "blocks_per_sm": 16}
+# knobs that only the 16-sample warp tiles read (block tiles size their own grid)
+WARP_ONLY = {"blocks_per_sm": 16}
 
 
 def candidates(space=None):

@@ -333,10 +333,12 @@ void free_scratch(WaveScratch &w) {
 
 // Render tiling: samples per tile (a warp tile, or a 256-thread block tile).
 constexpr int kRenderBlockTile = 16;        // samples per warp tile
-constexpr int kRenderBlockTiles = 1;        // FP32 renders use block tiles by default
+constexpr int kRenderBlockTiles = 4;        // FP32 renders use 128-sample block tiles of 128 threads
 // Defaults picked by the autotuner on the 16^3 / width-32 grid at 8 x 800x800.
 constexpr int kRenderInnerSteps = 4;
 constexpr int kRenderMinActive = 8;
+constexpr int kRenderBlockInnerSteps = 2;  // block tiles: a second evaluation of a tile in the round ...
+constexpr int kRenderBlockMinActive = 16;  // ... while at least 16 of its rays stay in its cell
 constexpr int kRenderTailRays = 131072;  // rounds this small finish one warp per ray
 constexpr int kRenderBlocksPerSM = 16;
 constexpr int kRenderStaticTiles = 2;
@@ -820,12 +822,15 @@ kns_status resolve_opts(kns_ctx *ctx, const kns_render_opts *opts, float eps, Re
     if (c.bf16 && !(c.eps_coarse >= eps && std::isfinite(c.eps_coarse)))
         return set_err(ctx, KNS_ERR_INVALID_ARG, "eps_coarse must be finite and >= eps");
     auto knob = [](int32_t v, int32_t def) { return v == 0 ? def : v; };
-    c.inner_steps = opts ? knob(opts->inner_steps, kRenderInnerSteps) : kRenderInnerSteps;
-    c.min_active = opts ? knob(opts->min_active, kRenderMinActive) : kRenderMinActive;
+    const int bt0 = opts ? knob(opts->block_tiles, kRenderBlockTiles) : kRenderBlockTiles;
+    const int def_inner = bt0 == 2 ? kRenderInnerSteps : kRenderBlockInnerSteps;
+    const int def_min = bt0 == 2 ? kRenderMinActive : kRenderBlockMinActive;
+    c.inner_steps = opts ? knob(opts->inner_steps, def_inner) : def_inner;
+    c.min_active = opts ? knob(opts->min_active, def_min) : def_min;
     c.tail_rays = opts ? knob(opts->tail_rays, kRenderTailRays) : kRenderTailRays;
     c.blocks_per_sm = opts ? knob(opts->blocks_per_sm, kRenderBlocksPerSM) : kRenderBlocksPerSM;
     c.static_tiles = (opts ? knob(opts->static_tiles, kRenderStaticTiles) : kRenderStaticTiles) == 1;
-    if (c.inner_steps < 1 || c.inner_steps > 1024 || c.min_active < 1 || c.min_active > 16 || c.tail_rays < -1 ||
+    if (c.inner_steps < 1 || c.inner_steps > 1024 || c.min_active < 1 || c.min_active > 256 || c.tail_rays < -1 ||
         c.blocks_per_sm < 1 || c.blocks_per_sm > 64 || (opts && (opts->static_tiles < 0 || opts->static_tiles > 2)) ||
         (opts && (opts->block_tiles < 0 || opts->block_tiles > 4)))
         return set_err(ctx, KNS_ERR_INVALID_ARG, "render tuning field out of range");

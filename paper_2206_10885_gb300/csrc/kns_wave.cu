@@ -332,97 +332,122 @@ __global__ void __launch_bounds__(NT, block_min_blocks<C, BT>()) wave_eval_block
             ray = ray_of(a, r, cam);
             clip_box(g, ray, t0, tf);
         }
-        if (tid < BT) {
-            s_x[0][tid] = active ? fmaf(t, ray.wx, ray.ox) : 0.f;
-            s_x[1][tid] = active ? fmaf(t, ray.wy, ray.oy) : 0.f;
-            s_x[2][tid] = active ? fmaf(t, ray.wz, ray.oz) : 0.f;
-        }
-        __syncthreads();
-        {
-            const int s = tid & (BT - 1);
-            encode_split<C::L, NH, BRS>(A0, s, tid / BT, s_x[0][s], s_x[1][s], s_x[2][s]);
-            if (tid < BT)
-#pragma unroll
-                for (int k = C::IN; k < C::INP; ++k) A0[k * BRS + s] = 0.f;  // encoding pad
-        }
-        if (fresh) {
-            const bool ok = mbar_wait(&bar, phase, 1u << 26);
-            phase ^= 1u;
-            if (__syncthreads_or(!ok)) {  // the weights never landed: report and leave
-                if (tid == 0) atomicCAS(a.status, 0, (int)6 /* KNS_ERR_TIMEOUT */);
-                return;
+        // Up to inner_steps evaluations of the tile: a sample whose step keeps it in this cell (an
+        // emit to the same key) is evaluated again at once, while at least min_active of them do;
+        // the others, and all of them at the last evaluation, leave as below.
+        bool fresh_wait = fresh;
+        for (int it = 0;; ++it) {
+            if (tid < BT) {
+                s_x[0][tid] = active ? fmaf(t, ray.wx, ray.ox) : 0.f;
+                s_x[1][tid] = active ? fmaf(t, ray.wy, ray.oy) : 0.f;
+                s_x[2][tid] = active ? fmaf(t, ray.wz, ray.oz) : 0.f;
             }
-        } else {
             __syncthreads();
-        }
-        block_layer<C::INP, C::W, BT, NT>(wsm + C::tW0, wsm + C::tb0, A0, P, g.beta, g.inv_beta);
-        float *src = P, *dst = Q;
+            {
+                const int s = tid & (BT - 1);
+                encode_split<C::L, NH, BRS>(A0, s, tid / BT, s_x[0][s], s_x[1][s], s_x[2][s]);
+                if (tid < BT)
 #pragma unroll
-        for (int l = 1; l < C::H; ++l) {
+                    for (int k = C::IN; k < C::INP; ++k) A0[k * BRS + s] = 0.f;  // encoding pad
+            }
+            if (fresh_wait) {
+                const bool ok = mbar_wait(&bar, phase, 1u << 26);
+                phase ^= 1u;
+                fresh_wait = false;
+                if (__syncthreads_or(!ok)) {  // the weights never landed: report and leave
+                    if (tid == 0) atomicCAS(a.status, 0, (int)6 /* KNS_ERR_TIMEOUT */);
+                    return;
+                }
+            } else {
+                __syncthreads();
+            }
+            block_layer<C::INP, C::W, BT, NT>(wsm + C::tW0, wsm + C::tb0, A0, P, g.beta, g.inv_beta);
+            float *src = P, *dst = Q;
+#pragma unroll
+            for (int l = 1; l < C::H; ++l) {
+                __syncthreads();
+                block_layer<C::W, C::W, BT, NT>(wsm + C::tWl(l), wsm + C::tbl(l), src, dst, g.beta, g.inv_beta);
+                float *tmp = src;
+                src = dst;
+                dst = tmp;
+            }
             __syncthreads();
-            block_layer<C::W, C::W, BT, NT>(wsm + C::tWl(l), wsm + C::tbl(l), src, dst, g.beta, g.inv_beta);
-            float *tmp = src;
-            src = dst;
-            dst = tmp;
-        }
-        __syncthreads();
-        if (tid < BT) {
-            // the d row: bias first, then one sequential FMA chain over k
-            float d = wsm[C::tbL];
-#pragma unroll 8
-            for (int k = 0; k < C::W; ++k) d = fmaf(wsm[C::tdL + k], src[k * BRS + tid], d);
-            n_eval += active ? 1u : 0u;
-            bool hit = false, emit = false, pend = false;
-            int ncell = -1;
+            // outcome of this evaluation: 0 none (inactive), 1 hit, 2 miss (written), 3 pending,
+            // 4 emit to ncell
+            int outcome = 0, ncell = -1;
             float t_eval = t;
-            if (active) {
-                ++steps;
-                const bool last_refine = a.coarse && steps - switched >= a.refine_steps;
-                if (fabsf(d) < a.eps || (last_refine && fabsf(d) < a.eps_coarse)) {
-                    hit = true;
-                    a.cell_ray[r] = c;
-                    a.t_ray[r] = t;
-                    a.steps_ray[r] = steps;
-                } else if (last_refine) {
-                    write_miss(a, r, steps);
-                } else {
-                    t += d;
-                    if (t > tf || t < t0 || steps >= a.max_steps) {
+            if (tid < BT) {
+                // the d row: bias first, then one sequential FMA chain over k
+                float d = wsm[C::tbL];
+#pragma unroll 8
+                for (int k = 0; k < C::W; ++k) d = fmaf(wsm[C::tdL + k], src[k * BRS + tid], d);
+                n_eval += active ? 1u : 0u;
+                if (active) {
+                    ++steps;
+                    const bool last_refine = a.coarse && steps - switched >= a.refine_steps;
+                    if (fabsf(d) < a.eps || (last_refine && fabsf(d) < a.eps_coarse)) {
+                        outcome = 1;
+                    } else if (last_refine) {
+                        outcome = 2;
                         write_miss(a, r, steps);
                     } else {
-                        // an occupied voxel gives the next cell at once; a ray that stepped into empty
-                        // space goes on the round's pending list for wave_advance_kernel, so that no
-                        // lane holds the block in a long voxel walk
-                        ncell = advance_fast(g, ray, t);
-                        if (ncell == -2) {
-                            pend = true;
-                            a.t_ray[r] = t;
-                            a.steps_ray[r] = steps;
-                        } else if (cycles && cycle_step(hist, t_eval, t)) {
-                            write_miss(a, r, a.max_steps);
-                            ncell = -1;
+                        t += d;
+                        if (t > tf || t < t0 || steps >= a.max_steps) {
+                            outcome = 2;
+                            write_miss(a, r, steps);
                         } else {
-                            emit = true;
-                            a.t_ray[r] = t;
-                            a.steps_ray[r] = steps;
-                            if (cycles) a.t_hist[r] = hist;
+                            // an occupied voxel gives the next cell at once; a ray that stepped into
+                            // empty space goes on the round's pending list for wave_advance_kernel, so
+                            // that no lane holds the block in a long voxel walk
+                            ncell = advance_fast(g, ray, t);
+                            if (ncell == -2) {
+                                outcome = 3;
+                            } else if (cycles && cycle_step(hist, t_eval, t)) {
+                                outcome = 2;
+                                write_miss(a, r, a.max_steps);
+                                ncell = -1;
+                            } else {
+                                outcome = 4;
+                            }
                         }
                     }
                 }
             }
-            const int hp = warp_append(&a.ctrl->n_hits, hit);
-            if (hit) a.hits[hp] = r;
-            const int qp = warp_append(&a.ctrl->n_live[nxt], emit);
-            if (emit) {
-                a.q[nxt][qp] = r;
-                a.qcell[nxt][qp] = ncell;
+            // samples that stay in this cell are evaluated again while enough of them do
+            const bool cand = outcome == 4 && ncell == c && it + 1 < a.inner_steps;
+            const int n_cand = __syncthreads_count(cand);
+            const bool again = n_cand > 0 && n_cand >= a.min_active;
+            const bool stay = cand && again;
+            if (tid < BT) {
+                const bool hit = outcome == 1, emit = outcome == 4 && !stay, pend = outcome == 3;
+                if (hit) {
+                    a.cell_ray[r] = c;
+                    a.t_ray[r] = t;
+                    a.steps_ray[r] = steps;
+                } else if (pend) {
+                    a.t_ray[r] = t;
+                    a.steps_ray[r] = steps;
+                } else if (emit) {
+                    a.t_ray[r] = t;
+                    a.steps_ray[r] = steps;
+                    if (cycles) a.t_hist[r] = hist;
+                }
+                const int hp = warp_append(&a.ctrl->n_hits, hit);
+                if (hit) a.hits[hp] = r;
+                const int qp = warp_append(&a.ctrl->n_live[nxt], emit);
+                if (emit) {
+                    a.q[nxt][qp] = r;
+                    a.qcell[nxt][qp] = ncell;
+                }
+                warp_count_cells(a.count[nxt], emit, ncell);
+                const int pp = warp_append(&a.ctrl->n_pend[cur], pend);
+                if (pend) {
+                    a.pend_r[cur][pp] = r;
+                    a.pend_t[cur][pp] = t_eval;
+                }
+                active = stay;
             }
-            warp_count_cells(a.count[nxt], emit, ncell);
-            const int pp = warp_append(&a.ctrl->n_pend[cur], pend);
-            if (pend) {
-                a.pend_r[cur][pp] = r;
-                a.pend_t[cur][pp] = t_eval;
-            }
+            if (!again) break;
         }
         __syncthreads();
     }

@@ -320,12 +320,15 @@ def test_schedule_knobs_do_not_change_results(kns, ctx):
                        dict(block_tiles=1, static_tiles=1, tail_rays=-1),
                        dict(block_tiles=3, static_tiles=2, tail_rays=4096),
                        dict(block_tiles=3, static_tiles=1, tail_rays=-1),
-                       dict(block_tiles=4, static_tiles=2, tail_rays=-1)]:
+                       dict(block_tiles=4, static_tiles=2, tail_rays=-1),
+                       dict(block_tiles=1, inner_steps=4, min_active=1, tail_rays=-1),
+                       dict(block_tiles=4, inner_steps=3, min_active=40, tail_rays=4096),
+                       dict(block_tiles=3, inner_steps=128, min_active=1, static_tiles=1, tail_rays=-1)]:
             got = gpu_render(kns, ctx, grid, cams, 160, 120, 128, 1e-4, tuning=tuning)
             for k in ref:
                 assert np.array_equal(ref[k], got[k]), (k, tuning)
         with pytest.raises(kns.KnsError):
-            kns.render(ctx, grid, cams, 160, 120, 128, 1e-4, tuning=dict(min_active=17))
+            kns.render(ctx, grid, cams, 160, 120, 128, 1e-4, tuning=dict(min_active=257))
         with pytest.raises(kns.KnsError):
             kns.render(ctx, grid, cams, 160, 120, 128, 1e-4, tuning=dict(block_tiles=5))
     finally:
