@@ -234,7 +234,8 @@ def run_reference(args, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args.workload, desc, cams, W, H, ms, eps, "fp64 oracle"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "%d seeded random rays of the workload over %d steps (%.1f s)"
+                             "sample": "%d rays drawn (seeded, with replacement) from the workload's rays over "
+                                       "%d steps (%.1f s)"
                                        % (total_rays, args.steps, total_s)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -365,7 +366,8 @@ def run_kns(args, rank, world, local_rank):
         if not args.no_cpu_baseline and world == 1:
             v, n, s, cores = oracle_rate(desc, w, cams, W, H, ms, eps, args.cpu_seconds)
             cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": "%d seeded random rays of the %d-ray workload (%.1f s of FP64 oracle work)"
+                   "sample": "%d rays drawn (seeded, with replacement) from the %d rays of the workload "
+                             "(%.1f s of FP64 oracle work)"
                              % (n, n_rays, s)}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
