@@ -1,7 +1,7 @@
 """Autotuner of the render schedule (the tuning fields of kns_render_opts).
 
 The knobs change only how work is scheduled on the device (rounds, in-tile steps, tile hand-out,
-launch width, per-thread tail), never a result; the tests check that renders are bit-identical
+launch width, tail), never a result; the tests check that renders are bit-identical
 across settings.  tune() times each candidate with CUDA events around kns_render, flushing L2
 between repetitions, and returns the fastest setting.  Results are cached per (device, grid shape,
 image shape, precision) in a JSON file next to this module (or the path in KNS_TUNE_CACHE).
