@@ -837,7 +837,6 @@ kns_status resolve_opts(kns_ctx *ctx, const kns_render_opts *opts, float eps, Re
     const int bt = opts ? knob(opts->block_tiles, kRenderBlockTiles) : kRenderBlockTiles;
     c.block_mode = bt == 2 ? 0 : bt;  // BF16 renders: the FP32 refinement tiles
     if (c.tail_rays < 0) c.tail_rays = 0;
-    if (c.bf16) c.tail_rays = 0;  // the one-warp-per-ray tail has no BF16 phase
     c.timing = opts && opts->timing == 1;
     return KNS_OK;
 }

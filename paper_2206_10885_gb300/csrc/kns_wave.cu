@@ -534,19 +534,24 @@ __device__ __forceinline__ float warp_sdf_trace(const float *__restrict__ wsm, f
 }
 
 // A tail round: one warp (one block) per ray, to the end.  Rays come in cell-sorted order (the cell
-// of a ray's position is its sort key); the round's tile counter hands them out.
+// of a ray's position is its sort key); the round's tile counter hands them out.  In a BF16 render
+// the tail takes the rays in the FP32 phase (the keys below NC, sorted first), with the block
+// tiles' refinement rule; the rays still in the BF16 phase stay with wave_eval_bf16_kernel.
 template <class C>
 __global__ void __launch_bounds__(32) wave_tail_warp_kernel(GridView g, WaveArgs a, int cur) {
     extern __shared__ __align__(128) float dyn[];
     __shared__ __align__(8) uint64_t bar;
     if (!a.ctrl->tail) return;
-    const int n = a.ctrl->n_live[cur];
+    // samples with FP32 keys: all of them in an FP32 render; in a BF16 render those sorted before the
+    // first BF16 key (off[] is this round's only when the round has samples)
+    const int n_live = a.ctrl->n_live[cur];
+    const int n = a.coarse ? min(n_live, a.off[a.NC]) : n_live;
     const int lane = threadIdx.x;
     float *wsm = dyn, *xin = dyn + C::TSIZE, *h0 = xin + C::INP, *h1 = h0 + C::W;
     for (int k = C::IN + lane; k < C::INP; k += 32) xin[k] = 0.f;  // encoding pad stays zero
     if (lane == 0) mbar_init(&bar, 1);
     __syncwarp();
-    const bool cycles = a.t_hist != nullptr;  // the tail runs in FP32 renders only
+    const bool cycles = a.t_hist != nullptr && !a.coarse;  // the FP32 phase of BF16 renders keeps none
     int cached = -1;
     uint32_t phase = 0;
     unsigned long long nsamples = 0;
@@ -568,6 +573,7 @@ __global__ void __launch_bounds__(32) wave_tail_warp_kernel(GridView g, WaveArgs
         clip_box(g, ray, t0, tf);
         float t = a.t_ray[r];
         int steps = a.steps_ray[r];
+        const int switched = a.coarse ? a.cell_ray[r] : 0;  // step count at the BF16 -> FP32 switch
         float4 hist = cycles ? a.t_hist[r] : no_history();
         bool hit = false;
         for (;;) {
@@ -586,10 +592,12 @@ __global__ void __launch_bounds__(32) wave_tail_warp_kernel(GridView g, WaveArgs
                                               fmaf(t, ray.wz, ray.oz), lane, g.beta, g.inv_beta);
             ++steps;
             ++nsamples;
-            if (fabsf(d) < a.eps) {
+            const bool last_refine = a.coarse && steps - switched >= a.refine_steps;
+            if (fabsf(d) < a.eps || (last_refine && fabsf(d) < a.eps_coarse)) {
                 hit = true;
                 break;
             }
+            if (last_refine) break;
             const float t_eval = t;
             t += d;
             if (t > tf || t < t0 || steps >= a.max_steps) break;
