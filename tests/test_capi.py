@@ -58,6 +58,8 @@ int main(void) {
          offsetof(kns_train_batch, s), offsetof(kns_train_batch, timing));
   printf("%zu %zu\\n", sizeof(kns_train_stats), offsetof(kns_train_stats, ms_fd_backward));
   printf("%zu %zu %zu\\n", sizeof(kns_pt_opts), offsetof(kns_pt_opts, seed), offsetof(kns_pt_opts, zenith));
+  printf("%zu %zu %zu\\n", sizeof(kns_render_stats), offsetof(kns_render_stats, ms_eval_fp32),
+         offsetof(kns_render_stats, samples_tail));
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -70,7 +72,9 @@ int main(void) {
             C.sizeof(capi.kns_train_batch),
             capi.kns_train_batch.n_eik.offset, capi.kns_train_batch.s.offset, capi.kns_train_batch.timing.offset,
             C.sizeof(capi.kns_train_stats), capi.kns_train_stats.ms_fd_backward.offset,
-            C.sizeof(capi.kns_pt_opts), capi.kns_pt_opts.seed.offset, capi.kns_pt_opts.zenith.offset]
+            C.sizeof(capi.kns_pt_opts), capi.kns_pt_opts.seed.offset, capi.kns_pt_opts.zenith.offset,
+            C.sizeof(capi.kns_render_stats), capi.kns_render_stats.ms_eval_fp32.offset,
+            capi.kns_render_stats.samples_tail.offset]
     assert vals == want
 
 
