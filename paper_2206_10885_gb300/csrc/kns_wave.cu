@@ -1,11 +1,13 @@
-// kns_wave.cu -- wavefront render kernels (FP32): ray generation, per-cell tile evaluation, shading.
+// kns_wave.cu -- wavefront render kernels (FP32): ray generation and the per-cell evaluation of
+// the sphere trace (Eq. 2, trace form: d only) -- block tiles (the default), warp tiles, and the
+// one-warp-per-ray tail.  Shading is in kns_shade.cu, the sort and the advance kernel in kns_sort.cu.
 // kns:instantiate (compiled once per grid configuration)
 //
-// Tile evaluation: a warp evaluates the SDF MLP of one cell (Eq. 2, trace form: d only) for up to
-// 16 samples at once as a register-blocked GEMM per layer.  Activations live in shared memory as
-// h[k][s] (k = input unit, s = sample); lane (sg, ng) = (lane / 8, lane % 8) accumulates samples
-// 4sg..4sg+3 against output units ng*W/8 .. ng*W/8 + W/8 - 1, so each shared-memory float4 of
-// activations and each float4 of k-major weights feed 16 (W = 32) or 32 (W = 64) FMAs.
+// Warp tiles: a warp evaluates the SDF MLP of one cell for up to 16 samples at once as a
+// register-blocked GEMM per layer.  Activations live in shared memory as h[k][s] (k = input unit,
+// s = sample); lane (sg, ng) = (lane / 8, lane % 8) accumulates samples 4sg..4sg+3 against output
+// units ng*W/8 .. ng*W/8 + W/8 - 1, so each shared-memory float4 of activations and each float4 of
+// k-major weights feed 16 (W = 32) or 32 (W = 64) FMAs.
 #include <atomic>
 
 #include "kns_wave.cuh"
@@ -164,15 +166,20 @@ __host__ __device__ constexpr int eval_smem_bytes() {
 }
 
 // ---------------------------------------------------------------- block tiles (FP32 renders)
-// Round k with tiles of up to 128 samples of one cell (sort granularity 128): a block of 256
-// threads stages the cell's k-major trace weights with one TMA bulk copy (kept while consecutive
-// tiles share the cell), encodes the samples into shared rows h[k][s] (row stride 132 floats, two
-// threads per sample), and runs each layer as a [W x K] by [K x 128] block GEMM: warp w owns output
-// units w*W/8 .. w*W/8 + W/8 - 1, lane l owns samples 4l .. 4l+3, so per input k one warp-uniform
-// float4 (or two) of weights and one float4 of activations feed 4*W/8 FMAs per thread.  Every output
-// is its bias followed by one FMA per input in ascending order and the d row is one sequential FMA
-// chain, the order of the per-thread evaluator, so d does not depend on the tile shape.  Threads
-// 0..127 then advance their sample (hit, miss, or emit to round k+1 with its next cell).
+// Round k with tiles of up to BT samples of one cell (BT = 128 or 256, the sort's granularity): a
+// block of NT threads takes tiles whose descriptors {cell, first sample, samples} the scan wrote
+// (thread 0 holds the next descriptor and the index after it in flight), stages the cell's k-major
+// trace weights with one TMA bulk copy (kept while consecutive tiles share the cell), encodes the
+// samples into shared rows h[k][s] (row stride BT + 4 floats, NT / BT threads per sample), and runs
+// each layer as a [W x K] by [K x BT] block GEMM: warp w owns a slice of the output units, lane l a
+// run of samples, so per input k one warp-uniform float4 of weights and one float4 of activations
+// feed 16 or more FMAs per thread.  Every output is its bias followed by one FMA per input in
+// ascending order and the d row is one sequential FMA chain, the order of the per-thread evaluator,
+// so d does not depend on the tile shape.  Threads 0..BT-1 then test and step their sample: a hit,
+// a miss, a step into an empty voxel (the round's pending list: wave_advance_kernel walks it to the
+// next occupied voxel), or an emit to round k+1 with its next cell -- unless enough of the tile's
+// samples stay in the cell, in which case those are evaluated again at once (inner_steps,
+// min_active).
 constexpr int BTHREADS = 256;  // default threads per block tile (two per sample in the encoding)
 // shared row stride (floats) of a BT-sample tile: row r starts in bank group r mod 8
 __host__ __device__ constexpr int block_rs(int BT) { return BT + 4; }
