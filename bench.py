@@ -289,8 +289,9 @@ def run_kns(args, rank, world, local_rank):
     mac_trace, mac_hit = mac_counts(desc)
     # kernels one render launches: generate, per round scan + scatter + FP32 eval + FP32 tail
     # (+ BF16 eval), shade; counted from the library's round counter
-    # gen + rounds x (scan, scatter, eval, tail, advance[, bf16 eval]) + hit count/scan/scatter + shade
-    launches_per_step = 5 + st["rounds"] * (5 + (1 if precision == kns.KNS_BF16 else 0))
+    # gen + rounds x (scan, scatter, eval, tail[, bf16 eval]) + an advance for every round but the
+    # last issued + hit count/scan/scatter + shade
+    launches_per_step = 4 + st["rounds"] * (5 + (1 if precision == kns.KNS_BF16 else 0))
 
     clocks = ClockSampler(local_rank).start() if rank == 0 else None
     if world > 1:
@@ -379,8 +380,8 @@ def run_kns(args, rank, world, local_rank):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
                 "clocks": clock_info, "gpu_launches": args.steps * launches_per_step, "tuning": tuning,
-                "launch_count_source": "library round counter: gen + rounds x (scan, scatter, eval, tail, advance[, bf16 eval]) + "
-                                      "hit sort (3) + shade",
+                "launch_count_source": "library round counter: gen + rounds x (scan, scatter, eval, tail[, bf16 eval]) + "
+                                      "(rounds - 1) advance + hit sort (3) + shade",
                 "step_ms_min": min(times), "step_ms_median": statistics.median(times)}
         print(json.dumps(line), flush=True)
     grid.free()
