@@ -116,7 +116,10 @@ def test_bf16_schedule_invariance(kns, ctx):
     try:
         ref = render_np(kns, ctx, grid, cams, 160, 120, 128, 1e-4, precision=kns.KNS_BF16)
         for tuning in [dict(inner_steps=1, min_active=1, static_tiles=2),
-                       dict(inner_steps=64, min_active=16, static_tiles=1, blocks_per_sm=2)]:
+                       dict(inner_steps=64, min_active=16, static_tiles=1, blocks_per_sm=2),
+                       dict(tail_rays=-1),  # the FP32 phase on block tiles to the end (no tail)
+                       dict(block_tiles=1, inner_steps=3, min_active=1, tail_rays=4096),
+                       dict(block_tiles=2, tail_rays=-1)]:
             got = render_np(kns, ctx, grid, cams, 160, 120, 128, 1e-4, precision=kns.KNS_BF16, tuning=tuning)
             for k in ref:
                 assert np.array_equal(ref[k], got[k]), (k, tuning)
