@@ -338,7 +338,7 @@ kns_status kns_train_step(kns_ctx *ctx, const kns_grid_desc *desc, const float *
  * run: an application that gives all device memory to its own pool allocator at start-up, or a
  * latency-bound loop that cannot take cudaMalloc's implicit device synchronisation.  The paper has
  * no counterpart; it is a deployment convenience.  Its scratch is a fixed device array built into
- * the library (about 10 MB on every GPU that loads it, kept until the process exits); the call
+ * the library (about 14 MB on every GPU that loads it, kept until the process exits); the call
  * allocates nothing and frees nothing.  The context and the grid must already exist (creating them
  * does allocate).  The first call on a device looks up the array's device address (once per
  * device), so make that first call before any stream capture.  All calls share the one array and

@@ -88,6 +88,20 @@ def test_null_context_is_rejected_on_the_host(lib):
     assert "NULL" in capi.kns_last_error(None)
     lib.kns_destroy(None)
     lib.kns_free_grid(None)
+    # every entry point that takes a context refuses NULL before touching the device
+    bad = capi.KNS_ERR_INVALID_ARG
+    assert lib.kns_render_noalloc(None, None, None, 1, 1, 1, 1, 1e-4, None, None) == bad
+    assert lib.kns_render_views(None, None, None, 1, 1, 1e-4, None, None) == bad
+    assert lib.kns_get_render_stats(None, None) == bad
+    assert lib.kns_trace_rays(None, None, None, None, 1, 1, 1e-4, None, None, None) == bad
+    assert lib.kns_path_trace(None, None, None, 1, 1, 1, None, 1, 1e-4, None, None, None) == bad
+    assert lib.kns_train_forward(None, None, None, None, None, None, None, None, None) == bad
+    assert lib.kns_train_backward(None, 1, None, None, None) == bad
+    assert lib.kns_train_step(None, None, None, None, None, None, None) == bad
+    assert lib.kns_train_get_stats(None, None) == bad
+    assert lib.kns_copy_occupancy(None, None, None, 0) == bad
+    assert lib.kns_grid_get_desc(None, None) == bad
+    assert lib.kns_load_grid_file(None, None, C.byref(h)) == bad
 
 
 def test_create_without_a_device_fails_cleanly(lib):
