@@ -111,3 +111,13 @@ def test_create_without_a_device_fails_cleanly(lib):
     with pytest.raises(capi.KnsError) as e:
         capi.kns_create(0)
     assert e.value.status in (capi.KNS_ERR_CUDA, capi.KNS_ERR_INVALID_ARG)
+
+
+def test_a_missing_library_raises_instead_of_falling_back(monkeypatch, tmp_path):
+    """The product path has no CPU fallback: without libkns.so every call fails loudly."""
+    monkeypatch.setattr(capi, "_lib", None)
+    monkeypatch.setattr(capi, "LIB_PATH", str(tmp_path / "libkns.so"))
+    with pytest.raises(ImportError, match="not built"):
+        capi.lib()
+    with pytest.raises(ImportError):
+        capi.kns_create(0)
