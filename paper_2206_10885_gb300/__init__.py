@@ -3,6 +3,21 @@
 PyTorch is used only to own device memory and streams; every step of the path
 runs in libkns.so's CUDA kernels.  The raw binding with the C names lives in
 ``_capi``; the helpers here allocate output tensors and marshal arguments.
+
+    import paper_2206_10885_gb300 as kns
+    from paper_2206_10885_gb300 import synth as S
+    desc, w, cams, W, H, max_steps, eps = S.workload("c2")     # synthetic grid and cameras
+    ctx = kns.Context(0)
+    grid = kns.Grid.load(ctx, desc, w)                         # weights resident in HBM
+    img = kns.render(ctx, grid, cams, W, H, max_steps, eps)    # dict of device tensors: rgb, depth,
+                                                               # normal, cell, steps, hit
+    d, z, g = kns.sdf(ctx, grid, points)                       # batch field query, points (n, 3) on cuda
+    grid.free(); ctx.close()
+
+kns.render_views (several views of one grid in one launch sequence), kns.trace_rays and
+kns.path_trace (explicit rays, Lambertian bounces), kns.train (NeuS loss with the hand-written
+backward as a torch.autograd.Function) and serve.RenderServer (continuous batching) build on the
+same context and grid handles.
 """
 from __future__ import annotations
 
