@@ -15,9 +15,14 @@
  *  - Argument errors are detected on the host before any work is enqueued.
  *  - Asynchrony: compute calls enqueue on the caller's CUDA stream
  *    (`cuda_stream`, a cudaStream_t; NULL = the legacy default stream) and
- *    return without waiting.  Device-side failures (a bounded wait that ran
- *    out, a bounds check that tripped) are recorded in a per-context status
- *    word and returned by the next kns_sync() on that context.
+ *    return without waiting.  A render also runs work on a stream the context
+ *    owns, forked from and joined back into the caller's stream with events
+ *    inside the call, so the render is complete, like any other work, when
+ *    the caller's stream reaches the point after it.  The render loop reads
+ *    a small pinned counter on the host between rounds, so renders cannot be
+ *    captured into a CUDA graph.  Device-side failures (a bounded wait that
+ *    ran out, a bounds check that tripped) are recorded in a per-context
+ *    status word and returned by the next kns_sync() on that context.
  *  - Memory: the caller owns every input and output buffer and passes plain
  *    pointers (device pointers unless stated "host").  The library never
  *    frees caller memory.  Grids own the device copies of their weights.
