@@ -66,8 +66,8 @@ typedef enum kns_status {
 
 /* Arithmetic of the render path. */
 enum { KNS_FP32 = 0, /* every MLP evaluation in FP32 on the CUDA cores */
-       KNS_BF16 = 1  /* trace MLPs in BF16 on the tensor cores (FP32 accumulate), then the
-                        last sphere steps, the normal and the colour in FP32 */ };
+       KNS_BF16 = 1  /* trace MLPs on the tensor cores as split BF16 products (hi + lo parts, FP32
+                        accumulation), then the last sphere step(s), the normal and the colour in FP32 */ };
 
 typedef struct kns_ctx kns_ctx;   /* opaque: one device, its scratch, its status word */
 typedef struct kns_grid kns_grid; /* opaque: one resident Kilo-grid */
@@ -114,10 +114,10 @@ typedef struct kns_frame {
  * the work, never a result; 0 selects the built-in default. */
 typedef struct kns_render_opts {
     int32_t precision;    /* KNS_FP32 or KNS_BF16 */
-    float eps_coarse;     /* KNS_BF16: hit threshold of the BF16 trace (<= 0: max(eps, 0.04)) */
-    int32_t refine_steps; /* KNS_BF16: FP32 evaluations after the BF16 hit before the FP32 field decides
-                             (<= 0: 64); the ray is a hit at the first |d| < eps, or at the last of them if
-                             |d| < eps_coarse there, else a miss */
+    float eps_coarse;     /* KNS_BF16: hit threshold of the BF16 trace (<= 0: eps) */
+    int32_t refine_steps; /* KNS_BF16: FP32 evaluations of a BF16 hit (<= 0: 2): the first re-evaluates the
+                             BF16 trace's last step; the ray is a hit at the first |d| < eps, or at the last
+                             of them if |d| < eps_coarse there, else a miss */
     /* tuning (0 = default) */
     int32_t inner_steps;   /* evaluations a tile may make per round while its rays stay in its cell (1..1024;
                               default 4 for warp tiles, 2 for block tiles) */
@@ -127,10 +127,14 @@ typedef struct kns_render_opts {
     int32_t blocks_per_sm; /* evaluation blocks (one warp each) launched per SM (1..64) */
     int32_t static_tiles;  /* 1: each block takes a contiguous run of tiles; 2: tiles handed out dynamically */
     int32_t timing;        /* 1: time each kernel class with CUDA events for kns_get_render_stats (adds host work) */
-    int32_t block_tiles;   /* FP32 evaluation (also the refinement phase of KNS_BF16): 1 = 128-sample tiles per
+    int32_t block_tiles;   /* FP32 evaluation (KNS_FP32 renders): 1 = 128-sample tiles per
                               256-thread block (block GEMMs); 3 = 256-sample tiles per 256 threads; 4 = 128-sample
                               tiles per 128 threads; 2 = 16-sample tiles per warp (in-tile stepping, min_active);
                               0 = default (4) */
+    int32_t bf16_inner_steps; /* KNS_BF16: evaluations a tensor-core tile may make per round while its rays stay in
+                                 its cell (1..1024; default 2) */
+    int32_t bf16_min_active;  /* KNS_BF16: a tensor-core tile continues while at least this many of its rays stay
+                                 (1..128; default 16) */
 } kns_render_opts;
 
 /* Counters of the last kns_render on a context (kns_get_render_stats). */
@@ -205,6 +209,21 @@ kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams
 /* Counters (and, when the render ran with opts->timing = 1, per-kernel-class device times) of the last
  * kns_render on this context.  Waits for that render to finish.  Errors: INVALID_ARG (no render yet), CUDA. */
 kns_status kns_get_render_stats(kns_ctx *ctx, kns_render_stats *out);
+
+/* One round of kns_render's wavefront sphere trace (Sec. 3.4.1): every ray still tracing takes its
+ * next sample (and, in-tile, possibly a few more). */
+typedef struct kns_round_info {
+    int32_t live;        /* samples queued for the round */
+    float ms_sort;       /* device time of the round's sort, FP32 and BF16 evaluation (opts->timing, else 0) */
+    float ms_eval_fp32;
+    float ms_eval_bf16;
+} kns_round_info;
+
+/* Per-round trace of the last render call on this context: writes min(*n_rounds, max_rounds) entries
+ * (rounds of all batches of the call, in order) and sets *n_rounds to the number of rounds.  Waits for
+ * the render to finish.  Errors: INVALID_ARG (NULL n_rounds, out NULL with max_rounds > 0, no render
+ * yet), CUDA. */
+kns_status kns_get_round_trace(kns_ctx *ctx, kns_round_info *out, int32_t max_rounds, int32_t *n_rounds);
 
 /* One view of a multi-view render: camera, image size and its own output buffers (device pointers for
  * W*H pixels, layout as kns_frame). */

@@ -51,6 +51,11 @@ class Context:
         """Counters (and per-kernel-class device ms when rendered with tuning={'timing': 1}) of the last render."""
         return capi.kns_get_render_stats(self.handle)
 
+    def round_trace(self) -> list:
+        """Per-round live samples (and per-class device ms when rendered with tuning={'timing': 1}) of the
+        last render call."""
+        return capi.kns_get_round_trace(self.handle)
+
     def close(self) -> None:
         if self.handle:
             capi.kns_destroy(self.handle)
@@ -109,7 +114,8 @@ def alloc_frame(n_pix: int, device="cuda", extras: bool = True):
     return t, f
 
 
-TUNING_FIELDS = ("inner_steps", "min_active", "tail_rays", "blocks_per_sm", "static_tiles", "timing", "block_tiles")
+TUNING_FIELDS = ("inner_steps", "min_active", "tail_rays", "blocks_per_sm", "static_tiles", "timing", "block_tiles",
+                 "bf16_inner_steps", "bf16_min_active")
 
 
 def render_opts(precision: int = KNS_FP32, eps_coarse: float = 0.0, refine_steps: int = -1, tuning=None):

@@ -79,7 +79,7 @@ class kns_render_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("eps_coarse", C.c_float), ("refine_steps", C.c_int32),
                 ("inner_steps", C.c_int32), ("min_active", C.c_int32), ("tail_rays", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("static_tiles", C.c_int32), ("timing", C.c_int32),
-                ("block_tiles", C.c_int32)]
+                ("block_tiles", C.c_int32), ("bf16_inner_steps", C.c_int32), ("bf16_min_active", C.c_int32)]
 
 
 class kns_render_stats(C.Structure):
@@ -87,6 +87,10 @@ class kns_render_stats(C.Structure):
                 ("samples_bf16", C.c_int64), ("ms_generate", C.c_float), ("ms_sort", C.c_float),
                 ("ms_eval_fp32", C.c_float), ("ms_eval_bf16", C.c_float), ("ms_shade", C.c_float),
                 ("ms_total", C.c_float), ("samples_tail", C.c_int64)]
+
+
+class kns_round_info(C.Structure):
+    _fields_ = [("live", C.c_int32), ("ms_sort", C.c_float), ("ms_eval_fp32", C.c_float), ("ms_eval_bf16", C.c_float)]
 
 
 _lib = None
@@ -134,6 +138,8 @@ def lib():
             L.kns_render_views.restype = st
             L.kns_get_render_stats.argtypes = [vp, C.POINTER(kns_render_stats)]
             L.kns_get_render_stats.restype = st
+            L.kns_get_round_trace.argtypes = [vp, C.POINTER(kns_round_info), C.c_int32, C.POINTER(C.c_int32)]
+            L.kns_get_round_trace.restype = st
             L.kns_trace_rays.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_int, C.c_float, C.POINTER(kns_frame),
                                          C.POINTER(kns_render_opts), vp]
             L.kns_trace_rays.restype = st
@@ -243,6 +249,14 @@ def kns_get_render_stats(ctx: int) -> dict:
     st = kns_render_stats()
     _check(lib().kns_get_render_stats(ctx, C.byref(st)), ctx)
     return {k: getattr(st, k) for k, _ in kns_render_stats._fields_}
+
+
+def kns_get_round_trace(ctx: int, max_rounds: int = 1024) -> list:
+    """Per-round (live samples, sort / FP32 / BF16 evaluation ms) of the last render call."""
+    buf = (kns_round_info * max_rounds)()
+    n = C.c_int32(0)
+    _check(lib().kns_get_round_trace(ctx, buf, max_rounds, C.byref(n)), ctx)
+    return [{k: getattr(buf[i], k) for k, _ in kns_round_info._fields_} for i in range(min(n.value, max_rounds))]
 
 
 def kns_sdf(ctx: int, grid: int, pts_ptr: int, n: int, sdf_ptr: int, feat_ptr: int = None, grad_ptr: int = None,

@@ -14,6 +14,7 @@
 #include "kns.h"
 #include "kns_device.cuh"
 #include "kns_kernels.h"
+#include "kns_tc.cuh"
 
 // Device scratch of the wavefront render, owned by the context and grown on demand.
 struct WaveScratch {
@@ -22,6 +23,7 @@ struct WaveScratch {
     int cams = 0;      // capacity in cameras
     float *t_ray = nullptr;
     float4 *t_hist = nullptr;  // last evaluated positions of each ray (cycle test)
+    int4 *trap = nullptr;      // BF16 renders: each ray's seam-trap tracker (kns_wave.cuh)
     int *steps_ray = nullptr, *cell_ray = nullptr, *q[2] = {nullptr, nullptr}, *qcell[2] = {nullptr, nullptr};
     int *sorted = nullptr, *hits = nullptr;
     int *cellbuf = nullptr;  // count[2], fill[2], off, tile_off (6 * (nc + 1) ints)
@@ -82,8 +84,13 @@ struct kns_ctx {
     kns_render_stats stats{};
     cudaStream_t stats_stream = nullptr;
     std::vector<cudaEvent_t> ev_pool;                   // timing events (created on demand)
-    std::vector<std::pair<int, int>> ev_marks;          // (kernel class, index of the begin event)
+    struct Mark {
+        int cls, ev, round;  // kernel class, index of its begin event, round (-1: outside the rounds)
+    };
+    std::vector<Mark> ev_marks;
     size_t ev_used = 0;
+    int cur_round = -1;                    // round being enqueued (tags timing marks)
+    std::vector<int> round_live;           // samples queued per round of the last render (-1: not read)
 };
 
 struct kns_grid {
@@ -93,7 +100,7 @@ struct kns_grid {
     float *d_w = nullptr;   // per-thread layout (shading, field queries, occupancy)
     float *d_wt = nullptr;  // k-major trace layout (wavefront tile GEMM)
     int wt_stride = 0;
-    unsigned char *d_wb = nullptr;  // BF16 mma fragment trace layout
+    unsigned char *d_wb = nullptr;  // BF16 hi/lo tensor-core trace layout (kns_tc.cuh)
     int wb_stride = 0;              // bytes per cell
     uint32_t *d_occ = nullptr;
     uint32_t *d_occ_coarse = nullptr;  // 8^3-voxel block mask (res % 8 == 0)
@@ -245,7 +252,9 @@ void convert_cell_trace(const kns_grid_desc &d, int dev_floats, const float *src
     dst[o] = src[s + (int64_t)kns::SDF_OUT * W];  // its bias
 }
 
-// Canonical SDF layers -> BF16 mma fragment layout (kns_device.cuh, Cfg::FR0..BSIZE), one cell.
+// Canonical SDF layers -> the tensor-core trace layout of kns_tc.cuh, one cell: every weight as a
+// BF16 pair hi = bf16(w), lo = bf16(w - hi) in the canonical K-major layout (row = output unit,
+// column = input), then the FP32 biases, the d row of the last layer and its bias.
 static uint16_t to_bf16(float f) {  // round to nearest even
     uint32_t u;
     std::memcpy(&u, &f, 4);
@@ -253,37 +262,44 @@ static uint16_t to_bf16(float f) {  // round to nearest even
     u += 0x7fffu + ((u >> 16) & 1u);
     return (uint16_t)(u >> 16);
 }
-void convert_cell_bf16(const kns_grid_desc &d, int bytes, int k0p, const float *src, unsigned char *dst) {
-    const int W = d.sdf_width, H = d.sdf_hidden, IN = 3 + 6 * d.pe_pos_L;
+static float from_bf16(uint16_t h) {
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+int tc_cell_bytes(const kns_grid_desc &d) {
+    return kns::tc::cell_bytes(d.sdf_width, d.sdf_hidden, kns::tc::k0_of(3 + 6 * d.pe_pos_L));
+}
+void convert_cell_tc(const kns_grid_desc &d, int bytes, const float *src, unsigned char *dst) {
+    const int W = d.sdf_width, H = d.sdf_hidden, IN = 3 + 6 * d.pe_pos_L, K0 = kns::tc::k0_of(IN);
     std::memset(dst, 0, bytes);
-    uint32_t *frag = (uint32_t *)dst;
-    int f = 0;  // fragment index
-    auto emit_layer = [&](const float *Wm, int kin, int kpad, int nout, int npad) {
-        // B[k][n] = W[n][k]; W is [nout][kin] row-major
-        auto B = [&](int k, int n) -> uint16_t { return (k < kin && n < nout) ? to_bf16(Wm[n * kin + k]) : 0; };
-        for (int kt = 0; kt < kpad / 16; ++kt)
-            for (int nt = 0; nt < npad / 8; ++nt, ++f)
-                for (int lane = 0; lane < 32; ++lane) {
-                    const int k = 16 * kt + 2 * (lane % 4), n = 8 * nt + lane / 4;
-                    frag[(f * 32 + lane) * 2 + 0] = (uint32_t)B(k, n) | ((uint32_t)B(k + 1, n) << 16);
-                    frag[(f * 32 + lane) * 2 + 1] = (uint32_t)B(k + 8, n) | ((uint32_t)B(k + 9, n) << 16);
-                }
+    auto emit_layer = [&](int l, const float *Wm, int kin) {
+        const int K = l == 0 ? K0 : W;
+        unsigned char *hi = dst + kns::tc::w_hi(l, W, K0), *lo = dst + kns::tc::w_lo(l, W, K0);
+        for (int n = 0; n < W; ++n)
+            for (int k = 0; k < kin; ++k) {
+                const float x = Wm[n * kin + k];
+                const uint16_t h = to_bf16(x), r = to_bf16(x - from_bf16(h));
+                std::memcpy(hi + kns::tc::canon_off(n, k, K), &h, 2);
+                std::memcpy(lo + kns::tc::canon_off(n, k, K), &r, 2);
+            }
     };
-    const int nfrag = (k0p / 16) * (W / 8) + (H - 1) * (W / 16) * (W / 8) + W / 16;
-    float *bias = (float *)(dst + nfrag * 256);
+    float *bias = reinterpret_cast<float *>(dst + kns::tc::bias_off(W, H, K0));
+    float *drow = reinterpret_cast<float *>(dst + kns::tc::drow_off(W, H, K0));
     int64_t s = 0;
-    emit_layer(src + s, IN, k0p, W, W);
+    emit_layer(0, src, IN);
     s += (int64_t)W * IN;
     for (int r = 0; r < W; ++r) bias[r] = src[s + r];
     s += W;
     for (int l = 1; l < H; ++l) {
-        emit_layer(src + s, W, W, W, W);
+        emit_layer(l, src + s, W);
         s += (int64_t)W * W;
         for (int r = 0; r < W; ++r) bias[l * W + r] = src[s + r];
         s += W;
     }
-    emit_layer(src + s, W, W, 1, 8);  // row 0 (d) of the last layer only
-    bias[H * W] = src[s + (int64_t)kns::SDF_OUT * W];
+    for (int c = 0; c < W; ++c) drow[c] = src[s + c];  // row 0 (d) of the last layer
+    drow[W] = src[s + (int64_t)kns::SDF_OUT * W];       // its bias
 }
 
 void fill_view(kns_grid *g) {
@@ -311,6 +327,7 @@ void fill_view(kns_grid *g) {
 void free_scratch(WaveScratch &w) {
     cudaFree(w.t_ray);
     cudaFree(w.t_hist);
+    cudaFree(w.trap);
     cudaFree(w.steps_ray);
     cudaFree(w.cell_ray);
     cudaFree(w.q[0]);
@@ -340,6 +357,9 @@ constexpr int kRenderMinActive = 8;
 constexpr int kRenderBlockInnerSteps = 2;  // block tiles: a second evaluation of a tile in the round ...
 constexpr int kRenderBlockMinActive = 16;  // ... while at least 16 of its rays stay in its cell
 constexpr int kRenderTailRays = 131072;  // rounds this small finish one warp per ray
+// tensor-core tiles (BF16 renders): a second evaluation while at least 16 rays stay in the cell
+constexpr int kRenderBf16InnerSteps = 2;
+constexpr int kRenderBf16MinActive = 16;
 constexpr int kRenderBlocksPerSM = 16;
 constexpr int kRenderStaticTiles = 2;
 
@@ -357,7 +377,7 @@ int timing_begin(kns_ctx *ctx, bool on, int cls, cudaStream_t s) {
     const int i = (int)ctx->ev_used;
     ctx->ev_used += 2;
     cudaEventRecord(ctx->ev_pool[i], s);
-    ctx->ev_marks.push_back({cls, i});
+    ctx->ev_marks.push_back({cls, i, ctx->cur_round});
     return i;
 }
 void timing_end(kns_ctx *ctx, int i, cudaStream_t s) {
@@ -379,6 +399,7 @@ kns_status ensure_scratch(kns_ctx *ctx, int64_t rays, int nc, int cams) {
     };
     alloc(&w.t_ray, sizeof(float) * R);
     alloc(&w.t_hist, sizeof(float4) * R);
+    alloc(&w.trap, sizeof(int4) * R);
     alloc(&w.steps_ray, sizeof(int) * R);
     alloc(&w.cell_ray, sizeof(int) * R);
     alloc(&w.q[0], sizeof(int) * R);
@@ -644,8 +665,7 @@ kns_status kns_load_grid(kns_ctx *ctx, const kns_grid_desc *desc, const float *h
         if (e == cudaSuccess) e = cudaMemcpy(g->d_wt, ht.data(), ht.size() * sizeof(float), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) {
-        int k0p = 0;
-        g->wb_stride = kns::bf16_cell_bytes(g->shape, &k0p);
+        g->wb_stride = tc_cell_bytes(d);
         std::vector<unsigned char> hb;
         try {
             hb.resize((size_t)(ncell * g->wb_stride));
@@ -656,7 +676,7 @@ kns_status kns_load_grid(kns_ctx *ctx, const kns_grid_desc *desc, const float *h
             return set_err(ctx, KNS_ERR_OUT_OF_MEMORY, "host staging allocation failed");
         }
         for (int64_t c = 0; c < ncell; ++c)
-            convert_cell_bf16(d, g->wb_stride, k0p, host_weights + c * pcell, hb.data() + c * g->wb_stride);
+            convert_cell_tc(d, g->wb_stride, host_weights + c * pcell, hb.data() + c * g->wb_stride);
         e = cudaMalloc(&g->d_wb, hb.size());
         if (e == cudaSuccess) e = cudaMemcpy(g->d_wb, hb.data(), hb.size(), cudaMemcpyHostToDevice);
     }
@@ -806,6 +826,7 @@ struct RenderCfg {
     float eps_coarse = 4e-3f;
     int refine_steps = 2, inner_steps = kRenderInnerSteps, min_active = kRenderMinActive,
         tail_rays = kRenderTailRays, blocks_per_sm = kRenderBlocksPerSM, static_tiles = 1;
+    int inner_steps_bf = kRenderBf16InnerSteps, min_active_bf = kRenderBf16MinActive;
     int block_mode = 1;  // 0 = 16-sample warp tiles; block tiles: 1 = 128 samples x 256 threads,
                          // 3 = 256 x 256, 4 = 128 x 128
 };
@@ -815,10 +836,10 @@ kns_status resolve_opts(kns_ctx *ctx, const kns_render_opts *opts, float eps, Re
     if (precision != KNS_FP32 && precision != KNS_BF16)
         return set_err(ctx, KNS_ERR_INVALID_ARG, "unknown precision %d", precision);
     c.bf16 = precision == KNS_BF16;
-    // defaults from the accuracy/speed sweep at 8 x 1920x1080: the BF16 phase stops 0.04 from the
-    // surface and FP32 gets up to 64 evaluations to converge
-    c.eps_coarse = (c.bf16 && opts && opts->eps_coarse > 0.f) ? opts->eps_coarse : std::max(eps, 0.04f);
-    c.refine_steps = (c.bf16 && opts && opts->refine_steps > 0) ? opts->refine_steps : 64;
+    // BF16 defaults: the split-BF16 trace is accurate to ~1e-5, so it runs to the FP32 threshold itself;
+    // FP32 then re-evaluates its last step and takes at most one more (two FP32 evaluations)
+    c.eps_coarse = (c.bf16 && opts && opts->eps_coarse > 0.f) ? opts->eps_coarse : eps;
+    c.refine_steps = (c.bf16 && opts && opts->refine_steps > 0) ? opts->refine_steps : 2;
     if (c.bf16 && !(c.eps_coarse >= eps && std::isfinite(c.eps_coarse)))
         return set_err(ctx, KNS_ERR_INVALID_ARG, "eps_coarse must be finite and >= eps");
     auto knob = [](int32_t v, int32_t def) { return v == 0 ? def : v; };
@@ -830,6 +851,10 @@ kns_status resolve_opts(kns_ctx *ctx, const kns_render_opts *opts, float eps, Re
     c.tail_rays = opts ? knob(opts->tail_rays, kRenderTailRays) : kRenderTailRays;
     c.blocks_per_sm = opts ? knob(opts->blocks_per_sm, kRenderBlocksPerSM) : kRenderBlocksPerSM;
     c.static_tiles = (opts ? knob(opts->static_tiles, kRenderStaticTiles) : kRenderStaticTiles) == 1;
+    c.inner_steps_bf = opts ? knob(opts->bf16_inner_steps, kRenderBf16InnerSteps) : kRenderBf16InnerSteps;
+    c.min_active_bf = opts ? knob(opts->bf16_min_active, kRenderBf16MinActive) : kRenderBf16MinActive;
+    if (c.inner_steps_bf < 1 || c.inner_steps_bf > 1024 || c.min_active_bf < 1 || c.min_active_bf > 128)
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "bf16 tuning field out of range");
     if (c.inner_steps < 1 || c.inner_steps > 1024 || c.min_active < 1 || c.min_active > 256 || c.tail_rays < -1 ||
         c.blocks_per_sm < 1 || c.blocks_per_sm > 64 || (opts && (opts->static_tiles < 0 || opts->static_tiles > 2)) ||
         (opts && (opts->block_tiles < 0 || opts->block_tiles > 4)))
@@ -844,6 +869,8 @@ kns_status resolve_opts(kns_ctx *ctx, const kns_render_opts *opts, float eps, Re
 void begin_stats(kns_ctx *ctx, cudaStream_t s, int64_t rays) {
     ctx->ev_marks.clear();
     ctx->ev_used = 0;
+    ctx->round_live.clear();
+    ctx->cur_round = -1;
     ctx->stats = kns_render_stats{};
     ctx->stats.rays = rays;
     ctx->stats_stream = s;
@@ -858,7 +885,7 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
                              bool last, const float *ray_o = nullptr, const float *ray_w = nullptr,
                              int64_t n_table = 0) {
     const int NC = grid->desc.N * grid->desc.N * grid->desc.N;
-    const int nkeys = cfg.bf16 ? 2 * NC : NC;
+    const int nkeys = NC;  // sort keys: cells
     const int nv = (int)views.size();
     kns_status st = ensure_scratch(ctx, rays, nkeys, nv);
     if (st != KNS_OK) return st;
@@ -887,16 +914,25 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
     a.wb = grid->d_wb;
     a.wb_stride = grid->wb_stride;
     a.btile = kRenderBlockTile;
-    a.btile_bf = kRenderBlockTile;
+    a.btile_bf = 128;  // tensor-core tiles: 128 samples
     a.inner_steps = cfg.inner_steps;
     a.tail_max = cfg.tail_rays;
     a.min_active = cfg.min_active;
+    a.inner_steps_bf = cfg.inner_steps_bf;
+    a.min_active_bf = cfg.min_active_bf;
     a.static_tiles = cfg.static_tiles;
     a.status = ctx->d_status;
     a.wt = grid->d_wt;
     a.wt_stride = grid->wt_stride;
     a.t_ray = w.t_ray;
     a.t_hist = w.t_hist;
+    a.trap = cfg.bf16 ? w.trap : nullptr;
+    {
+        const float ext = std::max(grid->desc.bbox_max[0] - grid->desc.bbox_min[0],
+                                   std::max(grid->desc.bbox_max[1] - grid->desc.bbox_min[1],
+                                            grid->desc.bbox_max[2] - grid->desc.bbox_min[2]));
+        a.trap_span = 0.01f * ext;
+    }
     a.steps_ray = w.steps_ray;
     a.cell_ray = w.cell_ray;
     a.q[0] = w.q[0];
@@ -934,19 +970,24 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
     // k - 2, its live count and round k - 3's pending count before launching round k, and stops when
     // both are zero (rounds k - 1 and k then hold nothing), so it runs at most two rounds ahead.
     int last_adv = -1;  // the last round whose advance kernel was launched
+    const int round0 = (int)ctx->round_live.size();  // rounds of earlier batches of this call
     for (int k = 0; k < 2 * max_steps + 2 && e == cudaSuccess; ++k) {
         const int cur = k & 1;
         if (k >= 2) {
             e = cudaEventSynchronize(ctx->ev_live[(k - 2) & 3]);
             const int *hl = ctx->h_live + 2 * ((k - 2) & 3);
+            if (e == cudaSuccess) ctx->round_live[round0 + k - 2] = hl[0];
             if (e != cudaSuccess || (hl[0] == 0 && hl[1] == 0)) break;
             // round k - 2's advance added to this round's counters
             e = cudaStreamWaitEvent(s, ctx->ev_adv[k & 1], 0);
             if (e != cudaSuccess) break;
         }
         ++ctx->stats.rounds;
-        // block tiles: the sort cuts tiles of the size the evaluation kernel takes
-        if (cfg.block_mode == 1 || cfg.block_mode == 4) a.btile = 128;
+        ctx->cur_round = round0 + k;
+        ctx->round_live.push_back(-1);
+        // the sort cuts tiles of the size the evaluation kernel takes: tensor-core tiles of 128 samples
+        // (BF16), block tiles of 128 or 256, or warp tiles of 16
+        if (cfg.bf16 || cfg.block_mode == 1 || cfg.block_mode == 4) a.btile = 128;
         else if (cfg.block_mode == 3) a.btile = 256;
         int tm = timing_begin(ctx, cfg.timing, kTSort, s);
         e = kns::launch_wave_scan(a, cur, s);
@@ -964,16 +1005,17 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
         }
         if (e == cudaSuccess) e = kns::launch_wave_scatter(a, cur, scatter_blocks, s);
         timing_end(ctx, tm, s);
-        tm = timing_begin(ctx, cfg.timing, kTEvalF32, s);
-        if (e == cudaSuccess)
-            e = kns::launch_wave_eval(grid->shape, grid->view, a, cur, eval_blocks, cfg.block_mode, ctx->sm_count, s);
-        timing_end(ctx, tm, s);
-        if (e == cudaSuccess && cfg.bf16) {
+        if (e == cudaSuccess && cfg.bf16) {  // tensor-core tiles only
             tm = timing_begin(ctx, cfg.timing, kTEvalBF16, s);
-            e = kns::launch_wave_eval_bf16(grid->shape, grid->view, a, cur, eval_blocks, s);
+            e = kns::launch_wave_eval_tc(grid->shape, grid->view, a, cur, ctx->sm_count, s);
+            timing_end(ctx, tm, s);
+        } else if (e == cudaSuccess) {  // FP32 tiles and the one-warp-per-ray tail
+            tm = timing_begin(ctx, cfg.timing, kTEvalF32, s);
+            e = kns::launch_wave_eval(grid->shape, grid->view, a, cur, eval_blocks, cfg.block_mode, ctx->sm_count, s);
             timing_end(ctx, tm, s);
         }
     }
+    ctx->cur_round = -1;
     // the side stream's last advance joins before the shading (it found nothing: the rounds ended)
     if (e == cudaSuccess && last_adv >= 0) e = cudaStreamWaitEvent(s, ctx->ev_adv[last_adv & 1], 0);
     if (e == cudaSuccess) {
@@ -981,6 +1023,8 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
         // hits sorted by cell, shaded on block tiles
         e = kns::launch_hit_sort(a, kns::shade_hit_tile(grid->desc.sdf_width), ctx->sm_count, s);
         if (e == cudaSuccess) e = kns::launch_shade_block(grid->shape, grid->view, a, ctx->sm_count, s);
+        // BF16: the hits the shading's FP32 evaluation did not confirm take their last FP32 steps
+        if (e == cudaSuccess && cfg.bf16) e = kns::launch_refine(grid->shape, grid->view, a, ctx->sm_count, s);
         timing_end(ctx, tm, s);
     }
     if (e != cudaSuccess) return cuda_err(ctx, e, "render launch");
@@ -1213,11 +1257,37 @@ kns_status kns_get_render_stats(kns_ctx *ctx, kns_render_stats *out) {
     float *dst[5] = {&st.ms_generate, &st.ms_sort, &st.ms_eval_fp32, &st.ms_eval_bf16, &st.ms_shade};
     for (const auto &m : ctx->ev_marks) {
         float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, ctx->ev_pool[m.second], ctx->ev_pool[m.second + 1]) == cudaSuccess)
-            *dst[m.first] += ms;
+        if (cudaEventElapsedTime(&ms, ctx->ev_pool[m.ev], ctx->ev_pool[m.ev + 1]) == cudaSuccess) *dst[m.cls] += ms;
     }
     st.ms_total = st.ms_generate + st.ms_sort + st.ms_eval_fp32 + st.ms_eval_bf16 + st.ms_shade;
     *out = st;
+    return KNS_OK;
+}
+
+kns_status kns_get_round_trace(kns_ctx *ctx, kns_round_info *out, int32_t max_rounds, int32_t *n_rounds) {
+    if (!ctx) return KNS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!n_rounds || max_rounds < 0 || (max_rounds > 0 && !out))
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "NULL n_rounds, or out NULL with max_rounds > 0");
+    if (!ctx->have_stats) return set_err(ctx, KNS_ERR_INVALID_ARG, "no render on this context yet");
+    DeviceScope ds(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(ctx->stats_stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "round trace");
+    const int n = (int)ctx->round_live.size();
+    // the last rounds' counts were copied to the pinned ring but not read by the render loop
+    for (int k = std::max(0, n - 4); k < n; ++k)
+        if (ctx->round_live[k] < 0) ctx->round_live[k] = ctx->h_live[2 * (k & 3)];
+    *n_rounds = n;
+    for (int k = 0; k < std::min(n, (int)max_rounds); ++k) out[k] = kns_round_info{ctx->round_live[k], 0.f, 0.f, 0.f};
+    for (const auto &m : ctx->ev_marks) {
+        if (m.round < 0 || m.round >= std::min(n, (int)max_rounds)) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->ev_pool[m.ev], ctx->ev_pool[m.ev + 1]) != cudaSuccess) continue;
+        kns_round_info &r = out[m.round];
+        if (m.cls == kTSort) r.ms_sort += ms;
+        else if (m.cls == kTEvalF32) r.ms_eval_fp32 += ms;
+        else if (m.cls == kTEvalBF16) r.ms_eval_bf16 += ms;
+    }
     return KNS_OK;
 }
 
@@ -1350,7 +1420,7 @@ extern "C" kns_status kns_render_noalloc(kns_ctx *ctx, const kns_grid *grid, con
     a.NC = NC;
     a.nkeys = NC;
     a.btile = kRenderBlockTile;
-    a.btile_bf = kRenderBlockTile;
+    a.btile_bf = 128;  // tensor-core tiles: 128 samples
     a.inner_steps = kRenderInnerSteps;
     a.tail_max = kRenderTailRays;
     a.min_active = kRenderMinActive;

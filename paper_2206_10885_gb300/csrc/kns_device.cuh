@@ -55,20 +55,6 @@ struct Cfg {
     static constexpr int tdL = tH1 + (H - 1) * HSZ;
     static constexpr int tbL = tdL + W;
     static constexpr int TSIZE = round32(tbL + 4);
-    // BF16 tensor-core trace layout (mma.m16n8k16 B fragments, then FP32 biases), bytes:
-    //   fragment (layer, kt, nt) = 32 lanes x uint2 {B[k][n], B[k+1][n]}, {B[k+8][n], B[k+9][n]} with
-    //   k = 16 kt + 2 (lane % 4), n = 8 nt + lane / 4 and B[k][n] = W[n][k] (zero outside the layer);
-    //   layers: 0 (K0P x W), 1..H-1 (W x W), last (W x 8, column 0 = the d row).
-    static constexpr int K0P = (INP + 15) / 16 * 16;
-    static constexpr int NT = W / 8, KT0 = K0P / 16, KTH = W / 16;
-    static constexpr int FR0 = 0;
-    __host__ __device__ static constexpr int FRl(int l) { return KT0 * NT + (l - 1) * KTH * NT; }
-    static constexpr int FRL = KT0 * NT + (H - 1) * KTH * NT;
-    static constexpr int NFRAG = FRL + KTH;
-    static constexpr int BB0 = NFRAG * 256;              // bias floats start (byte offset)
-    __host__ __device__ static constexpr int BBl(int l) { return BB0 + l * W * 4; }
-    static constexpr int BBL = BB0 + H * W * 4;          // 8 floats, [0] = bias of d
-    static constexpr int BSIZE = (BBL + 32 + 127) / 128 * 128;
 };
 
 // Everything a kernel needs to read a resident grid (passed by value).

@@ -42,25 +42,18 @@ cudaError_t launch_shade_block(const Shape &sh, const GridView &g, const WaveArg
     return dispatch(sh, [&](auto c) { return launch_shade_block_cfg<decltype(c)>(g, a, sm_count, s); });
 }
 
-cudaError_t launch_wave_eval_bf16(const Shape &sh, const GridView &g, const WaveArgs &a, int cur, int blocks,
-                                  cudaStream_t s) {
-    return dispatch(sh, [&](auto c) { return launch_wave_eval_bf16_cfg<decltype(c)>(g, a, cur, blocks, s); });
+cudaError_t launch_refine(const Shape &sh, const GridView &g, const WaveArgs &a, int sm_count, cudaStream_t s) {
+    return dispatch(sh, [&](auto c) { return launch_refine_cfg<decltype(c)>(g, a, sm_count, s); });
+}
+cudaError_t launch_wave_eval_tc(const Shape &sh, const GridView &g, const WaveArgs &a, int cur, int sm_count,
+                                cudaStream_t s) {
+    return dispatch(sh, [&](auto c) { return launch_wave_eval_tc_cfg<decltype(c)>(g, a, cur, sm_count, s); });
 }
 
 int trace_cell_floats(const Shape &sh) {
     int size = 0;
     dispatch(sh, [&](auto c) {
         size = decltype(c)::TSIZE;
-        return cudaSuccess;
-    });
-    return size;
-}
-
-int bf16_cell_bytes(const Shape &sh, int *k0p) {
-    int size = 0;
-    dispatch(sh, [&](auto c) {
-        size = decltype(c)::BSIZE;
-        *k0p = decltype(c)::K0P;
         return cudaSuccess;
     });
     return size;

@@ -26,6 +26,8 @@ struct WaveCtrl {
     unsigned long long samples_f32;   // SDF evaluations in FP32 (tiles and the tail)
     unsigned long long samples_bf16;  // SDF evaluations in BF16 tiles
     unsigned long long samples_tail;  // the part of samples_f32 evaluated by the one-warp-per-ray tail
+    int scan_part[2][128];            // per scan block of a round: its samples and tiles (the sort's scan)
+    int n_refine;                     // BF16 renders: hits the shading's FP32 evaluation did not confirm
 };
 
 // One view of a render: its camera, image size, first ray id and output buffers (device, 128 B).
@@ -49,17 +51,19 @@ struct WaveArgs {
     int *ray_view;         // view of each ray
     float eps;
     int NC;               // cells N^3
-    int nkeys;            // sort keys: key = cell + NC * coarse (NC for FP32 renders, 2 NC for BF16)
-    int coarse;           // 1: BF16 render (rays start in the coarse BF16 phase and refine in FP32)
-    float eps_coarse;     // BF16 phase hit threshold
-    int refine_steps;     // FP32 evaluations after a BF16 hit before the final decision
-    const unsigned char *wb;  // BF16 mma fragment trace weights
+    int nkeys;            // sort keys: the cells (NC)
+    int coarse;           // 1: BF16 render (tensor-core trace; FP32 re-evaluates its hits at shading)
+    float eps_coarse;     // BF16 trace hit threshold
+    int refine_steps;     // FP32 evaluations of a BF16 hit (the shading's first) before the final decision
+    const unsigned char *wb;  // BF16 hi/lo tensor-core trace weights (kns_tc.cuh)
     int wb_stride;            // bytes per cell
     int btile;            // samples per FP32 tile (cell-sorted samples are cut into such tiles)
     int btile_bf;         // samples per BF16 tile (keys >= NC)
     int inner_steps;      // sphere steps a tile may take in one round while its rays stay in its cells
     int tail_max;         // a round with at most this many rays is finished one warp per ray
     int min_active;       // warp tiles with fewer live rays hand them to the next round
+    int inner_steps_bf;   // the same two knobs for the tensor-core tiles of BF16 renders
+    int min_active_bf;
     int static_tiles;     // 1: contiguous runs of tiles per block (weight reuse); 0: dynamic
     int *status;          // context status word (kns_status of a device-side failure, 0 = fine)
     const float *wt;      // k-major trace weights (see kns_device.cuh)
@@ -67,6 +71,8 @@ struct WaveArgs {
     // per-ray state
     float *t_ray;
     float4 *t_hist;       // the ray's last four evaluated positions, newest first (NULL: no cycle test)
+    int4 *trap;           // BF16 renders: the ray's seam-trap tracker (NULL: none; kns_wave.cuh)
+    float trap_span;      // its span limit along the ray (scene units)
     int *steps_ray, *cell_ray;
     // wave queues (double-buffered), cell-sorted samples, hits
     int *q[2], *qcell[2];
@@ -74,7 +80,7 @@ struct WaveArgs {
     int *count[2], *fill[2];  // per-cell sample counts and scatter cursors
     int *off, *tile_off;      // NC+1 exclusive scans: samples and tiles per cell
     int4 *tiles;              // per tile of the round: key, first sorted sample, samples (max_tiles entries)
-    int *pend_r[2];           // per round parity: rays waiting for the occupancy DDA ...
+    int *pend_r[2];           // per round parity: rays waiting for the occupancy DDA (bit 31: BF16 phase) ...
     float *pend_t[2];         // ... and the position each was last evaluated at
     WaveCtrl *ctrl;
 };
@@ -92,7 +98,11 @@ cudaError_t launch_wave_eval_cfg(const GridView &g, const WaveArgs &a, int cur, 
 template <class C>
 cudaError_t launch_shade_block_cfg(const GridView &g, const WaveArgs &a, int sm_count, cudaStream_t s);
 template <class C>
-cudaError_t launch_wave_eval_bf16_cfg(const GridView &g, const WaveArgs &a, int cur, int blocks, cudaStream_t s);
+cudaError_t launch_wave_eval_tc_cfg(const GridView &g, const WaveArgs &a, int cur, int sm_count, cudaStream_t s);
+// BF16 renders, after the shading: the FP32 steps of the hits on the refinement list (pend_r[0],
+// pend_t[0] = the FP32 d at the ray's t), then their shading, one thread per ray.
+template <class C>
+cudaError_t launch_refine_cfg(const GridView &g, const WaveArgs &a, int sm_count, cudaStream_t s);
 template <class C>
 cudaError_t launch_sdf_cfg(const GridView &g, const float *pts, int64_t n, float *sdf, float *feat, float *grad,
                            cudaStream_t s);
@@ -102,16 +112,17 @@ cudaError_t launch_occ_cfg(const GridView &g, float thresh, uint32_t *words, cud
 bool shape_supported(const Shape &sh);
 int cell_floats(const Shape &sh);
 int trace_cell_floats(const Shape &sh);
-int bf16_cell_bytes(const Shape &sh, int *k0p);
+
 
 cudaError_t launch_wave_gen(const Shape &sh, const GridView &g, const WaveArgs &a, cudaStream_t s);
 cudaError_t launch_wave_eval(const Shape &sh, const GridView &g, const WaveArgs &a, int cur, int blocks,
                              int block_tiles, int sm_count, cudaStream_t s);
-cudaError_t launch_wave_eval_bf16(const Shape &sh, const GridView &g, const WaveArgs &a, int cur, int blocks,
-                                  cudaStream_t s);
+cudaError_t launch_wave_eval_tc(const Shape &sh, const GridView &g, const WaveArgs &a, int cur, int sm_count,
+                                cudaStream_t s);
 cudaError_t launch_wave_scan(const WaveArgs &a, int cur, cudaStream_t s);
 cudaError_t launch_hit_sort(const WaveArgs &a, int tile, int sm_count, cudaStream_t s);  // tile: shade_hit_tile
 cudaError_t launch_shade_block(const Shape &sh, const GridView &g, const WaveArgs &a, int sm_count, cudaStream_t s);
+cudaError_t launch_refine(const Shape &sh, const GridView &g, const WaveArgs &a, int sm_count, cudaStream_t s);
 inline int shade_hit_tile(int sdf_width) { return 4096 / sdf_width; }  // hits per shading tile
 cudaError_t launch_coarse_occupancy(const uint32_t *occ, int res, uint32_t *coarse, cudaStream_t s);
 cudaError_t launch_wave_scatter(const WaveArgs &a, int cur, int blocks, cudaStream_t s);

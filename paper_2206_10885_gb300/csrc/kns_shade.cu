@@ -299,6 +299,22 @@ __global__ void __launch_bounds__(STHREADS) shade_block_kernel(GridView g, WaveA
             for (int i = 0; i < 2; ++i) store_n<SPT>(rows + (L::Ud + o0 + i) * SRS + s0, out[i]);
         }
         __syncthreads();
+        if (a.coarse && tid < ST) {
+            // BF16 render: this FP32 evaluation re-evaluates the BF16 trace's last step; a hit it does not
+            // confirm (|d| >= eps) goes to the refinement list with its d, and is not shaded here
+            const int r = s_r[tid];
+            const float d = rows[L::Ud * SRS + tid];
+            const bool refine = r >= 0 && !(fabsf(d) < a.eps);
+            const int q = warp_append(&a.ctrl->n_refine, refine);
+            if (refine) {
+                a.pend_r[0][q] = r;
+                a.pend_t[0][q] = d;
+                s_r[tid] = -1;
+            }
+            const unsigned long long nv = warp_sum_u64(r >= 0 ? 1u : 0u);
+            if ((tid & 31) == 0 && nv) atomicAdd(&a.ctrl->samples_f32, nv);
+        }
+        __syncthreads();
         // reverse mode, in place: D_H = w_d . softplus'(A_H)
         {
             float act[OPT][SPT];

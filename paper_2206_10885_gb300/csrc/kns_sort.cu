@@ -1,8 +1,11 @@
 // kns_sort.cu -- per-wave counting sort of samples by cell (configuration independent).
 //
-// scan:    one block turns the wave's per-cell sample counts into exclusive offsets off[0..NC]
-//          and per-cell block-tile offsets tile_off[0..NC] (ceil(count / btile) tiles per cell),
-//          publishes the tile count, and clears the next wave's counters.
+// scan:    turns the wave's per-key sample counts into exclusive offsets off[0..nkeys] and per-key
+//          tile offsets tile_off[0..nkeys] (ceil(count / tile) tiles per key), writes one descriptor
+//          {key, first sample, samples} per tile, publishes the tile counts, and clears the next
+//          wave's counters.  Two launches of up to 128 blocks: each block sums a contiguous range of
+//          keys (wave_scan_part_kernel), then each block adds the sums of the blocks before it to a
+//          block-wide scan of its range (wave_scan_final_kernel) -- no block waits for another.
 // scatter: each sample goes to off[cell] + (its rank among the wave's samples of that cell);
 //          lanes of a warp that share a cell take consecutive slots with one atomic.
 #include "kns_wave.cuh"
@@ -47,58 +50,110 @@ __device__ __forceinline__ void block_scan2(int &a, int &b, int *wa, int *wb) {
     }
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) wave_scan_kernel(WaveArgs a, int cur) {
+constexpr int SCAN_MAX_BLOCKS = 128;     // WaveCtrl::scan_part entries
+constexpr int SCAN_KEYS_PER_BLOCK = 4096;
+inline int scan_blocks(int nkeys) {
+    const int b = (nkeys + SCAN_KEYS_PER_BLOCK - 1) / SCAN_KEYS_PER_BLOCK;
+    return b < 1 ? 1 : (b > SCAN_MAX_BLOCKS ? SCAN_MAX_BLOCKS : b);
+}
+// keys [k0, k1) of scan block b
+__device__ __forceinline__ void scan_range(int nkeys, int b, int &k0, int &k1) {
+    const int per = (nkeys + gridDim.x - 1) / gridDim.x;
+    k0 = min(nkeys, b * per);
+    k1 = min(nkeys, k0 + per);
+}
+__device__ __forceinline__ int key_tile(const WaveArgs &a, int c) { return c < a.NC ? a.btile : a.btile_bf; }
+
+// Block sums of the round's samples and tiles per key range; clears the next round's counters.
+__global__ void __launch_bounds__(SCAN_THREADS) wave_scan_part_kernel(WaveArgs a, int cur) {
     __shared__ int wa[32], wb[32];
-    const int nxt = cur ^ 1;
-    const int NC = a.nkeys;  // sort keys (cells, or cells x {fine, coarse})
-    // clear the next wave's counters (nothing reads them during this wave)
-    for (int c = threadIdx.x; c < NC; c += SCAN_THREADS) {
+    const int nxt = cur ^ 1, NK = a.nkeys;
+    int k0, k1;
+    scan_range(NK, blockIdx.x, k0, k1);
+    for (int c = k0 + threadIdx.x; c < k1; c += SCAN_THREADS) {  // nothing reads them during this round
         a.count[nxt][c] = 0;
         a.fill[nxt][c] = 0;
     }
-    if (threadIdx.x == 0) {
+    const int n_live = a.ctrl->n_live[cur];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.ctrl->n_live[nxt] = 0;
         a.ctrl->next_tile = 0;
         a.ctrl->next_tile_bf = 0;
         a.ctrl->n_pend[cur] = 0;  // this round's pending list (round k - 2's advance has read it)
+        a.ctrl->tail = n_live <= a.tail_max ? 1 : 0;  // a small round is finished one warp per ray
     }
-    const int n_live = a.ctrl->n_live[cur];
-    // a small round is finished one warp per ray (in cell-sorted order)
-    if (threadIdx.x == 0) a.ctrl->tail = n_live <= a.tail_max ? 1 : 0;
-    if (n_live == 0) {
-        if (threadIdx.x == 0) {
+    if (n_live == 0) return;
+    int sum = 0, tiles = 0;
+    for (int c = k0 + threadIdx.x; c < k1; c += SCAN_THREADS) {
+        const int n = a.count[cur][c], bt = key_tile(a, c);
+        sum += n;
+        tiles += (n + bt - 1) / bt;
+    }
+    block_scan2(sum, tiles, wa, wb);
+    if (threadIdx.x == SCAN_THREADS - 1) {
+        a.ctrl->scan_part[0][blockIdx.x] = sum;
+        a.ctrl->scan_part[1][blockIdx.x] = tiles;
+    }
+}
+
+// Offsets, tile offsets and tile descriptors of each block's key range: the sums of the blocks before
+// it plus a block-wide exclusive scan (each thread a contiguous run of keys, so descriptors come out
+// in key order).
+__global__ void __launch_bounds__(SCAN_THREADS) wave_scan_final_kernel(WaveArgs a, int cur) {
+    __shared__ int wa[32], wb[32];
+    __shared__ int base[2];
+    const int NK = a.nkeys;
+    if (a.ctrl->n_live[cur] == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
             a.ctrl->n_tiles = 0;
             a.ctrl->n_tiles_fine = 0;
         }
         return;
     }
-    // each thread owns a contiguous run of cells
-    const int per = (NC + SCAN_THREADS - 1) / SCAN_THREADS;
-    const int c0 = threadIdx.x * per, c1 = min(NC, c0 + per);
+    if (threadIdx.x < 32) {
+        int bs = 0, bt = 0;
+        for (int i = threadIdx.x; i < (int)blockIdx.x; i += 32) {
+            bs += a.ctrl->scan_part[0][i];
+            bt += a.ctrl->scan_part[1][i];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            bs += __shfl_xor_sync(FULL, bs, o);
+            bt += __shfl_xor_sync(FULL, bt, o);
+        }
+        if (threadIdx.x == 0) {
+            base[0] = bs;
+            base[1] = bt;
+        }
+    }
+    __syncthreads();
+    int k0, k1;
+    scan_range(NK, blockIdx.x, k0, k1);
+    const int per = (k1 - k0 + SCAN_THREADS - 1) / SCAN_THREADS;
+    const int c0 = min(k1, k0 + (int)threadIdx.x * per), c1 = min(k1, c0 + per);
     int sum = 0, tiles = 0;
     for (int c = c0; c < c1; ++c) {
-        const int n = a.count[cur][c];
-        const int bt = c < a.NC ? a.btile : a.btile_bf;  // FP32 keys, then BF16 keys
+        const int n = a.count[cur][c], bt = key_tile(a, c);
         sum += n;
         tiles += (n + bt - 1) / bt;
     }
     int incl_s = sum, incl_t = tiles;
     block_scan2(incl_s, incl_t, wa, wb);
-    int run_s = incl_s - sum, run_t = incl_t - tiles;
+    int run_s = base[0] + incl_s - sum, run_t = base[1] + incl_t - tiles;
     for (int c = c0; c < c1; ++c) {
-        const int n = a.count[cur][c];
-        const int bt = c < a.NC ? a.btile : a.btile_bf;
+        const int n = a.count[cur][c], bt = key_tile(a, c);
         a.off[c] = run_s;
         a.tile_off[c] = run_t;
         if (c == a.NC) a.ctrl->n_tiles_fine = run_t;  // first BF16 key: FP32 tiles end here
         for (int i = 0; i < n; i += bt) a.tiles[run_t++] = make_int4(c, run_s + i, min(bt, n - i), 0);
         run_s += n;
     }
-    if (threadIdx.x == SCAN_THREADS - 1) {
-        a.off[NC] = incl_s;
-        a.tile_off[NC] = incl_t;
-        a.ctrl->n_tiles = incl_t;
-        if (NC == a.NC) a.ctrl->n_tiles_fine = incl_t;  // FP32 render: every tile is FP32
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == SCAN_THREADS - 1) {
+        a.off[NK] = base[0] + incl_s;
+        a.tile_off[NK] = base[1] + incl_t;
+        a.ctrl->n_tiles = base[1] + incl_t;
+        // FP32 renders: every tile is an FP32 tile; BF16 renders: every tile is a tensor-core tile
+        if (NK == a.NC) a.ctrl->n_tiles_fine = a.coarse ? 0 : base[1] + incl_t;
     }
 }
 
@@ -149,7 +204,9 @@ cudaError_t launch_coarse_occupancy(const uint32_t *occ, int res, uint32_t *coar
 }
 
 cudaError_t launch_wave_scan(const WaveArgs &a, int cur, cudaStream_t s) {
-    wave_scan_kernel<<<1, SCAN_THREADS, 0, s>>>(a, cur);
+    const int nb = scan_blocks(a.nkeys);
+    wave_scan_part_kernel<<<nb, SCAN_THREADS, 0, s>>>(a, cur);
+    wave_scan_final_kernel<<<nb, SCAN_THREADS, 0, s>>>(a, cur);
     return cudaGetLastError();
 }
 
@@ -238,14 +295,14 @@ cudaError_t launch_hit_sort(const WaveArgs &a, int tile, int sm_count, cudaStrea
 // round's tiles.
 __global__ void __launch_bounds__(256) wave_advance_kernel(GridView g, WaveArgs a, int p) {
     const int n = a.ctrl->n_pend[p];
-    const bool cycles = a.t_hist != nullptr && !a.coarse;
     const int stride = gridDim.x * blockDim.x;
     const int bound = (n + 31) & ~31;  // warp-uniform loop bound
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < bound; i += stride) {
         bool emit = false;
-        int ncell = -1, r = 0;
+        int ncell = -1, r = 0, key = 0;
         if (i < n) {
             r = a.pend_r[p][i];
+            const bool cycles = a.t_hist != nullptr;
             const float t_eval = a.pend_t[p][i];
             int cam;
             const Ray ray = ray_of(a, r, cam);
@@ -257,22 +314,26 @@ __global__ void __launch_bounds__(256) wave_advance_kernel(GridView g, WaveArgs 
                 write_miss(a, r, a.steps_ray[r]);
             } else {
                 float4 hist = cycles ? a.t_hist[r] : no_history();
-                if (cycles && cycle_step(hist, t_eval, t)) {
+                // BF16 renders: the BF16 trace's cycle test (the rays on these lists are all in it)
+                const bool cyc = cycles && (a.coarse ? cycle_step_tol(hist, t_eval, t) : cycle_step(hist, t_eval, t));
+                if (cyc) {
                     write_miss(a, r, a.max_steps);
                     ncell = -1;
                 } else {
                     emit = true;
+                    key = ncell;
                     a.t_ray[r] = t;
                     if (cycles) a.t_hist[r] = hist;
+                    if (a.trap) a.trap[r] = trap_empty();  // a run of samples ends at an occupancy skip
                 }
             }
         }
         const int qp = warp_append(&a.ctrl->n_live[p], emit);
         if (emit) {
             a.q[p][qp] = r;
-            a.qcell[p][qp] = ncell;
+            a.qcell[p][qp] = key;
         }
-        warp_count_cells(a.count[p], emit, ncell);
+        warp_count_cells(a.count[p], emit, key);
     }
 }
 

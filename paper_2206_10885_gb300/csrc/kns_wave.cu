@@ -8,8 +8,6 @@
 // s = sample); lane (sg, ng) = (lane / 8, lane % 8) accumulates samples 4sg..4sg+3 against output
 // units ng*W/8 .. ng*W/8 + W/8 - 1, so each shared-memory float4 of activations and each float4 of
 // k-major weights feed 16 (W = 32) or 32 (W = 64) FMAs.
-#include <atomic>
-
 #include "kns_wave.cuh"
 
 namespace kns {
@@ -141,16 +139,16 @@ __global__ void __launch_bounds__(128) wave_gen_kernel(GridView g, WaveArgs a) {
                 a.t_ray[r] = t;
                 a.steps_ray[r] = 0;
                 if (a.t_hist) a.t_hist[r] = no_history();
+                if (a.trap) a.trap[r] = trap_empty();
             }
         }
     }
-    const int key = cell + (a.coarse ? a.NC : 0);  // BF16 renders start every ray in the coarse phase
     const int qp = warp_append(&a.ctrl->n_live[0], alive);
     if (alive) {
         a.q[0][qp] = r;
-        a.qcell[0][qp] = key;
+        a.qcell[0][qp] = cell;
     }
-    warp_count_cells(a.count[0], alive, key);
+    warp_count_cells(a.count[0], alive, cell);
 }
 
 // Round k: each warp (a block of its own) takes tiles of up to 16 cell-sorted samples of one cell,
@@ -543,7 +541,7 @@ __device__ __forceinline__ float warp_sdf_trace(const float *__restrict__ wsm, f
 // A tail round: one warp (one block) per ray, to the end.  Rays come in cell-sorted order (the cell
 // of a ray's position is its sort key); the round's tile counter hands them out.  In a BF16 render
 // the tail takes the rays in the FP32 phase (the keys below NC, sorted first), with the block
-// tiles' refinement rule; the rays still in the BF16 phase stay with wave_eval_bf16_kernel.
+// tiles' refinement rule; the rays still in the BF16 phase stay with wave_eval_tc_kernel.
 template <class C>
 __global__ void __launch_bounds__(32) wave_tail_warp_kernel(GridView g, WaveArgs a, int cur) {
     extern __shared__ __align__(128) float dyn[];
@@ -785,22 +783,6 @@ cudaError_t launch_wave_gen_cfg(const GridView &g, const WaveArgs &a, cudaStream
     wave_gen_kernel<C><<<grid, 128, 0, s>>>(g, a);
     return cudaGetLastError();
 }
-// Resident blocks per SM of a kernel with `smem` bytes of dynamic shared memory (registers and shared
-// memory both count), after allowing it the largest shared-memory carve-out; asked once per kernel.
-template <class K>
-cudaError_t resident_blocks(K kernel, int threads, int smem, std::atomic<int> &cache, int &out) {
-    out = cache.load();
-    if (out > 0) return cudaSuccess;
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100)) != cudaSuccess ||
-        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out, kernel, threads, smem)) != cudaSuccess)
-        return e;
-    if (out < 1) out = 1;
-    cache.store(out);
-    return cudaSuccess;
-}
-
 template <class C, int BT, int NT>
 cudaError_t launch_block_eval(const GridView &g, const WaveArgs &a, int cur, int sm_count, cudaStream_t s) {
     constexpr int smem = block_eval_smem_bytes<C, BT>();
