@@ -123,7 +123,8 @@ typedef struct kns_render_opts {
                               default 4 for warp tiles, 2 for block tiles) */
     int32_t min_active;    /* a tile continues only while at least this many of its rays stay in its cell
                               (1..256; a warp tile holds 16; default 8 for warp tiles, 16 for block tiles) */
-    int32_t tail_rays;     /* a round with at most this many rays is finished one warp per ray (>= 0; -1: never) */
+    int32_t tail_rays;     /* a round with at most this many rays is finished one warp per ray, in FP32 (>= 0;
+                              -1: never; default 131072, 32768 for KNS_BF16) */
     int32_t blocks_per_sm; /* evaluation blocks (one warp each) launched per SM (1..64) */
     int32_t static_tiles;  /* 1: each block takes a contiguous run of tiles; 2: tiles handed out dynamically */
     int32_t timing;        /* 1: time each kernel class with CUDA events for kns_get_render_stats (adds host work) */
@@ -135,6 +136,9 @@ typedef struct kns_render_opts {
                                  its cell (1..1024; default 2) */
     int32_t bf16_min_active;  /* KNS_BF16: a tensor-core tile continues while at least this many of its rays stay
                                  (1..128; default 16) */
+    int32_t bf16_rounds;      /* KNS_BF16: 1 = every round of the trace in one persistent launch (rounds run on the
+                                 device, no host synchronisation); 2 = one launch sequence per round driven by
+                                 the host; 0 = default (1).  Results are identical. */
 } kns_render_opts;
 
 /* Counters of the last kns_render on a context (kns_get_render_stats). */
@@ -214,9 +218,10 @@ kns_status kns_get_render_stats(kns_ctx *ctx, kns_render_stats *out);
  * next sample (and, in-tile, possibly a few more). */
 typedef struct kns_round_info {
     int32_t live;        /* samples queued for the round */
-    float ms_sort;       /* device time of the round's sort, FP32 and BF16 evaluation (opts->timing, else 0) */
-    float ms_eval_fp32;
-    float ms_eval_bf16;
+    float ms_sort;       /* device time of the round's sort (scan and scatter), FP32 and BF16 evaluation and, */
+    float ms_eval_fp32;  /* in a persistent BF16 trace, its empty-space walk: per-class CUDA events under     */
+    float ms_eval_bf16;  /* opts->timing for host-driven rounds, the device timer for the persistent trace    */
+    float ms_advance;
 } kns_round_info;
 
 /* Per-round trace of the last render call on this context: writes min(*n_rounds, max_rounds) entries

@@ -115,7 +115,7 @@ def alloc_frame(n_pix: int, device="cuda", extras: bool = True):
 
 
 TUNING_FIELDS = ("inner_steps", "min_active", "tail_rays", "blocks_per_sm", "static_tiles", "timing", "block_tiles",
-                 "bf16_inner_steps", "bf16_min_active")
+                 "bf16_inner_steps", "bf16_min_active", "bf16_rounds")
 
 
 def render_opts(precision: int = KNS_FP32, eps_coarse: float = 0.0, refine_steps: int = -1, tuning=None):

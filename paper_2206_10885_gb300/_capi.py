@@ -79,7 +79,8 @@ class kns_render_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("eps_coarse", C.c_float), ("refine_steps", C.c_int32),
                 ("inner_steps", C.c_int32), ("min_active", C.c_int32), ("tail_rays", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("static_tiles", C.c_int32), ("timing", C.c_int32),
-                ("block_tiles", C.c_int32), ("bf16_inner_steps", C.c_int32), ("bf16_min_active", C.c_int32)]
+                ("block_tiles", C.c_int32), ("bf16_inner_steps", C.c_int32), ("bf16_min_active", C.c_int32),
+                ("bf16_rounds", C.c_int32)]
 
 
 class kns_render_stats(C.Structure):
@@ -90,7 +91,8 @@ class kns_render_stats(C.Structure):
 
 
 class kns_round_info(C.Structure):
-    _fields_ = [("live", C.c_int32), ("ms_sort", C.c_float), ("ms_eval_fp32", C.c_float), ("ms_eval_bf16", C.c_float)]
+    _fields_ = [("live", C.c_int32), ("ms_sort", C.c_float), ("ms_eval_fp32", C.c_float), ("ms_eval_bf16", C.c_float),
+                ("ms_advance", C.c_float)]
 
 
 _lib = None

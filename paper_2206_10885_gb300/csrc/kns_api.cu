@@ -360,6 +360,9 @@ constexpr int kRenderTailRays = 131072;  // rounds this small finish one warp pe
 // tensor-core tiles (BF16 renders): a second evaluation while at least 16 rays stay in the cell
 constexpr int kRenderBf16InnerSteps = 2;
 constexpr int kRenderBf16MinActive = 16;
+// BF16 renders hand rounds of at most this many rays (live + pending) to the one-warp-per-ray FP32
+// tail: the best of 8K..512K on both 1080p workloads (a tensor-core round costs ~50 us however few its rays)
+constexpr int kRenderBf16TailRays = 32768;
 constexpr int kRenderBlocksPerSM = 16;
 constexpr int kRenderStaticTiles = 2;
 
@@ -827,6 +830,7 @@ struct RenderCfg {
     int refine_steps = 2, inner_steps = kRenderInnerSteps, min_active = kRenderMinActive,
         tail_rays = kRenderTailRays, blocks_per_sm = kRenderBlocksPerSM, static_tiles = 1;
     int inner_steps_bf = kRenderBf16InnerSteps, min_active_bf = kRenderBf16MinActive;
+    bool persistent = true;  // BF16: every round in one persistent launch
     int block_mode = 1;  // 0 = 16-sample warp tiles; block tiles: 1 = 128 samples x 256 threads,
                          // 3 = 256 x 256, 4 = 128 x 128
 };
@@ -848,13 +852,17 @@ kns_status resolve_opts(kns_ctx *ctx, const kns_render_opts *opts, float eps, Re
     const int def_min = bt0 == 2 ? kRenderMinActive : kRenderBlockMinActive;
     c.inner_steps = opts ? knob(opts->inner_steps, def_inner) : def_inner;
     c.min_active = opts ? knob(opts->min_active, def_min) : def_min;
-    c.tail_rays = opts ? knob(opts->tail_rays, kRenderTailRays) : kRenderTailRays;
+    const int def_tail = c.bf16 ? kRenderBf16TailRays : kRenderTailRays;
+    c.tail_rays = opts ? knob(opts->tail_rays, def_tail) : def_tail;
     c.blocks_per_sm = opts ? knob(opts->blocks_per_sm, kRenderBlocksPerSM) : kRenderBlocksPerSM;
     c.static_tiles = (opts ? knob(opts->static_tiles, kRenderStaticTiles) : kRenderStaticTiles) == 1;
     c.inner_steps_bf = opts ? knob(opts->bf16_inner_steps, kRenderBf16InnerSteps) : kRenderBf16InnerSteps;
     c.min_active_bf = opts ? knob(opts->bf16_min_active, kRenderBf16MinActive) : kRenderBf16MinActive;
     if (c.inner_steps_bf < 1 || c.inner_steps_bf > 1024 || c.min_active_bf < 1 || c.min_active_bf > 128)
         return set_err(ctx, KNS_ERR_INVALID_ARG, "bf16 tuning field out of range");
+    if (opts && (opts->bf16_rounds < 0 || opts->bf16_rounds > 2))
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "bf16_rounds must be 0, 1 or 2");
+    c.persistent = !(opts && opts->bf16_rounds == 2);
     if (c.inner_steps < 1 || c.inner_steps > 1024 || c.min_active < 1 || c.min_active > 256 || c.tail_rays < -1 ||
         c.blocks_per_sm < 1 || c.blocks_per_sm > 64 || (opts && (opts->static_tiles < 0 || opts->static_tiles > 2)) ||
         (opts && (opts->block_tiles < 0 || opts->block_tiles > 4)))
@@ -971,7 +979,18 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
     // both are zero (rounds k - 1 and k then hold nothing), so it runs at most two rounds ahead.
     int last_adv = -1;  // the last round whose advance kernel was launched
     const int round0 = (int)ctx->round_live.size();  // rounds of earlier batches of this call
-    for (int k = 0; k < 2 * max_steps + 2 && e == cudaSuccess; ++k) {
+    if (e == cudaSuccess && cfg.bf16 && cfg.persistent) {  // every round on the device, one launch
+        a.btile = 128;
+        const int tm = timing_begin(ctx, cfg.timing, kTEvalBF16, s);
+        e = kns::launch_trace_tc(grid->shape, grid->view, a, ctx->sm_count, s);
+        timing_end(ctx, tm, s);
+        if (e == cudaSuccess) {  // the rays of the round it left, one warp per ray (nothing when none)
+            const int tm2 = timing_begin(ctx, cfg.timing, kTEvalF32, s);
+            e = kns::launch_wave_tail(grid->shape, grid->view, a, -1, ctx->sm_count, s);
+            timing_end(ctx, tm2, s);
+        }
+    }
+    for (int k = 0; k < 2 * max_steps + 2 && e == cudaSuccess && !(cfg.bf16 && cfg.persistent); ++k) {
         const int cur = k & 1;
         if (k >= 2) {
             e = cudaEventSynchronize(ctx->ev_live[(k - 2) & 3]);
@@ -989,6 +1008,8 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
         // (BF16), block tiles of 128 or 256, or warp tiles of 16
         if (cfg.bf16 || cfg.block_mode == 1 || cfg.block_mode == 4) a.btile = 128;
         else if (cfg.block_mode == 3) a.btile = 256;
+        // BF16: the first round always runs on the tensor cores (no one-warp-per-ray tail)
+        a.tail_max = (cfg.bf16 && k == 0) ? -1 : cfg.tail_rays;
         int tm = timing_begin(ctx, cfg.timing, kTSort, s);
         e = kns::launch_wave_scan(a, cur, s);
         int *hl = ctx->h_live + 2 * (k & 3);
@@ -1005,9 +1026,12 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
         }
         if (e == cudaSuccess) e = kns::launch_wave_scatter(a, cur, scatter_blocks, s);
         timing_end(ctx, tm, s);
-        if (e == cudaSuccess && cfg.bf16) {  // tensor-core tiles only
+        if (e == cudaSuccess && cfg.bf16) {  // tensor-core tiles, or the one-warp-per-ray tail of a small round
             tm = timing_begin(ctx, cfg.timing, kTEvalBF16, s);
             e = kns::launch_wave_eval_tc(grid->shape, grid->view, a, cur, ctx->sm_count, s);
+            timing_end(ctx, tm, s);
+            tm = timing_begin(ctx, cfg.timing, kTEvalF32, s);
+            if (e == cudaSuccess) e = kns::launch_wave_tail(grid->shape, grid->view, a, cur, ctx->sm_count, s);
             timing_end(ctx, tm, s);
         } else if (e == cudaSuccess) {  // FP32 tiles and the one-warp-per-ray tail
             tm = timing_begin(ctx, cfg.timing, kTEvalF32, s);
@@ -1254,6 +1278,7 @@ kns_status kns_get_render_stats(kns_ctx *ctx, kns_render_stats *out) {
     st.samples_fp32 += (int64_t)hc.samples_f32;
     st.samples_bf16 += (int64_t)hc.samples_bf16;
     st.samples_tail += (int64_t)hc.samples_tail;
+    st.rounds += hc.rounds;  // a persistent BF16 trace counts its rounds on the device
     float *dst[5] = {&st.ms_generate, &st.ms_sort, &st.ms_eval_fp32, &st.ms_eval_bf16, &st.ms_shade};
     for (const auto &m : ctx->ev_marks) {
         float ms = 0.f;
@@ -1273,12 +1298,26 @@ kns_status kns_get_round_trace(kns_ctx *ctx, kns_round_info *out, int32_t max_ro
     DeviceScope ds(ctx->device);
     cudaError_t e = cudaStreamSynchronize(ctx->stats_stream);
     if (e != cudaSuccess) return cuda_err(ctx, e, "round trace");
+    kns::WaveCtrl hc{};
+    if (ctx->ws.ctrl) e = cudaMemcpy(&hc, ctx->ws.ctrl, sizeof(hc), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "round trace");
+    if (hc.rounds > 0) {  // the persistent BF16 trace: its own per-round counts and timer stamps
+        const int n = std::min(hc.rounds, kns::kMaxTraceRounds);
+        *n_rounds = n;
+        auto ms = [](unsigned long long a, unsigned long long b) { return (float)((double)(b - a) * 1e-6); };
+        for (int k = 0; k < std::min(n, (int)max_rounds); ++k) {
+            const unsigned long long t0 = k == 0 ? hc.start_ns : hc.round_end_ns[k - 1];
+            const unsigned long long *ph = hc.round_phase_ns[k];
+            out[k] = kns_round_info{hc.round_live[k], ms(t0, ph[2]), 0.f, ms(ph[2], ph[3]), ms(ph[3], hc.round_end_ns[k])};
+        }
+        return KNS_OK;
+    }
     const int n = (int)ctx->round_live.size();
     // the last rounds' counts were copied to the pinned ring but not read by the render loop
     for (int k = std::max(0, n - 4); k < n; ++k)
         if (ctx->round_live[k] < 0) ctx->round_live[k] = ctx->h_live[2 * (k & 3)];
     *n_rounds = n;
-    for (int k = 0; k < std::min(n, (int)max_rounds); ++k) out[k] = kns_round_info{ctx->round_live[k], 0.f, 0.f, 0.f};
+    for (int k = 0; k < std::min(n, (int)max_rounds); ++k) out[k] = kns_round_info{ctx->round_live[k], 0.f, 0.f, 0.f, 0.f};
     for (const auto &m : ctx->ev_marks) {
         if (m.round < 0 || m.round >= std::min(n, (int)max_rounds)) continue;
         float ms = 0.f;

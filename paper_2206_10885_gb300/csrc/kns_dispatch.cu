@@ -45,6 +45,13 @@ cudaError_t launch_shade_block(const Shape &sh, const GridView &g, const WaveArg
 cudaError_t launch_refine(const Shape &sh, const GridView &g, const WaveArgs &a, int sm_count, cudaStream_t s) {
     return dispatch(sh, [&](auto c) { return launch_refine_cfg<decltype(c)>(g, a, sm_count, s); });
 }
+cudaError_t launch_wave_tail(const Shape &sh, const GridView &g, const WaveArgs &a, int cur, int sm_count,
+                             cudaStream_t s) {
+    return dispatch(sh, [&](auto c) { return launch_wave_tail_cfg<decltype(c)>(g, a, cur, sm_count, s); });
+}
+cudaError_t launch_trace_tc(const Shape &sh, const GridView &g, const WaveArgs &a, int sm_count, cudaStream_t s) {
+    return dispatch(sh, [&](auto c) { return launch_trace_tc_cfg<decltype(c)>(g, a, sm_count, s); });
+}
 cudaError_t launch_wave_eval_tc(const Shape &sh, const GridView &g, const WaveArgs &a, int cur, int sm_count,
                                 cudaStream_t s) {
     return dispatch(sh, [&](auto c) { return launch_wave_eval_tc_cfg<decltype(c)>(g, a, cur, sm_count, s); });

@@ -26,9 +26,19 @@ struct WaveCtrl {
     unsigned long long samples_f32;   // SDF evaluations in FP32 (tiles and the tail)
     unsigned long long samples_bf16;  // SDF evaluations in BF16 tiles
     unsigned long long samples_tail;  // the part of samples_f32 evaluated by the one-warp-per-ray tail
-    int scan_part[2][128];            // per scan block of a round: its samples and tiles (the sort's scan)
+    int scan_part[2][256];            // per scan block of a round: its samples and tiles (the sort's scan)
     int n_refine;                     // BF16 renders: hits the shading's FP32 evaluation did not confirm
+    // persistent BF16 trace (one cooperative launch runs every round)
+    unsigned bar_count, bar_gen;      // grid barrier: arrivals, generation
+    int next_adv;                     // the previous round's pending rays handed out to warps
+    int rounds;                       // rounds it ran
+    int tail_parity;                  // queue parity of the round it left to the one-warp-per-ray tail
+    int round_live[512];              // samples queued for each round
+    unsigned long long round_end_ns[512];  // global timer at the end of each round
+    unsigned long long round_phase_ns[512][4];  // ... and at the end of its sort, scatter and tile phases
+    unsigned long long start_ns;      // global timer at its start
 };
+constexpr int kMaxTraceRounds = 512;
 
 // One view of a render: its camera, image size, first ray id and output buffers (device, 128 B).
 struct ViewDev {
@@ -95,10 +105,17 @@ cudaError_t launch_wave_advance(const GridView &g, const WaveArgs &a, int p, int
 template <class C>
 cudaError_t launch_wave_eval_cfg(const GridView &g, const WaveArgs &a, int cur, int blocks, int block_tiles,
                                  int sm_count, cudaStream_t s);
+// The one-warp-per-ray tail of a round (returns at once unless ctrl->tail is set).
+template <class C>
+cudaError_t launch_wave_tail_cfg(const GridView &g, const WaveArgs &a, int cur, int sm_count, cudaStream_t s);
 template <class C>
 cudaError_t launch_shade_block_cfg(const GridView &g, const WaveArgs &a, int sm_count, cudaStream_t s);
 template <class C>
 cudaError_t launch_wave_eval_tc_cfg(const GridView &g, const WaveArgs &a, int cur, int sm_count, cudaStream_t s);
+// Every round of a BF16 render after ray generation, in one cooperative launch (one block per SM);
+// the rounds run in the kernel, separated by grid barriers.
+template <class C>
+cudaError_t launch_trace_tc_cfg(const GridView &g, const WaveArgs &a, int sm_count, cudaStream_t s);
 // BF16 renders, after the shading: the FP32 steps of the hits on the refinement list (pend_r[0],
 // pend_t[0] = the FP32 d at the ray's t), then their shading, one thread per ray.
 template <class C>
@@ -119,6 +136,9 @@ cudaError_t launch_wave_eval(const Shape &sh, const GridView &g, const WaveArgs 
                              int block_tiles, int sm_count, cudaStream_t s);
 cudaError_t launch_wave_eval_tc(const Shape &sh, const GridView &g, const WaveArgs &a, int cur, int sm_count,
                                 cudaStream_t s);
+cudaError_t launch_trace_tc(const Shape &sh, const GridView &g, const WaveArgs &a, int sm_count, cudaStream_t s);
+cudaError_t launch_wave_tail(const Shape &sh, const GridView &g, const WaveArgs &a, int cur, int sm_count,
+                             cudaStream_t s);
 cudaError_t launch_wave_scan(const WaveArgs &a, int cur, cudaStream_t s);
 cudaError_t launch_hit_sort(const WaveArgs &a, int tile, int sm_count, cudaStream_t s);  // tile: shade_hit_tile
 cudaError_t launch_shade_block(const Shape &sh, const GridView &g, const WaveArgs &a, int sm_count, cudaStream_t s);

@@ -80,7 +80,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) wave_scan_part_kernel(WaveArgs a
         a.ctrl->next_tile = 0;
         a.ctrl->next_tile_bf = 0;
         a.ctrl->n_pend[cur] = 0;  // this round's pending list (round k - 2's advance has read it)
-        a.ctrl->tail = n_live <= a.tail_max ? 1 : 0;  // a small round is finished one warp per ray
+        // a small round is finished one warp per ray (its count includes the rays the previous round left
+        // in empty voxels, which join the next round: the same rule as the persistent BF16 trace)
+        a.ctrl->tail = n_live + a.ctrl->n_pend[nxt] <= a.tail_max ? 1 : 0;
     }
     if (n_live == 0) return;
     int sum = 0, tiles = 0;
@@ -297,44 +299,7 @@ __global__ void __launch_bounds__(256) wave_advance_kernel(GridView g, WaveArgs 
     const int n = a.ctrl->n_pend[p];
     const int stride = gridDim.x * blockDim.x;
     const int bound = (n + 31) & ~31;  // warp-uniform loop bound
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < bound; i += stride) {
-        bool emit = false;
-        int ncell = -1, r = 0, key = 0;
-        if (i < n) {
-            r = a.pend_r[p][i];
-            const bool cycles = a.t_hist != nullptr;
-            const float t_eval = a.pend_t[p][i];
-            int cam;
-            const Ray ray = ray_of(a, r, cam);
-            float t0, tf;
-            clip_box(g, ray, t0, tf);
-            float t = a.t_ray[r];
-            ncell = advance_ray(g, ray, t, tf);
-            if (ncell < 0) {
-                write_miss(a, r, a.steps_ray[r]);
-            } else {
-                float4 hist = cycles ? a.t_hist[r] : no_history();
-                // BF16 renders: the BF16 trace's cycle test (the rays on these lists are all in it)
-                const bool cyc = cycles && (a.coarse ? cycle_step_tol(hist, t_eval, t) : cycle_step(hist, t_eval, t));
-                if (cyc) {
-                    write_miss(a, r, a.max_steps);
-                    ncell = -1;
-                } else {
-                    emit = true;
-                    key = ncell;
-                    a.t_ray[r] = t;
-                    if (cycles) a.t_hist[r] = hist;
-                    if (a.trap) a.trap[r] = trap_empty();  // a run of samples ends at an occupancy skip
-                }
-            }
-        }
-        const int qp = warp_append(&a.ctrl->n_live[p], emit);
-        if (emit) {
-            a.q[p][qp] = r;
-            a.qcell[p][qp] = key;
-        }
-        warp_count_cells(a.count[p], emit, key);
-    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < bound; i += stride) advance_pending(g, a, p, p, i, n);
 }
 
 cudaError_t launch_wave_advance(const GridView &g, const WaveArgs &a, int p, int sm_count, cudaStream_t s) {

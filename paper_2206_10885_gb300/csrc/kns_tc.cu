@@ -113,61 +113,71 @@ __device__ __forceinline__ void issue_layer(uint32_t tmem, uint32_t a_hi, uint32
     tc::mma_commit(bar);
 }
 
-constexpr uint32_t kTcPolls = 1u << 26;  // bound of every mbarrier wait
+constexpr uint32_t kTcPolls = 1u << 26;    // bound of every mbarrier wait
+constexpr uint32_t kGridPolls = 1u << 22;  // bound of every grid-barrier wait (polls of ~0.1 us)
 
+// A warpgroup worker: 128 threads that evaluate tiles on their own weights, activation matrices,
+// tensor-memory columns and mbarriers, synchronised by their own named barrier.
+struct TcWorker {
+    unsigned char *wsm, *A;   // shared: the cell's weights, the activation matrices
+    uint64_t *bar_w, *bar_mma;
+    int *s_tile;              // 4 ints: key, first sample, samples, fresh
+    int *s_red;               // 4 ints: per-warp partial counts
+    uint32_t tmem;            // first tensor-memory column of the worker's accumulator
+    int bar;                  // named barrier id
+    int tid, warp;            // thread (0..127) and warp (0..3) within the worker
+    int cached;               // cell of the staged weights
+    uint32_t ph_w, ph_mma;    // mbarrier phases
+    bool w_pending, mma_pending;  // a weight copy / a tensor-core chain in flight
+    unsigned n_eval;          // samples this thread evaluated
+};
+
+__device__ __forceinline__ void wg_bar(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
+
+// Threads of the worker whose p is true (every thread of the worker calls it).
+__device__ __forceinline__ int wg_count(TcWorker &w, bool p) {
+    const unsigned b = __ballot_sync(FULL, p);
+    if ((w.tid & 31) == 0) w.s_red[w.warp] = __popc(b);
+    wg_bar(w.bar);
+    const int n = w.s_red[0] + w.s_red[1] + w.s_red[2] + w.s_red[3];
+    wg_bar(w.bar);
+    return n;
+}
+
+// One round of the BF16 trace for one worker: tiles [0, n_tiles) of the round, a contiguous run per
+// worker (gi of nw workers) or handed out one at a time.  Returns false when a wait ran out.
 template <class C>
-__global__ void __launch_bounds__(128) wave_eval_tc_kernel(GridView g, WaveArgs a, int cur) {
+__device__ bool tc_round(TcWorker &w, const GridView &g, const WaveArgs &a, int cur, int n_tiles, int gi, int nw) {
     using T = TcLayout<C>;
-    extern __shared__ __align__(1024) unsigned char dyn[];
-    __shared__ __align__(8) uint64_t bar_w, bar_mma;
-    __shared__ uint32_t s_tmem;
-    __shared__ int s_tile[4];  // key, start, len, fresh
-    const int n_tiles = a.ctrl->n_tiles;
-    if (n_tiles <= 0) return;  // uniform over the block, before any tensor memory is held
-    const int tid = threadIdx.x, warp = tid >> 5, nxt = cur ^ 1;
-    unsigned char *wsm = dyn, *A = dyn + T::SIZE;
-    const uint32_t w_base = tc::saddr(wsm), a_base = tc::saddr(A);
-    if (warp == 0) tc::tmem_alloc(&s_tmem, (uint32_t)T::W);
-    if (tid == 0) {
-        mbar_init(&bar_w, 1);
-        mbar_init(&bar_mma, 1);
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    const uint32_t tmem = s_tmem;
-    const uint32_t t_lane = tmem + ((uint32_t)(32 * warp) << 16);
-    const float *bias = reinterpret_cast<const float *>(wsm + T::BIAS);
-    const float *drow = reinterpret_cast<const float *>(wsm + T::DROW);
-    const int per = (n_tiles + gridDim.x - 1) / gridDim.x;
-    int next_static = blockIdx.x * per;
+    const int tid = w.tid, nxt = cur ^ 1;
+    const uint32_t w_base = tc::saddr(w.wsm), a_base = tc::saddr(w.A);
+    const uint32_t t_lane = w.tmem + ((uint32_t)(32 * w.warp) << 16);
+    const float *bias = reinterpret_cast<const float *>(w.wsm + T::BIAS);
+    const float *drow = reinterpret_cast<const float *>(w.wsm + T::DROW);
+    unsigned char *A = w.A;
+    const int per = (n_tiles + nw - 1) / nw;
+    int next_static = gi * per;
     const int end_static = min(n_tiles, next_static + per);
-    int cached = -1;
-    uint32_t ph_w = 0, ph_mma = 0;
-    bool w_pending = false, mma_pending = false;  // a copy or a product in flight (for a timeout exit)
-    bool failed = false;
-    unsigned n_eval = 0;
     const bool cycles = a.t_hist != nullptr;
     for (;;) {
         if (tid == 0) {
-            int tile = a.static_tiles ? (next_static < end_static ? next_static : n_tiles)
-                                      : atomicAdd(&a.ctrl->next_tile_bf, 1);
+            const int tile = a.static_tiles ? (next_static < end_static ? next_static : n_tiles)
+                                            : atomicAdd(&a.ctrl->next_tile_bf, 1);
             ++next_static;
             int4 d = make_int4(-1, 0, 0, 0);
             if (tile < n_tiles) d = a.tiles[tile];
-            const bool fresh = d.x >= 0 && d.x != cached;
-            if (fresh) bulk_load(wsm, a.wb + (int64_t)d.x * a.wb_stride, T::SIZE, &bar_w);
-            s_tile[0] = d.x;
-            s_tile[1] = d.y;
-            s_tile[2] = d.z;
-            s_tile[3] = fresh;
+            const bool fresh = d.x >= 0 && d.x != w.cached;
+            if (fresh) bulk_load(w.wsm, a.wb + (int64_t)d.x * a.wb_stride, T::SIZE, w.bar_w);
+            w.s_tile[0] = d.x;
+            w.s_tile[1] = d.y;
+            w.s_tile[2] = d.z;
+            w.s_tile[3] = fresh;
         }
-        __syncthreads();
-        const int key = s_tile[0], start = s_tile[1], len = s_tile[2];
-        const bool fresh = s_tile[3] != 0;
-        if (key < 0) break;
-        cached = key;
-        const int c = key;
+        wg_bar(w.bar);
+        const int c = w.s_tile[0], start = w.s_tile[1], len = w.s_tile[2];
+        const bool fresh = w.s_tile[3] != 0;
+        if (c < 0) break;
+        w.cached = c;
         bool active = tid < len;
         int r = 0, steps = 0;
         float t = 0.f, t0 = 0.f, tf = 0.f;
@@ -184,35 +194,29 @@ __global__ void __launch_bounds__(128) wave_eval_tc_kernel(GridView g, WaveArgs 
             ray = ray_of(a, r, cam);
             clip_box(g, ray, t0, tf);
         }
-        if (fresh) w_pending = true;
+        if (fresh) w.w_pending = true;
         for (int it = 0;; ++it) {
             if (active) encode_row<C, T>(A, tid, fmaf(t, ray.wx, ray.ox), fmaf(t, ray.wy, ray.oy), fmaf(t, ray.wz, ray.oz));
             tc::fence_async_smem();
-            if (w_pending) {
-                const bool ok = mbar_wait(&bar_w, ph_w, kTcPolls);
-                if (__syncthreads_or(!ok)) {
-                    failed = true;
-                    break;
-                }
-                ph_w ^= 1u;
-                w_pending = false;
+            if (w.w_pending) {
+                const bool ok = mbar_wait(w.bar_w, w.ph_w, kTcPolls);
+                if (wg_count(w, !ok) > 0) return false;
+                w.ph_w ^= 1u;
+                w.w_pending = false;
             }
-            // the hidden layers: products on the tensor cores, bias + softplus + split on the block
+            // the hidden layers: products on the tensor cores, bias + softplus + split on the worker
             float d = 0.f;
             for (int l = 0; l < C::H; ++l) {
-                __syncthreads();
+                wg_bar(w.bar);
                 if (tid == 0) {
                     tc::fence_after_sync();
-                    issue_layer<T>(tmem, a_base, w_base, l, &bar_mma);
+                    issue_layer<T>(w.tmem, a_base, w_base, l, w.bar_mma);
                 }
-                mma_pending = true;
-                const bool ok = mbar_wait(&bar_mma, ph_mma, kTcPolls);
-                if (__syncthreads_or(!ok)) {
-                    failed = true;
-                    break;
-                }
-                ph_mma ^= 1u;
-                mma_pending = false;
+                w.mma_pending = true;
+                const bool ok = mbar_wait(w.bar_mma, w.ph_mma, kTcPolls);
+                if (wg_count(w, !ok) > 0) return false;
+                w.ph_mma ^= 1u;
+                w.mma_pending = false;
                 tc::fence_after_sync();
                 if (__any_sync(FULL, active)) {
                     float dacc = drow[T::W];  // the d row's bias (stored right after the row)
@@ -235,11 +239,10 @@ __global__ void __launch_bounds__(128) wave_eval_tc_kernel(GridView g, WaveArgs 
                 tc::fence_async_smem();
                 tc::fence_before_sync();
             }
-            if (failed) break;
             // outcome: 0 none, 1 converged (hit list), 2 miss (written), 3 pending, 4 emit to ncell
             int outcome = 0, ncell = -1;
-            float t_eval = t;
-            n_eval += active ? 1u : 0u;
+            const float t_eval = t;
+            w.n_eval += active ? 1u : 0u;
             if (active) {
                 ++steps;
                 if (fabsf(d) < a.eps_coarse) {
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(128) wave_eval_tc_kernel(GridView g, WaveArgs 
                 }
             }
             const bool cand = outcome == 4 && ncell == c && it + 1 < a.inner_steps_bf;
-            const int n_cand = __syncthreads_count(cand);
+            const int n_cand = wg_count(w, cand);
             const bool again = n_cand > 0 && n_cand >= a.min_active_bf;
             const bool stay = cand && again;
             {
@@ -296,22 +299,321 @@ __global__ void __launch_bounds__(128) wave_eval_tc_kernel(GridView g, WaveArgs 
             }
             if (!again) break;
         }
-        if (failed) break;
-        __syncthreads();  // every thread is done with the weights and the tile's state
+        wg_bar(w.bar);  // every thread is done with the weights and the tile's state
     }
-    if (failed) {
-        if (tid == 0) atomicCAS(a.status, 0, (int)6 /* KNS_ERR_TIMEOUT */);
-        // let what is in flight land before the block leaves (bounded as well)
-        if (w_pending) mbar_wait(&bar_w, ph_w, kTcPolls);
-        if (mma_pending) mbar_wait(&bar_mma, ph_mma, kTcPolls);
+    return true;
+}
+
+// The end of a worker: after a failed wait, report it and let what is in flight land (bounded); add
+// the worker's evaluation count.
+__device__ __forceinline__ void tc_worker_done(TcWorker &w, const WaveArgs &a, bool ok) {
+    if (!ok) {
+        if (w.tid == 0) atomicCAS(a.status, 0, (int)6 /* KNS_ERR_TIMEOUT */);
+        if (w.w_pending) mbar_wait(w.bar_w, w.ph_w, kTcPolls);
+        if (w.mma_pending) mbar_wait(w.bar_mma, w.ph_mma, kTcPolls);
     }
-    {
-        const unsigned long long n = warp_sum_u64(n_eval);
-        if ((tid & 31) == 0 && n) atomicAdd(&a.ctrl->samples_bf16, n);
+    const unsigned long long n = warp_sum_u64(w.n_eval);
+    if ((w.tid & 31) == 0 && n) atomicAdd(&a.ctrl->samples_bf16, n);
+}
+
+// ---------------------------------------------------------------- one round per launch
+template <class C>
+__global__ void __launch_bounds__(128) wave_eval_tc_kernel(GridView g, WaveArgs a, int cur) {
+    using T = TcLayout<C>;
+    extern __shared__ __align__(1024) unsigned char dyn[];
+    __shared__ __align__(8) uint64_t bar_w, bar_mma;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_tile[4], s_red[4];
+    const int n_tiles = a.ctrl->n_tiles;
+    // uniform over the block, before any tensor memory is held; a small round (at most tail_rays rays)
+    // is finished one warp per ray by wave_tail_warp_kernel
+    if (n_tiles <= 0 || a.ctrl->tail) return;
+    const int tid = threadIdx.x;
+    if (tid < 32) tc::tmem_alloc(&s_tmem, (uint32_t)T::W);
+    if (tid == 0) {
+        mbar_init(&bar_w, 1);
+        mbar_init(&bar_mma, 1);
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_free(tmem, (uint32_t)T::W);
+    tc::fence_after_sync();
+    TcWorker w{dyn, dyn + T::SIZE, &bar_w, &bar_mma, s_tile, s_red, s_tmem, 1, tid, tid >> 5, -1, 0u, 0u,
+               false, false, 0u};
+    const bool ok = tc_round<C>(w, g, a, cur, n_tiles, blockIdx.x, gridDim.x);
+    tc_worker_done(w, a, ok);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid < 32) tc::tmem_free(s_tmem, (uint32_t)T::W);
+}
+
+// ---------------------------------------------------------------- every round in one launch
+// Grid-wide barrier of a cooperative launch (every block resident): the blocks' thread 0 count in on
+// a global counter; the last to arrive resets it and advances the generation the others poll.  Bounded:
+// false after kGridPolls polls (the caller reports KNS_ERR_TIMEOUT and leaves).  Block-uniform result.
+__device__ __forceinline__ bool grid_sync(WaveCtrl *ctrl, unsigned &gen, int *s_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned target = gen + 1;
+        __threadfence();
+        if (atomicAdd(&ctrl->bar_count, 1u) == gridDim.x - 1) {
+            atomicExch(&ctrl->bar_count, 0u);
+            __threadfence();
+            atomicExch(&ctrl->bar_gen, target);
+        } else {
+            uint32_t i = 0;
+            while (*(volatile unsigned *)&ctrl->bar_gen != target) {
+                if (++i > kGridPolls) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        gen = target;
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
+// Inclusive scan of two values over the block (blockDim.x a multiple of 32, at most 1024 threads).
+__device__ __forceinline__ void block_scan2_any(int &x, int &y, int *wx, int *wy) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(FULL, x, o), b = __shfl_up_sync(FULL, y, o);
+        if (lane >= o) {
+            x += a;
+            y += b;
+        }
+    }
+    if (lane == 31) {
+        wx[warp] = x;
+        wy[warp] = y;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int sx = lane < nw ? wx[lane] : 0, sy = lane < nw ? wy[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int a = __shfl_up_sync(FULL, sx, o), b = __shfl_up_sync(FULL, sy, o);
+            if (lane >= o) {
+                sx += a;
+                sy += b;
+            }
+        }
+        if (lane < nw) {
+            wx[lane] = sx;
+            wy[lane] = sy;
+        }
+    }
+    __syncthreads();
+    if (warp > 0) {
+        x += wx[warp - 1];
+        y += wy[warp - 1];
+    }
+    __syncthreads();
+}
+
+// Workers per block of the persistent trace: as many as shared memory holds, at most 4.
+template <class C>
+__host__ __device__ constexpr int tc_workers() {
+    constexpr int per = TcLayout<C>::SMEM, by_smem = (227 * 1024 - 2048) / per;
+    return by_smem < 1 ? 1 : (by_smem > 4 ? 4 : by_smem);
+}
+__host__ __device__ constexpr uint32_t pow2_cols(int n) {
+    return n <= 32 ? 32u : n <= 64 ? 64u : n <= 128 ? 128u : n <= 256 ? 256u : 512u;
+}
+
+// The rounds of a BF16 render after ray generation, in one cooperative launch of one block per SM
+// with NW warpgroup workers each.  Per round, separated by grid barriers: (1) per-block sums of the
+// round's per-cell sample counts and tiles, clearing the next round's counters; (2) exclusive offsets
+// and tile descriptors (each block adds the sums of the blocks before it to a scan of its cells);
+// (3) the scatter of the round's samples into cell order; (4) the tiles, on the workers, after which
+// each warp walks rays the previous round left in empty voxels to their next occupied voxel (they
+// join the next round, two rounds after they were left, as in host-driven rounds).  The loop ends
+// when a round emits nothing and leaves nothing pending, or hands the rest over: a round (after the
+// first) of at most tail_rays rays is sorted and scattered, ctrl->tail set, and finished by
+// wave_tail_warp_kernel.  Nothing is synchronised with the host.
+template <class C, int NW>
+__global__ void __launch_bounds__(NW * 128, 1) trace_tc_kernel(GridView g, WaveArgs a) {
+    using T = TcLayout<C>;
+    extern __shared__ __align__(1024) unsigned char dyn[];
+    __shared__ __align__(8) uint64_t bar_w[NW], bar_mma[NW];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_tile[NW][4], s_red[NW][4];
+    __shared__ int wx[32], wy[32], s_base[2], s_flag;
+    WaveCtrl *ctrl = a.ctrl;
+    const int tid = threadIdx.x, wk = tid >> 7;
+    constexpr uint32_t NCOL = pow2_cols(NW * C::W);
+    if (tid < 32) tc::tmem_alloc(&s_tmem, NCOL);
+    if (tid < NW) {
+        mbar_init(&bar_w[tid], 1);
+        mbar_init(&bar_mma[tid], 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    unsigned char *base = dyn + wk * T::SMEM;
+    TcWorker w{base, base + T::SIZE, &bar_w[wk], &bar_mma[wk], s_tile[wk], s_red[wk], s_tmem + (uint32_t)(wk * C::W),
+               1 + wk, tid & 127, (tid & 127) >> 5, -1, 0u, 0u, false, false, 0u};
+    if (blockIdx.x == 0 && tid == 0) ctrl->start_ns = globaltimer_ns();
+    unsigned gen = 0;
+    bool ok = true;
+    const int NK = a.nkeys, max_rounds = min(2 * a.max_steps + 2, kMaxTraceRounds);
+    int round = 0;
+    for (;; ++round) {
+        const int cur = round & 1, nxt = cur ^ 1;
+        // a round of at most tail_rays rays (after the first) is finished one warp per ray in FP32
+        // (wave_tail_warp_kernel, launched after this kernel): it is sorted and scattered, then the loop ends
+        const bool handover = round > 0 && ctrl->n_live[cur] + ctrl->n_pend[nxt] <= a.tail_max;
+        if (handover) {
+            // the rays the previous round left in empty voxels walk to their next occupied voxel first
+            // and join this round, which the tail then finishes
+            const int n = ctrl->n_pend[nxt], bound = (n + 31) & ~31;
+            for (int i = blockIdx.x * blockDim.x + tid; i < bound; i += gridDim.x * blockDim.x)
+                advance_pending(g, a, nxt, cur, i, n);
+            if (!(ok = grid_sync(ctrl, gen, &s_flag))) break;
+        }
+        const int per = (NK + gridDim.x - 1) / gridDim.x;
+        const int k0 = min(NK, (int)blockIdx.x * per), k1 = min(NK, k0 + per);
+        // (1) block sums; the next round's counters cleared; the round's control words reset
+        {
+            int sum = 0, tiles = 0;
+            for (int c = k0 + tid; c < k1; c += blockDim.x) {
+                const int n = a.count[cur][c];
+                sum += n;
+                tiles += (n + 127) >> 7;
+                a.count[nxt][c] = 0;
+                a.fill[nxt][c] = 0;
+            }
+            if (blockIdx.x == 0 && tid == 0) {
+                ctrl->n_live[nxt] = 0;
+                ctrl->n_pend[cur] = 0;
+                ctrl->next_tile_bf = 0;
+                ctrl->next_adv = 0;
+            }
+            block_scan2_any(sum, tiles, wx, wy);
+            if (tid == blockDim.x - 1) {
+                ctrl->scan_part[0][blockIdx.x] = sum;
+                ctrl->scan_part[1][blockIdx.x] = tiles;
+            }
+        }
+        if (!(ok = grid_sync(ctrl, gen, &s_flag))) break;
+        if (blockIdx.x == 0 && tid == 0) ctrl->round_phase_ns[round][0] = globaltimer_ns();
+        // (2) offsets and tile descriptors of this block's cells
+        {
+            if (tid < 32) {
+                int bs = 0, bt = 0;
+                for (int i = tid; i < (int)blockIdx.x; i += 32) {
+                    bs += ctrl->scan_part[0][i];
+                    bt += ctrl->scan_part[1][i];
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    bs += __shfl_xor_sync(FULL, bs, o);
+                    bt += __shfl_xor_sync(FULL, bt, o);
+                }
+                if (tid == 0) {
+                    s_base[0] = bs;
+                    s_base[1] = bt;
+                }
+            }
+            __syncthreads();
+            const int pt = (k1 - k0 + blockDim.x - 1) / blockDim.x;
+            const int c0 = min(k1, k0 + tid * pt), c1 = min(k1, c0 + pt);
+            int sum = 0, tiles = 0;
+            for (int c = c0; c < c1; ++c) {
+                const int n = a.count[cur][c];
+                sum += n;
+                tiles += (n + 127) >> 7;
+            }
+            int is = sum, it = tiles;
+            block_scan2_any(is, it, wx, wy);
+            int run_s = s_base[0] + is - sum, run_t = s_base[1] + it - tiles;
+            for (int c = c0; c < c1; ++c) {
+                const int n = a.count[cur][c];
+                a.off[c] = run_s;
+                for (int i = 0; i < n; i += 128) a.tiles[run_t++] = make_int4(c, run_s + i, min(128, n - i), 0);
+                run_s += n;
+            }
+            if (blockIdx.x == gridDim.x - 1 && tid == blockDim.x - 1) {
+                a.off[NK] = s_base[0] + is;
+                ctrl->n_tiles = s_base[1] + it;
+            }
+        }
+        if (!(ok = grid_sync(ctrl, gen, &s_flag))) break;
+        if (blockIdx.x == 0 && tid == 0) ctrl->round_phase_ns[round][1] = globaltimer_ns();
+        // (3) scatter into cell order
+        {
+            const int n = ctrl->n_live[cur], lane = tid & 31, bound = (n + 31) & ~31;
+            for (int i = blockIdx.x * blockDim.x + tid; i < bound; i += gridDim.x * blockDim.x) {
+                const bool pred = i < n;
+                const int c = pred ? a.qcell[cur][i] : 0, r = pred ? a.q[cur][i] : 0;
+                const unsigned m = __ballot_sync(FULL, pred);
+                if (pred) {
+                    const unsigned grp = __match_any_sync(m, c);
+                    const int leader = __ffs(grp) - 1;
+                    int b = 0;
+                    if (lane == leader) b = a.off[c] + atomicAdd(a.fill[cur] + c, __popc(grp));
+                    b = __shfl_sync(grp, b, leader);
+                    a.sorted[b + __popc(grp & lanemask_lt())] = r;
+                }
+            }
+        }
+        if (!(ok = grid_sync(ctrl, gen, &s_flag))) break;
+        if (blockIdx.x == 0 && tid == 0) ctrl->round_phase_ns[round][2] = globaltimer_ns();
+        if (handover) {
+            if (blockIdx.x == 0 && tid == 0) {
+                ctrl->tail = 1;
+                ctrl->next_tile = 0;
+                ctrl->round_phase_ns[round][3] = ctrl->round_end_ns[round] = globaltimer_ns();
+                ctrl->round_live[round] = ctrl->n_live[cur];
+                ctrl->tail_parity = cur;
+            }
+            break;
+        }
+        // (4) the tiles; then each warp takes rays the previous round left in empty voxels (32 at a time)
+        // and walks them to their next occupied voxel: they join the next round, as with the side-stream
+        // walk of host-driven rounds
+        {
+            const bool wok = tc_round<C>(w, g, a, cur, ctrl->n_tiles, blockIdx.x * NW + wk, gridDim.x * NW);
+            if (__syncthreads_or(!wok)) {
+                tc_worker_done(w, a, wok);
+                ok = false;
+                w.n_eval = 0;
+                break;
+            }
+            const int n = ctrl->n_pend[nxt];
+            for (;;) {
+                int b = 0;
+                if ((tid & 31) == 0) b = atomicAdd(&ctrl->next_adv, 32);
+                b = __shfl_sync(FULL, b, 0);
+                if (b >= n) break;
+                advance_pending(g, a, nxt, nxt, b + (tid & 31), n);
+            }
+        }
+        if (!(ok = grid_sync(ctrl, gen, &s_flag))) break;
+        if (blockIdx.x == 0 && tid == 0) ctrl->round_phase_ns[round][3] = globaltimer_ns();
+        if (blockIdx.x == 0 && tid == 0) {
+            ctrl->round_live[round] = ctrl->n_live[cur];
+            ctrl->round_end_ns[round] = globaltimer_ns();
+        }
+        // done when nothing was emitted and nothing waits in this round's pending list
+        if ((ctrl->n_live[nxt] == 0 && ctrl->n_pend[cur] == 0) || round + 1 >= max_rounds) break;
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+        ctrl->rounds = round + 1;
+        if (ok && !ctrl->tail && (ctrl->n_live[(round & 1) ^ 1] != 0 || ctrl->n_pend[round & 1] != 0))
+            atomicCAS(a.status, 0, (int)8 /* KNS_ERR_INTERNAL */);
+    }
+    if (!ok && tid == 0) atomicCAS(a.status, 0, (int)6 /* KNS_ERR_TIMEOUT */);
+    tc_worker_done(w, a, true);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid < 32) tc::tmem_free(s_tmem, NCOL);
 }
 
 template <class C>
@@ -319,8 +621,8 @@ cudaError_t launch_wave_eval_tc_cfg(const GridView &g, const WaveArgs &a, int cu
     using T = TcLayout<C>;
     static_assert(T::SMEM <= 200 * 1024, "tensor-core tile does not fit in shared memory");
     // Resident blocks per SM from the kernel's own resources (registers, shared memory, threads) and the
-    // tensor memory (W of 512 columns per block).  The occupancy query is not used here: for this kernel
-    // it reported one block per SM where its registers and shared memory allow five.
+    // tensor memory (W of 512 columns per block).  The occupancy query is not used here: it reports one
+    // block per SM for every kernel that allocates tensor memory.
     static std::atomic<int> per_sm{0};
     int nb = per_sm.load();
     if (nb <= 0) {
@@ -343,9 +645,26 @@ cudaError_t launch_wave_eval_tc_cfg(const GridView &g, const WaveArgs &a, int cu
     return cudaGetLastError();
 }
 
+template <class C>
+cudaError_t launch_trace_tc_cfg(const GridView &g, const WaveArgs &a, int sm_count, cudaStream_t s) {
+    constexpr int NW = tc_workers<C>();
+    constexpr int smem = NW * TcLayout<C>::SMEM;
+    static_assert(smem <= 227 * 1024, "persistent trace does not fit in shared memory");
+    auto kern = trace_tc_kernel<C, NW>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    GridView gv = g;
+    WaveArgs av = a;
+    void *args[] = {&gv, &av};
+    // one block per SM: every block is resident (the barriers need it), and a kernel that allocates tensor
+    // memory may have one block per SM in a cooperative launch
+    return cudaLaunchCooperativeKernel((void *)kern, dim3(sm_count), dim3(NW * 128), args, smem, s);
+}
+
 #ifdef KNS_W
 using InstCfg = Cfg<KNS_W, KNS_H, KNS_L, KNS_LD>;
 template cudaError_t launch_wave_eval_tc_cfg<InstCfg>(const GridView &, const WaveArgs &, int, int, cudaStream_t);
+template cudaError_t launch_trace_tc_cfg<InstCfg>(const GridView &, const WaveArgs &, int, cudaStream_t);
 #endif
 
 }  // namespace kns

@@ -539,24 +539,22 @@ __device__ __forceinline__ float warp_sdf_trace(const float *__restrict__ wsm, f
 }
 
 // A tail round: one warp (one block) per ray, to the end.  Rays come in cell-sorted order (the cell
-// of a ray's position is its sort key); the round's tile counter hands them out.  In a BF16 render
-// the tail takes the rays in the FP32 phase (the keys below NC, sorted first), with the block
-// tiles' refinement rule; the rays still in the BF16 phase stay with wave_eval_tc_kernel.
+// of a ray's position is its sort key); the round's tile counter hands them out.  In a BF16 render the
+// rays left in the round take their last steps here in FP32, with the BF16 trace's cycle test and seam
+// trap, and join the hit list when |d| < eps as the tensor-core tiles' rays do.
 template <class C>
 __global__ void __launch_bounds__(32) wave_tail_warp_kernel(GridView g, WaveArgs a, int cur) {
     extern __shared__ __align__(128) float dyn[];
     __shared__ __align__(8) uint64_t bar;
     if (!a.ctrl->tail) return;
-    // samples with FP32 keys: all of them in an FP32 render; in a BF16 render those sorted before the
-    // first BF16 key (off[] is this round's only when the round has samples)
-    const int n_live = a.ctrl->n_live[cur];
-    const int n = a.coarse ? min(n_live, a.off[a.NC]) : n_live;
+    if (cur < 0) cur = a.ctrl->tail_parity;  // the round the persistent BF16 trace left to the tail
+    const int n = a.ctrl->n_live[cur];
     const int lane = threadIdx.x;
     float *wsm = dyn, *xin = dyn + C::TSIZE, *h0 = xin + C::INP, *h1 = h0 + C::W;
     for (int k = C::IN + lane; k < C::INP; k += 32) xin[k] = 0.f;  // encoding pad stays zero
     if (lane == 0) mbar_init(&bar, 1);
     __syncwarp();
-    const bool cycles = a.t_hist != nullptr && !a.coarse;  // the FP32 phase of BF16 renders keeps none
+    const bool cycles = a.t_hist != nullptr;
     int cached = -1;
     uint32_t phase = 0;
     unsigned long long nsamples = 0;
@@ -578,8 +576,8 @@ __global__ void __launch_bounds__(32) wave_tail_warp_kernel(GridView g, WaveArgs
         clip_box(g, ray, t0, tf);
         float t = a.t_ray[r];
         int steps = a.steps_ray[r];
-        const int switched = a.coarse ? a.cell_ray[r] : 0;  // step count at the BF16 -> FP32 switch
         float4 hist = cycles ? a.t_hist[r] : no_history();
+        int4 trap = a.trap ? a.trap[r] : trap_empty();
         bool hit = false;
         for (;;) {
             if (cell != cached) {
@@ -597,21 +595,26 @@ __global__ void __launch_bounds__(32) wave_tail_warp_kernel(GridView g, WaveArgs
                                               fmaf(t, ray.wz, ray.oz), lane, g.beta, g.inv_beta);
             ++steps;
             ++nsamples;
-            const bool last_refine = a.coarse && steps - switched >= a.refine_steps;
-            if (fabsf(d) < a.eps || (last_refine && fabsf(d) < a.eps_coarse)) {
+            if (fabsf(d) < a.eps) {
                 hit = true;
                 break;
             }
-            if (last_refine) break;
+            // BF16 renders: the trace's seam trap (a trapped ray is the plain iteration's budget miss)
+            if (a.trap && trap_step(trap, t, d, cell, a.trap_span, 5.f * a.eps_coarse)) {
+                steps = a.max_steps;
+                break;
+            }
             const float t_eval = t;
             t += d;
             if (t > tf || t < t0 || steps >= a.max_steps) break;
             cell = advance_ray(g, ray, t, tf);
             if (cell < 0) break;
-            if (cycles && cycle_step(hist, t_eval, t)) {
+            if (cycles && (a.coarse ? cycle_step_tol(hist, t_eval, t) : cycle_step(hist, t_eval, t))) {
                 steps = a.max_steps;
                 break;
             }
+            // an occupancy skip ends the trap's run of samples (the skip moved t by more than d)
+            if (a.trap && t != t_eval + d) trap = trap_empty();
         }
         if (lane == 0) {
             if (hit) {
@@ -814,12 +817,18 @@ cudaError_t launch_wave_eval_cfg(const GridView &g, const WaveArgs &a, int cur, 
         wave_eval_kernel<C><<<blocks, 32, smem, s>>>(g, a, cur);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_wave_tail_cfg<C>(g, a, cur, sm_count, s);
+}
+
+template <class C>
+cudaError_t launch_wave_tail_cfg(const GridView &g, const WaveArgs &a, int cur, int sm_count, cudaStream_t s) {
     // one-warp blocks, as many as fit on the SMs at once (each holds one cell's weights)
     constexpr int tsmem = tail_smem_floats<C>() * (int)sizeof(float);
     static_assert(tsmem <= 64 * 1024, "tail weight slot does not fit");
     static std::atomic<int> tail_per_sm{0};
     int tail_blocks = 0;
-    if ((e = resident_blocks(wave_tail_warp_kernel<C>, 32, tsmem, tail_per_sm, tail_blocks)) != cudaSuccess) return e;
+    cudaError_t e = resident_blocks(wave_tail_warp_kernel<C>, 32, tsmem, tail_per_sm, tail_blocks);
+    if (e != cudaSuccess) return e;
     wave_tail_warp_kernel<C><<<sm_count * tail_blocks, 32, tsmem, s>>>(g, a, cur);
     return cudaGetLastError();
 }
@@ -829,6 +838,7 @@ using InstCfg = Cfg<KNS_W, KNS_H, KNS_L, KNS_LD>;
 template cudaError_t launch_wave_gen_cfg<InstCfg>(const GridView &, const WaveArgs &, cudaStream_t);
 template cudaError_t launch_wave_eval_cfg<InstCfg>(const GridView &, const WaveArgs &, int, int, int, int,
                                                    cudaStream_t);
+template cudaError_t launch_wave_tail_cfg<InstCfg>(const GridView &, const WaveArgs &, int, int, cudaStream_t);
 #endif
 
 }  // namespace kns

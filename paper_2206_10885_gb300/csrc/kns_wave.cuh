@@ -223,6 +223,55 @@ __device__ __forceinline__ int advance_fast(const GridView &g, const Ray &r, flo
     return cell_of(g, x, y, z);
 }
 
+// Entry i of the pending list of parity p_in (i < n; every lane of the warp calls it): the ray walks the
+// occupancy DDA from its position to its next occupied voxel (or leaves the grid: a miss), takes the
+// cycle test on the position reached, and joins the queue, counts and live counter of parity p_out.
+__device__ __forceinline__ void advance_pending(const GridView &g, const WaveArgs &a, int p_in, int p_out, int i,
+                                                int n) {
+    bool emit = false;
+    int ncell = -1, r = 0, key = 0;
+    if (i < n) {
+        r = a.pend_r[p_in][i];
+        const bool cycles = a.t_hist != nullptr;
+        const float t_eval = a.pend_t[p_in][i];
+        int cam;
+        const Ray ray = ray_of(a, r, cam);
+        float t0, tf;
+        clip_box(g, ray, t0, tf);
+        float t = a.t_ray[r];
+        ncell = advance_ray(g, ray, t, tf);
+        if (ncell < 0) {
+            write_miss(a, r, a.steps_ray[r]);
+        } else {
+            float4 hist = cycles ? a.t_hist[r] : no_history();
+            // BF16 renders: the BF16 trace's cycle test (the rays on these lists are all in it)
+            const bool cyc = cycles && (a.coarse ? cycle_step_tol(hist, t_eval, t) : cycle_step(hist, t_eval, t));
+            if (cyc) {
+                write_miss(a, r, a.max_steps);
+                ncell = -1;
+            } else {
+                emit = true;
+                key = ncell;
+                a.t_ray[r] = t;
+                if (cycles) a.t_hist[r] = hist;
+                if (a.trap) a.trap[r] = trap_empty();  // a run of samples ends at an occupancy skip
+            }
+        }
+    }
+    const int qp = warp_append(&a.ctrl->n_live[p_out], emit);
+    if (emit) {
+        a.q[p_out][qp] = r;
+        a.qcell[p_out][qp] = key;
+    }
+    warp_count_cells(a.count[p_out], emit, key);
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Resident blocks per SM of a kernel with `smem` bytes of dynamic shared memory (registers and shared
 // memory both count), after allowing it the largest shared-memory carve-out; asked once per kernel.
 template <class K>

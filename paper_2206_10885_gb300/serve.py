@@ -63,9 +63,10 @@ class RenderServer:
 
     Each slot runs a worker thread: it takes a batch (all admitted requests for the grid of the
     oldest one, up to max_batch_rays), renders it with one kns_render_views call on the slot's own
-    context and stream, waits for the stream and stamps the requests' completion time.  The host
-    waits inside a render (the round loop polls the live-ray count) happen in that thread, so
-    batches on different slots are issued and executed concurrently.
+    context and stream, waits for the stream and stamps the requests' completion time.  Host waits
+    inside a render (FP32 renders poll the live-ray count between rounds; BF16 renders run their
+    rounds in one persistent launch) happen in that thread, so batches on different slots are
+    issued and executed concurrently.
     """
 
     def __init__(self, grids: dict, device: int = 0, slots: int = 3, budget_bytes: int = 8 << 30,
@@ -75,9 +76,11 @@ class RenderServer:
         self.slots = [_Slot(device) for _ in range(slots)]
         self.grids = {}
         loader = self.slots[0].ctx
-        for name, (desc, w) in grids.items():
-            # a grid lives in device memory and is usable from every context on the device
-            self.grids[name] = Grid.load(loader, desc, w)
+        for name, spec in grids.items():
+            # (desc, weights[, occupancy words]); a grid lives in device memory and is usable from every
+            # context on the device
+            desc, w = spec[0], spec[1]
+            self.grids[name] = Grid.load(loader, desc, w, spec[2] if len(spec) > 2 else None)
         self.budget = budget_bytes
         self.max_batch_rays = max_batch_rays
         self.max_steps, self.eps, self.precision, self.tuning = max_steps, eps, precision, tuning

@@ -60,7 +60,7 @@ int main(void) {
   printf("%zu %zu %zu\\n", sizeof(kns_pt_opts), offsetof(kns_pt_opts, seed), offsetof(kns_pt_opts, zenith));
   printf("%zu %zu %zu\\n", sizeof(kns_render_stats), offsetof(kns_render_stats, ms_eval_fp32),
          offsetof(kns_render_stats, samples_tail));
-  printf("%zu %zu\\n", sizeof(kns_round_info), offsetof(kns_round_info, ms_eval_bf16));
+  printf("%zu %zu\\n", sizeof(kns_round_info), offsetof(kns_round_info, ms_advance));
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -76,7 +76,7 @@ int main(void) {
             C.sizeof(capi.kns_pt_opts), capi.kns_pt_opts.seed.offset, capi.kns_pt_opts.zenith.offset,
             C.sizeof(capi.kns_render_stats), capi.kns_render_stats.ms_eval_fp32.offset,
             capi.kns_render_stats.samples_tail.offset,
-            C.sizeof(capi.kns_round_info), capi.kns_round_info.ms_eval_bf16.offset]
+            C.sizeof(capi.kns_round_info), capi.kns_round_info.ms_advance.offset]
     assert vals == want
 
 

@@ -1,12 +1,11 @@
 """BF16 tensor-core render vs the FP64 oracle's render (needs a GPU).
 
-Gates (per result, on pixels where both the BF16 render and the oracle hit): depth within 1e-3
-scene units, RGB within 1/255 per channel, normal angle within 0.5 degrees, each on >= 99.9% of
-those pixels, with the FP32 refinement given up to 128 evaluations (refine_steps = 128).  Hit
-agreement is reported and must stay above 98%.  The library default (refine_steps = 64, faster)
-is held to >= 99.5% on each result: near-silhouette rays that bounce across a cell seam can end
-their refinement within eps_coarse of the surface and are then accepted where the FP32 trace
-(eps = 1e-4) keeps bouncing until its budget runs out.
+Gates, the precision form's stated accuracy (per result, on pixels where both the BF16 render and the
+oracle hit): depth within 1e-3 scene units, RGB within 1/255 per channel, normal angle within 0.5
+degrees, each on >= 99.9 % of those pixels; hit agreement >= 99.9 % of all pixels.  They hold for the
+library defaults (split-BF16 trace on the tensor cores to eps, FP32 re-evaluation of its last step at
+shading, the one-warp-per-ray FP32 tail for small rounds) and for the trace on the tensor cores alone
+(tail_rays = -1).
 """
 import numpy as np
 import pytest
@@ -59,10 +58,10 @@ def assert_bf16_gates(rep, bar=0.999):
     assert rep["depth_ok"] >= bar, rep
     assert rep["rgb_ok"] >= bar, rep
     assert rep["normal_ok"] >= bar, rep
-    assert rep["hit_agree"] >= 0.98, rep
+    assert rep["hit_agree"] >= bar, rep
 
 
-STRICT = dict(refine_steps=128)
+TC_ONLY = dict(tuning=dict(tail_rays=-1))  # every step of the trace on the tensor cores
 
 
 @pytest.mark.parametrize("gname,W,H", [("c2", 160, 120), ("c1", 64, 64)])
@@ -73,15 +72,15 @@ def test_bf16_accuracy_small(kns, ctx, gname, W, H):
     cams = S.orbit_cameras(3, W, H, seed=12)
     grid = kns.Grid.load(ctx, desc, w, occ)
     try:
-        g = render_np(kns, ctx, grid, cams, W, H, 128, 1e-4, precision=kns.KNS_BF16, **STRICT)
-        gd = render_np(kns, ctx, grid, cams, W, H, 128, 1e-4, precision=kns.KNS_BF16)
+        g = render_np(kns, ctx, grid, cams, W, H, 128, 1e-4, precision=kns.KNS_BF16)
+        gt = render_np(kns, ctx, grid, cams, W, H, 128, 1e-4, precision=kns.KNS_BF16, **TC_ONLY)
     finally:
         grid.free()
     o = O.render(desc, w, occ, cams, W, H, 128, 1e-4)
     rep = bf16_report(g, o)
     print(gname, rep)
     assert_bf16_gates(rep)
-    assert_bf16_gates(bf16_report(gd, o), bar=0.995)
+    assert_bf16_gates(bf16_report(gt, o))
 
 
 @pytest.mark.parametrize("gname", ["c3s", "c3l"])
@@ -93,8 +92,8 @@ def test_bf16_accuracy_1080p_sampled(kns, ctx, gname):
     cams = S.orbit_cameras(2, 1920, 1080, seed=1)
     grid = kns.Grid.load(ctx, desc, w, occ)
     try:
-        g = render_np(kns, ctx, grid, cams, 1920, 1080, 128, 1e-4, precision=kns.KNS_BF16, **STRICT)
-        gd = render_np(kns, ctx, grid, cams, 1920, 1080, 128, 1e-4, precision=kns.KNS_BF16)
+        g = render_np(kns, ctx, grid, cams, 1920, 1080, 128, 1e-4, precision=kns.KNS_BF16)
+        gt = render_np(kns, ctx, grid, cams, 1920, 1080, 128, 1e-4, precision=kns.KNS_BF16, **TC_ONLY)
     finally:
         grid.free()
     rng = np.random.default_rng(4)
@@ -105,23 +104,35 @@ def test_bf16_accuracy_1080p_sampled(kns, ctx, gname):
     rep = bf16_report({k: v[sel] for k, v in g.items()}, o)
     print(gname, rep)
     assert_bf16_gates(rep)
-    assert_bf16_gates(bf16_report({k: v[sel] for k, v in gd.items()}, o), bar=0.995)
+    assert_bf16_gates(bf16_report({k: v[sel] for k, v in gt.items()}, o))
 
 
 def test_bf16_schedule_invariance(kns, ctx):
+    """Schedule knobs never change a result.  Without the one-warp-per-ray tail (tail_rays = -1) the whole
+    trace runs on the tensor cores and every knob -- tile stepping, tile hand-out, blocks per SM, and the
+    persistent trace against host-driven rounds -- gives bit-identical renders."""
     desc = S.config_desc("c2")
     w = S.sal_sphere_grid(desc)
+    occ = O.occupancy(desc, w)
     cams = S.orbit_cameras(2, 160, 120, seed=8)
-    grid = kns.Grid.load(ctx, desc, w)
+    grid = kns.Grid.load(ctx, desc, w, occ)
     try:
-        ref = render_np(kns, ctx, grid, cams, 160, 120, 128, 1e-4, precision=kns.KNS_BF16)
-        for tuning in [dict(inner_steps=1, min_active=1, static_tiles=2),
-                       dict(inner_steps=64, min_active=16, static_tiles=1, blocks_per_sm=2),
-                       dict(tail_rays=-1),  # the FP32 phase on block tiles to the end (no tail)
-                       dict(block_tiles=1, inner_steps=3, min_active=1, tail_rays=4096),
-                       dict(block_tiles=2, tail_rays=-1)]:
-            got = render_np(kns, ctx, grid, cams, 160, 120, 128, 1e-4, precision=kns.KNS_BF16, tuning=tuning)
+        pure = dict(tail_rays=-1)
+        ref = render_np(kns, ctx, grid, cams, 160, 120, 128, 1e-4, precision=kns.KNS_BF16, tuning=pure)
+        for tuning in [dict(bf16_rounds=2),
+                       dict(bf16_rounds=2, bf16_inner_steps=1, bf16_min_active=1, static_tiles=2),
+                       dict(bf16_inner_steps=64, bf16_min_active=1),
+                       dict(bf16_inner_steps=8, bf16_min_active=32, static_tiles=2),
+                       dict(bf16_rounds=2, blocks_per_sm=2, block_tiles=2)]:
+            got = render_np(kns, ctx, grid, cams, 160, 120, 128, 1e-4, precision=kns.KNS_BF16,
+                            tuning=dict(pure, **tuning))
             for k in ref:
                 assert np.array_equal(ref[k], got[k]), (k, tuning)
+        # with the default tail the two schedules may hand a ray's last steps to FP32 in different rounds:
+        # the renders then agree within the BF16 gates
+        a = render_np(kns, ctx, grid, cams, 160, 120, 128, 1e-4, precision=kns.KNS_BF16)
+        b = render_np(kns, ctx, grid, cams, 160, 120, 128, 1e-4, precision=kns.KNS_BF16, tuning=dict(bf16_rounds=2))
+        rep = bf16_report(a, b)
+        assert rep["hit_agree"] >= 0.999 and rep["depth_ok"] >= 0.999 and rep["rgb_ok"] >= 0.999, rep
     finally:
         grid.free()

@@ -1,11 +1,14 @@
 """Multi-view batching and the continuous-batching render server (needs a GPU).
 
 A request's pixels must be the same whether it is rendered alone (kns_render) or inside a batch of
-requests of mixed resolutions (kns_render_views, the server): each ray's arithmetic is independent
-of the batch, so the results are identical bit for bit."""
+requests of mixed resolutions (kns_render_views, the server).  In FP32 each ray's arithmetic is
+independent of the batch, so the results are identical bit for bit.  In BF16 the batch decides which
+of a ray's last steps run in FP32 (the one-warp-per-ray tail of small rounds), so the results agree
+within the BF16 accuracy gates -- and both agree with the FP64 oracle within them."""
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_2206_10885_gb300 import synth as S
 
 pytestmark = pytest.mark.gpu
@@ -28,6 +31,23 @@ def solo(kns, ctx, grid, cam, W, H, **kw):
     return {k: v.cpu().numpy() for k, v in t.items()}
 
 
+def assert_within_bf16_gates(a, b, label):
+    """Two BF16 renders of the same pixels: hit agreement and, on pixels both hit, depth within 1e-3,
+    RGB within 1/255 and normal angle within 0.5 degrees, each on >= 99.9 % of pixels."""
+    ha, hb = a["hit"] == 1, b["hit"] == 1
+    both = ha & hb
+    n = max(1, ha.size)
+    assert np.sum(ha != hb) <= max(1, int(1e-3 * n)), (label, "hit agreement", int(np.sum(ha != hb)), n)
+    if both.sum() == 0:
+        return
+    dd = np.abs(a["depth"][both].astype(np.float64) - b["depth"][both])
+    dr = np.abs(a["rgb"][both].astype(np.float64) - b["rgb"][both]).max(axis=1)
+    ang = np.degrees(np.arccos(np.clip(np.sum(a["normal"][both].astype(np.float64) * b["normal"][both], axis=1), -1, 1)))
+    k = max(1, int(1e-3 * both.sum()))  # at most 0.1 % of both-hit pixels outside each gate
+    assert np.sum(dd > 1e-3) <= k and np.sum(dr > 1 / 255) <= k and np.sum(ang > 0.5) <= k, (label, dd.max(), dr.max(),
+                                                                                            ang.max())
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_views_batch_equals_solo_renders(kns, precision):
     desc = S.config_desc("c2")
@@ -43,8 +63,12 @@ def test_views_batch_equals_solo_renders(kns, precision):
             if W * H == 0:
                 continue
             ref = solo(kns, ctx, grid, cam, W, H, precision=precision)
-            for k in ref:
-                assert np.array_equal(ref[k], t[k].cpu().numpy()), (W, H, k)
+            got = {k: v.cpu().numpy() for k, v in t.items()}
+            if precision == kns.KNS_FP32:  # the FP32 path is schedule-invariant: identical bit for bit
+                for k in ref:
+                    assert np.array_equal(ref[k], got[k]), (W, H, k)
+            else:  # BF16: the batch decides which last steps run in FP32; results agree within the gates
+                assert_within_bf16_gates(ref, got, (W, H))
     finally:
         grid.free()
         ctx.close()
@@ -71,5 +95,47 @@ def test_server_mixed_stream_matches_solo(kns):
                     assert np.array_equal(ref[k], r.out[k].cpu().numpy()), (r.rid, k)
         finally:
             ctx.close()
+    finally:
+        server.close()
+
+
+def test_server_bf16_mixed_stream_matches_oracle(kns):
+    """BF16 serving of a 16^3 width-32 grid and a 32^3 width-64 grid (the workload's two grid shapes):
+    sampled pixels of every request of a mixed stream against the FP64 oracle, within the BF16 gates
+    (depth 1e-3, RGB 1/255, normal 0.5 degrees on >= 99.9 % of pixels both hit; hit agreement >= 99.9 %)."""
+    from paper_2206_10885_gb300 import serve
+    grids = {"s": (S.config_desc("c3s"), S.sal_sphere_grid(S.config_desc("c3s"), seed=0)),
+             "l": (S.config_desc("c3l"), S.sal_sphere_grid(S.config_desc("c3l"), seed=0))}
+    occs = {k: O.occupancy(d, w) for k, (d, w) in grids.items()}
+    server = serve.RenderServer({k: (d, w, occs[k]) for k, (d, w) in grids.items()}, slots=2,
+                                budget_bytes=256 << 20, max_batch_rays=400_000, precision=kns.KNS_BF16)
+    try:
+        stream = serve.poisson_stream(12, rate=500.0, seed=9, grids=["s", "l"],
+                                      resolutions=[(64, 64), (160, 120), (256, 256)])
+        stats = serve.run_stream(server, stream)
+        assert stats["requests"] == 12
+        rng = np.random.default_rng(3)
+        tot = agree = 0
+        bad = {"depth": 0, "rgb": 0, "normal": 0}
+        both_n = 0
+        for _, r in stream:
+            desc, w = grids[r.grid]
+            g = {k: v.cpu().numpy() for k, v in r.out.items()}
+            sel = np.unique(rng.integers(0, r.W * r.H, 400))
+            o = O.render(desc, w, occs[r.grid], r.cam[None], r.W, r.H, 128, 1e-4, sel=sel)
+            gs = {k: v[sel] for k, v in g.items()}
+            gh, oh = gs["hit"] == 1, o["hit"] == 1
+            tot += sel.size
+            agree += int(np.sum(gh == oh))
+            both = gh & oh
+            both_n += int(both.sum())
+            bad["depth"] += int(np.sum(np.abs(gs["depth"][both] - o["depth"][both]) > 1e-3))
+            bad["rgb"] += int(np.sum(np.abs(gs["rgb"][both] - o["rgb"][both]).max(axis=1) > 1 / 255))
+            cosang = np.clip(np.sum(gs["normal"][both] * o["normal"][both], axis=1), -1, 1)
+            bad["normal"] += int(np.sum(np.degrees(np.arccos(cosang)) > 0.5))
+        print("bf16 serving vs oracle: pixels", tot, "hit agreement", agree / tot, "both", both_n, bad)
+        assert agree >= 0.999 * tot
+        assert both_n > 300
+        assert all(v <= 1e-3 * both_n for v in bad.values()), bad
     finally:
         server.close()
