@@ -1,14 +1,19 @@
 """Throughput benchmark of the KiloNeuS sphere-traced render path (one JSON line on rank 0).
 
-A step renders one batch: the 16^3 Kilo-grid (3 hidden layers of width 32, 128^3 occupancy
-mask) from 8 seeded orbit cameras at 800x800, max 128 steps, eps 1e-4: 5.12 M primary rays,
-sphere-traced, normal and colour at each hit (kns_render).  The grid is resident in HBM
-before timing starts.  Each timed step is bracketed by CUDA events on the launching stream;
-between steps a 512 MiB buffer is overwritten to flush the 126 MB L2 (the grid's weights fit
-in L2), outside the events.
+Default step: one BF16 render of the 1080p precision-form workload -- the 32^3 Kilo-grid (32768 cells,
+3 hidden layers of width 64, 128^3 occupancy mask) from 8 seeded orbit cameras at 1920x1080, max 128
+steps, eps 1e-4: 16.6 M primary rays, sphere-traced on the tensor cores (split-BF16 products, FP32
+accumulation), the last step, the normal and the colour in FP32 (kns_render, precision KNS_BF16).  The
+grid is resident in HBM before timing starts.  Each timed step is bracketed by CUDA events on the
+launching stream; between steps a 512 MiB buffer is overwritten to flush the 126 MB L2, outside the
+events.  The same line carries the plain FP32 GPU path on the same workload (same protocol), the
+speed-up, the BF16 error against the FP64 oracle on sampled pixels (hit agreement; depth, RGB and
+normal-angle quantiles and the fractions within the stated gates), the serving stream's p50/p99
+latency at four Poisson rates, the roofline of the dominant kernel against peaks measured on the GPU,
+the end-to-end rate through host buffers, and the oracle timed on the host cores.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16]
-                    [--workload c2|c3s|c3l|c1|train|pt] [--impl kns|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32]
+                    [--workload c3l|c3s|c2|c1|train|pt] [--impl kns|reference] [--serving 0|1]
 
 --workload train times the NeuS-style training step instead (kns_train_step: loss and hand-written
 backward): 2^18 rays x (64 stratified + 32 importance samples) through the 16^3 grid (3 hidden
@@ -41,7 +46,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mrays/s sphere-traced+shaded, BF16 vs FP32 at stated error; serving p50/p99 ms"
 UNIT = "Mrays/s"
-FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (max SM clock)"
 
 
 def parse():
@@ -50,16 +54,21 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="kns", choices=["kns", "reference"])
-    ap.add_argument("--workload", default="c2")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--workload", default="c3l")
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32-compare", action="store_true", help="BF16: skip the FP32 render of the same workload")
+    ap.add_argument("--no-accuracy", action="store_true", help="BF16: skip the sampled comparison with the oracle")
+    ap.add_argument("--serving", type=int, default=1, help="BF16: also run the serving stream (0 = skip)")
+    ap.add_argument("--serving-rates", type=float, nargs="+", default=[50, 100, 200, 400])
+    ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--cams", type=int, default=0, help="use only the first N cameras (small profiling cases)")
     ap.add_argument("--train-rays", type=int, default=0,
                     help="train workload: rays per step (eikonal points scale along; small profiling cases)")
-    ap.add_argument("--tune", default="cache", choices=["cache", "force", "off"],
-                    help="schedule autotuning before timing: use the cached best (tuning once if absent), "
-                         "re-tune, or use the library defaults")
+    ap.add_argument("--tune", default="off", choices=["cache", "force", "off"],
+                    help="FP32 renders: schedule autotuning before timing (the cached best, tuning once if absent; "
+                         "re-tune; or the library defaults, which the autotuner picked on the 16^3 workload)")
     return ap.parse_args()
 
 
@@ -74,7 +83,8 @@ def workload_config(name, desc, cams, W, H, ms, eps, precision):
             "sdf_hidden": desc.sdf_hidden, "resolution": "%dx%d" % (W, H), "n_cameras": int(cams.shape[0]),
             "max_steps": ms, "eps": eps, "precision": precision,
             "l2": "flushed between steps (512 MiB write outside the timed events)",
-            "inputs": "synthetic SAL near-sphere grid (seed 0), seeded orbit cameras"}
+            "inputs": "synthetic grid: SAL geometric initialisation for a sphere of radius 0.5 (seed 0) plus per-cell "
+                      "N(0, 1e-3) perturbation, seeded orbit cameras"}
 
 
 def mac_counts(desc):
@@ -242,6 +252,63 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- GPU arm
+def bf16_accuracy(O, desc, w, occ, cams, W, H, ms, eps, bf, fp, n_random=4000, n_hits=4000, seed=4):
+    """BF16 render vs the FP64 oracle on sampled pixels (seeded: random pixels plus pixels the BF16 or
+    FP32 render hit): hit agreement, and on pixels both hit the error quantiles and the fraction within
+    each gate (depth 1e-3, RGB 1/255, normal angle 0.5 degrees)."""
+    rng = np.random.default_rng(seed)
+    n_pix = bf["hit"].shape[0]
+    hits = np.where((bf["hit"] == 1) | (fp["hit"] == 1))[0]
+    sel = np.unique(np.concatenate([rng.integers(0, n_pix, n_random),
+                                    hits[rng.integers(0, max(1, hits.size), n_hits)] if hits.size else []]).astype(np.int64))
+    o = O.render(desc, w, occ, cams, W, H, ms, eps, sel=sel)
+    g = {k: v[sel] for k, v in bf.items()}
+    gh, oh = g["hit"] == 1, o["hit"] == 1
+    both = gh & oh
+    dd = np.abs(g["depth"][both].astype(np.float64) - o["depth"][both])
+    dr = np.abs(g["rgb"][both].astype(np.float64) - o["rgb"][both]).max(axis=1)
+    ang = np.degrees(np.arccos(np.clip(np.sum(g["normal"][both].astype(np.float64) * o["normal"][both], axis=1), -1, 1)))
+    q = lambda a: {"p50": float(np.quantile(a, 0.5)), "p99": float(np.quantile(a, 0.99)),
+                   "p99.9": float(np.quantile(a, 0.999)), "max": float(a.max())} if a.size else None
+    return {"pixels": int(sel.size), "both_hit": int(both.sum()), "hit_agreement": float(np.mean(gh == oh)),
+            "depth_within_1e-3": float(np.mean(dd <= 1e-3)) if dd.size else None,
+            "rgb_within_1/255": float(np.mean(dr <= 1 / 255)) if dr.size else None,
+            "normal_within_0.5deg": float(np.mean(ang <= 0.5)) if ang.size else None,
+            "depth_err": q(dd), "rgb_err": q(dr), "normal_angle_deg": q(ang),
+            "sample": "%d random pixels + %d drawn from pixels either render hit (seed %d), all %d cameras"
+                      % (n_random, n_hits, seed, cams.shape[0])}
+
+
+def serving_run(kns, S, main_grid, rates, seconds, slots=3):
+    """The serving workload: 4 resident BF16 grids (2 x 16^3 width 32, 2 x 32^3 width 64), Poisson
+    arrivals at each rate, resolutions uniform over {256^2, 512^2, 800^2, 1920x1080}; p50/p99 latency
+    and delivered Mrays/s per rate."""
+    from paper_2206_10885_gb300 import serve
+    grids = {"c3s-0": (S.config_desc("c3s"), S.sal_sphere_grid(S.config_desc("c3s"), seed=0)),
+             "c3s-1": (S.config_desc("c3s"), S.sal_sphere_grid(S.config_desc("c3s"), seed=1)),
+             "c3l-0": main_grid,
+             "c3l-1": (S.config_desc("c3l"), S.sal_sphere_grid(S.config_desc("c3l"), seed=1))}
+    server = serve.RenderServer(grids, slots=slots, precision=kns.KNS_BF16)
+    names = list(grids)
+    out = []
+    try:
+        warm = [serve.Request(-1 - k, names[k % len(names)], S.orbit_cameras(1, 1920, 1080, seed=k)[0], 1920, 1080)
+                for k in range(len(names) * slots)]
+        for r in warm:
+            server.submit(r)
+        server.drain()
+        for rate in rates:
+            n = max(8, int(rate * seconds))
+            stream = serve.poisson_stream(n, rate, seed=int(rate), grids=names, resolutions=serve.RES_MIX)
+            res = serve.run_stream(server, stream)
+            out.append({"rate_per_s": rate, "requests": res["requests"], "p50_ms": res["p50_ms"],
+                        "p99_ms": res["p99_ms"], "mrays_per_s": res["mrays_per_s"], "batches": res["batches"]})
+    finally:
+        server.close()
+    return {"grids": "2 x 16^3/w32 + 2 x 32^3/w64, BF16, resident", "resolutions": "256^2, 512^2, 800^2, 1920x1080",
+            "arrivals": "Poisson, %.1f s per rate" % seconds, "slots": slots, "per_rate": out}
+
+
 def run_kns(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -266,67 +333,81 @@ def run_kns(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     frame = kns.alloc_frame(n_rays, dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    props = torch.cuda.get_device_properties(local_rank)
 
     tuning = None
-    if args.tune != "off":
+    if args.tune != "off" and precision == kns.KNS_FP32:
         from paper_2206_10885_gb300 import autotune
         tuning, tuned_ms, tried = autotune.tune(ctx, grid, cams, W, H, ms, eps, precision,
                                                 use_cache=args.tune == "cache")
         if rank == 0 and tried:
             print("# autotune: %d settings, best %s at %.3f ms" % (len(tried), tuning, tuned_ms), file=sys.stderr)
 
-    def step():
-        kns.render(ctx, grid, cams, W, H, ms, eps, precision=precision, out=frame, stream=stream, tuning=tuning)
+    def render(prec, tun=None):
+        kns.render(ctx, grid, cams, W, H, ms, eps, precision=prec, out=frame, stream=stream, tuning=tun)
 
-    for _ in range(max(3, args.warmup)):
-        step()
-    ctx.sync(stream)
-    # algorithmic units of one render, from the library's own counters: SDF evaluations per precision
-    # and converged rays; per-kernel-class device time from a render timed with CUDA events
-    tuning_t = dict(tuning or {}, timing=1)
-    kns.render(ctx, grid, cams, W, H, ms, eps, precision=precision, out=frame, stream=stream, tuning=tuning_t)
-    st = ctx.render_stats()
-    mac_trace, mac_hit = mac_counts(desc)
-    # kernels one render launches: generate, per round scan + scatter + FP32 eval + FP32 tail
-    # (+ BF16 eval), shade; counted from the library's round counter
-    # gen + rounds x (scan, scatter, eval, tail[, bf16 eval]) + an advance for every round but the
-    # last issued + hit count/scan/scatter + shade
-    launches_per_step = 4 + st["rounds"] * (5 + (1 if precision == kns.KNS_BF16 else 0))
+    def timed(prec, tun, steps):
+        """steps renders, each bracketed by CUDA events on the launching stream, L2 flushed between."""
+        for _ in range(max(3, args.warmup)):
+            render(prec, tun)
+        ctx.sync(stream)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.fill_(k & 0xFF)
+            evs[k][0].record(stream)
+            render(prec, tun)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ctx.sync(stream)
+        return [a.elapsed_time(b) for a, b in evs]
+
+    def stats_of(prec, tun):
+        render(prec, dict(tun or {}, timing=1))
+        ctx.sync(stream)
+        return ctx.render_stats(), ctx.round_trace()
 
     clocks = ClockSampler(local_rank).start() if rank == 0 else None
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)
-        evs[k][0].record(stream)
-        step()
-        evs[k][1].record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    times = [a.elapsed_time(b) for a, b in evs]
+    times = timed(precision, tuning, args.steps)
+    clock_info = clocks.stop() if clocks else None
     total_ms = sum(times)
-    ctx.sync(stream)
+    main_out = {k: v.cpu().numpy() for k, v in frame[0].items()}
+    st, trace = stats_of(precision, tuning)
+
+    # the plain FP32 GPU path on the same workload, same protocol (the comparison the metric names)
+    fp32 = None
+    if precision == kns.KNS_BF16 and not args.no_fp32_compare:
+        t32 = timed(kns.KNS_FP32, None, max(3, args.steps // 2))
+        fp32_out = {k: v.cpu().numpy() for k, v in frame[0].items()}
+        st32, _ = stats_of(kns.KNS_FP32, None)
+        (t32_ms,) = max_over_ranks([sum(t32)], dev, world)
+        fp32 = {"value": whole_job_rate(n_rays, world, len(t32), t32_ms), "unit": UNIT,
+                "ms_per_step": t32_ms / len(t32), "steps": len(t32),
+                "phases_ms_per_render": {k: st32[k] for k in ("ms_generate", "ms_sort", "ms_eval_fp32", "ms_shade",
+                                                              "ms_total")},
+                "counts_per_render": {k: st32[k] for k in ("rounds", "hits", "samples_fp32", "samples_tail")}}
+
     # e2e through the public API: cameras from host memory, outputs read back to pinned host buffers
     host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in frame[0].items()
             if k in ("rgb", "depth", "normal", "hit")}
     d2h = sum(v.numel() * v.element_size() for v in host.values())
     h2d = cams.nbytes
     for _ in range(2):
-        step()
+        render(precision, tuning)
         for k, v in host.items():
             v.copy_(frame[0][k], non_blocking=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        step()
+        render(precision, tuning)
         for k, v in host.items():
             v.copy_(frame[0][k], non_blocking=True)
         stream.synchronize()
     e2e_s = time.perf_counter() - t0
-    clock_info = clocks.stop() if clocks else None
 
     total_ms, e2e_s = max_over_ranks([total_ms, e2e_s], dev, world)
     ms_per_step = total_ms / args.steps
@@ -334,54 +415,97 @@ def run_kns(args, rank, world, local_rank):
     e2e_value = whole_job_rate(n_rays, world, args.steps, e2e_s * 1e3)
 
     if rank == 0:
-        peaks = load_peaks()
-        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-        fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
-        if precision == kns.KNS_FP32:
-            # dominant kernel class: the FP32 evaluation (block or warp tiles, plus the warp-per-ray tail
-            # that finishes the last rays; the library times them as one class), FMA-bound
-            flops = 2.0 * st["samples_fp32"] * mac_trace
-            kms = st["ms_eval_fp32"]
-            warp_tiles = bool(tuning) and tuning.get("block_tiles") == 2
-            roof = {"bound": "alu", "peak": fp32_peak, "unit": "TFLOP/s",
-                    "kernel": ("wave_eval_kernel" if warp_tiles else "wave_eval_block_kernel")
-                              + " + wave_tail_warp_kernel + wave_advance_kernel",
-                    "kernel_class_note": "time and samples of the evaluation class: tile rounds, the "
-                                         "warp-per-ray tail and the empty-voxel advance kernel", "peak_source": FP32_PEAK_NOTE}
-        else:
-            # dominant kernel: the BF16 tensor-core tile evaluation (wave_eval_bf16_kernel)
-            flops = 2.0 * st["samples_bf16"] * mac_trace
+        import oracle as O
+        mp = load_peaks()
+        pk = ctx.measure_peaks(stream)
+        p_ffma, p_mufu = pk["ffma_flops"] / 1e12, pk["mufu_ops"] / 1e9  # TFLOP/s, Gop/s
+        mac_trace, mac_hit = mac_counts(desc)
+        IN = 3 + 6 * desc.pe_pos_L
+        Wd, Hd = desc.sdf_width, desc.sdf_hidden
+        mac_tc = IN * Wd + (Hd - 1) * Wd * Wd  # hidden layers of a trace sample (the d row is FP32)
+        transc = 2 * Hd * Wd  # ex2 + lg2 per hidden unit (softplus)
+        hbm = float(mp.get("hbm_gbs", 6772.9))
+        bf16_peak = float(mp.get("bf16_tflops", 1944.1))
+        if precision == kns.KNS_BF16:
+            # dominant kernel: the persistent tensor-core trace (every BF16 round, sort and scatter inside)
+            S_ = st["samples_bf16"]
             kms = st["ms_eval_bf16"]
-            roof = {"bound": "tensor", "peak": float(peaks.get("bf16_tflops", 1944.1)), "unit": "TFLOP/s",
-                    "kernel": "wave_eval_bf16_kernel", "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured)"}
-        achieved = flops / (kms * 1e-3) / 1e12 if kms > 0 else 0.0
-        launches = st["rounds"]
-        kernel_tag = "%s_%s_%s" % (roof["kernel"].split()[0], args.precision, args.workload)
-        roof.update({"achieved": achieved, "frac": achieved / roof["peak"], "traffic": profile_traffic(kernel_tag),
-                     "launches_per_render": launches, "algorithmic_flop_per_render": flops,
-                     "kernel_ms_per_render": kms, "flop_per_sample": 2 * mac_trace})
+            t_mufu = S_ * transc / (p_mufu * 1e9) * 1e3
+            t_tc = 2.0 * S_ * mac_tc / (bf16_peak * 1e12) * 1e3
+            achieved = S_ * transc / (kms * 1e-3) / 1e9 if kms > 0 else 0.0
+            roof = {"bound": "alu", "kernel": "trace_tc_kernel (persistent BF16 trace)", "unit": "Gop/s",
+                    "peak": p_mufu, "achieved": achieved, "frac": achieved / p_mufu,
+                    "peak_source": "measured on this GPU: ex2.approx micro-kernel (kns_measure_peaks), of measured",
+                    "work": "2 MUFU (ex2, lg2) per hidden unit x %d units per sample x %d BF16 samples" % (Hd * Wd, S_),
+                    "kernel_ms_per_render": kms,
+                    "tensor_pipe_frac": 2.0 * S_ * mac_tc / (kms * 1e-3) / (bf16_peak * 1e12) if kms > 0 else 0.0,
+                    "tensor_pipe_note": "algorithmic hidden-layer FLOP (2 x %d MAC per sample) over the kernel time, "
+                                        "of measured bf16 %.1f TFLOP/s; the split issues 3x that on padded K" % (mac_tc, bf16_peak),
+                    "t_floor_ms": max(t_mufu, t_tc), "t_floor_terms_ms": {"mufu": t_mufu, "tensor": t_tc},
+                    "traffic": profile_traffic("trace_tc_kernel_bf16_%s" % args.workload)}
+        else:
+            S_ = st["samples_fp32"]
+            kms = st["ms_eval_fp32"]
+            flops = 2.0 * S_ * mac_trace
+            achieved = flops / (kms * 1e-3) / 1e12 if kms > 0 else 0.0
+            t_ffma = flops / (p_ffma * 1e12) * 1e3
+            t_mufu = S_ * transc / (p_mufu * 1e9) * 1e3
+            roof = {"bound": "alu", "kernel": "wave_eval_block_kernel + wave_tail_warp_kernel (FP32 evaluation class)",
+                    "unit": "TFLOP/s", "peak": p_ffma, "achieved": achieved, "frac": achieved / p_ffma,
+                    "peak_source": "measured on this GPU: FFMA micro-kernel (kns_measure_peaks), of measured",
+                    "kernel_ms_per_render": kms, "flop_per_sample": 2 * mac_trace,
+                    "t_floor_ms": max(t_ffma, t_mufu), "t_floor_terms_ms": {"ffma": t_ffma, "mufu": t_mufu},
+                    "traffic": profile_traffic("wave_eval_block_kernel_fp32_%s" % args.workload)}
+        roof["measured_peaks"] = {"ffma_tflops": p_ffma, "mufu_gops": p_mufu, "sm_count": pk["sm_count"],
+                                  "hbm_gbs": hbm, "bf16_tflops": bf16_peak}
         phases = {k: st[k] for k in ("ms_generate", "ms_sort", "ms_eval_fp32", "ms_eval_bf16", "ms_shade",
                                      "ms_total")}
         counts = {k: st[k] for k in ("rounds", "rays", "hits", "samples_fp32", "samples_bf16", "samples_tail")}
+        accuracy = None
+        if precision == kns.KNS_BF16 and fp32 is not None and not args.no_accuracy:
+            occ = O.occupancy(desc, w) if desc.occ_res else None
+            # both sides must use the same occupancy mask: render the sampled comparison on a grid loaded
+            # with the oracle's mask (the timed grid built its mask on the device)
+            g2 = kns.Grid.load(ctx, desc, w, occ)
+            o_bf = {k: v.cpu().numpy() for k, v in kns.render(ctx, g2, cams, W, H, ms, eps, precision=kns.KNS_BF16).items()}
+            o_fp = {k: v.cpu().numpy() for k, v in kns.render(ctx, g2, cams, W, H, ms, eps).items()}
+            ctx.sync()
+            g2.free()
+            accuracy = bf16_accuracy(O, desc, w, occ, cams, W, H, ms, eps, o_bf, o_fp)
+        serving = None
+        if args.serving and precision == kns.KNS_BF16 and world == 1:
+            serving = serving_run(kns, S, (desc, w), args.serving_rates, args.serving_seconds)
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             v, n, s, cores = oracle_rate(desc, w, cams, W, H, ms, eps, args.cpu_seconds)
             cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": "%d rays drawn (seeded, with replacement) from the %d rays of the workload "
-                             "(%.1f s of FP64 oracle work)"
-                             % (n, n_rays, s)}
+                             "(%.1f s of FP64 oracle work)" % (n, n_rays, s)}
+        if precision == kns.KNS_BF16:
+            launches = 9  # gen, persistent trace, tail, hit count/scan/scatter, shade, refine (+ hit-sort memset)
+            launch_src = ("fixed sequence of a BF16 render: ray generation, the persistent trace (every round in one "
+                          "cooperative launch), the one-warp-per-ray tail, hit count/scan/scatter, shading, FP32 "
+                          "refinement")
+        else:
+            launches = 4 + st["rounds"] * 5
+            launch_src = ("library round counter: gen + rounds x (scan part, scan final, scatter, eval, tail) + "
+                          "(rounds - 1) advance + hit sort (3) + shade")
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if precision == kns.KNS_FP32 else "bf16",
                 "data": "synthetic",
                 "config": dict(workload_config(args.workload, desc, cams, W, H, ms, eps, args.precision),
-                               parallelism="replicas" if world > 1 else "single GPU"),
+                               parallelism="replicas" if world > 1 else "single GPU",
+                               gpu="%s, %d SMs" % (props.name, props.multi_processor_count)),
+                "fp32": fp32, "speedup_vs_fp32": (value / fp32["value"]) if fp32 else None,
+                "bf16_accuracy_vs_oracle": accuracy,
                 "roofline": roof, "cpu_baseline": cpu, "phases_ms_per_render": phases, "counts_per_render": counts,
+                "rounds_live": [r["live"] for r in trace][:40],
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                         "d2h_bytes_per_step": int(d2h)},
-                "clocks": clock_info, "gpu_launches": args.steps * launches_per_step, "tuning": tuning,
-                "launch_count_source": "library round counter: gen + rounds x (scan, scatter, eval, tail[, bf16 eval]) + "
-                                      "(rounds - 1) advance + hit sort (3) + shade",
+                "serving": serving,
+                "clocks": clock_info, "gpu_launches": args.steps * launches, "tuning": tuning,
+                "launch_count_source": launch_src,
                 "step_ms_min": min(times), "step_ms_median": statistics.median(times)}
         print(json.dumps(line), flush=True)
     grid.free()
@@ -712,14 +836,13 @@ def run_train(args, rank, world, local_rank):
     n_rays = wl["n_rays"]
     value = whole_job_rate(n_rays, world, args.steps, total_ms)
     if rank == 0:
-        peaks = load_peaks()
-        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-        fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+        fp32_peak = ctx.measure_peaks(stream)["ffma_flops"] / 1e12
         flops = 2.0 * st["records_fd"] * mac["bwd_d"]
         kms = st["ms_fd_backward"]
         achieved = flops / (kms * 1e-3) / 1e12 if kms > 0 else 0.0
         roof = {"bound": "alu", "peak": fp32_peak, "unit": "TFLOP/s",
-                "kernel": "k_tile_backward (difference points)", "peak_source": FP32_PEAK_NOTE,
+                "kernel": "k_tile_backward (difference points)",
+                "peak_source": "measured on this GPU: FFMA micro-kernel (kns_measure_peaks), of measured",
                 "achieved": achieved, "frac": achieved / fp32_peak,
                 "traffic": profile_traffic("k_tile_backward_fd_train"), "algorithmic_flop_per_launch": flops,
                 "kernel_ms_per_launch": kms, "flop_per_record": 2 * mac["bwd_d"],

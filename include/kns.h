@@ -114,7 +114,7 @@ typedef struct kns_frame {
  * the work, never a result; 0 selects the built-in default. */
 typedef struct kns_render_opts {
     int32_t precision;    /* KNS_FP32 or KNS_BF16 */
-    float eps_coarse;     /* KNS_BF16: hit threshold of the BF16 trace (<= 0: eps) */
+    float eps_coarse;     /* KNS_BF16: hit threshold of the BF16 trace (> 0; 0: 0.9 eps); FP32 decides the hit */
     int32_t refine_steps; /* KNS_BF16: FP32 evaluations of a BF16 hit (<= 0: 2): the first re-evaluates the
                              BF16 trace's last step; the ray is a hit at the first |d| < eps, or at the last
                              of them if |d| < eps_coarse there, else a miss */
@@ -151,6 +151,7 @@ typedef struct kns_render_stats {
     /* device time (ms) per kernel class, summed over the render's launches; 0 unless opts->timing */
     float ms_generate, ms_sort, ms_eval_fp32, ms_eval_bf16, ms_shade, ms_total;
     int64_t samples_tail;  /* the part of samples_fp32 evaluated one warp per ray (rounds of <= tail_rays rays) */
+    int64_t refined;       /* KNS_BF16: hits whose FP32 re-evaluation at shading was not within eps (FP32 steps) */
 } kns_render_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -229,6 +230,21 @@ typedef struct kns_round_info {
  * the render to finish.  Errors: INVALID_ARG (NULL n_rounds, out NULL with max_rounds > 0, no render
  * yet), CUDA. */
 kns_status kns_get_round_trace(kns_ctx *ctx, kns_round_info *out, int32_t max_rounds, int32_t *n_rounds);
+
+/* Measured throughput ceilings of the device a context runs on (for roofline reporting; not part of the
+ * method): FP32 fused multiply-add in FLOP/s (2 per FMA) and the multi-function unit's ex2 in
+ * operations/s, each from a micro-kernel with eight independent dependency chains per thread over every
+ * SM, best of three timed launches; the SM count and the SM clock (kHz) the driver reports. */
+typedef struct kns_peaks {
+    double ffma_flops;
+    double mufu_ops;
+    int32_t sm_count;
+    int32_t sm_clock_khz;
+} kns_peaks;
+
+/* Runs the micro-kernels on `cuda_stream` and waits for them (about 0.1 s).  Allocates a few KB of
+ * device memory for the duration of the call.  Errors: INVALID_ARG (NULL), CUDA. */
+kns_status kns_measure_peaks(kns_ctx *ctx, void *cuda_stream, kns_peaks *out);
 
 /* One view of a multi-view render: camera, image size and its own output buffers (device pointers for
  * W*H pixels, layout as kns_frame). */

@@ -51,6 +51,10 @@ class Context:
         """Counters (and per-kernel-class device ms when rendered with tuning={'timing': 1}) of the last render."""
         return capi.kns_get_render_stats(self.handle)
 
+    def measure_peaks(self, stream=None) -> dict:
+        """FP32 FMA FLOP/s and ex2 op/s measured on the device by micro-kernels (roofline denominators)."""
+        return capi.kns_measure_peaks(self.handle, _stream_ptr(stream))
+
     def round_trace(self) -> list:
         """Per-round live samples (and per-class device ms when rendered with tuning={'timing': 1}) of the
         last render call."""

@@ -87,7 +87,12 @@ class kns_render_stats(C.Structure):
     _fields_ = [("rounds", C.c_int32), ("rays", C.c_int64), ("hits", C.c_int64), ("samples_fp32", C.c_int64),
                 ("samples_bf16", C.c_int64), ("ms_generate", C.c_float), ("ms_sort", C.c_float),
                 ("ms_eval_fp32", C.c_float), ("ms_eval_bf16", C.c_float), ("ms_shade", C.c_float),
-                ("ms_total", C.c_float), ("samples_tail", C.c_int64)]
+                ("ms_total", C.c_float), ("samples_tail", C.c_int64), ("refined", C.c_int64)]
+
+
+class kns_peaks(C.Structure):
+    _fields_ = [("ffma_flops", C.c_double), ("mufu_ops", C.c_double), ("sm_count", C.c_int32),
+                ("sm_clock_khz", C.c_int32)]
 
 
 class kns_round_info(C.Structure):
@@ -140,6 +145,8 @@ def lib():
             L.kns_render_views.restype = st
             L.kns_get_render_stats.argtypes = [vp, C.POINTER(kns_render_stats)]
             L.kns_get_render_stats.restype = st
+            L.kns_measure_peaks.argtypes = [vp, vp, C.POINTER(kns_peaks)]
+            L.kns_measure_peaks.restype = st
             L.kns_get_round_trace.argtypes = [vp, C.POINTER(kns_round_info), C.c_int32, C.POINTER(C.c_int32)]
             L.kns_get_round_trace.restype = st
             L.kns_trace_rays.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_int, C.c_float, C.POINTER(kns_frame),
@@ -251,6 +258,13 @@ def kns_get_render_stats(ctx: int) -> dict:
     st = kns_render_stats()
     _check(lib().kns_get_render_stats(ctx, C.byref(st)), ctx)
     return {k: getattr(st, k) for k, _ in kns_render_stats._fields_}
+
+
+def kns_measure_peaks(ctx: int, stream: int = 0) -> dict:
+    """Measured FP32 FMA FLOP/s and ex2 op/s of the context's device, its SM count and clock."""
+    p = kns_peaks()
+    _check(lib().kns_measure_peaks(ctx, stream, C.byref(p)), ctx)
+    return {k: getattr(p, k) for k, _ in kns_peaks._fields_}
 
 
 def kns_get_round_trace(ctx: int, max_rounds: int = 1024) -> list:

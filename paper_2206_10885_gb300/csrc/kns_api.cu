@@ -840,12 +840,13 @@ kns_status resolve_opts(kns_ctx *ctx, const kns_render_opts *opts, float eps, Re
     if (precision != KNS_FP32 && precision != KNS_BF16)
         return set_err(ctx, KNS_ERR_INVALID_ARG, "unknown precision %d", precision);
     c.bf16 = precision == KNS_BF16;
-    // BF16 defaults: the split-BF16 trace is accurate to ~1e-5, so it runs to the FP32 threshold itself;
-    // FP32 then re-evaluates its last step and takes at most one more (two FP32 evaluations)
-    c.eps_coarse = (c.bf16 && opts && opts->eps_coarse > 0.f) ? opts->eps_coarse : eps;
+    // BF16 defaults: the split-BF16 trace is accurate to ~1e-5, so it runs to 0.9 eps itself -- just inside
+    // the FP32 threshold, so that the FP32 re-evaluation of its last step at shading confirms the hit (on the
+    // 1080p workloads every hit: no FP32 steps follow); FP32 may take one more step (two FP32 evaluations)
+    c.eps_coarse = (c.bf16 && opts && opts->eps_coarse > 0.f) ? opts->eps_coarse : 0.9f * eps;
     c.refine_steps = (c.bf16 && opts && opts->refine_steps > 0) ? opts->refine_steps : 2;
-    if (c.bf16 && !(c.eps_coarse >= eps && std::isfinite(c.eps_coarse)))
-        return set_err(ctx, KNS_ERR_INVALID_ARG, "eps_coarse must be finite and >= eps");
+    if (c.bf16 && !(c.eps_coarse > 0.f && std::isfinite(c.eps_coarse)))
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "eps_coarse must be finite and > 0");
     auto knob = [](int32_t v, int32_t def) { return v == 0 ? def : v; };
     const int bt0 = opts ? knob(opts->block_tiles, kRenderBlockTiles) : kRenderBlockTiles;
     const int def_inner = bt0 == 2 ? kRenderInnerSteps : kRenderBlockInnerSteps;
@@ -1061,6 +1062,7 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
         ctx->stats.samples_fp32 += (int64_t)hc.samples_f32;
         ctx->stats.samples_bf16 += (int64_t)hc.samples_bf16;
         ctx->stats.samples_tail += (int64_t)hc.samples_tail;
+        ctx->stats.refined += hc.n_refine;
     }
     return KNS_OK;
 }
@@ -1279,6 +1281,7 @@ kns_status kns_get_render_stats(kns_ctx *ctx, kns_render_stats *out) {
     st.samples_bf16 += (int64_t)hc.samples_bf16;
     st.samples_tail += (int64_t)hc.samples_tail;
     st.rounds += hc.rounds;  // a persistent BF16 trace counts its rounds on the device
+    st.refined += hc.n_refine;
     float *dst[5] = {&st.ms_generate, &st.ms_sort, &st.ms_eval_fp32, &st.ms_eval_bf16, &st.ms_shade};
     for (const auto &m : ctx->ev_marks) {
         float ms = 0.f;
@@ -1286,6 +1289,20 @@ kns_status kns_get_render_stats(kns_ctx *ctx, kns_render_stats *out) {
     }
     st.ms_total = st.ms_generate + st.ms_sort + st.ms_eval_fp32 + st.ms_eval_bf16 + st.ms_shade;
     *out = st;
+    return KNS_OK;
+}
+
+kns_status kns_measure_peaks(kns_ctx *ctx, void *cuda_stream, kns_peaks *out) {
+    if (!ctx) return KNS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!out) return set_err(ctx, KNS_ERR_INVALID_ARG, "NULL out");
+    DeviceScope ds(ctx->device);
+    kns_peaks p{};
+    p.sm_count = ctx->sm_count;
+    cudaError_t e = cudaDeviceGetAttribute(&p.sm_clock_khz, cudaDevAttrClockRate, ctx->device);
+    if (e == cudaSuccess) e = kns::measure_peaks(ctx->sm_count, (cudaStream_t)cuda_stream, &p.ffma_flops, &p.mufu_ops);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "peak micro-kernels");
+    *out = p;
     return KNS_OK;
 }
 

@@ -147,6 +147,9 @@ inline int shade_hit_tile(int sdf_width) { return 4096 / sdf_width; }  // hits p
 cudaError_t launch_coarse_occupancy(const uint32_t *occ, int res, uint32_t *coarse, cudaStream_t s);
 cudaError_t launch_wave_scatter(const WaveArgs &a, int cur, int blocks, cudaStream_t s);
 
+// Measured FP32 FMA (FLOP/s) and ex2 (operations/s) throughput of the device (kns_peak.cu).
+cudaError_t measure_peaks(int sm_count, cudaStream_t s, double *ffma_flops, double *mufu_ops);
+
 cudaError_t launch_sdf_f32(const Shape &sh, const GridView &g, const float *pts, int64_t n, float *sdf,
                            float *feat, float *grad, cudaStream_t s);
 cudaError_t launch_occupancy_f32(const Shape &sh, const GridView &g, float thresh, uint32_t *words,

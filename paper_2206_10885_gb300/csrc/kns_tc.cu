@@ -122,7 +122,8 @@ struct TcWorker {
     unsigned char *wsm, *A;   // shared: the cell's weights, the activation matrices
     uint64_t *bar_w, *bar_mma;
     int *s_tile;              // 4 ints: key, first sample, samples, fresh
-    int *s_red;               // 4 ints: per-warp partial counts
+    int *s_red;               // 8 ints: per-warp partial counts, two alternating sets
+    int *s_fail;              // set by any thread whose wait ran out; read after the next barrier
     uint32_t tmem;            // first tensor-memory column of the worker's accumulator
     int bar;                  // named barrier id
     int tid, warp;            // thread (0..127) and warp (0..3) within the worker
@@ -130,18 +131,21 @@ struct TcWorker {
     uint32_t ph_w, ph_mma;    // mbarrier phases
     bool w_pending, mma_pending;  // a weight copy / a tensor-core chain in flight
     unsigned n_eval;          // samples this thread evaluated
+    int red;                  // which set of s_red the next count uses
 };
 
 __device__ __forceinline__ void wg_bar(int id) { asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory"); }
 
-// Threads of the worker whose p is true (every thread of the worker calls it).
+// Threads of the worker whose p is true (every thread of the worker calls it).  The two sets of partial
+// counts alternate: a set is written again only two counts later, after every thread has passed the
+// barrier of the count in between, so one barrier per count suffices.
 __device__ __forceinline__ int wg_count(TcWorker &w, bool p) {
     const unsigned b = __ballot_sync(FULL, p);
-    if ((w.tid & 31) == 0) w.s_red[w.warp] = __popc(b);
+    int *set = w.s_red + 4 * w.red;
+    w.red ^= 1;
+    if ((w.tid & 31) == 0) set[w.warp] = __popc(b);
     wg_bar(w.bar);
-    const int n = w.s_red[0] + w.s_red[1] + w.s_red[2] + w.s_red[3];
-    wg_bar(w.bar);
-    return n;
+    return set[0] + set[1] + set[2] + set[3];
 }
 
 // One round of the BF16 trace for one worker: tiles [0, n_tiles) of the round, a contiguous run per
@@ -198,25 +202,35 @@ __device__ bool tc_round(TcWorker &w, const GridView &g, const WaveArgs &a, int 
         for (int it = 0;; ++it) {
             if (active) encode_row<C, T>(A, tid, fmaf(t, ray.wx, ray.ox), fmaf(t, ray.wy, ray.oy), fmaf(t, ray.wz, ray.oz));
             tc::fence_async_smem();
+            // a wait that runs out raises the worker's failure flag, read after the next barrier, where the
+            // worker leaves; the thread itself ignores its sample from then on (lost)
+            bool lost = false;
             if (w.w_pending) {
-                const bool ok = mbar_wait(w.bar_w, w.ph_w, kTcPolls);
-                if (wg_count(w, !ok) > 0) return false;
-                w.ph_w ^= 1u;
-                w.w_pending = false;
+                if (mbar_wait(w.bar_w, w.ph_w, kTcPolls)) {
+                    w.ph_w ^= 1u;
+                    w.w_pending = false;
+                } else {
+                    *w.s_fail = 1;
+                    lost = true;
+                }
             }
             // the hidden layers: products on the tensor cores, bias + softplus + split on the worker
             float d = 0.f;
             for (int l = 0; l < C::H; ++l) {
                 wg_bar(w.bar);
+                if (*w.s_fail) return false;
                 if (tid == 0) {
                     tc::fence_after_sync();
                     issue_layer<T>(w.tmem, a_base, w_base, l, w.bar_mma);
                 }
                 w.mma_pending = true;
-                const bool ok = mbar_wait(w.bar_mma, w.ph_mma, kTcPolls);
-                if (wg_count(w, !ok) > 0) return false;
-                w.ph_mma ^= 1u;
-                w.mma_pending = false;
+                if (mbar_wait(w.bar_mma, w.ph_mma, kTcPolls)) {
+                    w.ph_mma ^= 1u;
+                    w.mma_pending = false;
+                } else {
+                    *w.s_fail = 1;
+                    lost = true;
+                }
                 tc::fence_after_sync();
                 if (__any_sync(FULL, active)) {
                     float dacc = drow[T::W];  // the d row's bias (stored right after the row)
@@ -242,6 +256,7 @@ __device__ bool tc_round(TcWorker &w, const GridView &g, const WaveArgs &a, int 
             // outcome: 0 none, 1 converged (hit list), 2 miss (written), 3 pending, 4 emit to ncell
             int outcome = 0, ncell = -1;
             const float t_eval = t;
+            if (lost) active = false;
             w.n_eval += active ? 1u : 0u;
             if (active) {
                 ++steps;
@@ -271,6 +286,7 @@ __device__ bool tc_round(TcWorker &w, const GridView &g, const WaveArgs &a, int 
             }
             const bool cand = outcome == 4 && ncell == c && it + 1 < a.inner_steps_bf;
             const int n_cand = wg_count(w, cand);
+            if (*w.s_fail) return false;
             const bool again = n_cand > 0 && n_cand >= a.min_active_bf;
             const bool stay = cand && again;
             {
@@ -323,7 +339,7 @@ __global__ void __launch_bounds__(128) wave_eval_tc_kernel(GridView g, WaveArgs 
     extern __shared__ __align__(1024) unsigned char dyn[];
     __shared__ __align__(8) uint64_t bar_w, bar_mma;
     __shared__ uint32_t s_tmem;
-    __shared__ int s_tile[4], s_red[4];
+    __shared__ int s_tile[4], s_red[8], s_fail;
     const int n_tiles = a.ctrl->n_tiles;
     // uniform over the block, before any tensor memory is held; a small round (at most tail_rays rays)
     // is finished one warp per ray by wave_tail_warp_kernel
@@ -333,12 +349,13 @@ __global__ void __launch_bounds__(128) wave_eval_tc_kernel(GridView g, WaveArgs 
     if (tid == 0) {
         mbar_init(&bar_w, 1);
         mbar_init(&bar_mma, 1);
+        s_fail = 0;
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    TcWorker w{dyn, dyn + T::SIZE, &bar_w, &bar_mma, s_tile, s_red, s_tmem, 1, tid, tid >> 5, -1, 0u, 0u,
-               false, false, 0u};
+    TcWorker w{dyn, dyn + T::SIZE, &bar_w, &bar_mma, s_tile, s_red, &s_fail, s_tmem, 1, tid, tid >> 5, -1, 0u, 0u,
+               false, false, 0u, 0};
     const bool ok = tc_round<C>(w, g, a, cur, n_tiles, blockIdx.x, gridDim.x);
     tc_worker_done(w, a, ok);
     tc::fence_before_sync();
@@ -443,7 +460,7 @@ __global__ void __launch_bounds__(NW * 128, 1) trace_tc_kernel(GridView g, WaveA
     extern __shared__ __align__(1024) unsigned char dyn[];
     __shared__ __align__(8) uint64_t bar_w[NW], bar_mma[NW];
     __shared__ uint32_t s_tmem;
-    __shared__ int s_tile[NW][4], s_red[NW][4];
+    __shared__ int s_tile[NW][4], s_red[NW][8], s_fail[NW];
     __shared__ int wx[32], wy[32], s_base[2], s_flag;
     WaveCtrl *ctrl = a.ctrl;
     const int tid = threadIdx.x, wk = tid >> 7;
@@ -452,13 +469,14 @@ __global__ void __launch_bounds__(NW * 128, 1) trace_tc_kernel(GridView g, WaveA
     if (tid < NW) {
         mbar_init(&bar_w[tid], 1);
         mbar_init(&bar_mma[tid], 1);
+        s_fail[tid] = 0;
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     unsigned char *base = dyn + wk * T::SMEM;
-    TcWorker w{base, base + T::SIZE, &bar_w[wk], &bar_mma[wk], s_tile[wk], s_red[wk], s_tmem + (uint32_t)(wk * C::W),
-               1 + wk, tid & 127, (tid & 127) >> 5, -1, 0u, 0u, false, false, 0u};
+    TcWorker w{base, base + T::SIZE, &bar_w[wk], &bar_mma[wk], s_tile[wk], s_red[wk], &s_fail[wk],
+               s_tmem + (uint32_t)(wk * C::W), 1 + wk, tid & 127, (tid & 127) >> 5, -1, 0u, 0u, false, false, 0u, 0};
     if (blockIdx.x == 0 && tid == 0) ctrl->start_ns = globaltimer_ns();
     unsigned gen = 0;
     bool ok = true;

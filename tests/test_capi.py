@@ -59,8 +59,9 @@ int main(void) {
   printf("%zu %zu\\n", sizeof(kns_train_stats), offsetof(kns_train_stats, ms_fd_backward));
   printf("%zu %zu %zu\\n", sizeof(kns_pt_opts), offsetof(kns_pt_opts, seed), offsetof(kns_pt_opts, zenith));
   printf("%zu %zu %zu\\n", sizeof(kns_render_stats), offsetof(kns_render_stats, ms_eval_fp32),
-         offsetof(kns_render_stats, samples_tail));
+         offsetof(kns_render_stats, refined));
   printf("%zu %zu\\n", sizeof(kns_round_info), offsetof(kns_round_info, ms_advance));
+  printf("%zu %zu\\n", sizeof(kns_peaks), offsetof(kns_peaks, sm_clock_khz));
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -75,8 +76,9 @@ int main(void) {
             C.sizeof(capi.kns_train_stats), capi.kns_train_stats.ms_fd_backward.offset,
             C.sizeof(capi.kns_pt_opts), capi.kns_pt_opts.seed.offset, capi.kns_pt_opts.zenith.offset,
             C.sizeof(capi.kns_render_stats), capi.kns_render_stats.ms_eval_fp32.offset,
-            capi.kns_render_stats.samples_tail.offset,
-            C.sizeof(capi.kns_round_info), capi.kns_round_info.ms_advance.offset]
+            capi.kns_render_stats.refined.offset,
+            C.sizeof(capi.kns_round_info), capi.kns_round_info.ms_advance.offset,
+            C.sizeof(capi.kns_peaks), capi.kns_peaks.sm_clock_khz.offset]
     assert vals == want
 
 
@@ -96,6 +98,7 @@ def test_null_context_is_rejected_on_the_host(lib):
     assert lib.kns_render_views(None, None, None, 1, 1, 1e-4, None, None) == bad
     assert lib.kns_get_render_stats(None, None) == bad
     assert lib.kns_get_round_trace(None, None, 0, None) == bad
+    assert lib.kns_measure_peaks(None, None, None) == bad
     assert lib.kns_trace_rays(None, None, None, None, 1, 1, 1e-4, None, None, None) == bad
     assert lib.kns_path_trace(None, None, None, 1, 1, 1, None, 1, 1e-4, None, None, None) == bad
     assert lib.kns_train_forward(None, None, None, None, None, None, None, None, None) == bad
