@@ -18,16 +18,21 @@
  *    return without waiting.  A render also runs work on a stream the context
  *    owns, forked from and joined back into the caller's stream with events
  *    inside the call, so the render is complete, like any other work, when
- *    the caller's stream reaches the point after it.  The render loop reads
- *    a small pinned counter on the host between rounds, so renders cannot be
- *    captured into a CUDA graph.  Device-side failures (a bounded wait that
+ *    the caller's stream reaches the point after it.  An FP32 render's loop
+ *    reads a small pinned counter on the host between rounds; a BF16 render
+ *    runs its rounds on the device in one persistent launch.  Renders are not
+ *    designed for capture into a CUDA graph.  Device-side failures (a bounded wait that
  *    ran out, a bounds check that tripped) are recorded in a per-context
  *    status word and returned by the next kns_sync() on that context.
  *  - Memory: the caller owns every input and output buffer and passes plain
  *    pointers (device pointers unless stated "host").  The library never
  *    frees caller memory.  Grids own the device copies of their weights.
  *  - Threads: a context may be used from several host threads; calls on one
- *    context are serialised internally.
+ *    context are serialised on the host.  Their GPU work shares the context's
+ *    scratch, so one context's renders must also be ordered on the GPU: issue
+ *    them on one stream, or order their streams with events (two renders of
+ *    one context running at once on different streams race).  Use a context
+ *    per concurrent stream, as the render server does.
  *
  * Canonical weight layout (host, FP32, every loader takes it)
  *   cells in x-fastest order, cell = ix + N*(iy + N*iz); per cell the SDF MLP
@@ -124,7 +129,7 @@ typedef struct kns_render_opts {
     int32_t min_active;    /* a tile continues only while at least this many of its rays stay in its cell
                               (1..256; a warp tile holds 16; default 8 for warp tiles, 16 for block tiles) */
     int32_t tail_rays;     /* a round with at most this many rays is finished one warp per ray, in FP32 (>= 0;
-                              -1: never; default 131072, 32768 for KNS_BF16) */
+                              -1: never; default 131072 at SDF width 32, 32768 at width 64 and for KNS_BF16) */
     int32_t blocks_per_sm; /* evaluation blocks (one warp each) launched per SM (1..64) */
     int32_t static_tiles;  /* 1: each block takes a contiguous run of tiles; 2: tiles handed out dynamically */
     int32_t timing;        /* 1: time each kernel class with CUDA events for kns_get_render_stats (adds host work) */
@@ -379,17 +384,21 @@ kns_status kns_train_step(kns_ctx *ctx, const kns_grid_desc *desc, const float *
 #define KNS_NOALLOC_MAX_CELLS 32768 /* N^3 of the grid */
 #define KNS_NOALLOC_MAX_CAMS 64
 
-/* kns_render (FP32, default schedule) for callers that may not allocate device memory while they
- * run: an application that gives all device memory to its own pool allocator at start-up, or a
- * latency-bound loop that cannot take cudaMalloc's implicit device synchronisation.  The paper has
- * no counterpart; it is a deployment convenience.  Its scratch is a fixed device array built into
+/* An FP32 render for callers that may not allocate device memory while they run: an application
+ * that gives all device memory to its own pool allocator at start-up, or a latency-bound loop that
+ * cannot take cudaMalloc's implicit device synchronisation.  The paper has no counterpart; it is a
+ * deployment convenience.  It runs kns_render's FP32 wavefront on 16-sample warp tiles and the
+ * one-warp-per-ray tail, without the cycle test (a cycling ray runs on until max_steps), and shades
+ * like kns_render: the outputs are kns_render's.  Its scratch is a fixed device array built into
  * the library (about 14 MB on every GPU that loads it, kept until the process exits); the call
- * allocates nothing and frees nothing.  The context and the grid must already exist (creating them
- * does allocate).  The first call on a device looks up the array's device address (once per
- * device), so make that first call before any stream capture.  All calls share the one array and
- * each clears the counters it needs, so calls that overlap on the GPU race: serialise them (one
- * stream, or events).  Arguments, outputs and errors as kns_render, plus INVALID_ARG when
- * n_cams*W*H > KNS_NOALLOC_MAX_RAYS, n_cams > KNS_NOALLOC_MAX_CAMS or N^3 > KNS_NOALLOC_MAX_CELLS. */
+ * allocates nothing and frees nothing.  The context and the grid must already exist: creating them
+ * allocates, and kns_create also loads the array on its device and looks up its address (should that
+ * fail there, the first kns_render_noalloc on the device does it, and that first call should then come
+ * before any stream capture).  All calls
+ * share the one array and each clears the counters it needs, so calls that overlap on the GPU race:
+ * serialise them (one stream, or events).  Arguments, outputs and errors as kns_render, plus
+ * INVALID_ARG when n_cams*W*H > KNS_NOALLOC_MAX_RAYS, n_cams > KNS_NOALLOC_MAX_CAMS or
+ * N^3 > KNS_NOALLOC_MAX_CELLS. */
 kns_status kns_render_noalloc(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams, int n_cams, int W,
                               int H, int max_steps, float eps, const kns_frame *out, void *cuda_stream);
 

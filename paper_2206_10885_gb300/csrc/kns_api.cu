@@ -356,12 +356,14 @@ constexpr int kRenderInnerSteps = 4;
 constexpr int kRenderMinActive = 8;
 constexpr int kRenderBlockInnerSteps = 2;  // block tiles: a second evaluation of a tile in the round ...
 constexpr int kRenderBlockMinActive = 16;  // ... while at least 16 of its rays stay in its cell
-constexpr int kRenderTailRays = 131072;  // rounds this small finish one warp per ray
+constexpr int kRenderTailRays = 131072;  // rounds this small finish one warp per ray (width 32)
 // tensor-core tiles (BF16 renders): a second evaluation while at least 16 rays stay in the cell
 constexpr int kRenderBf16InnerSteps = 2;
 constexpr int kRenderBf16MinActive = 16;
 // BF16 renders hand rounds of at most this many rays (live + pending) to the one-warp-per-ray FP32
-// tail: the best of 8K..512K on both 1080p workloads (a tensor-core round costs ~50 us however few its rays)
+// tail: the best of 8K..512K on both 1080p workloads (a tensor-core round costs ~50 us however few its rays);
+// FP32 renders of width-64 grids too (their tail warps hold 41 KB of weights each: 5 per SM), the best of
+// 8K..512K on the 32^3 width-64 workload (131072 stays best at width 32)
 constexpr int kRenderBf16TailRays = 32768;
 constexpr int kRenderBlocksPerSM = 16;
 constexpr int kRenderStaticTiles = 2;
@@ -526,6 +528,56 @@ kns_status ensure_train_scratch(kns_ctx *ctx, int64_t B, int S, int Ns, int64_t 
 
 }  // namespace
 
+// ------------------------------------------------------------------ allocation-free render
+//
+// kns_render_noalloc serves callers that must not allocate device memory once they are running:
+// an engine that hands all device memory to its own pool allocator up front, or a latency-bound
+// loop that cannot afford cudaMalloc's implicit device synchronisation.  Its scratch is one
+// file-scope device array sized for KNS_NOALLOC_MAX_RAYS rays, KNS_NOALLOC_MAX_CELLS cells and
+// KNS_NOALLOC_MAX_CAMS cameras (about 14 MB: twelve 1 MiB per-ray buffers, the per-cell counters and
+// offsets, the tile descriptors, the view table and the control words -- kNoAllocBytes below), held by
+// every GPU that loads the library until the process exits.  kns_create loads the array on its device
+// and looks up its address there, so the entry point itself allocates nothing.  Every call shares the
+// array, so calls that overlap on the GPU race; the counters that must start at zero are cleared by
+// each call.
+namespace {
+
+constexpr size_t kNoAllocAlign = 256;
+constexpr size_t align_up(size_t v) { return (v + kNoAllocAlign - 1) / kNoAllocAlign * kNoAllocAlign; }
+constexpr size_t kNoAllocRayBuf = align_up(sizeof(int) * (size_t)KNS_NOALLOC_MAX_RAYS);
+constexpr size_t kNoAllocCellBuf = align_up(sizeof(int) * 6 * (size_t)(KNS_NOALLOC_MAX_CELLS + 1));
+constexpr size_t kNoAllocViewBuf = align_up(sizeof(kns::ViewDev) * (size_t)KNS_NOALLOC_MAX_CAMS);
+constexpr size_t kNoAllocCtrlBuf = align_up(sizeof(kns::WaveCtrl));
+constexpr size_t kNoAllocTileBuf =
+    align_up(sizeof(int4) * (size_t)(KNS_NOALLOC_MAX_RAYS / 16 + KNS_NOALLOC_MAX_CELLS + 1));
+// t_ray, steps_ray, cell_ray, q[2], qcell[2], sorted, hits, ray_view, pend_r, pend_t: twelve per-ray
+// int/float buffers
+constexpr size_t kNoAllocBytes =
+    12 * kNoAllocRayBuf + kNoAllocCellBuf + kNoAllocViewBuf + kNoAllocCtrlBuf + kNoAllocTileBuf;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_dev_ptr[256] = {};  // device address of g_noalloc_scratch, per device ordinal
+
+// The host-side name g_noalloc_scratch is only a stand-in for the device array: its device address
+// is looked up once per device, with that device current -- by kns_create (the lookup loads the module
+// and with it the array), or, should that have failed, by the first kns_render_noalloc on the device.
+kns_status noalloc_scratch(kns_ctx *ctx, unsigned char **out) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (ctx->device < 0 || ctx->device >= 256) return set_err(ctx, KNS_ERR_INVALID_ARG, "device ordinal too large");
+    if (!g_noalloc_dev_ptr[ctx->device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_err(ctx, e, "cudaGetSymbolAddress(no-alloc scratch)");
+        g_noalloc_dev_ptr[ctx->device] = p;
+    }
+    *out = (unsigned char *)g_noalloc_dev_ptr[ctx->device];
+    return KNS_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 kns_status kns_create(int device, kns_ctx **out) {
@@ -563,6 +615,12 @@ kns_status kns_create(int device, kns_ctx **out) {
         cudaFreeHost(c->h_live);
         delete c;
         return cuda_err(nullptr, e, "context events and stream");
+    }
+    // the allocation-free entry point's array: loaded and located now, while allocating is allowed
+    unsigned char *scratch = nullptr;
+    if (noalloc_scratch(c, &scratch) != KNS_OK) {  // retried by the first kns_render_noalloc
+        c->err.clear();
+        cudaGetLastError();
     }
     *out = c;
     return KNS_OK;
@@ -835,7 +893,7 @@ struct RenderCfg {
                          // 3 = 256 x 256, 4 = 128 x 128
 };
 
-kns_status resolve_opts(kns_ctx *ctx, const kns_render_opts *opts, float eps, RenderCfg &c) {
+kns_status resolve_opts(kns_ctx *ctx, const kns_render_opts *opts, float eps, RenderCfg &c, int sdf_width) {
     const int precision = opts ? opts->precision : KNS_FP32;
     if (precision != KNS_FP32 && precision != KNS_BF16)
         return set_err(ctx, KNS_ERR_INVALID_ARG, "unknown precision %d", precision);
@@ -853,7 +911,7 @@ kns_status resolve_opts(kns_ctx *ctx, const kns_render_opts *opts, float eps, Re
     const int def_min = bt0 == 2 ? kRenderMinActive : kRenderBlockMinActive;
     c.inner_steps = opts ? knob(opts->inner_steps, def_inner) : def_inner;
     c.min_active = opts ? knob(opts->min_active, def_min) : def_min;
-    const int def_tail = c.bf16 ? kRenderBf16TailRays : kRenderTailRays;
+    const int def_tail = (c.bf16 || sdf_width >= 64) ? kRenderBf16TailRays : kRenderTailRays;
     c.tail_rays = opts ? knob(opts->tail_rays, def_tail) : def_tail;
     c.blocks_per_sm = opts ? knob(opts->blocks_per_sm, kRenderBlocksPerSM) : kRenderBlocksPerSM;
     c.static_tiles = (opts ? knob(opts->static_tiles, kRenderStaticTiles) : kRenderStaticTiles) == 1;
@@ -1098,7 +1156,7 @@ kns_status kns_render(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams
     if (!(eps > 0.f) || !std::isfinite(eps)) return set_err(ctx, KNS_ERR_INVALID_ARG, "eps must be > 0 and finite");
     if (!out->rgb || !out->depth) return set_err(ctx, KNS_ERR_INVALID_ARG, "rgb and depth buffers are required");
     RenderCfg cfg;
-    kns_status st = resolve_opts(ctx, opts, eps, cfg);
+    kns_status st = resolve_opts(ctx, opts, eps, cfg, grid->desc.sdf_width);
     if (st != KNS_OK) return st;
     if (n_cams == 0 || W == 0 || H == 0) return KNS_OK;
     if ((int64_t)W * H > INT32_MAX) return set_err(ctx, KNS_ERR_INVALID_ARG, "W*H exceeds 2^31-1");
@@ -1138,7 +1196,7 @@ kns_status kns_render_views(kns_ctx *ctx, const kns_grid *grid, const kns_view *
     if (max_steps < 1) return set_err(ctx, KNS_ERR_INVALID_ARG, "max_steps=%d < 1", max_steps);
     if (!(eps > 0.f) || !std::isfinite(eps)) return set_err(ctx, KNS_ERR_INVALID_ARG, "eps must be > 0 and finite");
     RenderCfg cfg;
-    kns_status st = resolve_opts(ctx, opts, eps, cfg);
+    kns_status st = resolve_opts(ctx, opts, eps, cfg, grid->desc.sdf_width);
     if (st != KNS_OK) return st;
     std::vector<kns::ViewDev> dv;
     int64_t rays = 0;
@@ -1176,7 +1234,7 @@ kns_status kns_trace_rays(kns_ctx *ctx, const kns_grid *grid, const float *origi
     if (max_steps < 1) return set_err(ctx, KNS_ERR_INVALID_ARG, "max_steps=%d < 1", max_steps);
     if (!(eps > 0.f) || !std::isfinite(eps)) return set_err(ctx, KNS_ERR_INVALID_ARG, "eps must be > 0 and finite");
     RenderCfg cfg;
-    kns_status st = resolve_opts(ctx, opts, eps, cfg);
+    kns_status st = resolve_opts(ctx, opts, eps, cfg, grid->desc.sdf_width);
     if (st != KNS_OK) return st;
     DeviceScope ds(ctx->device);
     // one view of rows of 4096 rays; rays past n in the last row are skipped
@@ -1209,7 +1267,7 @@ kns_status kns_path_trace(kns_ctx *ctx, const kns_grid *grid, const kns_camera *
     if (max_steps < 1) return set_err(ctx, KNS_ERR_INVALID_ARG, "max_steps=%d < 1", max_steps);
     if (!(eps > 0.f) || !std::isfinite(eps)) return set_err(ctx, KNS_ERR_INVALID_ARG, "eps must be > 0 and finite");
     RenderCfg cfg;
-    kns_status st = resolve_opts(ctx, opts, eps, cfg);
+    kns_status st = resolve_opts(ctx, opts, eps, cfg, grid->desc.sdf_width);
     if (st != KNS_OK) return st;
     DeviceScope ds(ctx->device);
     if ((st = ensure_pt_scratch(ctx, n, n_cams)) != KNS_OK) return st;
@@ -1364,51 +1422,6 @@ kns_status kns_sdf(kns_ctx *ctx, const kns_grid *grid, const float *pts, int64_t
 
 }  // extern "C"
 
-// ------------------------------------------------------------------ allocation-free render
-//
-// kns_render_noalloc serves callers that must not allocate device memory once they are running:
-// an engine that hands all device memory to its own pool allocator up front, or a latency-bound
-// loop that cannot afford cudaMalloc's implicit device synchronisation.  Its scratch is one
-// file-scope device array sized for KNS_NOALLOC_MAX_RAYS rays, KNS_NOALLOC_MAX_CELLS cells and
-// KNS_NOALLOC_MAX_CAMS cameras (about 10 MB, held by every GPU that loads the library until the
-// process exits).  Every call shares the array, so calls that overlap on the GPU race; the
-// counters that must start at zero are cleared by each call.
-namespace {
-
-constexpr size_t kNoAllocAlign = 256;
-constexpr size_t align_up(size_t v) { return (v + kNoAllocAlign - 1) / kNoAllocAlign * kNoAllocAlign; }
-constexpr size_t kNoAllocRayBuf = align_up(sizeof(int) * (size_t)KNS_NOALLOC_MAX_RAYS);
-constexpr size_t kNoAllocCellBuf = align_up(sizeof(int) * 6 * (size_t)(KNS_NOALLOC_MAX_CELLS + 1));
-constexpr size_t kNoAllocViewBuf = align_up(sizeof(kns::ViewDev) * (size_t)KNS_NOALLOC_MAX_CAMS);
-constexpr size_t kNoAllocCtrlBuf = align_up(sizeof(kns::WaveCtrl));
-constexpr size_t kNoAllocTileBuf =
-    align_up(sizeof(int4) * (size_t)(KNS_NOALLOC_MAX_RAYS / 16 + KNS_NOALLOC_MAX_CELLS + 1));
-// t_ray, steps_ray, cell_ray, q[2], qcell[2], sorted, hits, ray_view, pend_r, pend_t: twelve per-ray
-// int/float buffers
-constexpr size_t kNoAllocBytes =
-    12 * kNoAllocRayBuf + kNoAllocCellBuf + kNoAllocViewBuf + kNoAllocCtrlBuf + kNoAllocTileBuf;
-
-__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
-
-std::mutex g_noalloc_mu;
-void *g_noalloc_dev_ptr[256] = {};  // device address of g_noalloc_scratch, per device ordinal
-
-// The host-side name g_noalloc_scratch is only a stand-in for the device array: its device address
-// is looked up once per device, with that device current.
-kns_status noalloc_scratch(kns_ctx *ctx, unsigned char **out) {
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (ctx->device < 0 || ctx->device >= 256) return set_err(ctx, KNS_ERR_INVALID_ARG, "device ordinal too large");
-    if (!g_noalloc_dev_ptr[ctx->device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return cuda_err(ctx, e, "cudaGetSymbolAddress(no-alloc scratch)");
-        g_noalloc_dev_ptr[ctx->device] = p;
-    }
-    *out = (unsigned char *)g_noalloc_dev_ptr[ctx->device];
-    return KNS_OK;
-}
-
-}  // namespace
 
 extern "C" kns_status kns_render_noalloc(kns_ctx *ctx, const kns_grid *grid, const kns_camera *cams, int n_cams,
                                          int W, int H, int max_steps, float eps, const kns_frame *out,

@@ -19,6 +19,11 @@ DELTA_X = 1e-5
 TOL_DEPTH = 1e-4
 TOL_RGB = 1e-5
 TOL_NORMAL = 1e-4
+# hits outside the robust set on which both sides took the same decisions: their trajectories agree up
+# to the conditioning-amplified FP32 deviation, so depth, RGB and normal are held to looser bounds
+LOOSE_DEPTH = 1e-3
+LOOSE_RGB = 1e-3
+LOOSE_NORMAL = 1e-3
 
 
 def to_np(t):
@@ -26,8 +31,15 @@ def to_np(t):
 
 
 def compare_render(gpu: dict, ora: dict, min_agree: float = 0.999, tol_depth=TOL_DEPTH, tol_rgb=TOL_RGB,
-                   tol_normal=TOL_NORMAL, delta_d=DELTA_D, delta_x=DELTA_X, label=""):
-    """gpu: per-ray numpy arrays (same rays as ora).  Returns a summary dict; asserts the gates."""
+                   tol_normal=TOL_NORMAL, delta_d=DELTA_D, delta_x=DELTA_X, label="", min_robust: float = None,
+                   report: list = None):
+    """gpu: per-ray numpy arrays (same rays as ora).  Returns a summary dict; asserts the gates.
+
+    Gates: (1) identical hit, cell and step count on every decision-robust ray, and on >= min_agree of
+    all rays; (2) on robust hits, depth / RGB / normal within TOL_*; (3) the robust fraction is reported
+    and, given min_robust, held to it; (4) on every other hit where both sides took the same decisions
+    (same hit, cell and steps -- the near-threshold rays the robust set leaves out), depth, RGB and normal
+    within LOOSE_* on >= 99.9 % of them, so no part of the image goes unchecked."""
     n = ora["hit"].shape[0]
     g_hit = gpu["hit"].astype(bool)
     o_hit = ora["hit"].astype(bool)
@@ -42,14 +54,33 @@ def compare_render(gpu: dict, ora: dict, min_agree: float = 0.999, tol_depth=TOL
     dd = np.abs(gpu["depth"][both].astype(np.float64) - ora["depth"][both])
     dr = np.abs(gpu["rgb"][both].astype(np.float64) - ora["rgb"][both])
     dn = np.abs(gpu["normal"][both].astype(np.float64) - ora["normal"][both])
-    summary = dict(n=n, hits=int(o_hit.sum()), robust=float(robust.mean()), agree=agree,
+    # hits the robust set leaves out, where both sides still took the same decisions
+    rest = g_hit & o_hit & same_dec & ~robust
+    rd = np.abs(gpu["depth"][rest].astype(np.float64) - ora["depth"][rest])
+    rr = np.abs(gpu["rgb"][rest].astype(np.float64) - ora["rgb"][rest]).max(axis=1) if rest.any() else np.zeros(0)
+    rn = np.abs(gpu["normal"][rest].astype(np.float64) - ora["normal"][rest]).max(axis=1) if rest.any() else np.zeros(0)
+    rest_ok = (rd <= LOOSE_DEPTH) & (rr <= LOOSE_RGB) & (rn <= LOOSE_NORMAL)
+    summary = dict(n=n, hits=int(o_hit.sum()), robust=float(robust.mean()), robust_rays=int(robust.sum()),
+                   robust_hits=int(both.sum()), agree=agree,
                    max_depth_err=float(dd.max()) if dd.size else 0.0,
                    max_rgb_err=float(dr.max()) if dr.size else 0.0,
-                   max_normal_err=float(dn.max()) if dn.size else 0.0)
+                   max_normal_err=float(dn.max()) if dn.size else 0.0,
+                   other_same_decision_hits=int(rest.sum()),
+                   other_within_loose=float(rest_ok.mean()) if rest.any() else 1.0,
+                   other_max_depth_err=float(rd.max()) if rd.size else 0.0,
+                   other_max_rgb_err=float(rr.max()) if rr.size else 0.0,
+                   other_max_normal_err=float(rn.max()) if rn.size else 0.0)
+    print("parity", label, summary)
+    if report is not None:
+        report.append(dict(summary, label=label))
     if dd.size:
         assert dd.max() <= tol_depth, (label, summary)
         assert dr.max() <= tol_rgb, (label, summary)
         assert dn.max() <= tol_normal, (label, summary)
+    if rest.any():
+        assert rest_ok.mean() >= 0.999 or rest_ok.size - rest_ok.sum() <= 1, (label, "same-decision hits", summary)
+    if min_robust is not None:
+        assert summary["robust"] >= min_robust, (label, "robust fraction", summary)
     misses = ~g_hit
     assert np.all(np.isinf(gpu["depth"][misses])) and np.all(gpu["rgb"][misses] == 0)
     assert np.all(gpu["cell"][misses] == -1)

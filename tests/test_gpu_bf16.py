@@ -85,11 +85,10 @@ def test_bf16_accuracy_small(kns, ctx, gname, W, H):
 
 @pytest.mark.parametrize("gname", ["c3s", "c3l"])
 def test_bf16_accuracy_1080p_sampled(kns, ctx, gname):
-    """The 1080p launch (2 cameras, 16^3 width 32 and 32^3 width 64 grids) on sampled pixels."""
-    desc = S.config_desc(gname)
-    w = S.sal_sphere_grid(desc)
+    """The benchmark's 1080p launch (the workload's 8 cameras, 16^3 width 32 and 32^3 width 64 grids) on
+    sampled pixels."""
+    desc, w, cams, W_, H_, ms_, eps_ = S.workload(gname)
     occ = O.occupancy(desc, w)
-    cams = S.orbit_cameras(2, 1920, 1080, seed=1)
     grid = kns.Grid.load(ctx, desc, w, occ)
     try:
         g = render_np(kns, ctx, grid, cams, 1920, 1080, 128, 1e-4, precision=kns.KNS_BF16)
@@ -97,7 +96,7 @@ def test_bf16_accuracy_1080p_sampled(kns, ctx, gname):
     finally:
         grid.free()
     rng = np.random.default_rng(4)
-    n_pix = 2 * 1920 * 1080
+    n_pix = cams.shape[0] * 1920 * 1080
     hits = np.where(g["hit"] == 1)[0]
     sel = np.unique(np.concatenate([rng.integers(0, n_pix, 4000), hits[rng.integers(0, hits.size, 4000)]]))
     o = O.render(desc, w, occ, cams, 1920, 1080, 128, 1e-4, sel=sel)

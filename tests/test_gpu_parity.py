@@ -132,7 +132,7 @@ def test_render_c1_full(kns, ctx):
     finally:
         grid.free()
     o = O.render(desc, w, None, cams, W, H, ms, eps, delta_step=P.DELTA_STEP)
-    s = P.compare_render(g, o, label="c1")
+    s = P.compare_render(g, o, label="c1", min_robust=0.94)
     assert s["hits"] > 2000
 
 
@@ -148,8 +148,27 @@ def test_render_occupancy_ragged(kns, ctx):
     finally:
         grid.free()
     o = O.render(desc, w, occ, cams, 120, 100, 128, 1e-4, delta_step=P.DELTA_STEP)
-    s = P.compare_render(g, o, label="occ")
+    s = P.compare_render(g, o, label="occ", min_robust=0.85)
     assert s["hits"] > 2000
+
+
+def test_render_c3l_launch_sampled(kns, ctx):
+    """The 1080p launch the benchmark times (8 cameras x 1920x1080, 32^3 grid of width 64, mask, 128 steps)
+    in FP32, on sampled rays: the FP32 gates."""
+    desc, w, cams, W, H, ms, eps = S.workload("c3l")
+    occ = O.occupancy(desc, w)
+    grid = kns.Grid.load(ctx, desc, w, occ)
+    try:
+        g = gpu_render(kns, ctx, grid, cams, W, H, ms, eps)
+    finally:
+        grid.free()
+    rng = np.random.default_rng(1)
+    n_pix = cams.shape[0] * W * H
+    sel = np.unique(np.concatenate([rng.integers(0, n_pix, 2000),
+                                    np.where(g["hit"] == 1)[0][rng.integers(0, int(g["hit"].sum()), 2000)]]))
+    o = O.render(desc, w, occ, cams, W, H, ms, eps, sel=sel, delta_step=P.DELTA_STEP)
+    s = P.compare_render(sel_rows(g, sel), o, label="c3l-sampled", min_robust=0.8)
+    assert s["hits"] > 1500
 
 
 def test_render_full_size_sampled(kns, ctx):
@@ -166,7 +185,7 @@ def test_render_full_size_sampled(kns, ctx):
     sel = np.unique(np.concatenate([rng.integers(0, n_pix, 3000),
                                     np.where(g["hit"] == 1)[0][rng.integers(0, int(g["hit"].sum()), 3000)]]))
     o = O.render(desc, w, occ, cams, W, H, ms, eps, sel=sel, delta_step=P.DELTA_STEP)
-    s = P.compare_render(sel_rows(g, sel), o, label="c2-sampled")
+    s = P.compare_render(sel_rows(g, sel), o, label="c2-sampled", min_robust=0.84)
     assert s["hits"] > 2500
     # whole-image invariants: every hit has a unit normal and depth inside the box interval
     h = g["hit"] == 1
@@ -191,7 +210,7 @@ def test_render_plane_cell_colours(kns, ctx):
     o = O.render(desc, w, None, cams, 64, 48, 64, 1e-4, delta_step=P.DELTA_STEP)
     # an exact plane converges geometrically, so many steps land close to |d| = eps: every robust
     # ray must agree exactly; the non-robust remainder may flip
-    s = P.compare_render(g, o, min_agree=0.995, label="plane")
+    s = P.compare_render(g, o, min_agree=0.995, label="plane", min_robust=0.94)
     assert s["hits"] > 1000
 
 
@@ -210,7 +229,7 @@ def test_render_linear_colour_routes_normal_and_view(kns, ctx):
     finally:
         grid.free()
     o = O.render(desc, w, None, cams, 40, 40, 64, 1e-5, delta_step=P.DELTA_STEP)
-    s = P.compare_render(g, o, label="linear-colour")
+    s = P.compare_render(g, o, label="linear-colour", min_robust=0.6)
     assert s["hits"] > 1000
 
 
@@ -227,7 +246,7 @@ def test_render_other_configs(kns, ctx, width, hidden, L, LD):
     finally:
         grid.free()
     o = O.render(desc, w, occ, cams, 48, 40, 96, 1e-4, delta_step=P.DELTA_STEP)
-    P.compare_render(g, o, min_agree=0.995, label=str((width, hidden, L, LD)))
+    P.compare_render(g, o, min_agree=0.995, label=str((width, hidden, L, LD)), min_robust=0.83)
 
 
 def test_render_edge_cases(kns, ctx):
