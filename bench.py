@@ -153,9 +153,18 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
+# the sources each profiled kernel is compiled from: a committed capture counts only while they are unchanged
+KERNEL_SOURCES = {
+    "trace_tc_kernel": ["kns_tc.cu", "kns_tc.cuh", "kns_wave.cuh", "kns_device.cuh", "kns_kernels.h"],
+    "wave_eval_block_kernel": ["kns_wave.cu", "kns_wave.cuh", "kns_device.cuh", "kns_kernels.h"],
+    "k_tile_backward": ["kns_train_tile.cu", "kns_train.cuh", "kns_device.cuh", "kns_kernels.h"],
+}
+
+
 def profile_traffic(kernel_tag: str):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel sources still match."""
-    src_hash = kernel_source_hash()
+    """DRAM bytes per full launch from the committed ncu summary tagged kernel_tag, if the sources of
+    its kernel still hash to the summary's kernel_source_sha1 (else None: the counters are stale)."""
+    src_hash = kernel_source_hash(kernel_tag)
     pdir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(pdir):
         return None
@@ -171,12 +180,15 @@ def profile_traffic(kernel_tag: str):
     return None
 
 
-def kernel_source_hash() -> str:
-    h = hashlib.sha1()
+def kernel_source_hash(kernel_tag: str) -> str:
+    """sha1 over the kernel's source files (KERNEL_SOURCES, in that order), or over every csrc file."""
     cdir = os.path.join(ROOT, "paper_2206_10885_gb300", "csrc")
-    for fn in sorted(os.listdir(cdir)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(cdir, fn), "rb").read())
+    files = next((v for k, v in KERNEL_SOURCES.items() if kernel_tag.startswith(k)), None)
+    if files is None:
+        files = sorted(fn for fn in os.listdir(cdir) if fn.endswith((".cu", ".cuh", ".h")))
+    h = hashlib.sha1()
+    for fn in files:
+        h.update(open(os.path.join(cdir, fn), "rb").read())
     return h.hexdigest()
 
 

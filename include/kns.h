@@ -228,6 +228,7 @@ typedef struct kns_round_info {
     float ms_eval_fp32;  /* in a persistent BF16 trace, its empty-space walk: per-class CUDA events under     */
     float ms_eval_bf16;  /* opts->timing for host-driven rounds, the device timer for the persistent trace    */
     float ms_advance;
+    int32_t tiles;       /* tensor-core tiles of the round (persistent BF16 trace; 0 otherwise) */
 } kns_round_info;
 
 /* Per-round trace of the last render call on this context: writes min(*n_rounds, max_rounds) entries

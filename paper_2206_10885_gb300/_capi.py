@@ -97,7 +97,7 @@ class kns_peaks(C.Structure):
 
 class kns_round_info(C.Structure):
     _fields_ = [("live", C.c_int32), ("ms_sort", C.c_float), ("ms_eval_fp32", C.c_float), ("ms_eval_bf16", C.c_float),
-                ("ms_advance", C.c_float)]
+                ("ms_advance", C.c_float), ("tiles", C.c_int32)]
 
 
 _lib = None

@@ -102,9 +102,12 @@ struct kns_grid {
     int wt_stride = 0;
     unsigned char *d_wb = nullptr;  // BF16 hi/lo tensor-core trace layout (kns_tc.cuh)
     int wb_stride = 0;              // bytes per cell
+    float *d_ws = nullptr;          // shading layout (kns_shade.cu)
+    int ws_stride = 0;              // floats per cell
     uint32_t *d_occ = nullptr;
     uint32_t *d_occ_coarse = nullptr;  // 8^3-voxel block mask (res % 8 == 0)
     size_t occ_words64 = 0;
+    int occ_box[6] = {0, 0, 0, -1, -1, -1};  // index box of the occupied voxels (lo xyz, hi xyz)
     kns::GridView view{};
 };
 
@@ -307,6 +310,8 @@ void fill_view(kns_grid *g) {
     const kns_grid_desc &d = g->desc;
     v.w = g->d_w;
     v.cell_stride = kns::cell_floats(g->shape);
+    v.ws = g->d_ws;
+    v.ws_stride = g->ws_stride;
     v.N = d.N;
     for (int a = 0; a < 3; ++a) {
         v.bmin[a] = d.bbox_min[a];
@@ -318,6 +323,10 @@ void fill_view(kns_grid *g) {
     v.occ = g->d_occ;
     v.occ_coarse = g->d_occ_coarse;
     v.cres = d.occ_res / 8;
+    for (int a = 0; a < 3; ++a) {
+        v.olo[a] = g->occ_box[a];
+        v.ohi[a] = g->occ_box[3 + a];
+    }
     v.occ_res = d.occ_res;
     v.occ_per_cell = d.occ_res > 0 ? d.occ_res / d.N : 1;
     v.beta = d.softplus_beta;
@@ -741,10 +750,18 @@ kns_status kns_load_grid(kns_ctx *ctx, const kns_grid_desc *desc, const float *h
         e = cudaMalloc(&g->d_wb, hb.size());
         if (e == cudaSuccess) e = cudaMemcpy(g->d_wb, hb.data(), hb.size(), cudaMemcpyHostToDevice);
     }
+    if (e == cudaSuccess) {  // the shading layout, written on the device from the uploaded weights
+        g->ws_stride = kns::shade_cell_floats(g->shape);
+        e = cudaMalloc(&g->d_ws, (size_t)ncell * g->ws_stride * sizeof(float));
+        if (e == cudaSuccess)
+            e = kns::launch_shade_layout(g->shape, g->d_w, dev_floats, ncell, g->d_ws, g->ws_stride, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
     if (e != cudaSuccess) {
         cudaFree(g->d_w);
         cudaFree(g->d_wt);
         cudaFree(g->d_wb);
+        cudaFree(g->d_ws);
         delete g;
         return cuda_err(ctx, e, "grid upload");
     }
@@ -771,10 +788,21 @@ kns_status kns_load_grid(kns_ctx *ctx, const kns_grid_desc *desc, const float *h
             if (e == cudaSuccess) e = kns::launch_coarse_occupancy(g->d_occ, d.occ_res, g->d_occ_coarse, 0);
             if (e == cudaSuccess) e = cudaDeviceSynchronize();
         }
+        if (e == cudaSuccess) {
+            // the index box of the occupied voxels: the walk leaves (or never enters) it through empty space
+            int *d_box = nullptr;
+            const int init[6] = {d.occ_res, d.occ_res, d.occ_res, -1, -1, -1};
+            e = cudaMalloc(&d_box, sizeof(init));
+            if (e == cudaSuccess) e = cudaMemcpy(d_box, init, sizeof(init), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = kns::launch_occ_bounds(g->d_occ, d.occ_res, d_box, 0);
+            if (e == cudaSuccess) e = cudaMemcpy(g->occ_box, d_box, sizeof(init), cudaMemcpyDeviceToHost);
+            cudaFree(d_box);
+        }
         if (e != cudaSuccess) {
             cudaFree(g->d_w);
             cudaFree(g->d_wt);
             cudaFree(g->d_wb);
+            cudaFree(g->d_ws);
             cudaFree(g->d_occ);
             cudaFree(g->d_occ_coarse);
             delete g;
@@ -852,6 +880,7 @@ void kns_free_grid(kns_grid *g) {
         cudaFree(g->d_w);
         cudaFree(g->d_wt);
         cudaFree(g->d_wb);
+        cudaFree(g->d_ws);
         cudaFree(g->d_occ);
         cudaFree(g->d_occ_coarse);
     }
@@ -1383,7 +1412,8 @@ kns_status kns_get_round_trace(kns_ctx *ctx, kns_round_info *out, int32_t max_ro
         for (int k = 0; k < std::min(n, (int)max_rounds); ++k) {
             const unsigned long long t0 = k == 0 ? hc.start_ns : hc.round_end_ns[k - 1];
             const unsigned long long *ph = hc.round_phase_ns[k];
-            out[k] = kns_round_info{hc.round_live[k], ms(t0, ph[2]), 0.f, ms(ph[2], ph[3]), ms(ph[3], hc.round_end_ns[k])};
+            out[k] = kns_round_info{hc.round_live[k], ms(t0, ph[2]), 0.f, ms(ph[2], ph[3]), ms(ph[3], hc.round_end_ns[k]),
+                                    hc.round_tiles[k]};
         }
         return KNS_OK;
     }
@@ -1392,7 +1422,7 @@ kns_status kns_get_round_trace(kns_ctx *ctx, kns_round_info *out, int32_t max_ro
     for (int k = std::max(0, n - 4); k < n; ++k)
         if (ctx->round_live[k] < 0) ctx->round_live[k] = ctx->h_live[2 * (k & 3)];
     *n_rounds = n;
-    for (int k = 0; k < std::min(n, (int)max_rounds); ++k) out[k] = kns_round_info{ctx->round_live[k], 0.f, 0.f, 0.f, 0.f};
+    for (int k = 0; k < std::min(n, (int)max_rounds); ++k) out[k] = kns_round_info{ctx->round_live[k], 0.f, 0.f, 0.f, 0.f, 0};
     for (const auto &m : ctx->ev_marks) {
         if (m.round < 0 || m.round >= std::min(n, (int)max_rounds)) continue;
         float ms = 0.f;

@@ -72,6 +72,9 @@ struct GridView {
     float beta, inv_beta;
     const uint32_t *occ_coarse;  // bit per block of 8^3 voxels: any voxel occupied (NULL = none)
     int cres;                    // blocks per axis (occ_res / 8)
+    int olo[3], ohi[3];          // index box of the occupied voxels (inclusive; olo > ohi: none occupied)
+    const float *ws;             // shading layout of every cell (kns_shade.cu), one bulk copy per cell
+    int ws_stride;               // floats per cell of it
 };
 
 // ------------------------------------------------------------------ activations
@@ -383,6 +386,60 @@ __device__ __forceinline__ int unambiguous_index(float o, float w, float t, floa
     return (int)fminf(fmaxf(f, 0.f), (float)(res - 1));
 }
 
+// Outside the index box [olo, ohi] of the occupied voxels every voxel is empty, so the walk from a voxel
+// outside it either never finds an occupied voxel -- the ray is outside the box on an axis and moving
+// away from it (or parallel to it), or it leaves one of the box's slabs before it has entered all
+// three -- or crosses empty voxels up to the box's entry face.  Returns 0: the walk ends without an
+// occupied voxel; 1: (vx, vy, vz, T) is the voxel the walk enters the box in and the parameter of that
+// crossing (the entry axis' index is the box's first layer; the other two are taken from the position
+// at T, as for a coarse block's exit); 2: walk on from where the ray is (inside the box, or an entry
+// within 1e-3 voxel of another face, which the voxel walk settles).
+__device__ __forceinline__ int occ_box_entry(const GridView &g, const Ray &r, int &vx, int &vy, int &vz, float ix,
+                                             float iy, float iz, float &T) {
+    const int v[3] = {vx, vy, vz};
+    const float w[3] = {r.wx, r.wy, r.wz}, o[3] = {r.ox, r.oy, r.oz}, inv[3] = {ix, iy, iz};
+    if (v[0] >= g.olo[0] && v[0] <= g.ohi[0] && v[1] >= g.olo[1] && v[1] <= g.ohi[1] && v[2] >= g.olo[2] &&
+        v[2] <= g.ohi[2])
+        return 2;
+    if (g.olo[0] > g.ohi[0]) return 0;  // no voxel is occupied
+    float t_in = -INFINITY, t_out = INFINITY;
+    int ax = -1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const bool up = w[k] > 0.f, still = isinf(inv[k]);
+        if ((v[k] < g.olo[k] && (!up || still)) || (v[k] > g.ohi[k] && (up || still))) return 0;
+        if (still) continue;
+        // the crossing into the box's first layer on this axis (when outside it), and out of its last
+        if (v[k] < g.olo[k] || v[k] > g.ohi[k]) {
+            const float t = up ? dda_face_t(g.bmin[k], g.olo[k] - 1, true, g.ovox[k], o[k], inv[k])
+                               : dda_face_t(g.bmin[k], g.ohi[k] + 1, false, g.ovox[k], o[k], inv[k]);
+            if (t > t_in) {
+                t_in = t;
+                ax = k;
+            }
+        }
+        t_out = fminf(t_out, up ? dda_face_t(g.bmin[k], g.ohi[k], true, g.ovox[k], o[k], inv[k])
+                                : dda_face_t(g.bmin[k], g.olo[k], false, g.ovox[k], o[k], inv[k]));
+    }
+    if (t_in > t_out) return 0;  // it leaves a slab of the box before it has entered the others
+    int n[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (k == ax) {
+            n[k] = w[k] > 0.f ? g.olo[k] : g.ohi[k];
+        } else {
+            const float bm = g.bmin[k], sc = g.oscale[k];
+            n[k] = unambiguous_index(o[k], w[k], t_in, bm, sc, g.occ_res);
+            if (n[k] < g.olo[k] || n[k] > g.ohi[k]) return 2;  // ambiguous (or fuzzy): walk
+        }
+    }
+    vx = n[0];
+    vy = n[1];
+    vz = n[2];
+    T = t_in;
+    return 1;
+}
+
 // Integer 3D-DDA (Amanatides & Woo) from voxel (vx, vy, vz) to the entry of the next occupied voxel.
 // Returns true with te and the voxel updated; false when the ray leaves the grid or passes tf.
 // The crossing parameter of each axis is (face - o) / w (dda_face_t, by the reciprocal of w); after
@@ -390,7 +447,9 @@ __device__ __forceinline__ int unambiguous_index(float o, float w, float t, floa
 // the coarse mask marks empty are crossed in one step: the exit face is found among the block's
 // faces with the same formula and tie rule, and the other two voxel indices at the exit are taken
 // from the position there unless it lies within 1e-3 voxel of a face, in which case the block is
-// walked voxel by voxel.  Either way the voxel and parameter reached are those of the voxel walk.
+// walked voxel by voxel.  Outside the index box of the occupied voxels the walk jumps to the box's
+// entry, or ends when the ray cannot reach the box (occ_box_entry).  Either way the voxel and parameter
+// reached are those of the voxel walk.
 __device__ __forceinline__ bool dda_next(const GridView &g, const Ray &r, int &vx, int &vy, int &vz, float tf,
                                          float &te) {
     const int res = g.occ_res;
@@ -401,6 +460,20 @@ __device__ __forceinline__ bool dda_next(const GridView &g, const Ray &r, int &v
     float tz = dda_face_t(g.bmin[2], vz, uz, g.ovox[2], r.oz, iz);
     // at most 3*res voxel crossings before the ray leaves the grid
     for (int guard = 0; guard < 3 * res + 3; ++guard) {
+        float Tb;
+        const int ob = occ_box_entry(g, r, vx, vy, vz, ix, iy, iz, Tb);
+        if (ob == 0) return false;
+        if (ob == 1) {  // crossed the empty space up to the occupied voxels' box
+            if (Tb > tf) return false;
+            if (occ_test(g.occ, res, vx, vy, vz)) {
+                te = Tb;
+                return true;
+            }
+            tx = dda_face_t(g.bmin[0], vx, ux, g.ovox[0], r.ox, ix);
+            ty = dda_face_t(g.bmin[1], vy, uy, g.ovox[1], r.oy, iy);
+            tz = dda_face_t(g.bmin[2], vz, uz, g.ovox[2], r.oz, iz);
+            continue;
+        }
         if (coarse_empty(g, vx, vy, vz)) {
             // the last voxel of this block along each axis in the direction of travel
             const int bx = ux ? (vx | 7) : (vx & ~7), by = uy ? (vy | 7) : (vy & ~7), bz = uz ? (vz | 7) : (vz & ~7);

@@ -66,6 +66,21 @@ int trace_cell_floats(const Shape &sh) {
     return size;
 }
 
+int shade_cell_floats(const Shape &sh) {
+    int size = 0;
+    dispatch(sh, [&](auto c) {
+        size = shade_cell_floats_cfg<decltype(c)>();
+        return cudaSuccess;
+    });
+    return size;
+}
+cudaError_t launch_shade_layout(const Shape &sh, const float *w, int cell_stride, int64_t ncell, float *ws,
+                                int ws_stride, cudaStream_t s) {
+    return dispatch(sh, [&](auto c) {
+        return launch_shade_layout_cfg<decltype(c)>(w, cell_stride, ncell, ws, ws_stride, s);
+    });
+}
+
 bool shape_supported(const Shape &sh) {
     const bool wl = (sh.W == 32 || sh.W == 64) && (sh.H == 2 || sh.H == 3);
     const bool enc = (sh.L == 4 && sh.LD == 2) || (sh.L == 6 && sh.LD == 4);

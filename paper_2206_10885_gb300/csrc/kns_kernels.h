@@ -34,6 +34,7 @@ struct WaveCtrl {
     int rounds;                       // rounds it ran
     int tail_parity;                  // queue parity of the round it left to the one-warp-per-ray tail
     int round_live[512];              // samples queued for each round
+    int round_tiles[512];             // tiles of each round (persistent BF16 trace)
     unsigned long long round_end_ns[512];  // global timer at the end of each round
     unsigned long long round_phase_ns[512][4];  // ... and at the end of its sort, scatter and tile phases
     unsigned long long start_ns;      // global timer at its start
@@ -111,6 +112,11 @@ cudaError_t launch_wave_tail_cfg(const GridView &g, const WaveArgs &a, int cur, 
 template <class C>
 cudaError_t launch_shade_block_cfg(const GridView &g, const WaveArgs &a, int sm_count, cudaStream_t s);
 template <class C>
+int shade_cell_floats_cfg();
+template <class C>
+cudaError_t launch_shade_layout_cfg(const float *w, int cell_stride, int64_t ncell, float *ws, int ws_stride,
+                                    cudaStream_t s);
+template <class C>
 cudaError_t launch_wave_eval_tc_cfg(const GridView &g, const WaveArgs &a, int cur, int sm_count, cudaStream_t s);
 // Every round of a BF16 render after ray generation, in one cooperative launch (one block per SM);
 // the rounds run in the kernel, separated by grid barriers.
@@ -129,6 +135,9 @@ cudaError_t launch_occ_cfg(const GridView &g, float thresh, uint32_t *words, cud
 bool shape_supported(const Shape &sh);
 int cell_floats(const Shape &sh);
 int trace_cell_floats(const Shape &sh);
+int shade_cell_floats(const Shape &sh);
+cudaError_t launch_shade_layout(const Shape &sh, const float *w, int cell_stride, int64_t ncell, float *ws,
+                                int ws_stride, cudaStream_t s);
 
 
 cudaError_t launch_wave_gen(const Shape &sh, const GridView &g, const WaveArgs &a, cudaStream_t s);
@@ -145,6 +154,7 @@ cudaError_t launch_shade_block(const Shape &sh, const GridView &g, const WaveArg
 cudaError_t launch_refine(const Shape &sh, const GridView &g, const WaveArgs &a, int sm_count, cudaStream_t s);
 inline int shade_hit_tile(int sdf_width) { return 4096 / sdf_width; }  // hits per shading tile
 cudaError_t launch_coarse_occupancy(const uint32_t *occ, int res, uint32_t *coarse, cudaStream_t s);
+cudaError_t launch_occ_bounds(const uint32_t *occ, int res, int *bounds, cudaStream_t s);
 cudaError_t launch_wave_scatter(const WaveArgs &a, int cur, int blocks, cudaStream_t s);
 
 // Measured FP32 FMA (FLOP/s) and ex2 (operations/s) throughput of the device (kns_peak.cu).

@@ -4,7 +4,8 @@
 //
 // The hits of a render are counting-sorted by cell and cut into tiles of 4096 / W same-cell hits (128
 // for width 32, 64 for width 64).  A block of 256 threads stages the cell's weights in shared memory
-// (forward layers k-major, the layers the gradient runs back through row-major) and evaluates the
+// with one TMA bulk copy of the cell's block of the shading layout, which the grid load writes once
+// (forward layers k-major, the layers the gradient runs back through row-major), and evaluates the
 // tile as block GEMMs on rows of hits (row stride tile + 4 floats): thread (warp w, lane l) owns W/8
 // output units x tile/32 hits.  Forward:
 // A_l = softplus(W_l A_{l-1} + b_l), the 16 outputs [d, z].  Reverse mode in place: A_H becomes
@@ -12,6 +13,8 @@
 // encoding rows become W_0^T D_1; the chain rule through the encoding (d sin(fx) = f cos(fx) dx,
 // d cos(fx) = -f sin(fx) dx) gives grad d, normalised to n.  The colour MLP then runs on
 // u = [z, n, gamma(v), x].
+#include <algorithm>
+
 #include "kns_wave.cuh"
 
 namespace kns {
@@ -171,20 +174,39 @@ __device__ __forceinline__ void get_n(const float *rows, int row0, float (&v)[L:
     for (int i = 0; i < L::OPT; ++i) load_n<L::SPT>(rows + (row0 + o0_of<L>() + i) * L::SRS + s0_of<L>(), v[i]);
 }
 
+// The shading layout of every cell (grid load): slot j of cell c is canonical weight src_of(j), or 0.
+template <class C>
+__global__ void shade_layout_kernel(const float *__restrict__ w, int cell_stride, int64_t ncell, float *ws,
+                                    int ws_stride) {
+    const int64_t n = ncell * ws_stride;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i / ws_stride;
+        const int j = (int)(i - c * ws_stride);
+        const int k = j < SL<C>::END ? src_of<C>(j) : -1;
+        ws[i] = k >= 0 ? w[c * cell_stride + k] : 0.f;
+    }
+}
+
+constexpr uint32_t kShadePolls = 1u << 26;  // bound of the weight copy's wait
+
 template <class C>
 __global__ void __launch_bounds__(STHREADS) shade_block_kernel(GridView g, WaveArgs a) {
     using L = SL<C>;
     constexpr int W = C::W, ST = L::ST, SRS = L::SRS, OPT = L::OPT, SPT = L::SPT;
+    static_assert(L::END % 4 == 0, "the weight copy must be a multiple of 16 bytes");
     extern __shared__ __align__(16) float sdyn[];
     float *sw = sdyn;
     float *rows = sdyn + L::END;
     __shared__ float s_x[3][ST], s_v[3][ST], s_t[ST];
     __shared__ int s_r[ST];
     __shared__ int s_tile[3];
+    __shared__ __align__(8) uint64_t s_bar;
     const int tid = threadIdx.x;
     // padding rows stay zero
     for (int i = tid; i < L::ROWS * SRS; i += STHREADS) rows[i] = 0.f;
+    if (tid == 0) mbar_init(&s_bar, 1);
     __syncthreads();
+    uint32_t phase = 0;
     const int n_tiles = a.ctrl->n_tiles;
     // a contiguous run of tiles per block, so consecutive tiles mostly share the cell's staged
     // weights; thread 0 holds the next tile's descriptor (loaded a tile ahead)
@@ -202,14 +224,11 @@ __global__ void __launch_bounds__(STHREADS) shade_block_kernel(GridView g, WaveA
         }
         __syncthreads();
         const int c = s_tile[0], start = s_tile[1], len = s_tile[2];
-        if (c != cached) {  // stage the cell's weights (the previous tile finished with a barrier)
-            const float *cw = g.w + (int64_t)c * g.cell_stride;
-            for (int j = tid; j < L::END; j += STHREADS) {
-                const int k = src_of<C>(j);
-                sw[j] = k >= 0 ? __ldg(cw + k) : 0.f;
-            }
-            cached = c;
-        }
+        // a new cell: its weights are copied while the tile's rays are read and encoded (the previous
+        // tile finished with a barrier, so nobody reads the old weights any more)
+        const bool fresh = c != cached;
+        if (fresh && tid == 0) bulk_load(sw, g.ws + (int64_t)c * g.ws_stride, L::END * (uint32_t)sizeof(float), &s_bar);
+        cached = c;
         if (tid < ST) {
             float x = 0.f, y = 0.f, z = 0.f, wx = 0.f, wy = 0.f, wz = 1.f, t = 0.f;
             int r = -1;
@@ -251,6 +270,14 @@ __global__ void __launch_bounds__(STHREADS) shade_block_kernel(GridView g, WaveA
                     rows[(L::A0 + 3 + 6 * k + q) * SRS + s] = sn;
                     rows[(L::A0 + 6 + 6 * k + q) * SRS + s] = cs;
                 }
+            }
+        }
+        if (fresh) {
+            const bool ok = mbar_wait(&s_bar, phase, kShadePolls);
+            phase ^= 1u;
+            if (__syncthreads_or(!ok)) {  // the weights never landed: report and leave
+                if (tid == 0) atomicCAS(a.status, 0, (int)6 /* KNS_ERR_TIMEOUT */);
+                return;
             }
         }
         __syncthreads();
@@ -439,9 +466,24 @@ cudaError_t launch_shade_block_cfg(const GridView &g, const WaveArgs &a, int sm_
     return cudaGetLastError();
 }
 
+template <class C>
+int shade_cell_floats_cfg() {
+    return (SL<C>::END + 31) / 32 * 32;
+}
+template <class C>
+cudaError_t launch_shade_layout_cfg(const float *w, int cell_stride, int64_t ncell, float *ws, int ws_stride,
+                                    cudaStream_t s) {
+    const int64_t n = ncell * ws_stride;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 1 << 20);
+    shade_layout_kernel<C><<<(unsigned)blocks, 256, 0, s>>>(w, cell_stride, ncell, ws, ws_stride);
+    return cudaGetLastError();
+}
+
 #ifdef KNS_W
 using InstCfg = Cfg<KNS_W, KNS_H, KNS_L, KNS_LD>;
 template cudaError_t launch_shade_block_cfg<InstCfg>(const GridView &, const WaveArgs &, int, cudaStream_t);
+template int shade_cell_floats_cfg<InstCfg>();
+template cudaError_t launch_shade_layout_cfg<InstCfg>(const float *, int, int64_t, float *, int, cudaStream_t);
 #endif
 
 }  // namespace kns

@@ -199,6 +199,38 @@ __global__ void coarse_occupancy_kernel(const uint32_t *occ, int res, uint32_t *
     if ((threadIdx.x & 31) == 0 && b < nb) coarse[b >> 5] = ball;
 }
 
+// Index box of the occupied voxels: bounds[0..2] = the smallest x, y, z index of a set bit, bounds[3..5]
+// the largest (the caller initialises them to res and -1).  One thread per 32-bit word.
+__global__ void occ_bounds_kernel(const uint32_t *occ, int res, int *bounds) {
+    const int64_t nvox = (int64_t)res * res * res, nw = (nvox + 31) / 32;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nw) return;
+    uint32_t m = occ[i];
+    int lo[3] = {res, res, res}, hi[3] = {-1, -1, -1};
+    while (m) {
+        const int b = __ffs(m) - 1;
+        m &= m - 1;
+        const int64_t v = 32 * i + b;
+        if (v >= nvox) break;
+        const int c[3] = {(int)(v % res), (int)((v / res) % res), (int)(v / ((int64_t)res * res))};
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = min(lo[k], c[k]);
+            hi[k] = max(hi[k], c[k]);
+        }
+    }
+    if (hi[0] >= 0)
+        for (int k = 0; k < 3; ++k) {
+            atomicMin(bounds + k, lo[k]);
+            atomicMax(bounds + 3 + k, hi[k]);
+        }
+}
+
+cudaError_t launch_occ_bounds(const uint32_t *occ, int res, int *bounds, cudaStream_t s) {
+    const int64_t nw = ((int64_t)res * res * res + 31) / 32;
+    occ_bounds_kernel<<<(unsigned)((nw + 127) / 128), 128, 0, s>>>(occ, res, bounds);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_coarse_occupancy(const uint32_t *occ, int res, uint32_t *coarse, cudaStream_t s) {
     const int64_t nb = (int64_t)(res / 8) * (res / 8) * (res / 8);
     coarse_occupancy_kernel<<<(unsigned)((nb + 127) / 128), 128, 0, s>>>(occ, res, coarse);

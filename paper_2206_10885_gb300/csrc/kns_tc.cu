@@ -113,6 +113,16 @@ __device__ __forceinline__ void issue_layer(uint32_t tmem, uint32_t a_hi, uint32
     tc::mma_commit(bar);
 }
 
+// softplus_beta(s) = max(s, 0) + ln(1 + e^(-beta |s|)) / beta with the change of base to 2^x and log2 y
+// on the multi-function unit (PTX ex2.approx / lg2.approx) and the constants folded:
+// k_e = -beta log2(e), k_l = ln(2) / beta.
+__device__ __forceinline__ float softplus_mufu(float s, float k_e, float k_l) {
+    float e, l;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(k_e * fabsf(s)));
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(1.f + e));
+    return fmaf(l, k_l, fmaxf(s, 0.f));
+}
+
 constexpr uint32_t kTcPolls = 1u << 26;    // bound of every mbarrier wait
 constexpr uint32_t kGridPolls = 1u << 22;  // bound of every grid-barrier wait (polls of ~0.1 us)
 
@@ -163,13 +173,30 @@ __device__ bool tc_round(TcWorker &w, const GridView &g, const WaveArgs &a, int 
     int next_static = gi * per;
     const int end_static = min(n_tiles, next_static + per);
     const bool cycles = a.t_hist != nullptr;
+    const float k_e = -g.beta * 1.44269504088896341f, k_l = 0.693147180559945309f * g.inv_beta;
+    // thread 0 runs two tiles ahead: the next tile's descriptor is loaded and the one after it claimed
+    // while this tile is evaluated, so neither the claim nor the descriptor load waits at a tile's start
+    auto claim = [&]() -> int {
+        const int tile = a.static_tiles ? (next_static < end_static ? next_static : n_tiles)
+                                        : atomicAdd(&a.ctrl->next_tile_bf, 1);
+        ++next_static;
+        return tile;
+    };
+    int4 d_next = make_int4(-1, 0, 0, 0);
+    int t_after = n_tiles;
+    if (tid == 0) {
+        const int t0 = claim();
+        if (t0 < n_tiles) d_next = a.tiles[t0];
+        t_after = claim();
+    }
     for (;;) {
         if (tid == 0) {
-            const int tile = a.static_tiles ? (next_static < end_static ? next_static : n_tiles)
-                                            : atomicAdd(&a.ctrl->next_tile_bf, 1);
-            ++next_static;
-            int4 d = make_int4(-1, 0, 0, 0);
-            if (tile < n_tiles) d = a.tiles[tile];
+            const int4 d = d_next;
+            d_next = make_int4(-1, 0, 0, 0);
+            if (d.x >= 0 && t_after < n_tiles) {
+                d_next = a.tiles[t_after];
+                t_after = claim();
+            }
             const bool fresh = d.x >= 0 && d.x != w.cached;
             if (fresh) bulk_load(w.wsm, a.wb + (int64_t)d.x * a.wb_stride, T::SIZE, w.bar_w);
             w.s_tile[0] = d.x;
@@ -238,14 +265,28 @@ __device__ bool tc_round(TcWorker &w, const GridView &g, const WaveArgs &a, int 
                     for (int c0 = 0; c0 < T::W; c0 += 32) {
                         float v[32];
                         tc::tmem_ld32(t_lane + (uint32_t)c0, v);
+                        const float4 *b4 = reinterpret_cast<const float4 *>(bias + l * T::W + c0);
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) v[i] = softplus_f32(v[i] + bias[l * T::W + c0 + i], g.beta, g.inv_beta);
+                        for (int i = 0; i < 32; i += 4) {
+                            const float4 b = b4[i / 4];
+                            v[i] = softplus_mufu(v[i] + b.x, k_e, k_l);
+                            v[i + 1] = softplus_mufu(v[i + 1] + b.y, k_e, k_l);
+                            v[i + 2] = softplus_mufu(v[i + 2] + b.z, k_e, k_l);
+                            v[i + 3] = softplus_mufu(v[i + 3] + b.w, k_e, k_l);
+                        }
                         if (l + 1 < C::H) {
 #pragma unroll
                             for (int j = 0; j < 32; j += 8) put8<T>(A, tid, T::W, c0 + j, v + j);
                         } else {
+                            const float4 *d4 = reinterpret_cast<const float4 *>(drow + c0);
 #pragma unroll
-                            for (int i = 0; i < 32; ++i) dacc = fmaf(drow[c0 + i], v[i], dacc);
+                            for (int i = 0; i < 32; i += 4) {
+                                const float4 dw = d4[i / 4];
+                                dacc = fmaf(dw.x, v[i], dacc);
+                                dacc = fmaf(dw.y, v[i + 1], dacc);
+                                dacc = fmaf(dw.z, v[i + 2], dacc);
+                                dacc = fmaf(dw.w, v[i + 3], dacc);
+                            }
                         }
                     }
                     d = dacc;
@@ -560,6 +601,7 @@ __global__ void __launch_bounds__(NW * 128, 1) trace_tc_kernel(GridView g, WaveA
             if (blockIdx.x == gridDim.x - 1 && tid == blockDim.x - 1) {
                 a.off[NK] = s_base[0] + is;
                 ctrl->n_tiles = s_base[1] + it;
+                ctrl->round_tiles[round] = s_base[1] + it;
             }
         }
         if (!(ok = grid_sync(ctrl, gen, &s_flag))) break;

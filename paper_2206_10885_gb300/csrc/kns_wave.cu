@@ -485,28 +485,66 @@ __device__ __forceinline__ float encoding_entry(int k, float px, float py, float
 template <class C>
 constexpr int tail_smem_floats() { return C::TSIZE + C::INP + 2 * C::W; }
 
-// one layer of the warp product: out[o] = softplus(b[o] + sum_k Wt[k][o] in[k]), k ascending
+// vector of NPL consecutive floats (NPL = 1, 2 or 4): one shared-memory access per lane
+template <int NPL>
+struct VecF;
+template <>
+struct VecF<1> {
+    static __device__ __forceinline__ void load(const float *p, float *v) { v[0] = *p; }
+    static __device__ __forceinline__ void store(float *p, const float *v) { *p = v[0]; }
+};
+template <>
+struct VecF<2> {
+    static __device__ __forceinline__ void load(const float *p, float *v) {
+        const float2 x = *reinterpret_cast<const float2 *>(p);
+        v[0] = x.x;
+        v[1] = x.y;
+    }
+    static __device__ __forceinline__ void store(float *p, const float *v) {
+        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    }
+};
+template <>
+struct VecF<4> {
+    static __device__ __forceinline__ void load(const float *p, float *v) {
+        const float4 x = *reinterpret_cast<const float4 *>(p);
+        v[0] = x.x;
+        v[1] = x.y;
+        v[2] = x.z;
+        v[3] = x.w;
+    }
+    static __device__ __forceinline__ void store(float *p, const float *v) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+
+// One layer of the warp product, lane l owning the NPL = W/32 consecutive outputs NPL*l ...: one
+// vector load of their k-major weights feeds NPL FMAs.  out[o] = softplus(b[o] + sum_k Wt[k][o] in[k]),
+// one chain per output, k ascending -- the summation order of every FP32 evaluator, so d is
+// bit-identical to the tiles' (and to the shading's re-evaluation of a BF16 render's tail hits).
 template <int K, int W>
 __device__ __forceinline__ void warp_layer(const float *__restrict__ Wt, const float *__restrict__ b,
                                            const float *in, float *out, int lane, float beta, float inv_beta) {
     constexpr int NPL = W / 32;
-    float acc[NPL];
-#pragma unroll
-    for (int u = 0; u < NPL; ++u) acc[u] = b[lane + 32 * u];
+    static_assert(NPL == 1 || NPL == 2 || NPL == 4, "width must be 32, 64 or 128");
+    static_assert(K % 4 == 0, "layer input must be padded to 4");
+    const int o0 = NPL * lane;
+    float acc[NPL], w[NPL];
+    VecF<NPL>::load(b + o0, acc);
 #pragma unroll 4
     for (int k = 0; k < K; k += 4) {
         const float4 x = *reinterpret_cast<const float4 *>(in + k);
+        const float xs[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
-        for (int u = 0; u < NPL; ++u) {
-            const float *w = Wt + k * W + lane + 32 * u;
-            acc[u] = fmaf(w[0], x.x, acc[u]);
-            acc[u] = fmaf(w[W], x.y, acc[u]);
-            acc[u] = fmaf(w[2 * W], x.z, acc[u]);
-            acc[u] = fmaf(w[3 * W], x.w, acc[u]);
+        for (int c = 0; c < 4; ++c) {
+            VecF<NPL>::load(Wt + (k + c) * W + o0, w);
+#pragma unroll
+            for (int u = 0; u < NPL; ++u) acc[u] = fmaf(w[u], xs[c], acc[u]);
         }
     }
 #pragma unroll
-    for (int u = 0; u < NPL; ++u) out[lane + 32 * u] = softplus_f32(acc[u], beta, inv_beta);
+    for (int u = 0; u < NPL; ++u) acc[u] = softplus_f32(acc[u], beta, inv_beta);
+    VecF<NPL>::store(out + o0, acc);
     __syncwarp();
 }
 

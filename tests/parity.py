@@ -7,7 +7,12 @@ Tolerances (FP32 path):
     within DELTA_D of |d| = eps and none within DELTA_X of a cell or voxel face, of the box
     interval's ends, or of a DDA axis tie;
   - on robust rays both sides hit: depth within 1e-4 scene units, RGB within 1e-5 per channel,
-    normal within 1e-4 per component.
+    normal within 1e-4 per component;
+  - the robust fraction is reported, and held to a per-case floor where the test gives one (on the
+    SAL grids, whose SDF is not 1-Lipschitz, 65-97 % of rays are robust);
+  - on every other hit where both sides took the same decisions (same hit, cell and step count), the
+    same depth, RGB and normal bounds: the only rays left unchecked are those whose decisions differ,
+    at most 1 - min_agree of them.
 """
 import numpy as np
 
@@ -19,11 +24,6 @@ DELTA_X = 1e-5
 TOL_DEPTH = 1e-4
 TOL_RGB = 1e-5
 TOL_NORMAL = 1e-4
-# hits outside the robust set on which both sides took the same decisions: their trajectories agree up
-# to the conditioning-amplified FP32 deviation, so depth, RGB and normal are held to looser bounds
-LOOSE_DEPTH = 1e-3
-LOOSE_RGB = 1e-3
-LOOSE_NORMAL = 1e-3
 
 
 def to_np(t):
@@ -39,7 +39,7 @@ def compare_render(gpu: dict, ora: dict, min_agree: float = 0.999, tol_depth=TOL
     all rays; (2) on robust hits, depth / RGB / normal within TOL_*; (3) the robust fraction is reported
     and, given min_robust, held to it; (4) on every other hit where both sides took the same decisions
     (same hit, cell and steps -- the near-threshold rays the robust set leaves out), depth, RGB and normal
-    within LOOSE_* on >= 99.9 % of them, so no part of the image goes unchecked."""
+    within the same tol_*, so the only rays left unchecked are those whose decisions differ."""
     n = ora["hit"].shape[0]
     g_hit = gpu["hit"].astype(bool)
     o_hit = ora["hit"].astype(bool)
@@ -59,14 +59,14 @@ def compare_render(gpu: dict, ora: dict, min_agree: float = 0.999, tol_depth=TOL
     rd = np.abs(gpu["depth"][rest].astype(np.float64) - ora["depth"][rest])
     rr = np.abs(gpu["rgb"][rest].astype(np.float64) - ora["rgb"][rest]).max(axis=1) if rest.any() else np.zeros(0)
     rn = np.abs(gpu["normal"][rest].astype(np.float64) - ora["normal"][rest]).max(axis=1) if rest.any() else np.zeros(0)
-    rest_ok = (rd <= LOOSE_DEPTH) & (rr <= LOOSE_RGB) & (rn <= LOOSE_NORMAL)
+    rest_ok = (rd <= tol_depth) & (rr <= tol_rgb) & (rn <= tol_normal)
     summary = dict(n=n, hits=int(o_hit.sum()), robust=float(robust.mean()), robust_rays=int(robust.sum()),
                    robust_hits=int(both.sum()), agree=agree,
                    max_depth_err=float(dd.max()) if dd.size else 0.0,
                    max_rgb_err=float(dr.max()) if dr.size else 0.0,
                    max_normal_err=float(dn.max()) if dn.size else 0.0,
                    other_same_decision_hits=int(rest.sum()),
-                   other_within_loose=float(rest_ok.mean()) if rest.any() else 1.0,
+                   other_within_tol=float(rest_ok.mean()) if rest.any() else 1.0,
                    other_max_depth_err=float(rd.max()) if rd.size else 0.0,
                    other_max_rgb_err=float(rr.max()) if rr.size else 0.0,
                    other_max_normal_err=float(rn.max()) if rn.size else 0.0)
@@ -78,7 +78,7 @@ def compare_render(gpu: dict, ora: dict, min_agree: float = 0.999, tol_depth=TOL
         assert dr.max() <= tol_rgb, (label, summary)
         assert dn.max() <= tol_normal, (label, summary)
     if rest.any():
-        assert rest_ok.mean() >= 0.999 or rest_ok.size - rest_ok.sum() <= 1, (label, "same-decision hits", summary)
+        assert rest_ok.all(), (label, "same-decision hits outside the robust set", summary)
     if min_robust is not None:
         assert summary["robust"] >= min_robust, (label, "robust fraction", summary)
     misses = ~g_hit

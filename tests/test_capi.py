@@ -60,7 +60,7 @@ int main(void) {
   printf("%zu %zu %zu\\n", sizeof(kns_pt_opts), offsetof(kns_pt_opts, seed), offsetof(kns_pt_opts, zenith));
   printf("%zu %zu %zu\\n", sizeof(kns_render_stats), offsetof(kns_render_stats, ms_eval_fp32),
          offsetof(kns_render_stats, refined));
-  printf("%zu %zu\\n", sizeof(kns_round_info), offsetof(kns_round_info, ms_advance));
+  printf("%zu %zu\\n", sizeof(kns_round_info), offsetof(kns_round_info, tiles));
   printf("%zu %zu\\n", sizeof(kns_peaks), offsetof(kns_peaks, sm_clock_khz));
   return 0;
 }''')
@@ -77,7 +77,7 @@ int main(void) {
             C.sizeof(capi.kns_pt_opts), capi.kns_pt_opts.seed.offset, capi.kns_pt_opts.zenith.offset,
             C.sizeof(capi.kns_render_stats), capi.kns_render_stats.ms_eval_fp32.offset,
             capi.kns_render_stats.refined.offset,
-            C.sizeof(capi.kns_round_info), capi.kns_round_info.ms_advance.offset,
+            C.sizeof(capi.kns_round_info), capi.kns_round_info.tiles.offset,
             C.sizeof(capi.kns_peaks), capi.kns_peaks.sm_clock_khz.offset]
     assert vals == want
 
