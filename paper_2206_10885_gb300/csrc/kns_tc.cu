@@ -13,9 +13,12 @@
 //     A_hi W_hi + A_lo W_hi + A_hi W_lo accumulated in FP32 in tensor memory (the lo x lo term is
 //     below the FP32 accumulation error of the others), so d carries ~1e-5 relative error instead of
 //     plain BF16's ~4e-3 -- enough for the BF16 phase to take the trace to the surface itself;
+//   - the activation matrices A_hi, A_lo live in tensor memory beside the accumulator (thread s
+//     writes row s with tcgen05.st), so the MMA takes A from tensor memory and B from shared memory,
+//     and a worker's shared memory holds only the cell's weights;
 //   - one thread issues the layer's tcgen05.mma chain and commits it to an mbarrier; the block then
 //     reads its accumulator rows with tcgen05.ld, adds the bias and applies the softplus in FP32,
-//     and writes the next layer's A_hi / A_lo rows back to shared memory (or, after the last hidden
+//     and writes the next layer's A_hi / A_lo rows back to tensor memory (or, after the last hidden
 //     layer, forms d with the FP32 d row);
 //   - each sample is then tested and stepped: |d| < eps_coarse ends the BF16 trace -- the ray joins
 //     the hit list at this t, where the shading re-evaluates it in FP32 (and kns_fp32.cu's refinement
@@ -31,8 +34,9 @@
 
 namespace kns {
 
-// The cell layout of kns_tc.cuh for configuration C, and the block's shared memory: the weights,
-// then the activation matrices A_hi, A_lo (128 rows x the widest layer input).
+// The cell layout of kns_tc.cuh for configuration C (a worker's shared memory), and the worker's
+// tensor-memory columns: the FP32 accumulator (W columns), then the activation matrices A_hi and A_lo
+// (128 lanes = rows, the widest layer input along the columns, two BF16 values per column).
 template <class C>
 struct TcLayout {
     static constexpr int W = C::W, H = C::H;
@@ -44,33 +48,34 @@ struct TcLayout {
     static constexpr int BIAS = tc::bias_off(W, H, K0);
     static constexpr int DROW = tc::drow_off(W, H, K0);
     static constexpr int SIZE = tc::cell_bytes(W, H, K0);
-    static constexpr int ABYTES = 128 * KA * 2;
-    static constexpr int SMEM = SIZE + 2 * ABYTES;
+    static constexpr int SMEM = SIZE;
+    static constexpr int ACOLS = KA / 2;            // tensor-memory columns of one activation matrix
+    static constexpr int TCOLS = W + 2 * ACOLS;     // a worker's tensor-memory columns
 };
 
-// Writes values v[0..7] as columns k0..k0+7 of row `row` of the K-column activation matrices
-// (hi at A, lo at A + ABYTES): two 16-byte stores.
+// Writes values v[0..15] as columns k0..k0+15 of this thread's row of the activation matrices in
+// tensor memory (ta: A_hi's first column in this warp's lanes; A_lo follows ACOLS columns later).
+// Every thread of the warp takes part.
 template <class T>
-__device__ __forceinline__ void put8(unsigned char *A, int row, int K, int k0, const float *v) {
-    uint32_t h[4], l[4];
+__device__ __forceinline__ void put16(uint32_t ta, int k0, const float *v) {
+    uint32_t h[8], l[8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 8; ++i) {
         const __nv_bfloat162 hh = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
         const __nv_bfloat162 ll =
             __floats2bfloat162_rn(v[2 * i] - __low2float(hh), v[2 * i + 1] - __high2float(hh));
         h[i] = *reinterpret_cast<const uint32_t *>(&hh);
         l[i] = *reinterpret_cast<const uint32_t *>(&ll);
     }
-    const int o = tc::canon_off(row, k0, K);
-    *reinterpret_cast<uint4 *>(A + o) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4 *>(A + T::ABYTES + o) = make_uint4(l[0], l[1], l[2], l[3]);
+    tc::tmem_st8(ta + (uint32_t)(k0 / 2), h);
+    tc::tmem_st8(ta + (uint32_t)(T::ACOLS + k0 / 2), l);
 }
 
 // Encoding of Eq. 1 for row `row` (K0 columns, zero beyond IN): sin and cos of pi p once, then the
 // double-angle recurrences sin 2a = 2 sin a cos a, cos 2a = (cos a - sin a)(cos a + sin a) for the
 // higher frequencies (error ~1e-6 at the highest, below the hi/lo split's resolution).
 template <class C, class T>
-__device__ __forceinline__ void encode_row(unsigned char *A, int row, float px, float py, float pz) {
+__device__ __forceinline__ void encode_row(uint32_t ta, float px, float py, float pz) {
     float in[T::K0];
     in[0] = px;
     in[1] = py;
@@ -93,22 +98,22 @@ __device__ __forceinline__ void encode_row(unsigned char *A, int row, float px, 
 #pragma unroll
     for (int k = C::IN; k < T::K0; ++k) in[k] = 0.f;
 #pragma unroll
-    for (int k0 = 0; k0 < T::K0; k0 += 8) put8<T>(A, row, T::K0, k0, in + k0);
+    for (int k0 = 0; k0 < T::K0; k0 += 16) put16<T>(ta, k0, in + k0);
 }
 
-// One hidden layer on the tensor cores: D = A_hi W_hi + A_lo W_hi + A_hi W_lo over K = kin(l).
+// One hidden layer on the tensor cores: D = A_hi W_hi + A_lo W_hi + A_hi W_lo over K = kin(l), A in
+// tensor memory (ta: A_hi's first column; one K = 16 slice is 8 columns), W in shared memory.
 template <class T>
-__device__ __forceinline__ void issue_layer(uint32_t tmem, uint32_t a_hi, uint32_t w_base, int l, uint64_t *bar) {
+__device__ __forceinline__ void issue_layer(uint32_t tmem, uint32_t ta, uint32_t w_base, int l, uint64_t *bar) {
     constexpr uint32_t idesc = tc::idesc_bf16_f32(128, T::W);
     const int K = T::kin(l);
-    const uint32_t sbo = 16u * K, a_lo = a_hi + T::ABYTES, w_hi = w_base + T::hi(l), w_lo = w_base + T::lo(l);
+    const uint32_t sbo = 16u * K, w_hi = w_base + T::hi(l), w_lo = w_base + T::lo(l);
     for (int ks = 0; ks < K / 16; ++ks) {
-        const uint32_t o = 256u * ks;
-        const uint64_t ah = tc::smem_desc(a_hi + o, 128, sbo), al = tc::smem_desc(a_lo + o, 128, sbo);
+        const uint32_t o = 256u * ks, ah = ta + 8u * ks, al = ta + (uint32_t)T::ACOLS + 8u * ks;
         const uint64_t bh = tc::smem_desc(w_hi + o, 128, sbo), bl = tc::smem_desc(w_lo + o, 128, sbo);
-        tc::mma_bf16(tmem, ah, bh, idesc, ks > 0 ? 1u : 0u);
-        tc::mma_bf16(tmem, al, bh, idesc, 1u);
-        tc::mma_bf16(tmem, ah, bl, idesc, 1u);
+        tc::mma_bf16_ta(tmem, ah, bh, idesc, ks > 0 ? 1u : 0u);
+        tc::mma_bf16_ta(tmem, al, bh, idesc, 1u);
+        tc::mma_bf16_ta(tmem, ah, bl, idesc, 1u);
     }
     tc::mma_commit(bar);
 }
@@ -129,12 +134,12 @@ constexpr uint32_t kGridPolls = 1u << 22;  // bound of every grid-barrier wait (
 // A warpgroup worker: 128 threads that evaluate tiles on their own weights, activation matrices,
 // tensor-memory columns and mbarriers, synchronised by their own named barrier.
 struct TcWorker {
-    unsigned char *wsm, *A;   // shared: the cell's weights, the activation matrices
+    unsigned char *wsm;       // shared: the cell's weights
     uint64_t *bar_w, *bar_mma;
     int *s_tile;              // 4 ints: key, first sample, samples, fresh
     int *s_red;               // 8 ints: per-warp partial counts, two alternating sets
     int *s_fail;              // set by any thread whose wait ran out; read after the next barrier
-    uint32_t tmem;            // first tensor-memory column of the worker's accumulator
+    uint32_t tmem;            // first tensor-memory column of the worker's accumulator (A_hi, A_lo follow)
     int bar;                  // named barrier id
     int tid, warp;            // thread (0..127) and warp (0..3) within the worker
     int cached;               // cell of the staged weights
@@ -164,11 +169,11 @@ template <class C>
 __device__ bool tc_round(TcWorker &w, const GridView &g, const WaveArgs &a, int cur, int n_tiles, int gi, int nw) {
     using T = TcLayout<C>;
     const int tid = w.tid, nxt = cur ^ 1;
-    const uint32_t w_base = tc::saddr(w.wsm), a_base = tc::saddr(w.A);
-    const uint32_t t_lane = w.tmem + ((uint32_t)(32 * w.warp) << 16);
+    const uint32_t w_base = tc::saddr(w.wsm), ta = w.tmem + (uint32_t)T::W;  // A_hi's first column
+    const uint32_t t_lane = w.tmem + ((uint32_t)(32 * w.warp) << 16);       // this warp's lanes
+    const uint32_t ta_lane = ta + ((uint32_t)(32 * w.warp) << 16);
     const float *bias = reinterpret_cast<const float *>(w.wsm + T::BIAS);
     const float *drow = reinterpret_cast<const float *>(w.wsm + T::DROW);
-    unsigned char *A = w.A;
     const int per = (n_tiles + nw - 1) / nw;
     int next_static = gi * per;
     const int end_static = min(n_tiles, next_static + per);
@@ -227,8 +232,11 @@ __device__ bool tc_round(TcWorker &w, const GridView &g, const WaveArgs &a, int 
         }
         if (fresh) w.w_pending = true;
         for (int it = 0;; ++it) {
-            if (active) encode_row<C, T>(A, tid, fmaf(t, ray.wx, ray.ox), fmaf(t, ray.wy, ray.oy), fmaf(t, ray.wz, ray.oz));
-            tc::fence_async_smem();
+            // (tensor-memory stores are warp-wide: a warp with a live sample encodes every lane's row;
+            // the rows of idle lanes are never read back)
+            if (__any_sync(FULL, active))
+                encode_row<C, T>(ta_lane, fmaf(t, ray.wx, ray.ox), fmaf(t, ray.wy, ray.oy), fmaf(t, ray.wz, ray.oz));
+            tc::tmem_wait_st();
             // a wait that runs out raises the worker's failure flag, read after the next barrier, where the
             // worker leaves; the thread itself ignores its sample from then on (lost)
             bool lost = false;
@@ -248,7 +256,7 @@ __device__ bool tc_round(TcWorker &w, const GridView &g, const WaveArgs &a, int 
                 if (*w.s_fail) return false;
                 if (tid == 0) {
                     tc::fence_after_sync();
-                    issue_layer<T>(w.tmem, a_base, w_base, l, w.bar_mma);
+                    issue_layer<T>(w.tmem, ta, w_base, l, w.bar_mma);
                 }
                 w.mma_pending = true;
                 if (mbar_wait(w.bar_mma, w.ph_mma, kTcPolls)) {
@@ -262,12 +270,12 @@ __device__ bool tc_round(TcWorker &w, const GridView &g, const WaveArgs &a, int 
                 if (__any_sync(FULL, active)) {
                     float dacc = drow[T::W];  // the d row's bias (stored right after the row)
 #pragma unroll
-                    for (int c0 = 0; c0 < T::W; c0 += 32) {
-                        float v[32];
-                        tc::tmem_ld32(t_lane + (uint32_t)c0, v);
+                    for (int c0 = 0; c0 < T::W; c0 += 16) {
+                        float v[16];
+                        tc::tmem_ld16(t_lane + (uint32_t)c0, v);
                         const float4 *b4 = reinterpret_cast<const float4 *>(bias + l * T::W + c0);
 #pragma unroll
-                        for (int i = 0; i < 32; i += 4) {
+                        for (int i = 0; i < 16; i += 4) {
                             const float4 b = b4[i / 4];
                             v[i] = softplus_mufu(v[i] + b.x, k_e, k_l);
                             v[i + 1] = softplus_mufu(v[i + 1] + b.y, k_e, k_l);
@@ -275,12 +283,11 @@ __device__ bool tc_round(TcWorker &w, const GridView &g, const WaveArgs &a, int 
                             v[i + 3] = softplus_mufu(v[i + 3] + b.w, k_e, k_l);
                         }
                         if (l + 1 < C::H) {
-#pragma unroll
-                            for (int j = 0; j < 32; j += 8) put8<T>(A, tid, T::W, c0 + j, v + j);
+                            put16<T>(ta_lane, c0, v);
                         } else {
                             const float4 *d4 = reinterpret_cast<const float4 *>(drow + c0);
 #pragma unroll
-                            for (int i = 0; i < 32; i += 4) {
+                            for (int i = 0; i < 16; i += 4) {
                                 const float4 dw = d4[i / 4];
                                 dacc = fmaf(dw.x, v[i], dacc);
                                 dacc = fmaf(dw.y, v[i + 1], dacc);
@@ -291,7 +298,7 @@ __device__ bool tc_round(TcWorker &w, const GridView &g, const WaveArgs &a, int 
                     }
                     d = dacc;
                 }
-                tc::fence_async_smem();
+                tc::tmem_wait_st();
                 tc::fence_before_sync();
             }
             // outcome: 0 none, 1 converged (hit list), 2 miss (written), 3 pending, 4 emit to ncell
@@ -373,6 +380,11 @@ __device__ __forceinline__ void tc_worker_done(TcWorker &w, const WaveArgs &a, b
     if ((w.tid & 31) == 0 && n) atomicAdd(&a.ctrl->samples_bf16, n);
 }
 
+// Tensor-memory columns allocated for n: the next power of two, at least 32.
+__host__ __device__ constexpr uint32_t pow2_cols(int n) {
+    return n <= 32 ? 32u : n <= 64 ? 64u : n <= 128 ? 128u : n <= 256 ? 256u : 512u;
+}
+
 // ---------------------------------------------------------------- one round per launch
 template <class C>
 __global__ void __launch_bounds__(128) wave_eval_tc_kernel(GridView g, WaveArgs a, int cur) {
@@ -386,7 +398,8 @@ __global__ void __launch_bounds__(128) wave_eval_tc_kernel(GridView g, WaveArgs 
     // is finished one warp per ray by wave_tail_warp_kernel
     if (n_tiles <= 0 || a.ctrl->tail) return;
     const int tid = threadIdx.x;
-    if (tid < 32) tc::tmem_alloc(&s_tmem, (uint32_t)T::W);
+    constexpr uint32_t NCOL = pow2_cols(T::TCOLS);
+    if (tid < 32) tc::tmem_alloc(&s_tmem, NCOL);
     if (tid == 0) {
         mbar_init(&bar_w, 1);
         mbar_init(&bar_mma, 1);
@@ -395,13 +408,13 @@ __global__ void __launch_bounds__(128) wave_eval_tc_kernel(GridView g, WaveArgs 
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    TcWorker w{dyn, dyn + T::SIZE, &bar_w, &bar_mma, s_tile, s_red, &s_fail, s_tmem, 1, tid, tid >> 5, -1, 0u, 0u,
+    TcWorker w{dyn, &bar_w, &bar_mma, s_tile, s_red, &s_fail, s_tmem, 1, tid, tid >> 5, -1, 0u, 0u,
                false, false, 0u, 0};
     const bool ok = tc_round<C>(w, g, a, cur, n_tiles, blockIdx.x, gridDim.x);
     tc_worker_done(w, a, ok);
     tc::fence_before_sync();
     __syncthreads();
-    if (tid < 32) tc::tmem_free(s_tmem, (uint32_t)T::W);
+    if (tid < 32) tc::tmem_free(s_tmem, NCOL);
 }
 
 // ---------------------------------------------------------------- every round in one launch
@@ -475,14 +488,13 @@ __device__ __forceinline__ void block_scan2_any(int &x, int &y, int *wx, int *wy
     __syncthreads();
 }
 
-// Workers per block of the persistent trace: as many as shared memory holds, at most 4.
+// Workers per block of the persistent trace: as many as shared memory and the 512 tensor-memory
+// columns hold, at most 4 (four warpgroups of 128 threads: 128 registers a thread).
 template <class C>
 __host__ __device__ constexpr int tc_workers() {
-    constexpr int per = TcLayout<C>::SMEM, by_smem = (227 * 1024 - 2048) / per;
-    return by_smem < 1 ? 1 : (by_smem > 4 ? 4 : by_smem);
-}
-__host__ __device__ constexpr uint32_t pow2_cols(int n) {
-    return n <= 32 ? 32u : n <= 64 ? 64u : n <= 128 ? 128u : n <= 256 ? 256u : 512u;
+    constexpr int by_smem = (227 * 1024 - 2048) / TcLayout<C>::SMEM, by_tmem = 512 / TcLayout<C>::TCOLS;
+    constexpr int n = by_smem < by_tmem ? by_smem : by_tmem;
+    return n < 1 ? 1 : (n > 4 ? 4 : n);
 }
 
 // The rounds of a BF16 render after ray generation, in one cooperative launch of one block per SM
@@ -505,7 +517,7 @@ __global__ void __launch_bounds__(NW * 128, 1) trace_tc_kernel(GridView g, WaveA
     __shared__ int wx[32], wy[32], s_base[2], s_flag;
     WaveCtrl *ctrl = a.ctrl;
     const int tid = threadIdx.x, wk = tid >> 7;
-    constexpr uint32_t NCOL = pow2_cols(NW * C::W);
+    constexpr uint32_t NCOL = pow2_cols(NW * T::TCOLS);
     if (tid < 32) tc::tmem_alloc(&s_tmem, NCOL);
     if (tid < NW) {
         mbar_init(&bar_w[tid], 1);
@@ -516,8 +528,8 @@ __global__ void __launch_bounds__(NW * 128, 1) trace_tc_kernel(GridView g, WaveA
     __syncthreads();
     tc::fence_after_sync();
     unsigned char *base = dyn + wk * T::SMEM;
-    TcWorker w{base, base + T::SIZE, &bar_w[wk], &bar_mma[wk], s_tile[wk], s_red[wk], &s_fail[wk],
-               s_tmem + (uint32_t)(wk * C::W), 1 + wk, tid & 127, (tid & 127) >> 5, -1, 0u, 0u, false, false, 0u, 0};
+    TcWorker w{base, &bar_w[wk], &bar_mma[wk], s_tile[wk], s_red[wk], &s_fail[wk],
+               s_tmem + (uint32_t)(wk * T::TCOLS), 1 + wk, tid & 127, (tid & 127) >> 5, -1, 0u, 0u, false, false, 0u, 0};
     if (blockIdx.x == 0 && tid == 0) ctrl->start_ns = globaltimer_ns();
     unsigned gen = 0;
     bool ok = true;
@@ -681,7 +693,7 @@ cudaError_t launch_wave_eval_tc_cfg(const GridView &g, const WaveArgs &a, int cu
     using T = TcLayout<C>;
     static_assert(T::SMEM <= 200 * 1024, "tensor-core tile does not fit in shared memory");
     // Resident blocks per SM from the kernel's own resources (registers, shared memory, threads) and the
-    // tensor memory (W of 512 columns per block).  The occupancy query is not used here: it reports one
+    // tensor memory (accumulator and activation columns, of 512 per SM).  The occupancy query is not used here: it reports one
     // block per SM for every kernel that allocates tensor memory.
     static std::atomic<int> per_sm{0};
     int nb = per_sm.load();
@@ -698,7 +710,7 @@ cudaError_t launch_wave_eval_tc_cfg(const GridView &g, const WaveArgs &a, int cu
         const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;  // allocated per warp in units of 256
         const int by_regs = regs_sm / (regs_warp * 4);
         const int by_smem = smem_sm / (T::SMEM + (int)fa.sharedSizeBytes + reserved);
-        nb = std::max(1, std::min(std::min(by_regs, by_smem), std::min(16, 512 / C::W)));
+        nb = std::max(1, std::min(std::min(by_regs, by_smem), std::min(16, 512 / (int)pow2_cols(T::TCOLS))));
         per_sm.store(nb);
     }
     wave_eval_tc_kernel<C><<<sm_count * nb, 128, T::SMEM, s>>>(g, a, cur);
