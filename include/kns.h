@@ -129,7 +129,8 @@ typedef struct kns_render_opts {
     int32_t min_active;    /* a tile continues only while at least this many of its rays stay in its cell
                               (1..256; a warp tile holds 16; default 8 for warp tiles, 16 for block tiles) */
     int32_t tail_rays;     /* a round with at most this many rays is finished one warp per ray, in FP32 (>= 0;
-                              -1: never; default 131072 at SDF width 32, 32768 at width 64 and for KNS_BF16) */
+                              -1: never; default: KNS_FP32 131072 at SDF width 32, 32768 at width 64; KNS_BF16
+                              32768 at width 32, 16384 at width 64) */
     int32_t blocks_per_sm; /* evaluation blocks (one warp each) launched per SM (1..64) */
     int32_t static_tiles;  /* 1: each block takes a contiguous run of tiles; 2: tiles handed out dynamically */
     int32_t timing;        /* 1: time each kernel class with CUDA events for kns_get_render_stats (adds host work) */
@@ -138,12 +139,14 @@ typedef struct kns_render_opts {
                               tiles per 128 threads; 2 = 16-sample tiles per warp (in-tile stepping, min_active);
                               0 = default (4) */
     int32_t bf16_inner_steps; /* KNS_BF16: evaluations a tensor-core tile may make per round while its rays stay in
-                                 its cell (1..1024; default 2) */
+                                 its cell (1..1024; default 4 at SDF width 32, 2 at width 64) */
     int32_t bf16_min_active;  /* KNS_BF16: a tensor-core tile continues while at least this many of its rays stay
                                  (1..128; default 16) */
     int32_t bf16_rounds;      /* KNS_BF16: 1 = every round of the trace in one persistent launch (rounds run on the
                                  device, no host synchronisation); 2 = one launch sequence per round driven by
-                                 the host; 0 = default (1).  Results are identical. */
+                                 the host; 0 = default (1).  Results are identical when no round is handed
+                                 to the tail (tail_rays = -1); with the hand-over they agree within the
+                                 BF16 accuracy gates. */
 } kns_render_opts;
 
 /* Counters of the last kns_render on a context (kns_get_render_stats). */

@@ -367,13 +367,15 @@ constexpr int kRenderBlockInnerSteps = 2;  // block tiles: a second evaluation o
 constexpr int kRenderBlockMinActive = 16;  // ... while at least 16 of its rays stay in its cell
 constexpr int kRenderTailRays = 131072;  // rounds this small finish one warp per ray (width 32)
 // tensor-core tiles (BF16 renders): a second evaluation while at least 16 rays stay in the cell
-constexpr int kRenderBf16InnerSteps = 2;
+constexpr int kRenderBf16InnerSteps = 2;        // width 64
+constexpr int kRenderBf16InnerStepsNarrow = 4;  // width 32
 constexpr int kRenderBf16MinActive = 16;
 // BF16 renders hand rounds of at most this many rays (live + pending) to the one-warp-per-ray FP32
 // tail: the best of 8K..512K on both 1080p workloads (a tensor-core round costs ~50 us however few its rays);
 // FP32 renders of width-64 grids too (their tail warps hold 41 KB of weights each: 5 per SM), the best of
 // 8K..512K on the 32^3 width-64 workload (131072 stays best at width 32)
 constexpr int kRenderBf16TailRays = 32768;
+constexpr int kRenderBf16TailRaysWide = 16384;  // BF16 renders of width-64 grids
 constexpr int kRenderBlocksPerSM = 16;
 constexpr int kRenderStaticTiles = 2;
 
@@ -940,11 +942,16 @@ kns_status resolve_opts(kns_ctx *ctx, const kns_render_opts *opts, float eps, Re
     const int def_min = bt0 == 2 ? kRenderMinActive : kRenderBlockMinActive;
     c.inner_steps = opts ? knob(opts->inner_steps, def_inner) : def_inner;
     c.min_active = opts ? knob(opts->min_active, def_min) : def_min;
-    const int def_tail = (c.bf16 || sdf_width >= 64) ? kRenderBf16TailRays : kRenderTailRays;
+    // the hand-over to the one-warp-per-ray tail and the BF16 tiles' in-tile evaluations, by width (the
+    // best of a sweep over 12,288 .. 131,072 rays and 1 .. 8 evaluations at 8 x 1920x1080): FP32 131,072 at
+    // width 32, 32,768 at 64; BF16 32,768 rays and 4 evaluations at width 32, 16,384 and 2 at width 64
+    const int def_tail = c.bf16 ? (sdf_width >= 64 ? kRenderBf16TailRaysWide : kRenderBf16TailRays)
+                                : (sdf_width >= 64 ? kRenderBf16TailRays : kRenderTailRays);
+    const int def_inner_bf = sdf_width >= 64 ? kRenderBf16InnerSteps : kRenderBf16InnerStepsNarrow;
     c.tail_rays = opts ? knob(opts->tail_rays, def_tail) : def_tail;
     c.blocks_per_sm = opts ? knob(opts->blocks_per_sm, kRenderBlocksPerSM) : kRenderBlocksPerSM;
     c.static_tiles = (opts ? knob(opts->static_tiles, kRenderStaticTiles) : kRenderStaticTiles) == 1;
-    c.inner_steps_bf = opts ? knob(opts->bf16_inner_steps, kRenderBf16InnerSteps) : kRenderBf16InnerSteps;
+    c.inner_steps_bf = opts ? knob(opts->bf16_inner_steps, def_inner_bf) : def_inner_bf;
     c.min_active_bf = opts ? knob(opts->bf16_min_active, kRenderBf16MinActive) : kRenderBf16MinActive;
     if (c.inner_steps_bf < 1 || c.inner_steps_bf > 1024 || c.min_active_bf < 1 || c.min_active_bf > 128)
         return set_err(ctx, KNS_ERR_INVALID_ARG, "bf16 tuning field out of range");
