@@ -67,8 +67,8 @@ def parse():
     ap.add_argument("--train-rays", type=int, default=0,
                     help="train workload: rays per step (eikonal points scale along; small profiling cases)")
     ap.add_argument("--tune", default="off", choices=["cache", "force", "off"],
-                    help="FP32 renders: schedule autotuning before timing (the cached best, tuning once if absent; "
-                         "re-tune; or the library defaults, which the autotuner picked on the 16^3 workload)")
+                    help="schedule autotuning of the timed precision before timing (the cached best, tuning once "
+                         "if absent; re-tune; or the library defaults, picked by sweeps at these workloads)")
     return ap.parse_args()
 
 
@@ -348,7 +348,7 @@ def run_kns(args, rank, world, local_rank):
     props = torch.cuda.get_device_properties(local_rank)
 
     tuning = None
-    if args.tune != "off" and precision == kns.KNS_FP32:
+    if args.tune != "off":
         from paper_2206_10885_gb300 import autotune
         tuning, tuned_ms, tried = autotune.tune(ctx, grid, cams, W, H, ms, eps, precision,
                                                 use_cache=args.tune == "cache")

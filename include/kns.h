@@ -20,8 +20,7 @@
  *    inside the call, so the render is complete, like any other work, when
  *    the caller's stream reaches the point after it.  An FP32 render's loop
  *    reads a small pinned counter on the host between rounds; a BF16 render
- *    runs its rounds on the device in one persistent launch.  Renders are not
- *    designed for capture into a CUDA graph.  Device-side failures (a bounded wait that
+ *    runs its rounds on the device in one persistent launch.  Device-side failures (a bounded wait that
  *    ran out, a bounds check that tripped) are recorded in a per-context
  *    status word and returned by the next kns_sync() on that context.
  *  - Memory: the caller owns every input and output buffer and passes plain
@@ -397,8 +396,7 @@ kns_status kns_train_step(kns_ctx *ctx, const kns_grid_desc *desc, const float *
  * the library (about 14 MB on every GPU that loads it, kept until the process exits); the call
  * allocates nothing and frees nothing.  The context and the grid must already exist: creating them
  * allocates, and kns_create also loads the array on its device and looks up its address (should that
- * fail there, the first kns_render_noalloc on the device does it, and that first call should then come
- * before any stream capture).  All calls
+ * fail there, the first kns_render_noalloc on the device does it).  All calls
  * share the one array and each clears the counters it needs, so calls that overlap on the GPU race:
  * serialise them (one stream, or events).  Arguments, outputs and errors as kns_render, plus
  * INVALID_ARG when n_cams*W*H > KNS_NOALLOC_MAX_RAYS, n_cams > KNS_NOALLOC_MAX_CAMS or

@@ -1,8 +1,9 @@
 """Autotuner of the render schedule (the tuning fields of kns_render_opts).
 
 The knobs change only how work is scheduled on the device (rounds, in-tile steps, tile hand-out,
-launch width, tail), never a result; the tests check that renders are bit-identical
-across settings.  tune() times each candidate with CUDA events around kns_render, flushing L2
+launch width, tail).  FP32 renders are bit-identical across settings (tested); a BF16 render's
+results depend on which rays reach the FP32 tail, within the BF16 accuracy gates (tested at the
+defaults and across the schedule forms).  tune() times each candidate with CUDA events around kns_render, flushing L2
 between repetitions, and returns the fastest setting.  Results are cached per (device, grid shape,
 image shape, precision) in a JSON file next to this module (or the path in KNS_TUNE_CACHE).
 """
@@ -25,6 +26,17 @@ SPACE = {
     "blocks_per_sm": (8, 16, 32),
     "tail_rays": (-1, 131072, 262144, 524288),
 }
+# BF16 renders: the hand-over to the FP32 tail and the tensor-core tiles' in-tile evaluations
+SPACE_BF16 = {
+    "tail_rays": (8192, 16384, 24576, 32768, 65536),
+    "bf16_inner_steps": (1, 2, 4, 8),
+    "bf16_min_active": (4, 16, 32),
+}
+
+
+def space_for(precision: int):
+    """The default search space of a precision (0 = FP32, 1 = BF16)."""
+    return SPACE_BF16 if precision == 1 else SPACE
 
 
 def _key(grid, n_cams, W, H, max_steps, precision, device_name):
@@ -111,7 +123,7 @@ def tune(ctx, grid, cams, W, H, max_steps, eps, precision=0, space=None, use_cac
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda:%d" % ctx.device)
     results = []
     t_start = time.time()
-    for tuning in candidates(space):
+    for tuning in candidates(space or space_for(precision)):
         ms = time_setting(kns, ctx, grid, cams, W, H, max_steps, eps, precision, tuning, out, flush)
         results.append((tuning, ms))
         if verbose:

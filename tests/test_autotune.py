@@ -47,3 +47,15 @@ def test_explicit_space_is_respected():
     want = {tuple(sorted(dict(zip(sorted(space), v), blocks_per_sm=16).items()))
             for v in itertools.product(*(space[k] for k in sorted(space)))}
     assert got == want
+
+
+def test_bf16_space_is_the_bf16_knobs():
+    assert A.space_for(1) is A.SPACE_BF16 and A.space_for(0) is A.SPACE
+    cands = list(A.candidates(A.SPACE_BF16))
+    n = 1
+    for v in A.SPACE_BF16.values():
+        n *= len(v)
+    assert len(cands) == n
+    assert all(set(c) == {"tail_rays", "bf16_inner_steps", "bf16_min_active"} for c in cands)
+    assert all(c["tail_rays"] > 0 and 1 <= c["bf16_inner_steps"] <= 1024 and 1 <= c["bf16_min_active"] <= 128
+               for c in cands)
