@@ -254,6 +254,14 @@ typedef struct kns_peaks {
  * device memory for the duration of the call.  Errors: INVALID_ARG (NULL), CUDA. */
 kns_status kns_measure_peaks(kns_ctx *ctx, void *cuda_stream, kns_peaks *out);
 
+/* Self-test of the failure path of the bounded device waits (not part of the method): runs, on
+ * cuda_stream, a wait that nothing satisfies with a short poll limit -- which = 0: an mbarrier wait of
+ * the kind a tensor-core tile makes for its weights and products; 1: the persistent trace's grid
+ * barrier, with one of two blocks never arriving -- and waits for it.  The waiting threads give up,
+ * record KNS_ERR_TIMEOUT in the context's status word (returned and cleared by the next kns_sync) and
+ * return; the context stays usable.  Errors: INVALID_ARG (which not 0 or 1), CUDA. */
+kns_status kns_selftest_timeout(kns_ctx *ctx, int32_t which, void *cuda_stream);
+
 /* One view of a multi-view render: camera, image size and its own output buffers (device pointers for
  * W*H pixels, layout as kns_frame). */
 typedef struct kns_view {

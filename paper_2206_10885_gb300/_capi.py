@@ -147,6 +147,8 @@ def lib():
             L.kns_get_render_stats.restype = st
             L.kns_measure_peaks.argtypes = [vp, vp, C.POINTER(kns_peaks)]
             L.kns_measure_peaks.restype = st
+            L.kns_selftest_timeout.argtypes = [vp, C.c_int32, vp]
+            L.kns_selftest_timeout.restype = st
             L.kns_get_round_trace.argtypes = [vp, C.POINTER(kns_round_info), C.c_int32, C.POINTER(C.c_int32)]
             L.kns_get_round_trace.restype = st
             L.kns_trace_rays.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_int, C.c_float, C.POINTER(kns_frame),
@@ -273,6 +275,11 @@ def kns_get_round_trace(ctx: int, max_rounds: int = 1024) -> list:
     n = C.c_int32(0)
     _check(lib().kns_get_round_trace(ctx, buf, max_rounds, C.byref(n)), ctx)
     return [{k: getattr(buf[i], k) for k, _ in kns_round_info._fields_} for i in range(min(n.value, max_rounds))]
+
+
+def kns_selftest_timeout(ctx: int, which: int, stream: int = 0) -> None:
+    """Runs a device wait that nothing satisfies (0: mbarrier, 1: grid barrier); the next sync reports it."""
+    _check(lib().kns_selftest_timeout(ctx, which, stream), ctx)
 
 
 def kns_sdf(ctx: int, grid: int, pts_ptr: int, n: int, sdf_ptr: int, feat_ptr: int = None, grad_ptr: int = None,

@@ -1400,6 +1400,23 @@ kns_status kns_measure_peaks(kns_ctx *ctx, void *cuda_stream, kns_peaks *out) {
     return KNS_OK;
 }
 
+kns_status kns_selftest_timeout(kns_ctx *ctx, int32_t which, void *cuda_stream) {
+    if (!ctx) return KNS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (which != 0 && which != 1) return set_err(ctx, KNS_ERR_INVALID_ARG, "which must be 0 or 1");
+    DeviceScope ds(ctx->device);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    kns::WaveCtrl *ctrl = nullptr;  // a fresh control block: its barrier words start at zero
+    cudaError_t e = cudaMalloc(&ctrl, sizeof(kns::WaveCtrl));
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctrl, 0, sizeof(kns::WaveCtrl), s);
+    // ~4 ms of polling for the grid barrier, a few ms for the mbarrier's suspending polls
+    if (e == cudaSuccess) e = kns::launch_selftest_timeout(ctrl, ctx->d_status, which, which == 0 ? 4096u : 65536u, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(ctrl);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "wait self-test");
+    return KNS_OK;
+}
+
 kns_status kns_get_round_trace(kns_ctx *ctx, kns_round_info *out, int32_t max_rounds, int32_t *n_rounds) {
     if (!ctx) return KNS_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(ctx->mu);

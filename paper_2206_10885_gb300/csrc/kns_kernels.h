@@ -155,6 +155,7 @@ cudaError_t launch_refine(const Shape &sh, const GridView &g, const WaveArgs &a,
 inline int shade_hit_tile(int sdf_width) { return 4096 / sdf_width; }  // hits per shading tile
 cudaError_t launch_coarse_occupancy(const uint32_t *occ, int res, uint32_t *coarse, cudaStream_t s);
 cudaError_t launch_occ_bounds(const uint32_t *occ, int res, int *bounds, cudaStream_t s);
+cudaError_t launch_selftest_timeout(WaveCtrl *ctrl, int *status, int which, uint32_t polls, cudaStream_t s);
 cudaError_t launch_wave_scatter(const WaveArgs &a, int cur, int blocks, cudaStream_t s);
 
 // Measured FP32 FMA (FLOP/s) and ex2 (operations/s) throughput of the device (kns_peak.cu).

@@ -1,10 +1,11 @@
-// kns_peak.cu -- measured throughput ceilings of the pipes the render's kernels lean on: FP32 fused
+// kns_peak.cu -- measured throughput ceilings of the pipes the render's kernels lean on (and a
+// self-test of the bounded device waits, at the end): FP32 fused
 // multiply-add (the FP32 MLPs) and the multi-function unit's ex2 (the softplus of every hidden unit
 // costs an ex2 and an lg2).  Each micro-kernel keeps eight independent dependency chains per thread
 // on every SM and is timed with CUDA events; the roofline of the render is formed against these.
 #include <cuda_runtime.h>
 
-#include "kns_kernels.h"
+#include "kns_wave.cuh"
 
 namespace kns {
 
@@ -80,6 +81,32 @@ cudaError_t measure_peaks(int sm_count, cudaStream_t s, double *ffma_flops, doub
     if (e1) cudaEventDestroy(e1);
     if (sink) cudaFree(sink);
     return e;
+}
+
+// ---------------------------------------------------------------- self-test of the bounded waits
+// A wait that nothing satisfies, with a short poll limit: which = 0, the mbarrier wait of a tile (no
+// arrival ever comes); which = 1, the persistent trace's grid barrier with block 1 of 2 never arriving.
+// The waiting threads give up after `polls` polls and record KNS_ERR_TIMEOUT in the status word, as a
+// render's waits do, and the kernel returns.
+__global__ void __launch_bounds__(128) selftest_timeout_kernel(WaveCtrl *ctrl, int *status, int which,
+                                                               uint32_t polls) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_flag;
+    if (which == 0) {
+        if (threadIdx.x == 0) mbar_init(&bar, 1);
+        __syncthreads();
+        const bool ok = mbar_wait(&bar, 0u, polls);  // phase 0 needs one arrival; none is made
+        if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicCAS(status, 0, (int)6 /* KNS_ERR_TIMEOUT */);
+    } else {
+        if (blockIdx.x == 1) return;  // this block never reaches the barrier
+        unsigned gen = 0;
+        if (!grid_sync(ctrl, gen, &s_flag, polls) && threadIdx.x == 0) atomicCAS(status, 0, (int)6);
+    }
+}
+
+cudaError_t launch_selftest_timeout(WaveCtrl *ctrl, int *status, int which, uint32_t polls, cudaStream_t s) {
+    selftest_timeout_kernel<<<which == 0 ? 1 : 2, 128, 0, s>>>(ctrl, status, which, polls);
+    return cudaGetLastError();
 }
 
 }  // namespace kns

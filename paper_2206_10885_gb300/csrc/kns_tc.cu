@@ -129,7 +129,6 @@ __device__ __forceinline__ float softplus_mufu(float s, float k_e, float k_l) {
 }
 
 constexpr uint32_t kTcPolls = 1u << 26;    // bound of every mbarrier wait
-constexpr uint32_t kGridPolls = 1u << 22;  // bound of every grid-barrier wait (polls of ~0.1 us)
 
 // A warpgroup worker: 128 threads that evaluate tiles on their own weights, activation matrices,
 // tensor-memory columns and mbarriers, synchronised by their own named barrier.
@@ -418,37 +417,6 @@ __global__ void __launch_bounds__(128) wave_eval_tc_kernel(GridView g, WaveArgs 
 }
 
 // ---------------------------------------------------------------- every round in one launch
-// Grid-wide barrier of a cooperative launch (every block resident): the blocks' thread 0 count in on
-// a global counter; the last to arrive resets it and advances the generation the others poll.  Bounded:
-// false after kGridPolls polls (the caller reports KNS_ERR_TIMEOUT and leaves).  Block-uniform result.
-__device__ __forceinline__ bool grid_sync(WaveCtrl *ctrl, unsigned &gen, int *s_flag) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        const unsigned target = gen + 1;
-        __threadfence();
-        if (atomicAdd(&ctrl->bar_count, 1u) == gridDim.x - 1) {
-            atomicExch(&ctrl->bar_count, 0u);
-            __threadfence();
-            atomicExch(&ctrl->bar_gen, target);
-        } else {
-            uint32_t i = 0;
-            while (*(volatile unsigned *)&ctrl->bar_gen != target) {
-                if (++i > kGridPolls) {
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        gen = target;
-        *s_flag = ok;
-    }
-    __syncthreads();
-    return *s_flag != 0;
-}
-
 // Inclusive scan of two values over the block (blockDim.x a multiple of 32, at most 1024 threads).
 __device__ __forceinline__ void block_scan2_any(int &x, int &y, int *wx, int *wy) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;

@@ -266,6 +266,39 @@ __device__ __forceinline__ void advance_pending(const GridView &g, const WaveArg
     warp_count_cells(a.count[p_out], emit, key);
 }
 
+constexpr uint32_t kGridPolls = 1u << 22;  // bound of every grid-barrier wait (polls of ~0.1 us)
+
+// Grid-wide barrier of a cooperative launch (every block resident): the blocks' thread 0 count in on
+// a global counter; the last to arrive resets it and advances the generation the others poll.  Bounded:
+// false after kGridPolls polls (the caller reports KNS_ERR_TIMEOUT and leaves).  Block-uniform result.
+__device__ __forceinline__ bool grid_sync(WaveCtrl *ctrl, unsigned &gen, int *s_flag, uint32_t polls = kGridPolls) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned target = gen + 1;
+        __threadfence();
+        if (atomicAdd(&ctrl->bar_count, 1u) == gridDim.x - 1) {
+            atomicExch(&ctrl->bar_count, 0u);
+            __threadfence();
+            atomicExch(&ctrl->bar_gen, target);
+        } else {
+            uint32_t i = 0;
+            while (*(volatile unsigned *)&ctrl->bar_gen != target) {
+                if (++i > polls) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        gen = target;
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
