@@ -118,7 +118,8 @@ struct RL {
     __host__ __device__ static constexpr int A(int l) { return 28 + (l - 1) * 36; }
     __host__ __device__ static constexpr int D(int l) { return 28 + 36 * H + (l - 1) * 32; }
     static constexpr int Dout = 28 + 68 * H;
-    static constexpr int FD_ROWS = Dout + 4;
+    // difference records backward in place: D_l over A_l (rows 0..31; the one row stays), then Dout
+    static constexpr int DoutF = 28 + 36 * H, FDI_ROWS = DoutF + 4;
     static constexpr int Ud = Dout + 16, U = Ud + 1, Hc = U + 36, Dh = Hc + 36, Dc = Dh + 32;
     static constexpr int C_ROWS = Dc + 4;
     // forward-only kernels: A0, two ping-pong layers, then (centres) the output row, U and Hc
@@ -426,12 +427,15 @@ struct GemmLayer {
 template <int H, bool CENTRE>
 struct GemmPlan {
     static constexpr int NL = H + 1 + (CENTRE ? 2 : 0);
+    // the delta rows of layer l's output: difference records keep D_l in place of A_l
+    __host__ __device__ static constexpr int drow(int l) { return CENTRE ? RL<H>::D(l) : RL<H>::A(l); }
+    __host__ __device__ static constexpr int dout() { return CENTRE ? RL<H>::Dout : RL<H>::DoutF; }
     __device__ static GemmLayer layer(int l) {
         using L = WL<H>;
         using R = RL<H>;
-        if (l == 0) return {R::D(1), 8, R::A0, 7, 32, 27, L::cW0, L::cb0};
-        if (l < H) return {R::D(l + 1), 8, R::A(l), 9, 32, 32, L::cH + (l - 1) * L::HL, L::cH + (l - 1) * L::HL + 1024};
-        if (l == H) return {R::Dout, CENTRE ? 4 : 1, R::A(H), 9, CENTRE ? 16 : 1, 32, L::cWo, L::cbo};
+        if (l == 0) return {drow(1), 8, R::A0, 7, 32, 27, L::cW0, L::cb0};
+        if (l < H) return {drow(l + 1), 8, R::A(l), 9, 32, 32, L::cH + (l - 1) * L::HL, L::cH + (l - 1) * L::HL + 1024};
+        if (l == H) return {dout(), CENTRE ? 4 : 1, R::A(H), 9, CENTRE ? 16 : 1, 32, L::cWo, L::cbo};
         if (l == H + 1) return {R::Dh, 8, R::U, 9, 32, 33, L::cC0, L::cc0};
         return {R::Dc, 1, R::Hc, 9, 3, 32, L::cC1, L::cc1};
     }
@@ -440,7 +444,7 @@ struct GemmPlan {
 };
 
 struct Blk {
-    int drow, OB, arow, IB, out_real, in_real, cW, cb, ob, ib;
+    int drow, OB, arow, IB, out_real, in_real, cW, cb, ob, ib, layer;
 };
 
 template <class Plan>
@@ -453,6 +457,7 @@ __device__ __forceinline__ Blk block_of(int b) {
         const GemmLayer G = Plan::layer(l);
         const int n = G.OB * G.IB;
         if (b < n) {
+            k.layer = l;
             k.drow = G.drow;
             k.OB = G.OB;
             k.arow = G.arow;
@@ -483,10 +488,11 @@ __device__ __forceinline__ Blk block_of(int b) {
     return k;
 }
 
+// layer >= 0: only the blocks of that plan layer
 template <class Plan>
-__device__ __forceinline__ void grad_tile(const float *rows, int b, float (&acc)[16]) {
+__device__ __forceinline__ void grad_tile(const float *rows, int b, float (&acc)[16], int layer = -1) {
     const Blk k = block_of<Plan>(b);
-    if (k.drow < 0) return;
+    if (k.drow < 0 || (layer >= 0 && k.layer != layer)) return;
     const float *D = rows + (k.drow + k.ob) * RS;
     const float *A = rows + (k.arow + k.ib) * RS;
     const int sd = k.OB * RS, sa = k.IB * RS;
@@ -551,11 +557,11 @@ __device__ __forceinline__ void hidden_backward(const float *sw, float *rows, fl
 // CENTRE: sample-centre records (colour MLP + SDF with upstream on d and z; writes the difference
 // records' upstream).  Otherwise: difference records (SDF with upstream on d only).
 template <int H, bool CENTRE>
-__global__ void __launch_bounds__(TPB, 1) k_tile_backward(TrainArgs a) {
+__global__ void __launch_bounds__(TPB, CENTRE ? 1 : 2) k_tile_backward(TrainArgs a) {
     using L = WL<H>;
     using R = RL<H>;
     using Plan = GemmPlan<H, CENTRE>;
-    constexpr int NROWS = CENTRE ? R::C_ROWS : R::FD_ROWS;
+    constexpr int NROWS = CENTRE ? R::C_ROWS : R::FDI_ROWS;
     extern __shared__ float4 smem4[];
     float *rows = reinterpret_cast<float *>(smem4);
     float *sw = rows + NROWS * RS;
@@ -606,7 +612,7 @@ __global__ void __launch_bounds__(TPB, 1) k_tile_backward(TrainArgs a) {
                     if (CENTRE) {
                         if (q >= 0) centre_inputs(a, rows, R::U, tid, q);
                     } else {
-                        rows[R::Dout * RS + tid] = q >= 0 ? a.g_fd[q] : 0.f;
+                        rows[R::DoutF * RS + tid] = q >= 0 ? a.g_fd[q] : 0.f;
                     }
                 }
             }
@@ -709,25 +715,53 @@ __global__ void __launch_bounds__(TPB, 1) k_tile_backward(TrainArgs a) {
                         for (int jj = 0; jj < 4; ++jj) acc2[i][jj] *= dsoftplus_act(act[i][jj], a.beta);
                     store_rows(rows, R::D(H), acc2);
                 }
+                hidden_backward<H>(sw, rows, a.beta);
+                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < Plan::NB; ++k) grad_tile<Plan>(rows, tid + k * TPB, acc[k]);
+                __syncthreads();
             } else {
-                // D_H = Wo[0] g . softplus'(A_H)
-                float act[4][4], dd[4][4];
-                load_rows(rows, R::A(H), act);
-                const float4 g4 = *reinterpret_cast<const float4 *>(rows + R::Dout * RS + r0_t());
-                const float g[4] = {g4.x, g4.y, g4.z, g4.w};
+                // Difference records, deltas in place of the activations (so two blocks fit per SM): each
+                // layer's weight gradient is taken while its input activations are still in their rows.
+                // Output layer first (Dout x A_H), then D_H = Wo[0] g . softplus'(A_H) over A_H.
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float w = sw[L::Wo + o0_32() + i];
+                for (int k = 0; k < Plan::NB; ++k) grad_tile<Plan>(rows, tid + k * TPB, acc[k], H);
+                __syncthreads();
+                {
+                    float act[4][4], dd[4][4];
+                    load_rows(rows, R::A(H), act);
+                    const float4 g4 = *reinterpret_cast<const float4 *>(rows + R::DoutF * RS + r0_t());
+                    const float g[4] = {g4.x, g4.y, g4.z, g4.w};
 #pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) dd[i][jj] = w * g[jj] * dsoftplus_act(act[i][jj], a.beta);
+                    for (int i = 0; i < 4; ++i) {
+                        const float w = sw[L::Wo + o0_32() + i];
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) dd[i][jj] = w * g[jj] * dsoftplus_act(act[i][jj], a.beta);
+                    }
+                    store_rows(rows, R::A(H), dd);  // each thread reads and writes only its own block
                 }
-                store_rows(rows, R::D(H), dd);
-            }
-            hidden_backward<H>(sw, rows, a.beta);
-            __syncthreads();
+                // hidden layer l: its weight gradient (D_{l+1} x A_l), then D_l over A_l
 #pragma unroll
-            for (int k = 0; k < Plan::NB; ++k) grad_tile<Plan>(rows, tid + k * TPB, acc[k]);
-            __syncthreads();
+                for (int l = H - 1; l >= 1; --l) {
+                    __syncthreads();
+#pragma unroll
+                    for (int k = 0; k < Plan::NB; ++k) grad_tile<Plan>(rows, tid + k * TPB, acc[k], l);
+                    __syncthreads();
+                    float dacc[4][4], act[4][4];
+                    zero(dacc);
+                    mm32<32, 32>(sw + L::Wr(l), rows + R::A(l + 1) * RS, dacc);
+                    load_rows(rows, R::A(l), act);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) dacc[i][jj] *= dsoftplus_act(act[i][jj], a.beta);
+                    store_rows(rows, R::A(l), dacc);
+                }
+                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < Plan::NB; ++k) grad_tile<Plan>(rows, tid + k * TPB, acc[k], 0);
+                __syncthreads();
+            }
         }
         float *gcell = a.grad + (int64_t)cell * a.p_cell;
 #pragma unroll
@@ -742,7 +776,7 @@ template <int H>
 size_t centre_fwd_smem() { return ((size_t)RL<H>::FC_ROWS * RS + WL<H>::FC) * sizeof(float); }
 template <int H>
 size_t backward_smem(bool centre) {
-    return ((size_t)(centre ? RL<H>::C_ROWS : RL<H>::FD_ROWS) * RS + (centre ? WL<H>::END : WL<H>::BS)) *
+    return ((size_t)(centre ? RL<H>::C_ROWS : RL<H>::FDI_ROWS) * RS + (centre ? WL<H>::END : WL<H>::BS)) *
            sizeof(float);
 }
 
@@ -774,7 +808,8 @@ cudaError_t backward_h(const TrainArgs &a, int64_t chunks, int sm_count, cudaStr
     const size_t sm = backward_smem<H>(CENTRE);
     cudaError_t e = set_smem(k_tile_backward<H, CENTRE>, sm);
     if (e != cudaSuccess) return e;
-    k_tile_backward<H, CENTRE><<<grid_for(sm_count, 1, chunks), TPB, sm, s>>>(a);
+    // difference records hold their deltas in place of the activations: two blocks fit per SM
+    k_tile_backward<H, CENTRE><<<grid_for(sm_count, CENTRE ? 1 : 2, chunks), TPB, sm, s>>>(a);
     return cudaGetLastError();
 }
 
