@@ -184,7 +184,11 @@ kns_status kns_sync(kns_ctx *ctx, void *cuda_stream, int64_t timeout_ms);
 /* Upload a Kilo-grid (Sec. 3.1).  host_weights: canonical FP32 layout (header comment), exactly
  * n_floats = N^3 * (SDF + colour parameters) floats, host memory, copied.  occ_words: host uint64
  * occupancy words for desc->occ_res (copied), or NULL to build the mask on the device as
- * |d(voxel centre)| < voxel diagonal when occ_res > 0.  The call returns after the upload.
+ * |d(voxel centre)| < voxel diagonal when occ_res > 0.  The call returns after the upload.  The grid
+ * keeps four device copies of the weights, each in the layout one kernel family stages with bulk
+ * copies (per-thread FP32, the FP32 tiles' k-major layout, the tensor-core split-BF16 layout, the
+ * shading layout: about 200 KB per cell at width 64, 6.5 GB for 32^3 cells), the occupancy mask,
+ * its 8^3-block mask and the index box of its occupied voxels.
  * Errors: INVALID_ARG (NULL pointer, n_floats mismatch, N or occ_res out of range),
  * UNSUPPORTED (a width, depth or encoding the kernels are not built for), OUT_OF_MEMORY, CUDA. */
 kns_status kns_load_grid(kns_ctx *ctx, const kns_grid_desc *desc, const float *host_weights,
