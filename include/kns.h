@@ -187,7 +187,7 @@ kns_status kns_sync(kns_ctx *ctx, void *cuda_stream, int64_t timeout_ms);
  * |d(voxel centre)| < voxel diagonal when occ_res > 0.  The call returns after the upload.  The grid
  * keeps four device copies of the weights, each in the layout one kernel family stages with bulk
  * copies (per-thread FP32, the FP32 tiles' k-major layout, the tensor-core split-BF16 layout, the
- * shading layout: about 200 KB per cell at width 64, 6.5 GB for 32^3 cells), the occupancy mask,
+ * shading layout: about 235 KB per cell at width 64, 7.7 GB for 32^3 cells), the occupancy mask,
  * its 8^3-block mask and the index box of its occupied voxels.
  * Errors: INVALID_ARG (NULL pointer, n_floats mismatch, N or occ_res out of range),
  * UNSUPPORTED (a width, depth or encoding the kernels are not built for), OUT_OF_MEMORY, CUDA. */
