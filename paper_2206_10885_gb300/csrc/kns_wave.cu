@@ -522,25 +522,33 @@ struct VecF<4> {
 // vector load of their k-major weights feeds NPL FMAs.  out[o] = softplus(b[o] + sum_k Wt[k][o] in[k]),
 // one chain per output, k ascending -- the summation order of every FP32 evaluator, so d is
 // bit-identical to the tiles' (and to the shading's re-evaluation of a BF16 render's tail hits).
+// The inputs are taken in groups of G: the weights and inputs of group g + 1 are loaded into registers
+// while group g's FMAs run, so the chain waits on neither (a lane's two chains at width 64 are the
+// only dependence left).
 template <int K, int W>
 __device__ __forceinline__ void warp_layer(const float *__restrict__ Wt, const float *__restrict__ b,
                                            const float *in, float *out, int lane, float beta, float inv_beta) {
     constexpr int NPL = W / 32;
     static_assert(NPL == 1 || NPL == 2 || NPL == 4, "width must be 32, 64 or 128");
     static_assert(K % 4 == 0, "layer input must be padded to 4");
+    constexpr int G = K % 8 == 0 ? 8 : 4, NG = K / G;
     const int o0 = NPL * lane;
-    float acc[NPL], w[NPL];
+    float acc[NPL], w[2][G][NPL], x[2][G];
     VecF<NPL>::load(b + o0, acc);
-#pragma unroll 4
-    for (int k = 0; k < K; k += 4) {
-        const float4 x = *reinterpret_cast<const float4 *>(in + k);
-        const float xs[4] = {x.x, x.y, x.z, x.w};
+    auto fetch = [&](int g, int buf) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            VecF<NPL>::load(Wt + (k + c) * W + o0, w);
+        for (int c = 0; c < G; c += 4) VecF<4>::load(in + g * G + c, &x[buf][c]);
 #pragma unroll
-            for (int u = 0; u < NPL; ++u) acc[u] = fmaf(w[u], xs[c], acc[u]);
-        }
+        for (int c = 0; c < G; ++c) VecF<NPL>::load(Wt + (g * G + c) * W + o0, w[buf][c]);
+    };
+    fetch(0, 0);
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+        if (g + 1 < NG) fetch(g + 1, (g + 1) & 1);
+#pragma unroll
+        for (int c = 0; c < G; ++c)
+#pragma unroll
+            for (int u = 0; u < NPL; ++u) acc[u] = fmaf(w[g & 1][c][u], x[g & 1][c], acc[u]);
     }
 #pragma unroll
     for (int u = 0; u < NPL; ++u) acc[u] = softplus_f32(acc[u], beta, inv_beta);
@@ -548,12 +556,34 @@ __device__ __forceinline__ void warp_layer(const float *__restrict__ Wt, const f
     __syncwarp();
 }
 
+// The d row: its bias, then one sequential chain over the last hidden layer (every lane forms it);
+// the row and the activations are loaded a group of 16 ahead of the chain.
+template <int W>
+__device__ __forceinline__ float warp_d_row(const float *__restrict__ drow, float bias, const float *h) {
+    constexpr int G = 16, NG = W / G;
+    float wv[2][G], hv[2][G];
+    auto fetch = [&](int g, int buf) {
+#pragma unroll
+        for (int c = 0; c < G; c += 4) {
+            VecF<4>::load(drow + g * G + c, &wv[buf][c]);
+            VecF<4>::load(h + g * G + c, &hv[buf][c]);
+        }
+    };
+    float d = bias;
+    fetch(0, 0);
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+        if (g + 1 < NG) fetch(g + 1, (g + 1) & 1);
+#pragma unroll
+        for (int c = 0; c < G; ++c) d = fmaf(wv[g & 1][c], hv[g & 1][c], d);
+    }
+    return d;
+}
+
+// The SDF trace form of one sample whose encoded input row is in xin.
 template <class C>
-__device__ __forceinline__ float warp_sdf_trace(const float *__restrict__ wsm, float *xin, float *h0, float *h1,
-                                                float px, float py, float pz, int lane, float beta,
-                                                float inv_beta) {
-    for (int k = lane; k < C::IN; k += 32) xin[k] = encoding_entry(k, px, py, pz);
-    __syncwarp();
+__device__ __forceinline__ float warp_sdf_trace(const float *__restrict__ wsm, const float *xin, float *h0, float *h1,
+                                                int lane, float beta, float inv_beta) {
     warp_layer<C::INP, C::W>(wsm + C::tW0, wsm + C::tb0, xin, h0, lane, beta, inv_beta);
     float *src = h0, *dst = h1;
 #pragma unroll
@@ -563,17 +593,7 @@ __device__ __forceinline__ float warp_sdf_trace(const float *__restrict__ wsm, f
         src = dst;
         dst = tmp;
     }
-    float d = wsm[C::tbL];
-#pragma unroll
-    for (int k = 0; k < C::W; k += 4) {
-        const float4 w = *reinterpret_cast<const float4 *>(wsm + C::tdL + k);
-        const float4 h = *reinterpret_cast<const float4 *>(src + k);
-        d = fmaf(w.x, h.x, d);
-        d = fmaf(w.y, h.y, d);
-        d = fmaf(w.z, h.z, d);
-        d = fmaf(w.w, h.w, d);
-    }
-    return d;
+    return warp_d_row<C::W>(wsm + C::tdL, wsm[C::tbL], src);
 }
 
 // A tail round: one warp (one block) per ray, to the end.  Rays come in cell-sorted order (the cell
@@ -618,9 +638,18 @@ __global__ void __launch_bounds__(32) wave_tail_warp_kernel(GridView g, WaveArgs
         int4 trap = a.trap ? a.trap[r] : trap_empty();
         bool hit = false;
         for (;;) {
-            if (cell != cached) {
+            // a new cell's weights are copied while the sample is encoded
+            const bool fresh = cell != cached;
+            if (fresh) {
                 __syncwarp();  // every lane is done with the slot's previous cell
                 if (lane == 0) bulk_load(wsm, a.wt + (int64_t)cell * a.wt_stride, C::TSIZE * sizeof(float), &bar);
+            }
+            {
+                const float px = fmaf(t, ray.wx, ray.ox), py = fmaf(t, ray.wy, ray.oy),
+                            pz = fmaf(t, ray.wz, ray.oz);
+                for (int k = lane; k < C::IN; k += 32) xin[k] = encoding_entry(k, px, py, pz);
+            }
+            if (fresh) {
                 const bool ok = mbar_wait(&bar, phase, 1u << 26);
                 phase ^= 1u;
                 if (!__all_sync(FULL, ok)) {  // the weights never landed: report and leave
@@ -629,8 +658,8 @@ __global__ void __launch_bounds__(32) wave_tail_warp_kernel(GridView g, WaveArgs
                 }
                 cached = cell;
             }
-            const float d = warp_sdf_trace<C>(wsm, xin, h0, h1, fmaf(t, ray.wx, ray.ox), fmaf(t, ray.wy, ray.oy),
-                                              fmaf(t, ray.wz, ray.oz), lane, g.beta, g.inv_beta);
+            __syncwarp();
+            const float d = warp_sdf_trace<C>(wsm, xin, h0, h1, lane, g.beta, g.inv_beta);
             ++steps;
             ++nsamples;
             if (fabsf(d) < a.eps) {
