@@ -194,6 +194,23 @@ kns_status kns_sync(kns_ctx *ctx, void *cuda_stream, int64_t timeout_ms);
 kns_status kns_load_grid(kns_ctx *ctx, const kns_grid_desc *desc, const float *host_weights,
                          size_t n_floats, const uint64_t *occ_words, kns_grid **out);
 
+/* Upload n_grids Kilo-grids of one descriptor as one resident stack, so that one kns_render_views call
+ * can render views of different grids (a render server's requests for several scenes, Sec. 3.4.1's
+ * renderer applied to each).  host_weights: the n_grids grids' canonical FP32 weights back to back
+ * (n_floats = n_grids * N^3 * parameters per cell); occ_words: the n_grids occupancy masks back to back
+ * (ceil(occ_res^3 / 64) words each), or NULL to build each from its own grid as kns_load_grid does.
+ * Every grid of the stack keeps its own weights, mask, 8^3-block mask and results: a view of grid k
+ * renders exactly as a kns_render of grid k loaded alone (bit for bit in FP32).  kns_render and
+ * kns_render_noalloc render grid 0 of a stack; kns_render_views picks the grid per view (kns_view.grid).
+ * The stack's device memory is n_grids times a single grid's.  Errors: as kns_load_grid, plus
+ * INVALID_ARG for n_grids < 1 or more than 262,144 cells in all (the BF16 seam trap's cell field). */
+kns_status kns_load_grid_stack(kns_ctx *ctx, const kns_grid_desc *desc, int32_t n_grids, const float *host_weights,
+                               size_t n_floats, const uint64_t *occ_words, kns_grid **out);
+
+/* The number of grids a grid object holds (1 unless it came from kns_load_grid_stack).  Errors:
+ * INVALID_ARG (NULL pointer). */
+kns_status kns_grid_stack_size(const kns_grid *grid, int32_t *n_grids);
+
 /* Load a grid file ("KNS1" header, canonical FP32 weights, optional occupancy words; all
  * little-endian).  Errors: as kns_load_grid, plus FORMAT for a bad magic, version or size. */
 kns_status kns_load_grid_file(kns_ctx *ctx, const char *path, kns_grid **out);
@@ -204,7 +221,8 @@ void kns_free_grid(kns_grid *grid);
 /* Copy a grid's descriptor to *out (host). */
 kns_status kns_grid_get_desc(const kns_grid *grid, kns_grid_desc *out);
 
-/* Copy the grid's occupancy mask into host_words (n_words uint64 words, host).  Synchronous.
+/* Copy the grid's occupancy mask into host_words (n_words uint64 words, host; a stack: its grids'
+ * masks back to back, ceil(occ_res^3 / 64) words each).  Synchronous.
  * Errors: INVALID_ARG (no mask, or n_words too small), CUDA. */
 kns_status kns_copy_occupancy(kns_ctx *ctx, const kns_grid *grid, uint64_t *host_words, size_t n_words);
 
@@ -266,19 +284,23 @@ kns_status kns_measure_peaks(kns_ctx *ctx, void *cuda_stream, kns_peaks *out);
  * return; the context stays usable.  Errors: INVALID_ARG (which not 0 or 1), CUDA. */
 kns_status kns_selftest_timeout(kns_ctx *ctx, int32_t which, void *cuda_stream);
 
-/* One view of a multi-view render: camera, image size and its own output buffers (device pointers for
- * W*H pixels, layout as kns_frame). */
+/* One view of a multi-view render: camera, image size, its own output buffers (device pointers for
+ * W*H pixels, layout as kns_frame) and which grid of a stack it renders (0 for a single grid; its
+ * output cell ids are that grid's). */
 typedef struct kns_view {
     kns_camera cam;
     int32_t W, H;
     kns_frame out;
+    int32_t grid;
+    int32_t reserved; /* 0 */
 } kns_view;
 
-/* Sphere-trace and shade several views of one grid in one launch sequence (Sec. 3.4.1): the views may
- * differ in camera and resolution (requests of a render server).  views: host array, read before the
- * call returns; each view writes only its own buffers, and every pixel gets the same result as a
- * kns_render of that view alone.  Views with W*H = 0 are skipped.  Errors: INVALID_ARG (NULL grid or
- * views, a view with negative size or without rgb/depth, more than 2^31-1 rays in total,
+/* Sphere-trace and shade several views of one grid, or of the grids of a stack, in one launch sequence
+ * (Sec. 3.4.1): the views may differ in camera, resolution and grid (requests of a render server).
+ * views: host array, read before the call returns; each view writes only its own buffers, and every
+ * pixel gets the same result as a kns_render of that view alone (of its grid loaded alone).  Views
+ * with W*H = 0 are skipped.  Errors: INVALID_ARG (NULL grid or views, a view with negative size,
+ * without rgb/depth or with a grid index outside the stack, more than 2^31-1 rays in total,
  * max_steps < 1, eps <= 0, bad opts), CUDA, OUT_OF_MEMORY. */
 kns_status kns_render_views(kns_ctx *ctx, const kns_grid *grid, const kns_view *views, int n_views, int max_steps,
                             float eps, const kns_render_opts *opts, void *cuda_stream);

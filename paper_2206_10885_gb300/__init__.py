@@ -86,13 +86,30 @@ class Grid:
         return cls(ctx, h, desc)
 
     @classmethod
+    def load_stack(cls, ctx: Context, desc, weights_list, occ_list=None) -> "Grid":
+        """kns_load_grid_stack: several grids of one descriptor as one resident object; a view of
+        render_views picks its grid by index (the request's optional fourth element)."""
+        w = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float32).ravel() for x in weights_list]))
+        occ = None
+        if occ_list is not None:
+            occ = np.ascontiguousarray(np.concatenate([np.asarray(o, dtype=np.uint64).ravel() for o in occ_list]))
+        h = capi.kns_load_grid_stack(ctx.handle, desc, len(weights_list), w.ctypes.data, w.size,
+                                     None if occ is None else occ.ctypes.data)
+        return cls(ctx, h, desc)
+
+    @property
+    def n_grids(self) -> int:
+        return capi.kns_grid_stack_size(self.handle)
+
+    @classmethod
     def from_file(cls, ctx: Context, path: str) -> "Grid":
         h = capi.kns_load_grid_file(ctx.handle, path)
         return cls(ctx, h, capi.kns_grid_get_desc(h))
 
     def occupancy(self) -> np.ndarray:
+        """The occupancy mask words (a stack: its grids' masks back to back)."""
         res = int(self.desc.occ_res)
-        out = np.zeros((res ** 3 + 63) // 64, dtype=np.uint64)
+        out = np.zeros(self.n_grids * ((res ** 3 + 63) // 64), dtype=np.uint64)
         capi.kns_copy_occupancy(self.ctx.handle, self.handle, out.ctypes.data, out.size)
         return out
 
@@ -151,18 +168,21 @@ def render(ctx: Context, grid: Grid, cams: np.ndarray, W: int, H: int, max_steps
 
 def render_views(ctx: Context, grid: Grid, requests, max_steps: int, eps: float, precision: int = KNS_FP32,
                  stream=None, outs=None, tuning=None, eps_coarse: float = 0.0, refine_steps: int = -1):
-    """kns_render_views: several (camera[16], W, H) views of one grid in one launch sequence.
+    """kns_render_views: several (camera[16], W, H[, grid]) views in one launch sequence; grid picks the
+    grid of a stack (Grid.load_stack; 0 when absent).
 
     Returns one dict of output tensors per request (allocated here unless `outs` gives them).
     """
     import ctypes as C
     if outs is None:
-        outs = [alloc_frame(int(W) * int(H), "cuda:%d" % ctx.device) for _, W, H in requests]
+        outs = [alloc_frame(int(req[1]) * int(req[2]), "cuda:%d" % ctx.device) for req in requests]
     arr = (capi.kns_view * max(1, len(requests)))()
-    for i, ((cam, W, H), (t, f)) in enumerate(zip(requests, outs)):
+    for i, (req, (t, f)) in enumerate(zip(requests, outs)):
+        cam, W, H = req[0], req[1], req[2]
         cam = np.ascontiguousarray(cam, dtype=np.float32).reshape(16)
         C.memmove(C.addressof(arr[i].cam), cam.ctypes.data, 64)
         arr[i].W, arr[i].H = int(W), int(H)
+        arr[i].grid = int(req[3]) if len(req) > 3 else 0
         arr[i].out = f
     capi.kns_render_views(ctx.handle, grid.handle, arr if requests else [], max_steps, eps,
                           render_opts(precision, eps_coarse, refine_steps, tuning), _stream_ptr(stream))

@@ -52,7 +52,8 @@ class kns_frame(C.Structure):
 
 
 class kns_view(C.Structure):
-    _fields_ = [("cam", kns_camera), ("W", C.c_int32), ("H", C.c_int32), ("out", kns_frame)]
+    _fields_ = [("cam", kns_camera), ("W", C.c_int32), ("H", C.c_int32), ("out", kns_frame), ("grid", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class kns_train_batch(C.Structure):
@@ -124,6 +125,11 @@ def lib():
             L.kns_sync.restype = st
             L.kns_load_grid.argtypes = [vp, C.POINTER(kns_grid_desc), vp, C.c_size_t, vp, C.POINTER(vp)]
             L.kns_load_grid.restype = st
+            L.kns_load_grid_stack.argtypes = [vp, C.POINTER(kns_grid_desc), C.c_int32, vp, C.c_size_t, vp,
+                                              C.POINTER(vp)]
+            L.kns_load_grid_stack.restype = st
+            L.kns_grid_stack_size.argtypes = [vp, C.POINTER(C.c_int32)]
+            L.kns_grid_stack_size.restype = st
             L.kns_load_grid_file.argtypes = [vp, C.c_char_p, C.POINTER(vp)]
             L.kns_load_grid_file.restype = st
             L.kns_free_grid.argtypes = [vp]
@@ -212,6 +218,21 @@ def kns_load_grid(ctx: int, desc, host_weights_ptr: int, n_floats: int, occ_word
     d = desc_struct(desc)
     _check(lib().kns_load_grid(ctx, C.byref(d), host_weights_ptr, n_floats, occ_words_ptr, C.byref(h)), ctx)
     return h.value
+
+
+def kns_load_grid_stack(ctx: int, desc, n_grids: int, host_weights_ptr: int, n_floats: int,
+                        occ_words_ptr: int = None) -> int:
+    h = C.c_void_p()
+    d = desc_struct(desc)
+    _check(lib().kns_load_grid_stack(ctx, C.byref(d), n_grids, host_weights_ptr, n_floats, occ_words_ptr,
+                                     C.byref(h)), ctx)
+    return h.value
+
+
+def kns_grid_stack_size(grid: int) -> int:
+    n = C.c_int32(0)
+    _check(lib().kns_grid_stack_size(grid, C.byref(n)), None)
+    return n.value
 
 
 def kns_load_grid_file(ctx: int, path: str) -> int:

@@ -108,6 +108,8 @@ struct kns_grid {
     uint32_t *d_occ_coarse = nullptr;  // 8^3-voxel block mask (res % 8 == 0)
     size_t occ_words64 = 0;
     int occ_box[6] = {0, 0, 0, -1, -1, -1};  // index box of the occupied voxels (lo xyz, hi xyz)
+    int n_sub = 1;  // grids in the stack (kns_load_grid_stack): cells, layouts and masks back to back
+    int *d_boxes = nullptr;  // a stack: each grid's occupied-voxel index box (6 ints per grid)
     kns::GridView view{};
 };
 
@@ -305,6 +307,17 @@ void convert_cell_tc(const kns_grid_desc &d, int bytes, const float *src, unsign
     drow[W] = src[s + (int64_t)kns::SDF_OUT * W];       // its bias
 }
 
+// 64-bit words of one grid's occupancy mask, and 32-bit words of its 8^3-block mask (0 without one).
+size_t occ_words64_per_grid(const kns_grid_desc &d) {
+    const int64_t nvox = (int64_t)d.occ_res * d.occ_res * d.occ_res;
+    return d.occ_res > 0 ? (size_t)((nvox + 63) / 64) : 0;
+}
+size_t coarse_words_per_grid(const kns_grid_desc &d) {
+    if (d.occ_res <= 0 || d.occ_res % 8 != 0) return 0;
+    const int64_t nb = (int64_t)(d.occ_res / 8) * (d.occ_res / 8) * (d.occ_res / 8);
+    return (size_t)((nb + 31) / 32);
+}
+
 void fill_view(kns_grid *g) {
     kns::GridView &v = g->view;
     const kns_grid_desc &d = g->desc;
@@ -331,6 +344,11 @@ void fill_view(kns_grid *g) {
     v.occ_per_cell = d.occ_res > 0 ? d.occ_res / d.N : 1;
     v.beta = d.softplus_beta;
     v.inv_beta = 1.f / d.softplus_beta;
+    v.cell_base = 0;
+    v.ncl = d.N * d.N * d.N;
+    v.occ_words = (int)(2 * occ_words64_per_grid(d));
+    v.coarse_words = (int)coarse_words_per_grid(d);
+    v.sub_boxes = g->d_boxes;
 }
 
 void free_scratch(WaveScratch &w) {
@@ -366,6 +384,8 @@ constexpr int kRenderMinActive = 8;
 constexpr int kRenderBlockInnerSteps = 2;  // block tiles: a second evaluation of a tile in the round ...
 constexpr int kRenderBlockMinActive = 16;  // ... while at least 16 of its rays stay in its cell
 constexpr int kRenderTailRays = 131072;  // rounds this small finish one warp per ray (width 32)
+// Cells of all grids of a stack: the BF16 seam trap keeps a cell number in 19 bits.
+constexpr int64_t kMaxStackCells = 262144;
 // tensor-core tiles (BF16 renders): a second evaluation while at least 16 rays stay in the cell
 constexpr int kRenderBf16InnerSteps = 2;        // width 64
 constexpr int kRenderBf16InnerStepsNarrow = 4;  // width 32
@@ -690,16 +710,21 @@ kns_status kns_sync(kns_ctx *ctx, void *cuda_stream, int64_t timeout_ms) {
     return KNS_OK;
 }
 
-kns_status kns_load_grid(kns_ctx *ctx, const kns_grid_desc *desc, const float *host_weights, size_t n_floats,
-                         const uint64_t *occ_words, kns_grid **out) {
-    if (!ctx) return KNS_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lk(ctx->mu);
+// Uploads n_sub grids of one descriptor as one resident object (n_sub = 1: a single grid): their cells
+// are numbered back to back (grid k's cell c is k N^3 + c) in every weight layout, and their occupancy
+// masks and 8^3-block masks follow each other, each built from its own grid's SDF.
+static kns_status load_grid_impl(kns_ctx *ctx, const kns_grid_desc *desc, const float *host_weights,
+                                 size_t n_floats, int n_sub, const uint64_t *occ_words, kns_grid **out) {
     if (!desc || !host_weights || !out) return set_err(ctx, KNS_ERR_INVALID_ARG, "NULL desc, weights or out");
     *out = nullptr;
     kns_status st = check_desc(ctx, *desc);
     if (st != KNS_OK) return st;
     const kns_grid_desc d = *desc;
-    const int64_t ncell = (int64_t)d.N * d.N * d.N;
+    const int64_t ncl = (int64_t)d.N * d.N * d.N;
+    if (n_sub < 1 || (int64_t)n_sub * ncl > kMaxStackCells)
+        return set_err(ctx, KNS_ERR_INVALID_ARG, "n_grids=%d: 1 .. %lld cells in all", n_sub,
+                       (long long)kMaxStackCells);
+    const int64_t ncell = ncl * n_sub;
     const int64_t pcell = canon_sdf_params(d) + canon_col_params(d);
     if ((int64_t)n_floats != ncell * pcell)
         return set_err(ctx, KNS_ERR_INVALID_ARG, "n_floats=%zu, the descriptor needs %lld", n_floats,
@@ -709,6 +734,7 @@ kns_status kns_load_grid(kns_ctx *ctx, const kns_grid_desc *desc, const float *h
     if (!g) return set_err(ctx, KNS_ERR_OUT_OF_MEMORY, "host allocation failed");
     g->ctx = ctx;
     g->desc = d;
+    g->n_sub = n_sub;
     g->shape = kns::Shape{d.sdf_width, d.sdf_hidden, d.pe_pos_L, d.pe_dir_L};
     const int dev_floats = kns::cell_floats(g->shape);
     std::vector<float> host;
@@ -768,37 +794,54 @@ kns_status kns_load_grid(kns_ctx *ctx, const kns_grid_desc *desc, const float *h
         return cuda_err(ctx, e, "grid upload");
     }
     if (d.occ_res > 0) {
-        const int64_t nvox = (int64_t)d.occ_res * d.occ_res * d.occ_res;
-        g->occ_words64 = (size_t)((nvox + 63) / 64);
+        const size_t w64 = occ_words64_per_grid(d), cw = coarse_words_per_grid(d);
+        g->occ_words64 = w64 * (size_t)n_sub;
         e = cudaMalloc(&g->d_occ, g->occ_words64 * 8);
         if (e == cudaSuccess) e = cudaMemset(g->d_occ, 0, g->occ_words64 * 8);
         if (e == cudaSuccess && occ_words)
             e = cudaMemcpy(g->d_occ, occ_words, g->occ_words64 * 8, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && cw) e = cudaMalloc(&g->d_occ_coarse, cw * 4 * (size_t)n_sub);
         fill_view(g);
-        if (e == cudaSuccess && !occ_words) {
-            float diag = 0.f;
-            for (int a = 0; a < 3; ++a) diag += g->view.ovox[a] * g->view.ovox[a];
-            diag = std::sqrt(diag);
-            kns::GridView v = g->view;
-            v.occ = nullptr;
-            e = kns::launch_occupancy_f32(g->shape, v, diag, g->d_occ, 0);
-            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        float diag = 0.f;
+        for (int a = 0; a < 3; ++a) diag += g->view.ovox[a] * g->view.ovox[a];
+        diag = std::sqrt(diag);
+        int box[6] = {d.occ_res, d.occ_res, d.occ_res, -1, -1, -1};  // the union of the grids' boxes
+        std::vector<int> boxes((size_t)6 * n_sub);
+        for (int k = 0; k < n_sub && e == cudaSuccess; ++k) {
+            uint32_t *occ_k = reinterpret_cast<uint32_t *>(g->d_occ) + 2 * w64 * (size_t)k;
+            if (!occ_words) {
+                kns::GridView v = g->view;
+                v.occ = nullptr;
+                v.occ_coarse = nullptr;
+                v.cell_base = (int)(k * ncl);  // grid k's cells
+                e = kns::launch_occupancy_f32(g->shape, v, diag, occ_k, 0);
+                if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            }
+            if (e == cudaSuccess && cw) {
+                e = kns::launch_coarse_occupancy(occ_k, d.occ_res, g->d_occ_coarse + cw * (size_t)k, 0);
+                if (e == cudaSuccess) e = cudaDeviceSynchronize();
+            }
+            if (e == cudaSuccess) {
+                // the index box of the occupied voxels: the walk leaves (or never enters) it through empty space
+                int *d_box = nullptr;
+                int init[6] = {d.occ_res, d.occ_res, d.occ_res, -1, -1, -1};
+                e = cudaMalloc(&d_box, sizeof(init));
+                if (e == cudaSuccess) e = cudaMemcpy(d_box, init, sizeof(init), cudaMemcpyHostToDevice);
+                if (e == cudaSuccess) e = kns::launch_occ_bounds(occ_k, d.occ_res, d_box, 0);
+                if (e == cudaSuccess) e = cudaMemcpy(init, d_box, sizeof(init), cudaMemcpyDeviceToHost);
+                cudaFree(d_box);
+                for (int a = 0; a < 3; ++a) {
+                    box[a] = std::min(box[a], init[a]);
+                    box[3 + a] = std::max(box[3 + a], init[3 + a]);
+                }
+                for (int a = 0; a < 6; ++a) boxes[6 * k + a] = init[a];
+            }
         }
-        if (e == cudaSuccess && d.occ_res % 8 == 0) {
-            const int64_t nb = (int64_t)(d.occ_res / 8) * (d.occ_res / 8) * (d.occ_res / 8);
-            e = cudaMalloc(&g->d_occ_coarse, (size_t)((nb + 31) / 32) * 4);
-            if (e == cudaSuccess) e = kns::launch_coarse_occupancy(g->d_occ, d.occ_res, g->d_occ_coarse, 0);
-            if (e == cudaSuccess) e = cudaDeviceSynchronize();
-        }
-        if (e == cudaSuccess) {
-            // the index box of the occupied voxels: the walk leaves (or never enters) it through empty space
-            int *d_box = nullptr;
-            const int init[6] = {d.occ_res, d.occ_res, d.occ_res, -1, -1, -1};
-            e = cudaMalloc(&d_box, sizeof(init));
-            if (e == cudaSuccess) e = cudaMemcpy(d_box, init, sizeof(init), cudaMemcpyHostToDevice);
-            if (e == cudaSuccess) e = kns::launch_occ_bounds(g->d_occ, d.occ_res, d_box, 0);
-            if (e == cudaSuccess) e = cudaMemcpy(g->occ_box, d_box, sizeof(init), cudaMemcpyDeviceToHost);
-            cudaFree(d_box);
+        for (int a = 0; a < 6; ++a) g->occ_box[a] = box[a];
+        if (e == cudaSuccess && n_sub > 1) {  // each grid of a stack walks to its own box
+            e = cudaMalloc(&g->d_boxes, boxes.size() * sizeof(int));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(g->d_boxes, boxes.data(), boxes.size() * sizeof(int), cudaMemcpyHostToDevice);
         }
         if (e != cudaSuccess) {
             cudaFree(g->d_w);
@@ -807,12 +850,33 @@ kns_status kns_load_grid(kns_ctx *ctx, const kns_grid_desc *desc, const float *h
             cudaFree(g->d_ws);
             cudaFree(g->d_occ);
             cudaFree(g->d_occ_coarse);
+            cudaFree(g->d_boxes);
             delete g;
             return cuda_err(ctx, e, "occupancy");
         }
     }
     fill_view(g);
     *out = g;
+    return KNS_OK;
+}
+
+kns_status kns_load_grid(kns_ctx *ctx, const kns_grid_desc *desc, const float *host_weights, size_t n_floats,
+                         const uint64_t *occ_words, kns_grid **out) {
+    if (!ctx) return KNS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    return load_grid_impl(ctx, desc, host_weights, n_floats, 1, occ_words, out);
+}
+
+kns_status kns_load_grid_stack(kns_ctx *ctx, const kns_grid_desc *desc, int32_t n_grids, const float *host_weights,
+                               size_t n_floats, const uint64_t *occ_words, kns_grid **out) {
+    if (!ctx) return KNS_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    return load_grid_impl(ctx, desc, host_weights, n_floats, n_grids, occ_words, out);
+}
+
+kns_status kns_grid_stack_size(const kns_grid *grid, int32_t *n_grids) {
+    if (!grid || !n_grids) return KNS_ERR_INVALID_ARG;
+    *n_grids = grid->n_sub;
     return KNS_OK;
 }
 
@@ -885,6 +949,7 @@ void kns_free_grid(kns_grid *g) {
         cudaFree(g->d_ws);
         cudaFree(g->d_occ);
         cudaFree(g->d_occ_coarse);
+        cudaFree(g->d_boxes);
     }
     delete g;
 }
@@ -987,7 +1052,7 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
                              int64_t rays, int max_steps, float eps, const RenderCfg &cfg, cudaStream_t s,
                              bool last, const float *ray_o = nullptr, const float *ray_w = nullptr,
                              int64_t n_table = 0) {
-    const int NC = grid->desc.N * grid->desc.N * grid->desc.N;
+    const int NC = grid->n_sub * grid->desc.N * grid->desc.N * grid->desc.N;  // every grid of a stack
     const int nkeys = NC;  // sort keys: cells
     const int nv = (int)views.size();
     kns_status st = ensure_scratch(ctx, rays, nkeys, nv);
@@ -1161,8 +1226,9 @@ kns_status render_views_impl(kns_ctx *ctx, const kns_grid *grid, const std::vect
     return KNS_OK;
 }
 
-kns::ViewDev make_view(const kns_camera &cam, int W, int H, int64_t ray_base, const kns_frame &out) {
+kns::ViewDev make_view(const kns_camera &cam, int W, int H, int64_t ray_base, const kns_frame &out, int grid = 0) {
     kns::ViewDev v{};
+    v.grid = grid;
     std::memcpy(v.cam, &cam, sizeof(float) * 16);
     v.rgb = out.rgb;
     v.depth = out.depth;
@@ -1243,8 +1309,10 @@ kns_status kns_render_views(kns_ctx *ctx, const kns_grid *grid, const kns_view *
         if (n == 0) continue;
         if (!v.out.rgb || !v.out.depth)
             return set_err(ctx, KNS_ERR_INVALID_ARG, "view %d: rgb and depth buffers are required", i);
+        if (v.grid < 0 || v.grid >= grid->n_sub)
+            return set_err(ctx, KNS_ERR_INVALID_ARG, "view %d: grid %d of a stack of %d", i, v.grid, grid->n_sub);
         if (rays + n > INT32_MAX) return set_err(ctx, KNS_ERR_INVALID_ARG, "views hold more than 2^31-1 rays");
-        dv.push_back(make_view(v.cam, v.W, v.H, rays, v.out));
+        dv.push_back(make_view(v.cam, v.W, v.H, rays, v.out, v.grid));
         rays += n;
     }
     if (dv.empty()) return KNS_OK;

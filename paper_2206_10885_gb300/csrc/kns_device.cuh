@@ -75,7 +75,33 @@ struct GridView {
     int olo[3], ohi[3];          // index box of the occupied voxels (inclusive; olo > ohi: none occupied)
     const float *ws;             // shading layout of every cell (kns_shade.cu), one bulk copy per cell
     int ws_stride;               // floats per cell of it
+    // A stack of grids of one shape (kns_load_grid_stack) numbers the cells of grid k from k * ncl and keeps
+    // the grids' occupancy masks back to back; sub_grid() gives the view of grid k (a single grid: k = 0).
+    int cell_base;     // number of this grid's first cell
+    int ncl;           // cells of one grid, N^3
+    int occ_words;     // 32-bit words of one grid's occupancy mask
+    int coarse_words;  // 32-bit words of one grid's coarse mask
+    const int *sub_boxes;  // a stack: each grid's index box of occupied voxels (lo xyz, hi xyz); else NULL
 };
+
+// The view of grid k of a stack: its cell numbers and occupancy masks (the weights of every grid of the
+// stack are indexed by cell number already).
+__device__ __forceinline__ GridView sub_grid(const GridView &g, int k) {
+    GridView s = g;
+    if (k > 0) {
+        s.cell_base = k * g.ncl;
+        if (s.occ) s.occ += (size_t)k * g.occ_words;
+        if (s.occ_coarse) s.occ_coarse += (size_t)k * g.coarse_words;
+    }
+    if (g.sub_boxes) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            s.olo[a] = __ldg(g.sub_boxes + 6 * k + a);
+            s.ohi[a] = __ldg(g.sub_boxes + 6 * k + 3 + a);
+        }
+    }
+    return s;
+}
 
 // ------------------------------------------------------------------ activations
 __device__ __forceinline__ float softplus_f32(float s, float beta, float inv_beta) {
@@ -316,7 +342,7 @@ __device__ __forceinline__ int cell_of(const GridView &g, float x, float y, floa
     const int ix = grid_axis(x, g.bmin[0], g.cscale[0], g.N);
     const int iy = grid_axis(y, g.bmin[1], g.cscale[1], g.N);
     const int iz = grid_axis(z, g.bmin[2], g.cscale[2], g.N);
-    return ix + g.N * (iy + g.N * iz);
+    return g.cell_base + ix + g.N * (iy + g.N * iz);
 }
 
 __device__ __forceinline__ bool occ_test(const uint32_t *__restrict__ occ, int res, int ix, int iy, int iz) {

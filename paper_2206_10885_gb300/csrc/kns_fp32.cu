@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(128) occupancy_kernel(GridView g, float thresh
         const float y = g.bmin[1] + ((float)iy + 0.5f) * g.ovox[1];
         const float z = g.bmin[2] + ((float)iz + 0.5f) * g.ovox[2];
         const int f = g.occ_per_cell;
-        const int cell = ix / f + g.N * (iy / f + g.N * (iz / f));
+        const int cell = g.cell_base + ix / f + g.N * (iy / f + g.N * (iz / f));
         const float d = sdf_trace_f32<C>(g.w + (int64_t)cell * g.cell_stride, x, y, z, g.beta, g.inv_beta);
         occ = fabsf(d) < thresh;
     }
@@ -65,8 +65,9 @@ __global__ void __launch_bounds__(128) refine_kernel(GridView g, WaveArgs a) {
         int steps = a.steps_ray[r], cell = a.cell_ray[r];
         int cam;
         const Ray ray = ray_of(a, r, cam);
+        const GridView gv = sub_grid(g, a.views[cam].grid);  // the ray's grid (a stack of grids)
         float t0, tf;
-        clip_box(g, ray, t0, tf);
+        clip_box(gv, ray, t0, tf);
         bool hit = false;
         for (int ev = 1;; ++ev) {
             if (fabsf(d) < a.eps) {
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(128) refine_kernel(GridView g, WaveArgs a) {
             }
             t += d;
             if (t > tf || t < t0 || steps >= a.max_steps) break;
-            cell = advance_ray(g, ray, t, tf);
+            cell = advance_ray(gv, ray, t, tf);
             if (cell < 0) break;
             d = sdf_trace_f32<C>(g.w + (int64_t)cell * g.cell_stride, fmaf(t, ray.wx, ray.ox), fmaf(t, ray.wy, ray.oy),
                                  fmaf(t, ray.wz, ray.oz), g.beta, g.inv_beta);
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(128) refine_kernel(GridView g, WaveArgs a) {
             V.normal[3 * p + 1] = nrm[1];
             V.normal[3 * p + 2] = nrm[2];
         }
-        if (V.cell) V.cell[p] = cell;
+        if (V.cell) V.cell[p] = cell - gv.cell_base;  // the cell within the view's grid
         if (V.steps) V.steps[p] = steps;
         if (V.hit) V.hit[p] = 1;
     }

@@ -47,7 +47,7 @@ struct ViewDev {
     float *rgb, *depth, *normal;
     int32_t *cell, *steps;
     uint8_t *hit;
-    int W, H, ray_base, pad;
+    int W, H, ray_base, grid;  // grid: which grid of a stack the view renders (0 for a single grid)
 };
 
 // Everything the wavefront kernels read and write (device pointers; passed by value).

@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(STHREADS) shade_block_kernel(GridView g, WaveA
                     V.normal[3 * px + 1] = n[1];
                     V.normal[3 * px + 2] = n[2];
                 }
-                if (V.cell) V.cell[px] = c;
+                if (V.cell) V.cell[px] = c - V.grid * g.ncl;  // the cell within the view's grid
                 if (V.steps) V.steps[px] = a.steps_ray[r];
                 if (V.hit) V.hit[px] = 1;
             }

@@ -213,6 +213,7 @@ __device__ bool tc_round(TcWorker &w, const GridView &g, const WaveArgs &a, int 
         const bool fresh = w.s_tile[3] != 0;
         if (c < 0) break;
         w.cached = c;
+        const GridView gt = sub_grid(g, c / g.ncl);  // the grid of the tile's cell (a stack of grids)
         bool active = tid < len;
         int r = 0, steps = 0;
         float t = 0.f, t0 = 0.f, tf = 0.f;
@@ -227,7 +228,7 @@ __device__ bool tc_round(TcWorker &w, const GridView &g, const WaveArgs &a, int 
             if (a.trap) trap = a.trap[r];
             int cam;
             ray = ray_of(a, r, cam);
-            clip_box(g, ray, t0, tf);
+            clip_box(gt, ray, t0, tf);
         }
         if (fresh) w.w_pending = true;
         for (int it = 0;; ++it) {
@@ -318,7 +319,7 @@ __device__ bool tc_round(TcWorker &w, const GridView &g, const WaveArgs &a, int 
                         outcome = 2;
                         write_miss(a, r, steps);
                     } else {
-                        ncell = advance_fast(g, ray, t);
+                        ncell = advance_fast(gt, ray, t);
                         if (ncell == -2) {
                             outcome = 3;
                         } else if (cycles && cycle_step_tol(hist, t_eval, t)) {

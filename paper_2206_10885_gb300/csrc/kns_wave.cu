@@ -126,12 +126,13 @@ __global__ void __launch_bounds__(128) wave_gen_kernel(GridView g, WaveArgs a) {
     if (valid) {
         a.ray_view[r] = view;
         const Ray ray = a.ray_o ? table_ray(a, r) : make_ray(V.cam, i, j);
+        const GridView gv = sub_grid(g, V.grid);
         float t0, tf;
-        if (!clip_box(g, ray, t0, tf)) {
+        if (!clip_box(gv, ray, t0, tf)) {
             write_miss(a, r, 0);
         } else {
             float t = t0;
-            cell = advance_ray(g, ray, t, tf);
+            cell = advance_ray(gv, ray, t, tf);
             if (cell < 0) {
                 write_miss(a, r, 0);
             } else {
@@ -320,6 +321,7 @@ __global__ void __launch_bounds__(NT, block_min_blocks<C, BT>()) wave_eval_block
         const bool fresh = s_tile[3] != 0;
         if (c < 0) break;
         cached = c;
+        const GridView gt = sub_grid(g, c / g.ncl);  // the grid of the tile's cell (a stack of grids)
         // samples: threads 0..127 own sample s = tid
         bool active = tid < len;
         int r = 0, steps = 0, switched = 0;
@@ -335,7 +337,7 @@ __global__ void __launch_bounds__(NT, block_min_blocks<C, BT>()) wave_eval_block
             if (a.coarse) switched = a.cell_ray[r];
             int cam;
             ray = ray_of(a, r, cam);
-            clip_box(g, ray, t0, tf);
+            clip_box(gt, ray, t0, tf);
         }
         // Up to inner_steps evaluations of the tile: a sample whose step keeps it in this cell (an
         // emit to the same key) is evaluated again at once, while at least min_active of them do;
@@ -404,7 +406,7 @@ __global__ void __launch_bounds__(NT, block_min_blocks<C, BT>()) wave_eval_block
                             // an occupied voxel gives the next cell at once; a ray that stepped into
                             // empty space goes on the round's pending list for wave_advance_kernel, so
                             // that no lane holds the block in a long voxel walk
-                            ncell = advance_fast(g, ray, t);
+                            ncell = advance_fast(gt, ray, t);
                             if (ncell == -2) {
                                 outcome = 3;
                             } else if (cycles && cycle_step(hist, t_eval, t)) {
@@ -600,7 +602,7 @@ __device__ __forceinline__ float warp_sdf_trace(const float *__restrict__ wsm, c
 // of a ray's position is its sort key); the round's tile counter hands them out.  In a BF16 render the
 // rays left in the round take their last steps here in FP32, with the BF16 trace's cycle test and seam
 // trap, and join the hit list when |d| < eps as the tensor-core tiles' rays do.
-template <class C>
+template <class C, bool STACK>
 __global__ void __launch_bounds__(32) wave_tail_warp_kernel(GridView g, WaveArgs a, int cur) {
     extern __shared__ __align__(128) float dyn[];
     __shared__ __align__(8) uint64_t bar;
@@ -630,8 +632,11 @@ __global__ void __launch_bounds__(32) wave_tail_warp_kernel(GridView g, WaveArgs
         int cell = lo;
         int cam;
         const Ray ray = ray_of(a, r, cam);
+        GridView gs;
+        if constexpr (STACK) gs = sub_grid(g, cell / g.ncl);  // the ray's grid in a stack of grids
+        const GridView &gr = STACK ? gs : g;
         float t0, tf;
-        clip_box(g, ray, t0, tf);
+        clip_box(gr, ray, t0, tf);
         float t = a.t_ray[r];
         int steps = a.steps_ray[r];
         float4 hist = cycles ? a.t_hist[r] : no_history();
@@ -674,7 +679,7 @@ __global__ void __launch_bounds__(32) wave_tail_warp_kernel(GridView g, WaveArgs
             const float t_eval = t;
             t += d;
             if (t > tf || t < t0 || steps >= a.max_steps) break;
-            cell = advance_ray(g, ray, t, tf);
+            cell = advance_ray(gr, ray, t, tf);
             if (cell < 0) break;
             if (cycles && (a.coarse ? cycle_step_tol(hist, t_eval, t) : cycle_step(hist, t_eval, t))) {
                 steps = a.max_steps;
@@ -746,6 +751,7 @@ __global__ void __launch_bounds__(32) wave_eval_kernel(GridView g, WaveArgs a, i
         len = __shfl_sync(FULL, len, 0);
         const bool fresh = c != cached;
         cached = c;
+        const GridView gt = sub_grid(g, c / g.ncl);  // the grid of the tile's cell (a stack of grids)
         const int s = lane & 15;
         bool active = lane < TILE && s < len;
         int r = 0, steps = 0, switched = 0;
@@ -761,7 +767,7 @@ __global__ void __launch_bounds__(32) wave_eval_kernel(GridView g, WaveArgs a, i
             if (a.coarse) switched = a.cell_ray[r];  // step count at the BF16 -> FP32 switch
             int cam;
             ray = ray_of(a, r, cam);
-            clip_box(g, ray, t0, tf);
+            clip_box(gt, ray, t0, tf);
         }
         if (fresh) {
             const bool ok = mbar_wait(&bar, phase, 1u << 26);
@@ -817,7 +823,7 @@ __global__ void __launch_bounds__(32) wave_eval_kernel(GridView g, WaveArgs a, i
                         write_miss(a, r, steps);
                         active = false;
                     } else {
-                        ncell = advance_ray(g, ray, t, tf);
+                        ncell = advance_ray(gt, ray, t, tf);
                         if (ncell < 0) {
                             write_miss(a, r, steps);
                             active = false;
@@ -894,9 +900,15 @@ cudaError_t launch_wave_tail_cfg(const GridView &g, const WaveArgs &a, int cur, 
     static_assert(tsmem <= 64 * 1024, "tail weight slot does not fit");
     static std::atomic<int> tail_per_sm{0};
     int tail_blocks = 0;
-    cudaError_t e = resident_blocks(wave_tail_warp_kernel<C>, 32, tsmem, tail_per_sm, tail_blocks);
+    cudaError_t e = resident_blocks(wave_tail_warp_kernel<C, false>, 32, tsmem, tail_per_sm, tail_blocks);
     if (e != cudaSuccess) return e;
-    wave_tail_warp_kernel<C><<<sm_count * tail_blocks, 32, tsmem, s>>>(g, a, cur);
+    if (g.sub_boxes) {  // a stack of grids (same resources)
+        e = cudaFuncSetAttribute(wave_tail_warp_kernel<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, tsmem);
+        if (e != cudaSuccess) return e;
+        wave_tail_warp_kernel<C, true><<<sm_count * tail_blocks, 32, tsmem, s>>>(g, a, cur);
+    } else {
+        wave_tail_warp_kernel<C, false><<<sm_count * tail_blocks, 32, tsmem, s>>>(g, a, cur);
+    }
     return cudaGetLastError();
 }
 

@@ -203,7 +203,7 @@ __device__ __forceinline__ int advance_ray(const GridView &g, const Ray &r, floa
             if (!dda_next(g, r, vx, vy, vz, tf, te)) return -1;
             t = te;
             const int f = g.occ_per_cell;
-            return vx / f + g.N * (vy / f + g.N * (vz / f));
+            return g.cell_base + vx / f + g.N * (vy / f + g.N * (vz / f));
         }
     }
     return cell_of(g, x, y, z);
@@ -236,10 +236,11 @@ __device__ __forceinline__ void advance_pending(const GridView &g, const WaveArg
         const float t_eval = a.pend_t[p_in][i];
         int cam;
         const Ray ray = ray_of(a, r, cam);
+        const GridView gv = sub_grid(g, a.views[cam].grid);
         float t0, tf;
-        clip_box(g, ray, t0, tf);
+        clip_box(gv, ray, t0, tf);
         float t = a.t_ray[r];
-        ncell = advance_ray(g, ray, t, tf);
+        ncell = advance_ray(gv, ray, t, tf);
         if (ncell < 0) {
             write_miss(a, r, a.steps_ray[r]);
         } else {

@@ -62,6 +62,7 @@ int main(void) {
          offsetof(kns_render_stats, refined));
   printf("%zu %zu\\n", sizeof(kns_round_info), offsetof(kns_round_info, tiles));
   printf("%zu %zu\\n", sizeof(kns_peaks), offsetof(kns_peaks, sm_clock_khz));
+  printf("%zu %zu %zu\\n", sizeof(kns_view), offsetof(kns_view, out), offsetof(kns_view, grid));
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -78,7 +79,8 @@ int main(void) {
             C.sizeof(capi.kns_render_stats), capi.kns_render_stats.ms_eval_fp32.offset,
             capi.kns_render_stats.refined.offset,
             C.sizeof(capi.kns_round_info), capi.kns_round_info.tiles.offset,
-            C.sizeof(capi.kns_peaks), capi.kns_peaks.sm_clock_khz.offset]
+            C.sizeof(capi.kns_peaks), capi.kns_peaks.sm_clock_khz.offset,
+            C.sizeof(capi.kns_view), capi.kns_view.out.offset, capi.kns_view.grid.offset]
     assert vals == want
 
 
@@ -108,6 +110,9 @@ def test_null_context_is_rejected_on_the_host(lib):
     assert lib.kns_copy_occupancy(None, None, None, 0) == bad
     assert lib.kns_grid_get_desc(None, None) == bad
     assert lib.kns_load_grid_file(None, None, C.byref(h)) == bad
+    assert lib.kns_load_grid_stack(None, None, 2, None, 0, None, C.byref(h)) == bad
+    n = C.c_int32(0)
+    assert lib.kns_grid_stack_size(None, C.byref(n)) == bad
 
 
 def test_create_without_a_device_fails_cleanly(lib):

@@ -74,7 +74,53 @@ def test_views_batch_equals_solo_renders(kns, precision):
         ctx.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_stack_views_equal_grids_alone(kns, precision):
+    """Three grids of one shape loaded as a stack: a batch of views of all three renders every view as
+    the grid loaded alone renders it (FP32 bit for bit, BF16 within the gates), each grid keeps its own
+    occupancy mask, and a view naming a grid outside the stack is refused."""
+    desc = S.config_desc("c2")
+    ws = [S.sal_sphere_grid(desc, seed=s) for s in (0, 7, 11)]
+    ctx = kns.Context(0)
+    stack = kns.Grid.load_stack(ctx, desc, ws)
+    alone = [kns.Grid.load(ctx, desc, w) for w in ws]
+    try:
+        assert stack.n_grids == 3 and alone[0].n_grids == 1
+        occ_stack = stack.occupancy()
+        per = occ_stack.size // 3
+        for k in range(3):
+            assert np.array_equal(occ_stack[k * per:(k + 1) * per], alone[k].occupancy()), k
+        sizes = [(64, 48, 2), (131, 77, 0), (1, 1, 1), (0, 5, 2), (200, 160, 1), (17, 240, 0), (96, 96, 2)]
+        reqs = [(S.orbit_cameras(1, W, H, seed=40 + i)[0], W, H, k) for i, (W, H, k) in enumerate(sizes)]
+        got = kns.render_views(ctx, stack, reqs, 128, 1e-4, precision=precision)
+        ctx.sync()
+        for (cam, W, H, k), t in zip(reqs, got):
+            if W * H == 0:
+                continue
+            ref = solo(kns, ctx, alone[k], cam, W, H, precision=precision)
+            g = {key: v.cpu().numpy() for key, v in t.items()}
+            if precision == kns.KNS_FP32:
+                for key in ref:
+                    assert np.array_equal(ref[key], g[key]), (W, H, k, key)
+            else:
+                assert_within_bf16_gates(ref, g, (W, H, k))
+        # the stack's grids differ: the same view of two grids is not the same image
+        a, b = kns.render_views(ctx, stack, [(reqs[0][0], 64, 48, 0), (reqs[0][0], 64, 48, 1)], 128, 1e-4,
+                                precision=precision)
+        ctx.sync()
+        assert not np.array_equal(a["depth"].cpu().numpy(), b["depth"].cpu().numpy())
+        with pytest.raises(kns.KnsError):
+            kns.render_views(ctx, stack, [(reqs[0][0], 8, 8, 3)], 128, 1e-4, precision=precision)
+    finally:
+        for g in alone:
+            g.free()
+        stack.free()
+        ctx.close()
+
+
 def test_server_mixed_stream_matches_solo(kns):
+    """Two grids of one shape: the server stacks them, batches requests for both into one launch
+    sequence, and every request equals its grid's solo render (loaded alone) bit for bit."""
     from paper_2206_10885_gb300 import serve
     grids = {}
     for name, seed in (("a", 0), ("b", 7)):
@@ -87,33 +133,38 @@ def test_server_mixed_stream_matches_solo(kns):
         stats = serve.run_stream(server, stream)
         assert stats["requests"] == 40 and stats["p99_ms"] >= stats["p50_ms"] > 0
         assert stats["batches"] < 40  # requests were batched
+        assert stats["mixed_batches"] > 0, stats  # and batches held requests for both grids
         ctx = kns.Context(0)
+        alone = {name: kns.Grid.load(ctx, d, w) for name, (d, w) in grids.items()}
         try:
             for _, r in stream:
-                ref = solo(kns, ctx, server.grids[r.grid], r.cam, r.W, r.H)
+                ref = solo(kns, ctx, alone[r.grid], r.cam, r.W, r.H)
                 for k in ref:
                     assert np.array_equal(ref[k], r.out[k].cpu().numpy()), (r.rid, k)
         finally:
+            for g in alone.values():
+                g.free()
             ctx.close()
     finally:
         server.close()
 
 
 def test_server_bf16_mixed_stream_matches_oracle(kns):
-    """BF16 serving of a 16^3 width-32 grid and a 32^3 width-64 grid (the workload's two grid shapes):
-    sampled pixels of every request of a mixed stream against the FP64 oracle, within the BF16 gates
+    """BF16 serving of two 16^3 width-32 grids (one stack) and a 32^3 width-64 grid (the workload's two grid
+    shapes): sampled pixels of every request of a mixed stream against the FP64 oracle, within the BF16 gates
     (depth 1e-3, RGB 1/255, normal 0.5 degrees on >= 99.9 % of pixels both hit; hit agreement >= 99.9 %)."""
     from paper_2206_10885_gb300 import serve
     grids = {"s": (S.config_desc("c3s"), S.sal_sphere_grid(S.config_desc("c3s"), seed=0)),
+             "t": (S.config_desc("c3s"), S.sal_sphere_grid(S.config_desc("c3s"), seed=1)),
              "l": (S.config_desc("c3l"), S.sal_sphere_grid(S.config_desc("c3l"), seed=0))}
     occs = {k: O.occupancy(d, w) for k, (d, w) in grids.items()}
     server = serve.RenderServer({k: (d, w, occs[k]) for k, (d, w) in grids.items()}, slots=2,
                                 budget_bytes=256 << 20, max_batch_rays=400_000, precision=kns.KNS_BF16)
     try:
-        stream = serve.poisson_stream(12, rate=500.0, seed=9, grids=["s", "l"],
+        stream = serve.poisson_stream(15, rate=500.0, seed=9, grids=["s", "t", "l"],
                                       resolutions=[(64, 64), (160, 120), (256, 256)])
         stats = serve.run_stream(server, stream)
-        assert stats["requests"] == 12
+        assert stats["requests"] == 15
         rng = np.random.default_rng(3)
         tot = agree = 0
         bad = {"depth": 0, "rgb": 0, "normal": 0}

@@ -19,6 +19,7 @@ def bare_server(budget, max_rays):
     s.in_flight_bytes = 0
     s.in_flight = 0
     s.batches = 0
+    s.mixed_batches = 0
     s.cv = threading.Condition()
     return s
 
@@ -43,6 +44,28 @@ def test_batch_takes_the_oldest_grid_in_order_up_to_the_ray_cap():
     assert g == "a" and [r.rid for r in take] == [4]
     assert s._take_batch() == (None, [])
     assert s.batches == 3
+
+
+def test_batch_spans_the_grids_of_one_stack():
+    """Grids loaded as one stack (equal descriptors) share batches: the oldest request's stack decides,
+    and every admitted request for any of its grids joins, in order."""
+    s = bare_server(budget=1 << 40, max_rays=1 << 30)
+    s.group_of = {"a": "k32", "b": "k32", "c": "k64"}
+    s.pending.extend([req(0, "a", 64, 64), req(1, "c", 64, 64), req(2, "b", 64, 64), req(3, "a", 32, 32),
+                      req(4, "c", 16, 16)])
+    key, take = s._take_batch()
+    assert key == "k32" and [r.rid for r in take] == [0, 2, 3]
+    assert s.mixed_batches == 1
+    key, take = s._take_batch()
+    assert key == "k64" and [r.rid for r in take] == [1, 4]
+    assert s.mixed_batches == 1 and s.batches == 2
+
+
+def test_grids_stack_by_descriptor():
+    from paper_2206_10885_gb300 import synth as S
+    a, b, c = S.config_desc("c3s"), S.config_desc("c2"), S.config_desc("c3l")
+    assert SV.desc_key(a) == SV.desc_key(b)      # same shape: one stack
+    assert SV.desc_key(a) != SV.desc_key(c)      # another width and N: a stack of its own
 
 
 def test_a_request_larger_than_the_cap_goes_alone():
