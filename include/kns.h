@@ -200,8 +200,9 @@ kns_status kns_load_grid(kns_ctx *ctx, const kns_grid_desc *desc, const float *h
  * (n_floats = n_grids * N^3 * parameters per cell); occ_words: the n_grids occupancy masks back to back
  * (ceil(occ_res^3 / 64) words each), or NULL to build each from its own grid as kns_load_grid does.
  * Every grid of the stack keeps its own weights, mask, 8^3-block mask and results: a view of grid k
- * renders exactly as a kns_render of grid k loaded alone (bit for bit in FP32).  kns_render and
- * kns_render_noalloc render grid 0 of a stack; kns_render_views picks the grid per view (kns_view.grid).
+ * renders exactly as a kns_render of grid k loaded alone (bit for bit in FP32).  kns_render_views picks
+ * the grid per view (kns_view.grid); kns_render, kns_render_noalloc, kns_trace_rays, kns_path_trace
+ * and kns_sdf use grid 0 of a stack.
  * The stack's device memory is n_grids times a single grid's.  Errors: as kns_load_grid, plus
  * INVALID_ARG for n_grids < 1 or more than 262,144 cells in all (the BF16 seam trap's cell field). */
 kns_status kns_load_grid_stack(kns_ctx *ctx, const kns_grid_desc *desc, int32_t n_grids, const float *host_weights,
