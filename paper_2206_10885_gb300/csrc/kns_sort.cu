@@ -265,31 +265,36 @@ __global__ void __launch_bounds__(256) wave_hit_count_kernel(WaveArgs a) {
 }
 
 __global__ void __launch_bounds__(SCAN_THREADS) wave_hit_scan_kernel(WaveArgs a, int tile) {
-    __shared__ int wa[32], wb[32];
+    // one block walks the cells in chunks of SCAN_THREADS consecutive cells (coalesced loads), each
+    // chunk scanned across the block and offset by the chunks before it
+    __shared__ int wa[32], wb[32], s_base[2];
     const int NC = a.NC;
-    const int per = (NC + SCAN_THREADS - 1) / SCAN_THREADS;
-    const int c0 = threadIdx.x * per, c1 = min(NC, c0 + per);
-    int sum = 0, tiles = 0;
-    for (int c = c0; c < c1; ++c) {
-        const int n = a.count[0][c];
-        sum += n;
-        tiles += (n + tile - 1) / tile;
+    if (threadIdx.x == 0) s_base[0] = s_base[1] = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < NC; c0 += SCAN_THREADS) {
+        const int c = c0 + (int)threadIdx.x;
+        const int n = c < NC ? a.count[0][c] : 0, nt = (n + tile - 1) / tile;
+        int incl_s = n, incl_t = nt;
+        block_scan2(incl_s, incl_t, wa, wb);
+        const int base_s = s_base[0], base_t = s_base[1];
+        if (c < NC) {
+            int run_s = base_s + incl_s - n, run_t = base_t + incl_t - nt;
+            a.off[c] = run_s;
+            a.tile_off[c] = run_t;
+            a.fill[0][c] = 0;
+            for (int i = 0; i < n; i += tile) a.tiles[run_t++] = make_int4(c, run_s + i, min(tile, n - i), 0);
+        }
+        __syncthreads();  // every thread has read the bases (and block_scan2's partials)
+        if (threadIdx.x == SCAN_THREADS - 1) {
+            s_base[0] = base_s + incl_s;
+            s_base[1] = base_t + incl_t;
+        }
+        __syncthreads();
     }
-    int incl_s = sum, incl_t = tiles;
-    block_scan2(incl_s, incl_t, wa, wb);
-    int run_s = incl_s - sum, run_t = incl_t - tiles;
-    for (int c = c0; c < c1; ++c) {
-        const int n = a.count[0][c];
-        a.off[c] = run_s;
-        a.tile_off[c] = run_t;
-        a.fill[0][c] = 0;
-        for (int i = 0; i < n; i += tile) a.tiles[run_t++] = make_int4(c, run_s + i, min(tile, n - i), 0);
-        run_s += n;
-    }
-    if (threadIdx.x == SCAN_THREADS - 1) {
-        a.off[NC] = incl_s;
-        a.tile_off[NC] = incl_t;
-        a.ctrl->n_tiles = incl_t;
+    if (threadIdx.x == 0) {
+        a.off[NC] = s_base[0];
+        a.tile_off[NC] = s_base[1];
+        a.ctrl->n_tiles = s_base[1];
     }
 }
 
