@@ -314,10 +314,12 @@ def serving_run(kns, S, main_grid, rates, seconds, slots=3):
             stream = serve.poisson_stream(n, rate, seed=int(rate), grids=names, resolutions=serve.RES_MIX)
             res = serve.run_stream(server, stream)
             out.append({"rate_per_s": rate, "requests": res["requests"], "p50_ms": res["p50_ms"],
-                        "p99_ms": res["p99_ms"], "mrays_per_s": res["mrays_per_s"], "batches": res["batches"]})
+                        "p99_ms": res["p99_ms"], "mrays_per_s": res["mrays_per_s"], "batches": res["batches"],
+                        "batches_with_two_grids": res["mixed_batches"]})
     finally:
         server.close()
-    return {"grids": "2 x 16^3/w32 + 2 x 32^3/w64, BF16, resident", "resolutions": "256^2, 512^2, 800^2, 1920x1080",
+    return {"grids": "2 x 16^3/w32 + 2 x 32^3/w64, BF16, resident, stacked per shape (a batch may hold both grids "
+                     "of a shape)", "resolutions": "256^2, 512^2, 800^2, 1920x1080",
             "arrivals": "Poisson, %.1f s per rate" % seconds, "slots": slots, "per_rate": out}
 
 
